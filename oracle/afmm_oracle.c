@@ -214,7 +214,10 @@ void orc_green_grad(double r, double r1, double x, int N, double *G, double *Gr,
     orc_legendre_q(p.t, p.k2, p.kp2, Nw, g_rule, Gw);
     double c = 1.0 / (2.0 * ORC_PI * sqrt(r * r1));
     for (int n = 0; n <= Nw; ++n) Gw[n] *= c;
-    double w = r * r - r1 * r1 - x * x;
+    /* Reading: the factor r^2 - r1^2 - x^2 of the Appendix A first-derivative forms is
+     * evaluated as (r - r1)(r + r1) - x^2; forming r^2 - r1^2 directly cancels
+     * catastrophically when r1 -> r (near-coincident pairs). */
+    double w = (r - r1) * (r + r1) - x * x;
     for (int n = 0; n <= N; ++n) {
         double g = Gw[n], gm = (n == 0) ? Gw[1] : Gw[n - 1];
         double nu = n - 0.5;
@@ -277,7 +280,7 @@ int orc_gbar(double r, double r1, double x, int N, int P, double *g)
         fxp[q] = x * vp[q] + (q >= 1 ? vp[q - 1] : 0.0);
         fxm[q] = x * vm[q] + (q >= 1 ? vm[q - 1] : 0.0);
     }
-    double c = r * r - r1 * r1;
+    double c = (r - r1) * (r + r1);
     orc_taylor_cmx2(c, x, P, vp, hp);
     orc_taylor_cmx2(c, x, P, vm, hm);
     orc_taylor_cmx2(-c, x, P, vp, hp1);
