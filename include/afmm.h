@@ -1,0 +1,172 @@
+/*
+ * afmm.h -- C ABI of libafmm, a GB300 (sm_103a) implementation of the cylindrical-
+ * coordinate Fast Multipole Method of M. J. Carley, "A Fast Multipole Method for
+ * axisymmetric domains" (arXiv 2301.01179).
+ *
+ * Problem (Sec. 2, Eq. analysis:sum): given ring sources at (r_i, z_i), i = 1..Ns, with
+ * Fourier coefficients S_i^(n), n = 0..N, and field points (r_j, z_j), j = 1..Nf, evaluate
+ *     Phi^(n)(r_j, z_j) = sum_i S_i^(n) G^(n)(r_j, r_i, z_j - z_i),   n = 0..N,
+ * with the modal Green's function (Eq. analysis:gfunc, Appendix A)
+ *     G^(n)(r, r1, x) = Q_{n-1/2}(chi) / (2 pi sqrt(r r1)),  chi = (r^2 + r1^2 + x^2)/(2 r r1).
+ * Only n >= 0 is computed: the source is real, so S^(-n) = conj(S^(n)) (Sec. 2).
+ *
+ * Conventions for every entry point:
+ *  - All array arguments are DEVICE pointers (cudaMalloc'd or torch CUDA storage) to
+ *    IEEE float64 data, unless a comment says otherwise.  The caller owns them.
+ *  - Amplitude and result arrays are mode-major planes with real and imaginary parts in
+ *    separate arrays: q_re[n * ns + i] is Re S_i^(n); phi_re[n * nf + j] is Re Phi^(n)_j.
+ *    Points stay in the caller's order.
+ *  - Radii must be finite and > 0 (the kernel divides by sqrt(r r1)); z must be finite.
+ *  - Work is enqueued on the CUDA stream bound to the plan (or passed explicitly) and is
+ *    asynchronous: the caller synchronises before reading results.  Plan creation
+ *    synchronises its stream once (it reads the tree depth back to the host).
+ *  - Nothing aborts or throws: every call returns an afmm_status.  A coincident source and
+ *    field point (rho_- = 0, the logarithmic singularity of Appendix A) contributes 0.
+ */
+#ifndef AFMM_H
+#define AFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AFMM_OK = 0,
+    AFMM_EINVAL = 1,       /* bad size, option, NULL pointer, r <= 0 or non-finite coordinate */
+    AFMM_ENOMEM = 2,       /* device allocation failed */
+    AFMM_ECUDA = 3,        /* a CUDA call or kernel launch failed (see afmm_last_cuda_error) */
+    AFMM_ETIMEOUT = 4,     /* reserved: a bounded device-side wait ran out */
+    AFMM_EUNSUPPORTED = 5  /* valid request the library does not implement (e.g. depth > 16) */
+} afmm_status;
+
+typedef enum {
+    AFMM_FP64 = 0,  /* every stage in FP64 */
+    AFMM_MIXED = 1  /* FP64 Legendre recursion and elliptic start values; FP32 bulk
+                       accumulation (compensated) and FP32 expansions (Sec. 2 with scaled
+                       coordinates, Eq. gfunc:scaled) */
+} afmm_precision;
+
+/* Options of the FMM (Sec. 3, Algorithm 1).  Zero-initialise and set what you need;
+ * afmm_options_default() fills the defaults. */
+typedef struct {
+    int order;          /* expansion order M (moments i+j <= M, locals k+l <= M); >= 0 */
+    int leaf_size;      /* depth rule: smallest d >= 2 whose non-empty leaves hold at most
+                           leaf_size sources on average; >= 1 */
+    int depth_override; /* 0: use the leaf_size rule; 2..16: use this depth */
+    int precision;      /* afmm_precision */
+    double fwd_switch;  /* Legendre recursion: forward iff 2 N acosh(chi) <= fwd_switch
+                           (0: default 9).  The paper's fixed switch is chi < 1.008. */
+    int miller_extra;   /* Miller start L = N + ceil(miller_extra / acosh(chi)) + 2 (0: 15) */
+} afmm_options;
+
+typedef struct afmm_plan_s *afmm_plan;
+
+/* Plan metadata (host struct filled by afmm_plan_info). */
+typedef struct {
+    int depth;          /* tree depth d */
+    int n_modes;        /* N + 1 */
+    int order;          /* M */
+    int precision;
+    double r0, z0, side;        /* domain square [r0, r0+side] x [z0, z0+side] */
+    int64_t ns, nf;
+    int64_t n_boxes[17];        /* boxes holding sources or field points, per level */
+    int64_t near_pairs;         /* (field point, source) pairs summed directly by the FMM */
+    int64_t s2l_pairs;          /* (field box, source box) S2L applications, all levels */
+    int64_t expansions;         /* Green's-function expansions generated per evaluation */
+} afmm_plan_info_t;
+
+void afmm_options_default(afmm_options *opt);
+
+/* Build a plan over sources (src_r, src_z)[ns] and field points (tgt_r, tgt_z)[nf]:
+ * validates the coordinates on the device, chooses the depth, sorts both point sets by
+ * Morton key into a uniform quadtree over the square domain (Sec. 2.1 and Algorithm 1,
+ * first two steps), and allocates all scratch the evaluations need, so that afmm_eval,
+ * afmm_grad, afmm_direct and afmm_adjoint allocate nothing.  The plan copies the
+ * coordinates (the caller may free them) and is bound to `stream` (cudaStream_t, NULL =
+ * legacy default stream).  n_modes = N + 1 >= 1.
+ * Errors: EINVAL (ns < 1, nf < 1, n_modes < 1, bad options, NULL pointers, non-finite or
+ * r <= 0 coordinates), ENOMEM, ECUDA, EUNSUPPORTED (depth > 16 required). */
+afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, const double *src_z,
+                             int64_t nf, const double *tgt_r, const double *tgt_z, int n_modes,
+                             const afmm_options *opt, void *stream);
+
+/* Release the plan and its device memory (synchronises the plan's stream). NULL is ignored. */
+void afmm_plan_destroy(afmm_plan p);
+
+afmm_status afmm_plan_info(afmm_plan p, afmm_plan_info_t *info);
+
+/* FMM evaluation of Eq. analysis:sum by Algorithm 1: leaf moments (Eq. analysis:moments),
+ * upward shifts (Eq. analysis:shift), per level the local shift (Eq. analysis:l2l) and the
+ * FO/BO/FI/BI source-to-local operators (Eq. analysis:s2l, Sec. 2.2) built from
+ * Green's-function expansions per radial station, then local expansions plus direct
+ * near-neighbour sums at the field points.  q: [n_modes][ns]; phi: [n_modes][nf]. */
+afmm_status afmm_eval(afmm_plan p, const double *q_re, const double *q_im, double *phi_re,
+                      double *phi_im);
+
+/* As afmm_eval, plus the field gradient dPhi/dr and dPhi/dz at the field points (from the
+ * first derivatives of G, Appendix A, in the near field and the derivative of the local
+ * expansion in the far field).  phi_re/phi_im may be NULL. All outputs [n_modes][nf]. */
+afmm_status afmm_grad(afmm_plan p, const double *q_re, const double *q_im, double *phi_re,
+                      double *phi_im, double *dr_re, double *dr_im, double *dz_re, double *dz_im);
+
+/* Direct O(Ns Nf) evaluation of Eq. analysis:sum over all pairs (the paper's reference
+ * method, Sec. 4).  Layouts as afmm_eval. */
+afmm_status afmm_direct(afmm_plan p, const double *q_re, const double *q_im, double *phi_re,
+                        double *phi_im);
+
+/* Direct evaluation with field gradient; phi_re/phi_im may be NULL. */
+afmm_status afmm_direct_grad(afmm_plan p, const double *q_re, const double *q_im, double *phi_re,
+                             double *phi_im, double *dr_re, double *dr_im, double *dz_re,
+                             double *dz_im);
+
+/* Adjoint of afmm_eval for a real loss L(Phi).  Input gphi = dL/dRe(Phi) + i dL/dIm(Phi)
+ * ([n_modes][nf]; for L = sum |Phi - T|^2 it is 2 (Phi - T)).  Outputs:
+ *   gq = dL/dRe(S) + i dL/dIm(S)            [n_modes][ns]
+ *   g_src_r[i] = dL/dr_i, g_src_z[i] = dL/dz_i   [ns]
+ * G is real, symmetric in r <-> r1 and even in x (Sec. 2.2), so this is the FMM on the
+ * same tree with sources and field points exchanged and strengths gphi, evaluating the
+ * potential A and gradient (B, C) at the sources: gq = A, dL/dr_i = sum_n Re(S conj B),
+ * dL/dz_i = sum_n Re(S conj C).  Legendre recursions are recomputed, not stored. */
+afmm_status afmm_adjoint(afmm_plan p, const double *q_re, const double *q_im, const double *gphi_re,
+                         const double *gphi_im, double *gq_re, double *gq_im, double *g_src_r,
+                         double *g_src_z);
+
+/* Adjoint of afmm_direct (same outputs, all-pairs sums). */
+afmm_status afmm_adjoint_direct(afmm_plan p, const double *q_re, const double *q_im,
+                                const double *gphi_re, const double *gphi_im, double *gq_re,
+                                double *gq_im, double *g_src_r, double *g_src_z);
+
+/* Unit-level evaluators (no plan), on `stream`:
+ * afmm_green: G^(n)(r[p], r1[p], x[p]) for n = 0..n_modes-1 and p < npairs, written to
+ *   G[n * npairs + p] (Eq. analysis:gfunc, Legendre recursion of Eq. gfunc:recursion with
+ *   start values of Eq. gfunc:Q0).  If Gr and Gx are non-NULL also dG/dr and dG/dx
+ *   (Appendix A first-derivative forms).  FP64 throughout. */
+afmm_status afmm_green(int64_t npairs, const double *r, const double *r1, const double *x,
+                       int n_modes, double *G, double *Gr, double *Gx, void *stream);
+
+/* afmm_green_expansion: Taylor coefficients gbar^(n)_{i,j,k}(r, r1, x) (Eq. gfunc:gnbar) for
+ * i + j + k <= P, n = 0..n_modes-1, at npts points, from the x-recursion
+ * (Eq. gfunc:derivatives:x), the closed first-derivative forms and the Laplace recursion
+ * (Eq. gfunc:laplace).  Output dense: out[((p * n_modes + n) * (P+1) + i) * (P+1) + j) *
+ * (P+1) + k], zero where i+j+k > P.  P <= 48. Requires r != r1 or x != 0 at every point. */
+afmm_status afmm_green_expansion(int64_t npts, const double *r, const double *r1, const double *x,
+                                 int n_modes, int P, double *out, void *stream);
+
+/* Human-readable status; afmm_last_cuda_error: the last CUDA error string seen by this
+ * thread's calls (static storage; "no error" if none). */
+const char *afmm_status_string(afmm_status s);
+const char *afmm_last_cuda_error(void);
+
+/* Per-kernel timing of the last afmm_eval / afmm_grad / afmm_adjoint on this plan, in
+ * milliseconds, measured with CUDA events on the plan's stream when timing is enabled:
+ * names are "tree", "p2m", "m2m", "gexp", "s2l", "l2l", "near" (L2P + P2P), "perm".
+ * afmm_set_timing(p, 1) enables event recording (adds event records, no sync). */
+afmm_status afmm_set_timing(afmm_plan p, int enable);
+afmm_status afmm_get_timing(afmm_plan p, const char *name, double *ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AFMM_H */

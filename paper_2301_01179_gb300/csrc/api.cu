@@ -1,0 +1,353 @@
+// api.cu -- the C ABI of libafmm (include/afmm.h): plan life cycle and the orchestration
+// of Algorithm 1 (FMM), the direct sum and the adjoint on the plan's stream.
+#include <cstdio>
+#include <cstring>
+#include <cstdlib>
+#include <new>
+#include "common.cuh"
+
+namespace afmm {
+
+static thread_local char g_cuda_err[256] = "no error";
+
+void set_cuda_error(cudaError_t e)
+{
+    snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+afmm_status dalloc(afmm_plan p, void **ptr, size_t bytes)
+{
+    *ptr = nullptr;
+    if (p->nalloc >= (int)(sizeof(p->allocs) / sizeof(p->allocs[0]))) return AFMM_ENOMEM;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        set_cuda_error(e);
+        cudaGetLastError();
+        return AFMM_ENOMEM;
+    }
+    p->allocs[p->nalloc++] = q;
+    *ptr = q;
+    return AFMM_OK;
+}
+
+void make_rec_tab(RecTab *t)
+{
+    static double c[AFMM_REC_TAB + 2];
+    c[0] = 1.0;
+    c[1] = 1.0;
+    for (int n = 2; n < AFMM_REC_TAB + 2; ++n) c[n] = c[n - 2] * (2.0 * n - 3.0) / (2.0 * n - 1.0);
+    for (int n = 0; n < AFMM_REC_TAB; ++n)
+        t->gam[n] = n >= 2 ? 4.0 * (n - 1) * c[n - 1] / ((2.0 * n - 3.0) * c[n - 2]) : 0.0;
+    for (int n = 0; n < AFMM_MAX_MODES; ++n) t->c[n] = c[n];
+}
+
+static void tmark(afmm_plan p, int idx)
+{
+    if (p->timing && idx < 16) cudaEventRecord(p->ev[idx], p->stream);
+}
+
+static float tdiff(afmm_plan p, int a, int b)
+{
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, p->ev[a], p->ev[b]);
+    return ms;
+}
+
+}  // namespace afmm
+
+using namespace afmm;
+
+extern "C" {
+
+void afmm_options_default(afmm_options *opt)
+{
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->order = 8;
+    opt->leaf_size = 32;
+    opt->depth_override = 0;
+    opt->precision = AFMM_FP64;
+    opt->fwd_switch = 0.0;
+    opt->miller_extra = 0;
+}
+
+const char *afmm_status_string(afmm_status s)
+{
+    switch (s) {
+    case AFMM_OK: return "ok";
+    case AFMM_EINVAL: return "invalid argument";
+    case AFMM_ENOMEM: return "out of device memory";
+    case AFMM_ECUDA: return "CUDA error";
+    case AFMM_ETIMEOUT: return "device wait timed out";
+    case AFMM_EUNSUPPORTED: return "unsupported request";
+    }
+    return "unknown status";
+}
+
+const char *afmm_last_cuda_error(void) { return g_cuda_err; }
+
+void afmm_plan_destroy(afmm_plan p)
+{
+    if (!p) return;
+    cudaStreamSynchronize(p->stream);
+    for (int i = 0; i < p->nalloc; ++i) cudaFree(p->allocs[i]);
+    if (p->timing)
+        for (int i = 0; i < 16; ++i) cudaEventDestroy(p->ev[i]);
+    delete p->rec;
+    delete p;
+}
+
+afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, const double *src_z, int64_t nf,
+                             const double *tgt_r, const double *tgt_z, int n_modes, const afmm_options *opt_in,
+                             void *stream)
+{
+    if (!out) return AFMM_EINVAL;
+    *out = nullptr;
+    afmm_options opt;
+    if (opt_in)
+        opt = *opt_in;
+    else
+        afmm_options_default(&opt);
+    if (ns < 1 || nf < 1 || ns > 0x3fffffff || nf > 0x3fffffff) return AFMM_EINVAL;
+    if (n_modes < 1 || n_modes > AFMM_MAX_MODES) return AFMM_EINVAL;
+    if (!src_r || !src_z || !tgt_r || !tgt_z) return AFMM_EINVAL;
+    if (opt.order < 0 || opt.leaf_size < 1 || opt.depth_override < 0 || opt.depth_override == 1 ||
+        opt.depth_override > AFMM_MAX_LEVEL || opt.fwd_switch < 0.0 || opt.miller_extra < 0)
+        return AFMM_EINVAL;
+    if (opt.precision != AFMM_FP64 && opt.precision != AFMM_MIXED) return AFMM_EINVAL;
+    if (opt.order > AFMM_MAX_ORDER) return AFMM_EUNSUPPORTED;
+    if (opt.precision == AFMM_MIXED) return AFMM_EUNSUPPORTED;
+
+    afmm_plan p = new (std::nothrow) afmm_plan_s();
+    if (!p) return AFMM_ENOMEM;
+    p->rec = new (std::nothrow) RecTab();
+    if (!p->rec) {
+        delete p;
+        return AFMM_ENOMEM;
+    }
+    make_rec_tab(p->rec);
+    p->stream = (cudaStream_t)stream;
+    p->ns = ns;
+    p->nf = nf;
+    p->nmodes = n_modes;
+    p->N = n_modes - 1;
+    p->M = opt.order;
+    p->ncoef = (opt.order + 1) * (opt.order + 2) / 2;
+    p->precision = opt.precision;
+    p->opt = opt;
+    p->pp.fwd_switch = opt.fwd_switch > 0.0 ? opt.fwd_switch : 9.0;
+    p->pp.miller_extra = opt.miller_extra > 0 ? (double)opt.miller_extra : 15.0;
+
+    afmm_status s = build_tree(p, src_r, src_z, tgt_r, tgt_z);
+    if (s == AFMM_OK) s = make_shift_tables(p);
+    // evaluation scratch: nothing is allocated by the evaluation calls
+    const int nm = p->nmodes, nc = p->ncoef;
+    const int64_t nmax = p->n_max;
+    if (s == AFMM_OK) s = dalloc_t(p, &p->qs_re, (size_t)nm * nmax);
+    if (s == AFMM_OK) s = dalloc_t(p, &p->qs_im, (size_t)nm * nmax);
+    if (s == AFMM_OK) s = dalloc_t(p, &p->acc_buf, (size_t)6 * nm * p->ns);
+    int64_t gcap = 0, nexp = 0;
+    for (int l = 2; s == AFMM_OK && l <= p->d; ++l) {
+        Level &v = p->lv[l];
+        size_t per = (size_t)v.nbox * nm * nc;
+        s = dalloc_t(p, &v.mom_re, per);
+        if (s == AFMM_OK) s = dalloc_t(p, &v.mom_im, per);
+        if (s == AFMM_OK) s = dalloc_t(p, &v.loc_re, per);
+        if (s == AFMM_OK) s = dalloc_t(p, &v.loc_im, per);
+        int64_t g = (int64_t)v.nstation * 16 * nm * (p->M + 1) * (p->M + 1) * (2 * p->M + 1);
+        if (g > gcap) gcap = g;
+        nexp += (int64_t)v.nstation * 12;
+    }
+    p->expansions = nexp;
+    if (s == AFMM_OK && gcap > 0) s = dalloc_t(p, &p->gexp, gcap);
+    p->gexp_cap = gcap;
+    // direct sums over few field points are split over sources: room for the partials
+    // of up to 64 splits of the smaller point set, at most 1 GB
+    if (s == AFMM_OK) {
+        int64_t nmin = p->ns < p->nf ? p->ns : p->nf;
+        double want = 64.0 * 6.0 * nm * (double)nmin;
+        if (want > 1.25e8) want = 1.25e8;
+        p->part_cap = (int64_t)want;
+        s = dalloc_t(p, &p->part_buf, (size_t)p->part_cap);
+    }
+    if (s == AFMM_OK) {
+        cudaError_t e = cudaStreamSynchronize(p->stream);
+        if (e != cudaSuccess) {
+            set_cuda_error(e);
+            s = AFMM_ECUDA;
+        }
+    }
+    if (s != AFMM_OK) {
+        afmm_plan_destroy(p);
+        return s;
+    }
+    *out = p;
+    return AFMM_OK;
+}
+
+afmm_status afmm_plan_info(afmm_plan p, afmm_plan_info_t *info)
+{
+    if (!p || !info) return AFMM_EINVAL;
+    memset(info, 0, sizeof(*info));
+    info->depth = p->d;
+    info->n_modes = p->nmodes;
+    info->order = p->M;
+    info->precision = p->precision;
+    info->r0 = p->r0;
+    info->z0 = p->z0;
+    info->side = p->L;
+    info->ns = p->ns;
+    info->nf = p->nf;
+    for (int l = 0; l <= AFMM_MAX_LEVEL; ++l) info->n_boxes[l] = p->lv[l].nbox;
+    info->near_pairs = p->near_pairs;
+    info->s2l_pairs = p->s2l_pairs;
+    info->expansions = p->expansions;
+    return AFMM_OK;
+}
+
+afmm_status afmm_set_timing(afmm_plan p, int enable)
+{
+    if (!p) return AFMM_EINVAL;
+    if (enable && !p->timing) {
+        for (int i = 0; i < 16; ++i) AFMM_CUDA(cudaEventCreate(&p->ev[i]));
+        p->timing = 1;
+    }
+    return AFMM_OK;
+}
+
+afmm_status afmm_get_timing(afmm_plan p, const char *name, double *ms)
+{
+    if (!p || !name || !ms) return AFMM_EINVAL;
+    static const char *names[] = {"perm", "p2m", "m2m", "gexp", "s2l", "l2l", "near", "total"};
+    for (int i = 0; i < 8; ++i)
+        if (!strcmp(name, names[i])) {
+            *ms = p->t_ms[i];
+            return AFMM_OK;
+        }
+    return AFMM_EINVAL;
+}
+
+static afmm_status run_fmm(afmm_plan p, int dir, const double *q_re, const double *q_im, int grad, double *o_re,
+                           double *o_im, double *dr_re, double *dr_im, double *dz_re, double *dz_im)
+{
+    tmark(p, 0);
+    AFMM_TRY(launch_permute(p, dir, q_re, q_im));
+    tmark(p, 1);
+    AFMM_TRY(far_field(p, dir));
+    tmark(p, 8);
+    AFMM_TRY(launch_near(p, dir, 1, grad, o_re, o_im, dr_re, dr_im, dz_re, dz_im, 0));
+    tmark(p, 9);
+    if (p->timing) {
+        AFMM_CUDA(cudaEventSynchronize(p->ev[9]));
+        p->t_ms[0] = tdiff(p, 0, 1);
+        p->t_ms[1] = tdiff(p, 1, 2);
+        p->t_ms[2] = tdiff(p, 2, 3);
+        p->t_ms[6] = tdiff(p, 8, 9);
+        p->t_ms[7] = tdiff(p, 0, 9);
+    }
+    return AFMM_OK;
+}
+
+afmm_status afmm_eval(afmm_plan p, const double *q_re, const double *q_im, double *phi_re, double *phi_im)
+{
+    if (!p || !q_re || !q_im || !phi_re || !phi_im) return AFMM_EINVAL;
+    return run_fmm(p, 0, q_re, q_im, 0, phi_re, phi_im, nullptr, nullptr, nullptr, nullptr);
+}
+
+afmm_status afmm_grad(afmm_plan p, const double *q_re, const double *q_im, double *phi_re, double *phi_im,
+                      double *dr_re, double *dr_im, double *dz_re, double *dz_im)
+{
+    if (!p || !q_re || !q_im || !dr_re || !dr_im || !dz_re || !dz_im) return AFMM_EINVAL;
+    return run_fmm(p, 0, q_re, q_im, 1, phi_re, phi_im, dr_re, dr_im, dz_re, dz_im);
+}
+
+afmm_status afmm_direct(afmm_plan p, const double *q_re, const double *q_im, double *phi_re, double *phi_im)
+{
+    if (!p || !q_re || !q_im || !phi_re || !phi_im) return AFMM_EINVAL;
+    AFMM_TRY(launch_permute(p, 0, q_re, q_im));
+    return launch_near(p, 0, 0, 0, phi_re, phi_im, nullptr, nullptr, nullptr, nullptr, 1);
+}
+
+afmm_status afmm_direct_grad(afmm_plan p, const double *q_re, const double *q_im, double *phi_re, double *phi_im,
+                             double *dr_re, double *dr_im, double *dz_re, double *dz_im)
+{
+    if (!p || !q_re || !q_im || !dr_re || !dr_im || !dz_re || !dz_im) return AFMM_EINVAL;
+    AFMM_TRY(launch_permute(p, 0, q_re, q_im));
+    return launch_near(p, 0, 0, 1, phi_re, phi_im, dr_re, dr_im, dz_re, dz_im, 1);
+}
+
+// dL/dr_i = sum_n Re(S conj B), dL/dz_i = sum_n Re(S conj C)
+__global__ void k_adjoint_combine(const double *__restrict__ q_re, const double *__restrict__ q_im,
+                                  const double *__restrict__ acc, int nm, int64_t ns, double *__restrict__ g_r,
+                                  double *__restrict__ g_z)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    const size_t P = (size_t)nm * ns;
+    double ar = 0.0, az = 0.0;
+    for (int n = 0; n < nm; ++n) {
+        size_t o = (size_t)n * ns + i;
+        ar = fma(q_re[o], acc[2 * P + o], ar);
+        ar = fma(q_im[o], acc[3 * P + o], ar);
+        az = fma(q_re[o], acc[4 * P + o], az);
+        az = fma(q_im[o], acc[5 * P + o], az);
+    }
+    g_r[i] = ar;
+    g_z[i] = az;
+}
+
+static afmm_status run_adjoint(afmm_plan p, int direct, const double *q_re, const double *q_im,
+                               const double *gphi_re, const double *gphi_im, double *gq_re, double *gq_im,
+                               double *g_r, double *g_z)
+{
+    const size_t P = (size_t)p->nmodes * p->ns;
+    double *A = p->acc_buf;
+    // transposed problem: "sources" are the field points with strengths gphi, evaluated at
+    // the sources with gradient
+    if (direct) {
+        AFMM_TRY(launch_permute(p, 1, gphi_re, gphi_im));
+        AFMM_TRY(launch_near(p, 1, 0, 1, gq_re, gq_im, A + 2 * P, A + 3 * P, A + 4 * P, A + 5 * P, 1));
+    } else {
+        AFMM_TRY(run_fmm(p, 1, gphi_re, gphi_im, 1, gq_re, gq_im, A + 2 * P, A + 3 * P, A + 4 * P, A + 5 * P));
+    }
+    unsigned nb = (unsigned)((p->ns + 255) / 256);
+    k_adjoint_combine<<<nb, 256, 0, p->stream>>>(q_re, q_im, A, p->nmodes, p->ns, g_r, g_z);
+    AFMM_LAUNCH_CHECK();
+    return AFMM_OK;
+}
+
+afmm_status afmm_adjoint(afmm_plan p, const double *q_re, const double *q_im, const double *gphi_re,
+                         const double *gphi_im, double *gq_re, double *gq_im, double *g_src_r, double *g_src_z)
+{
+    if (!p || !q_re || !q_im || !gphi_re || !gphi_im || !gq_re || !gq_im || !g_src_r || !g_src_z) return AFMM_EINVAL;
+    return run_adjoint(p, 0, q_re, q_im, gphi_re, gphi_im, gq_re, gq_im, g_src_r, g_src_z);
+}
+
+afmm_status afmm_adjoint_direct(afmm_plan p, const double *q_re, const double *q_im, const double *gphi_re,
+                                const double *gphi_im, double *gq_re, double *gq_im, double *g_src_r,
+                                double *g_src_z)
+{
+    if (!p || !q_re || !q_im || !gphi_re || !gphi_im || !gq_re || !gq_im || !g_src_r || !g_src_z) return AFMM_EINVAL;
+    return run_adjoint(p, 1, q_re, q_im, gphi_re, gphi_im, gq_re, gq_im, g_src_r, g_src_z);
+}
+
+afmm_status afmm_green(int64_t npairs, const double *r, const double *r1, const double *x, int n_modes, double *G,
+                       double *Gr, double *Gx, void *stream)
+{
+    if (npairs < 0 || !r || !r1 || !x || !G || n_modes < 1 || n_modes > AFMM_MAX_MODES) return AFMM_EINVAL;
+    if ((Gr == nullptr) != (Gx == nullptr)) return AFMM_EINVAL;
+    if (npairs == 0) return AFMM_OK;
+    return launch_green(npairs, r, r1, x, n_modes, G, Gr, Gx, (cudaStream_t)stream);
+}
+
+afmm_status afmm_green_expansion(int64_t npts, const double *r, const double *r1, const double *x, int n_modes, int P,
+                                 double *out, void *stream)
+{
+    if (npts < 0 || !r || !r1 || !x || !out || n_modes < 1 || n_modes > AFMM_MAX_MODES || P < 0 || P > 48)
+        return AFMM_EINVAL;
+    if (npts == 0) return AFMM_OK;
+    return launch_green_expansion(npts, r, r1, x, n_modes, P, out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

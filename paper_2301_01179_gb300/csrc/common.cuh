@@ -1,0 +1,186 @@
+// common.cuh -- internal definitions shared by the libafmm translation units.
+//
+// Plan layout in HBM (all device arrays, FP64 unless noted):
+//   sorted points   s_r, s_z [ns], t_r, t_z [nf]; s_perm, t_perm (sorted -> caller index)
+//   Morton keys     s_key, t_key (uint32, level-16 interleave of (ir, iz), sorted)
+//   per level l     boxes present in sources U field points, sorted by Morton key:
+//                   key, src/tgt index ranges, parent, child range, 27-slot S2L table,
+//                   9-slot neighbour table (leaf level), S2L work units
+//   eval scratch    strengths in sorted order [n_modes][n] (pre-scaled by the Legendre
+//                   recursion constants), moments and locals [box][mode][coef] per level,
+//                   Green's-function expansions of one level [station][16][mode][slab]
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+#include "../../include/afmm.h"
+
+#define AFMM_MAX_LEVEL 16
+#define AFMM_MAX_MODES 129     // n_modes <= 129 (N <= 128)
+#define AFMM_MAX_ORDER 16      // expansion order M <= 16
+#define AFMM_NEAR_WARPS 4      // warps per near-field block
+
+namespace afmm {
+
+// ----------------------------------------------------------------------------------------
+// error handling: every CUDA call is checked; the last CUDA error string is kept per thread
+// ----------------------------------------------------------------------------------------
+void set_cuda_error(cudaError_t e);
+
+#define AFMM_CUDA(call)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) {                          \
+            ::afmm::set_cuda_error(e_);                   \
+            return e_ == cudaErrorMemoryAllocation ? AFMM_ENOMEM : AFMM_ECUDA; \
+        }                                                 \
+    } while (0)
+
+#define AFMM_LAUNCH_CHECK() AFMM_CUDA(cudaGetLastError())
+
+#define AFMM_TRY(expr)                                    \
+    do {                                                  \
+        afmm_status s_ = (expr);                          \
+        if (s_ != AFMM_OK) return s_;                     \
+    } while (0)
+
+// ----------------------------------------------------------------------------------------
+// Legendre recursion constants.  With G_n = c_n y_n, c_0 = c_1 = 1,
+// c_n = c_{n-2} (2n-3)/(2n-1), the three-term recursion of Eq. gfunc:recursion becomes
+//     y_n = gam_n chi y_{n-1} - y_{n-2}   (forward)
+//     y_{n-2} = gam_n chi y_{n-1} - y_n   (backward)
+// with gam_n = 4 (n-1) c_{n-1} / ((2n-3) c_{n-2}); one multiply and one FMA per step.
+// The table is passed by value as a kernel argument (constant bank, warp-uniform reads).
+// The backward sweep may start above N: entries run to AFMM_REC_TAB.
+// ----------------------------------------------------------------------------------------
+#define AFMM_REC_TAB 600
+struct RecTab {
+    double gam[AFMM_REC_TAB];  // gam[n], n >= 2
+    double c[AFMM_MAX_MODES];  // c[n], n <= 128
+};
+void make_rec_tab(RecTab *t);
+
+struct PairParams {
+    double fwd_switch;   // forward iff 2 N acosh(chi) <= fwd_switch (and acosh(chi) <= 0.96)
+    double miller_extra; // L = N + ceil(miller_extra / acosh(chi)) + 2
+};
+
+// ----------------------------------------------------------------------------------------
+// quadtree
+// ----------------------------------------------------------------------------------------
+__host__ __device__ inline uint32_t morton_spread(uint32_t v)
+{
+    v &= 0xffffu;
+    v = (v | (v << 8)) & 0x00ff00ffu;
+    v = (v | (v << 4)) & 0x0f0f0f0fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+__host__ __device__ inline uint32_t morton_compact(uint32_t v)
+{
+    v &= 0x55555555u;
+    v = (v | (v >> 1)) & 0x33333333u;
+    v = (v | (v >> 2)) & 0x0f0f0f0fu;
+    v = (v | (v >> 4)) & 0x00ff00ffu;
+    v = (v | (v >> 8)) & 0x0000ffffu;
+    return v;
+}
+// radial index in the odd bits, axial index in the even bits
+__host__ __device__ inline uint32_t morton_key(uint32_t ir, uint32_t iz)
+{
+    return (morton_spread(ir) << 1) | morton_spread(iz);
+}
+__host__ __device__ inline uint32_t morton_ir(uint32_t k) { return morton_compact(k >> 1); }
+__host__ __device__ inline uint32_t morton_iz(uint32_t k) { return morton_compact(k); }
+
+struct Level {
+    int64_t nbox = 0;
+    uint32_t *key = nullptr;     // [nbox] Morton key at this level (2l bits), sorted
+    int2 *srng = nullptr;        // [nbox] [begin, end) into sorted sources
+    int2 *trng = nullptr;        // [nbox] [begin, end) into sorted field points
+    int32_t *parent = nullptr;   // [nbox] index at level l-1 (level >= 3)
+    int2 *child = nullptr;       // [nbox] child index range at level l+1 (level < d)
+    int32_t *s2l = nullptr;      // [nbox][27] interaction-list box index or -1
+    int32_t *nbr = nullptr;      // [nbox][9] neighbour box index or -1 (leaf level only)
+    int64_t nunit = 0;           // S2L work units: up to 32 boxes of one column and parity
+    int32_t *unit_box = nullptr; // [nunit][32] box indices (-1 pad)
+    int32_t *unit_col = nullptr; // [nunit] column (radial index) | axial parity << 30
+    int nstation = 0;            // occupied columns
+    int32_t *station_of_col = nullptr;  // [2^l] compact station index or -1
+    int32_t *col_of_station = nullptr;  // [nstation]
+    double *mom_re = nullptr, *mom_im = nullptr;  // [nbox][nmodes][ncoef]
+    double *loc_re = nullptr, *loc_im = nullptr;  // [nbox][nmodes][ncoef]
+    float *mom32 = nullptr, *loc32 = nullptr;     // MIXED: [nbox][nmodes][2][ncoef]
+};
+
+struct NearUnit {       // one warp of near-field work: up to 32 field points of one leaf
+    int32_t box;        // leaf box index
+    int32_t begin, end; // field-point range (sorted order)
+};
+
+}  // namespace afmm
+
+struct afmm_plan_s {
+    cudaStream_t stream = nullptr;
+    int64_t ns = 0, nf = 0;
+    int nmodes = 0, N = 0, M = 0, d = 0, ncoef = 0, precision = 0;
+    afmm_options opt;
+    afmm::PairParams pp;
+    afmm::RecTab *rec = nullptr;  // host copy (passed by value to kernels)
+    double r0 = 0, z0 = 0, L = 1;
+    // sorted points
+    double *s_r = nullptr, *s_z = nullptr, *t_r = nullptr, *t_z = nullptr;
+    int32_t *s_perm = nullptr, *t_perm = nullptr;
+    uint32_t *s_key = nullptr, *t_key = nullptr;
+    afmm::Level lv[AFMM_MAX_LEVEL + 1];
+    // near-field work units per direction (0: field points <- sources, 1: transposed)
+    int64_t n_near_unit[2] = {0, 0};
+    afmm::NearUnit *near_unit[2] = {nullptr, nullptr};
+    int64_t n_dir_unit[2] = {0, 0};  // direct (all pairs): units of 32 points
+    afmm::NearUnit *dir_unit[2] = {nullptr, nullptr};
+    // eval scratch
+    double *qs_re = nullptr, *qs_im = nullptr;  // [nmodes][max(ns,nf)] strengths, sorted, * c_n
+    double *gexp = nullptr;                     // expansions of one level
+    int64_t gexp_cap = 0;                       // doubles
+    double *m2m_tab = nullptr;                  // [4][2][(M+1)^2] shift tables (see farfield.cu)
+    double *l2l_tab = nullptr;
+    double *acc_buf = nullptr;                  // [6][nmodes][max(ns,nf)] adjoint temporaries
+    double *part_buf = nullptr;                 // direct sums split over sources: partials
+    int64_t part_cap = 0;                       // doubles in part_buf
+    int64_t n_max = 0;
+    // statistics
+    int64_t near_pairs = 0, s2l_pairs = 0, expansions = 0;
+    // timing
+    int timing = 0;
+    cudaEvent_t ev[16];
+    int nev = 0;
+    double t_ms[8] = {0};
+    // device allocations to free
+    void *allocs[512];
+    int nalloc = 0;
+};
+
+namespace afmm {
+afmm_status dalloc(afmm_plan p, void **ptr, size_t bytes);
+template <typename T>
+inline afmm_status dalloc_t(afmm_plan p, T **ptr, size_t count)
+{
+    return dalloc(p, (void **)ptr, count * sizeof(T) + 16);
+}
+
+// tree.cu
+afmm_status build_tree(afmm_plan p, const double *src_r, const double *src_z, const double *tgt_r,
+                       const double *tgt_z);
+// nearfield.cu
+afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *phi_re, double *phi_im,
+                        double *dr_re, double *dr_im, double *dz_re, double *dz_im, int direct);
+afmm_status launch_green(int64_t npairs, const double *r, const double *r1, const double *x, int n_modes,
+                         double *G, double *Gr, double *Gx, cudaStream_t st);
+afmm_status launch_permute(afmm_plan p, int dir, const double *q_re, const double *q_im);
+// farfield.cu
+afmm_status far_field(afmm_plan p, int dir);
+afmm_status launch_green_expansion(int64_t npts, const double *r, const double *r1, const double *x,
+                                   int n_modes, int P, double *out, cudaStream_t st);
+afmm_status make_shift_tables(afmm_plan p);
+}  // namespace afmm

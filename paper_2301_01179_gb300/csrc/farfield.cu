@@ -1,0 +1,753 @@
+// farfield.cu -- the far-field half of Algorithm 1: leaf moments (Eq. analysis:moments),
+// upward shifts (Eq. analysis:shift), Green's-function Taylor expansions per radial station
+// (Appendix A), source-to-local operators FO/BO/FI/BI (Eq. analysis:s2l, Sec. 2.2) and
+// downward local shifts (Eq. analysis:l2l).
+//
+// Representation (scaled by the box size h of the level; mathematically identical to the
+// paper's moments S_ij and local coefficients Phi_kl):
+//   moments  Shat_ij = sum_q S_q U^i W^j / j!,   U = (r_q - c_r)/h, W = -(z_q - c_z)/h
+//            ( = (-1)^j S_ij / (j! h^{i+j}) )
+//   locals   F_kl = h^{k+l} Phi_kl      (Phi(r, z) = sum F_kl u^k v^l, u = (r-c_r)/h, ...)
+//   expansion Ehat_{a,b,c} = c! h^{a+b+c} gbar_{a,b,c}(r_big, r_small, |x|)
+// so that the FO operator is  F_kl += (1/l!) sum_ij Shat_ij Ehat_{k,i,j+l}:  BO flips the sign
+// of odd c (G is even in x), FI/BI exchange the first two indices of Ehat (G is symmetric in
+// r <-> r1).  Every S2L application is then a plain FP64 FMA contraction.
+//
+// The expansions are generated per level for every occupied radial station and the twelve
+// offsets (|dr|, |dz|) in 0..3, not both <= 1 (Sec. 2.2: "twelve" expansions per station),
+// in box units (Eq. gfunc:scaled): gbar at (R_s + |dr|, R_s, |dz|), R_s = r_small / h.
+#include <cstring>
+#include <vector>
+#include "common.cuh"
+#include "pair.cuh"
+
+namespace afmm {
+
+__host__ __device__ inline int cix(int i, int j, int M) { return i * (M + 1) - i * (i - 1) / 2 + j; }
+
+// ------------------------------------------------------------------------------------
+// shift tables (host): the child sits at +-h_child/2 from the parent centre, i.e. at
+// alpha = (bit - 1/2)/2 parent-box units.
+//  M2M (hat moments):   Shat^p_ij = sum_{q<=i, v<=j} Ar[br][i][q] Bz[bz][j][v] Shat^c_{i-q,j-v}
+//        Ar[i][q] = C(i,q) alpha^q 2^{q-i},  Bz[j][v] = beta^v / v! 2^{v-j}, beta = -alpha_z
+//  L2L (plain locals):  F^c_im = sum_{k>=i} Lr[br][i][k] sum_{l>=m} Lz[bz][m][l] F^p_kl
+//        Lr[i][k] = C(k,i) 2^{-i} alpha^{k-i},  Lz[m][l] = C(l,m) 2^{-m} gamma^{l-m}
+// layout: tab[((which * 2 + bit) * (M+1) + i) * (M+1) + q]
+// ------------------------------------------------------------------------------------
+afmm_status make_shift_tables(afmm_plan p)
+{
+    int M = p->M, W = M + 1;
+    std::vector<double> m2m(2 * 2 * W * W, 0.0), l2l(2 * 2 * W * W, 0.0);
+    auto C = [](int n, int k) {
+        double b = 1.0;
+        for (int t = 1; t <= k; ++t) b = b * (n - k + t) / t;
+        return b;
+    };
+    for (int bit = 0; bit < 2; ++bit) {
+        double al = (bit - 0.5) / 2.0;  // (c_child - c_parent) / h_parent
+        for (int i = 0; i <= M; ++i)
+            for (int q = 0; q <= M; ++q) {
+                // M2M radial
+                if (q <= i) m2m[((0 * 2 + bit) * W + i) * W + q] = C(i, q) * pow(al, q) * pow(2.0, q - i);
+                // M2M axial, W = -(z - c)/h: beta = -al
+                double be = -al, fv = 1.0;
+                for (int t = 2; t <= q; ++t) fv *= t;
+                if (q <= i) m2m[((1 * 2 + bit) * W + i) * W + q] = pow(be, q) / fv * pow(2.0, q - i);
+                // L2L radial / axial (gamma = al for z as well)
+                if (q >= i) {
+                    l2l[((0 * 2 + bit) * W + i) * W + q] = C(q, i) * pow(2.0, -i) * pow(al, q - i);
+                    l2l[((1 * 2 + bit) * W + i) * W + q] = C(q, i) * pow(2.0, -i) * pow(al, q - i);
+                }
+            }
+    }
+    AFMM_TRY(dalloc_t(p, &p->m2m_tab, m2m.size()));
+    AFMM_TRY(dalloc_t(p, &p->l2l_tab, l2l.size()));
+    AFMM_CUDA(cudaMemcpy(p->m2m_tab, m2m.data(), m2m.size() * sizeof(double), cudaMemcpyHostToDevice));
+    AFMM_CUDA(cudaMemcpy(p->l2l_tab, l2l.data(), l2l.size() * sizeof(double), cudaMemcpyHostToDevice));
+    return AFMM_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// P2M: hat moments of every leaf box (zero for boxes without source-role points)
+// ------------------------------------------------------------------------------------
+__global__ void k_p2m(const uint32_t *__restrict__ key, const int2 *__restrict__ rng, int64_t nbox,
+                      const double *__restrict__ sr, const double *__restrict__ sz, const double *__restrict__ q_re,
+                      const double *__restrict__ q_im, int64_t nsrc, int nm, int M, double r0, double z0, double h,
+                      const RecTab tab, double *__restrict__ mom_re, double *__restrict__ mom_im)
+{
+    extern __shared__ double sm[];
+    const int nc = (M + 1) * (M + 2) / 2;
+    double *mono = sm;                       // [32][nc]
+    double *acc = mono + 32 * nc;            // [2][nm][nc]
+    double *invf = acc + 2 * (size_t)nm * nc;  // [M+1] 1/j!
+    int64_t b = blockIdx.x;
+    if (b >= nbox) return;
+    for (int i = threadIdx.x; i < 2 * nm * nc; i += blockDim.x) acc[i] = 0.0;
+    if (threadIdx.x == 0) {
+        double f = 1.0;
+        for (int j = 0; j <= M; ++j) {
+            if (j > 0) f *= j;
+            invf[j] = 1.0 / f;
+        }
+    }
+    uint32_t k = key[b];
+    double cr = r0 + ((double)morton_ir(k) + 0.5) * h, cz = z0 + ((double)morton_iz(k) + 0.5) * h;
+    int2 R = rng[b];
+    __syncthreads();
+    for (int s0 = R.x; s0 < R.y; s0 += 32) {
+        int cnt = min(32, R.y - s0);
+        // monomials U^i W^j / j! of the chunk's points
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+            double U = (sr[s0 + t] - cr) / h, Wv = -(sz[s0 + t] - cz) / h;
+            double ui = 1.0;
+            for (int i = 0; i <= M; ++i) {
+                double wj = ui;
+                for (int j = 0; i + j <= M; ++j) {
+                    mono[t * nc + cix(i, j, M)] = wj * invf[j];
+                    wj *= Wv;
+                }
+                ui *= U;
+            }
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < nm * nc; o += blockDim.x) {
+            int n = o / nc, c = o % nc;
+            double ar = acc[o], ai = acc[nm * nc + o];
+            for (int t = 0; t < cnt; ++t) {
+                double m = mono[t * nc + c];
+                ar = fma(q_re[(size_t)n * nsrc + s0 + t], m, ar);
+                ai = fma(q_im[(size_t)n * nsrc + s0 + t], m, ai);
+            }
+            acc[o] = ar;
+            acc[nm * nc + o] = ai;
+        }
+        __syncthreads();
+    }
+    // amplitudes carry the recursion constant c_n: divide it out
+    for (int o = threadIdx.x; o < nm * nc; o += blockDim.x) {
+        int n = o / nc;
+        double ic = 1.0 / tab.c[n];
+        mom_re[(size_t)b * nm * nc + o] = acc[o] * ic;
+        mom_im[(size_t)b * nm * nc + o] = acc[nm * nc + o] * ic;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// M2M: parent hat moments from the children (separable radial then axial shift)
+// ------------------------------------------------------------------------------------
+__global__ void k_m2m(const int2 *__restrict__ child, const uint32_t *__restrict__ ckey, int64_t npar, int nm, int M,
+                      const double *__restrict__ tab, const double *__restrict__ cre, const double *__restrict__ cim,
+                      double *__restrict__ pre, double *__restrict__ pim)
+{
+    extern __shared__ double sm[];
+    const int nc = (M + 1) * (M + 2) / 2, W = M + 1;
+    double *X = sm;          // [2][nc]
+    double *T = X + 2 * nc;  // [4][W][W] tables
+    for (int i = threadIdx.x; i < 4 * W * W; i += blockDim.x) T[i] = tab[i];
+    int64_t P = blockIdx.x;
+    __syncthreads();
+    if (P >= npar) return;
+    int2 ch = child[P];
+    for (int n = 0; n < nm; ++n) {
+        double accr[2] = {0, 0}, acci[2] = {0, 0};  // outputs o = tid, tid + blockDim (nc <= 2 * blockDim)
+        for (int c = ch.x; c < ch.y; ++c) {
+            uint32_t k = ckey[c];
+            int br = morton_ir(k) & 1, bz = morton_iz(k) & 1;
+            const double *Ar = T + (0 * 2 + br) * W * W, *Bz = T + (1 * 2 + bz) * W * W;
+            const double *sr_ = cre + ((size_t)c * nm + n) * nc, *si_ = cim + ((size_t)c * nm + n) * nc;
+            // X_{i,j} = sum_q Ar[i][q] S_{i-q, j}
+            for (int o = threadIdx.x; o < nc; o += blockDim.x) {
+                int i = 0, rem = o;
+                while (rem >= M + 1 - i) { rem -= M + 1 - i; ++i; }
+                int j = rem;
+                double xr = 0, xi = 0;
+                for (int q = 0; q <= i; ++q) {
+                    double a = Ar[i * W + q];
+                    int s = cix(i - q, j, M);
+                    xr = fma(a, sr_[s], xr);
+                    xi = fma(a, si_[s], xi);
+                }
+                X[o] = xr;
+                X[nc + o] = xi;
+            }
+            __syncthreads();
+            for (int h = 0; h < 2; ++h) {
+                int o = threadIdx.x + h * blockDim.x;
+                if (o >= nc) break;
+                int i = 0, rem = o;
+                while (rem >= M + 1 - i) { rem -= M + 1 - i; ++i; }
+                int j = rem;
+                for (int v = 0; v <= j; ++v) {
+                    double bcoef = Bz[j * W + v];
+                    int s = cix(i, j - v, M);
+                    accr[h] = fma(bcoef, X[s], accr[h]);
+                    acci[h] = fma(bcoef, X[nc + s], acci[h]);
+                }
+            }
+            __syncthreads();
+        }
+        for (int h = 0; h < 2; ++h) {
+            int o = threadIdx.x + h * blockDim.x;
+            if (o >= nc) break;
+            pre[((size_t)P * nm + n) * nc + o] = accr[h];
+            pim[((size_t)P * nm + n) * nc + o] = acci[h];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// L2L: child locals from the parent (overwrites; level-2 locals start at zero)
+// ------------------------------------------------------------------------------------
+__global__ void k_l2l(const int32_t *__restrict__ parent, const uint32_t *__restrict__ key, int64_t nbox, int nm, int M,
+                      const double *__restrict__ tab, const double *__restrict__ fre_p, const double *__restrict__ fim_p,
+                      double *__restrict__ fre, double *__restrict__ fim)
+{
+    extern __shared__ double sm[];
+    const int nc = (M + 1) * (M + 2) / 2, W = M + 1;
+    double *Y = sm;          // [2][nc]
+    double *T = Y + 2 * nc;  // [4][W][W]
+    for (int i = threadIdx.x; i < 4 * W * W; i += blockDim.x) T[i] = tab[i];
+    int64_t b = blockIdx.x;
+    __syncthreads();
+    if (b >= nbox) return;
+    int32_t P = parent ? parent[b] : -1;
+    uint32_t k = key[b];
+    int br = morton_ir(k) & 1, bz = morton_iz(k) & 1;
+    const double *Lr = T + (0 * 2 + br) * W * W, *Lz = T + (1 * 2 + bz) * W * W;
+    for (int n = 0; n < nm; ++n) {
+        double *or_ = fre + ((size_t)b * nm + n) * nc, *oi_ = fim + ((size_t)b * nm + n) * nc;
+        if (P < 0) {
+            for (int o = threadIdx.x; o < nc; o += blockDim.x) or_[o] = oi_[o] = 0.0;
+            continue;
+        }
+        const double *pr = fre_p + ((size_t)P * nm + n) * nc, *pi = fim_p + ((size_t)P * nm + n) * nc;
+        // Y_{k,m} = sum_{l >= m} Lz[m][l] F_{k,l}
+        for (int o = threadIdx.x; o < nc; o += blockDim.x) {
+            int kk = 0, rem = o;
+            while (rem >= M + 1 - kk) { rem -= M + 1 - kk; ++kk; }
+            int m = rem;
+            double yr = 0, yi = 0;
+            for (int l = m; kk + l <= M; ++l) {
+                double c = Lz[m * W + l];
+                int s = cix(kk, l, M);
+                yr = fma(c, pr[s], yr);
+                yi = fma(c, pi[s], yi);
+            }
+            Y[o] = yr;
+            Y[nc + o] = yi;
+        }
+        __syncthreads();
+        // F^c_{i,m} = sum_{k >= i} Lr[i][k] Y_{k,m}
+        for (int o = threadIdx.x; o < nc; o += blockDim.x) {
+            int i = 0, rem = o;
+            while (rem >= M + 1 - i) { rem -= M + 1 - i; ++i; }
+            int m = rem;
+            double fr = 0, fi = 0;
+            for (int kk = i; kk + m <= M; ++kk) {
+                double c = Lr[i * W + kk];
+                int s = cix(kk, m, M);
+                fr = fma(c, Y[s], fr);
+                fi = fma(c, Y[nc + s], fi);
+            }
+            or_[o] = fr;
+            oi_[o] = fi;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Green's-function Taylor coefficients gbar^(n)_{a,b,c}(r, r1, x), a <= A, b <= B,
+// a + b + c <= P, all modes, one point per block.
+//   1. G^(n) by the pair routine (AGM start values + Legendre recursion);
+//   2. x-derivatives gbar_{0,0,k} by the coupled recursion of Eq. gfunc:derivatives:x;
+//   3. gbar_{1,0,k}, gbar_{0,1,k}, gbar_{1,1,k} from the closed forms (Appendix A);
+//   4. the Laplace equation (Eq. gfunc:laplace) in the source radius raises b and in the
+//      field radius raises a.  Expanding r^2 G_rr + r G_r - n^2 G + r^2 G_xx = 0 in the
+//      radial offset gives, for each Taylor coefficient,
+//        (a+1)(a+2) r^2 g_{a+2} + (a+1)(2a+1) r g_{a+1} + (a^2 - n^2) g_a
+//          + (c+1)(c+2) [r^2 g_{a,c+2} + 2 r g_{a-1,c+2} + g_{a-2,c+2}] = 0
+//      (the same with r1, b for the source side); this three-term form is used here.
+// out[((n * (A+1) + a) * (B+1) + b) * (P+1) + c], scaled by scale * c! when fact != 0.
+// ------------------------------------------------------------------------------------
+struct ExpJob {
+    double r, r1, x;   // evaluation point (box units for S2L)
+    double *out;       // slab base for this point (modes consecutive)
+};
+
+__device__ void gbar_block(double r, double r1, double x, int N, int P, int A, int Bm, const RecTab &tab,
+                           const PairParams &pp, double *sm, double *out, double scale, int fact)
+{
+    const int Nw = N < 1 ? 1 : N;
+    const int nmw = Nw + 1;
+    const int Q = P + 1;
+    double *gam = sm;                       // [AFMM_REC_TAB]
+    double *ys = gam + AFMM_REC_TAB;        // [nmw][32]
+    double *tv = ys + (size_t)nmw * 32;     // Taylor vectors [10][Q]
+    double *g00 = tv + 10 * Q;              // [nmw][Q]
+    double *g10 = g00 + (size_t)nmw * Q;
+    double *g01 = g10 + (size_t)nmw * Q;
+    double *g11 = g01 + (size_t)nmw * Q;
+    double *G = g11 + (size_t)nmw * Q;      // [nmw]
+    for (int i = threadIdx.x; i < AFMM_REC_TAB; i += blockDim.x) gam[i] = tab.gam[i];
+    __syncthreads();
+    // 1. G^(n), n = 0..Nw (warp 0; lanes 1..31 run inactive pairs)
+    if (threadIdx.x < 32) {
+        double inv2w = 0.5 / (r * r1);
+        PairGeom g;
+        pair_geom(r, x, r1, 0.0, inv2w, threadIdx.x == 0, g);
+        double s = pair_sequence(g, inv2w, Nw, pp, gam, ys + threadIdx.x, 32);
+        if (threadIdx.x == 0)
+            for (int n = 0; n <= Nw; ++n) G[n] = s * tab.c[n] * ys[n * 32];
+    }
+    // 2. Taylor coefficients in x of 1/rho_pm^2 and the rational factors of Appendix A
+    if (threadIdx.x == 0) {
+        double *vp = tv, *vm = tv + Q, *fxp = tv + 2 * Q, *fxm = tv + 3 * Q, *hp = tv + 4 * Q, *hm = tv + 5 * Q;
+        double *hp1 = tv + 6 * Q, *hm1 = tv + 7 * Q, *dhp = tv + 8 * Q, *dhm = tv + 9 * Q;
+        for (int sgn = 0; sgn < 2; ++sgn) {
+            double aa = sgn == 0 ? r + r1 : r - r1;
+            double *v = sgn == 0 ? vp : vm;
+            double u0 = aa * aa + x * x, iu0 = 1.0 / u0;
+            v[0] = iu0;
+            if (P >= 1) v[1] = -2.0 * x * iu0 * iu0;
+            for (int q = 2; q <= P; ++q) v[q] = -(2.0 * x * v[q - 1] + v[q - 2]) * iu0;
+        }
+        double cc = r * r - r1 * r1;
+        for (int q = 0; q <= P; ++q) {
+            fxp[q] = x * vp[q] + (q >= 1 ? vp[q - 1] : 0.0);
+            fxm[q] = x * vm[q] + (q >= 1 ? vm[q - 1] : 0.0);
+            double a1 = q >= 1 ? 2.0 * x : 0.0;
+            hp[q] = (cc - x * x) * vp[q] - (q >= 1 ? a1 * vp[q - 1] : 0.0) - (q >= 2 ? vp[q - 2] : 0.0);
+            hm[q] = (cc - x * x) * vm[q] - (q >= 1 ? a1 * vm[q - 1] : 0.0) - (q >= 2 ? vm[q - 2] : 0.0);
+            hp1[q] = (-cc - x * x) * vp[q] - (q >= 1 ? a1 * vp[q - 1] : 0.0) - (q >= 2 ? vp[q - 2] : 0.0);
+            hm1[q] = (-cc - x * x) * vm[q] - (q >= 1 ? a1 * vm[q - 1] : 0.0) - (q >= 2 ? vm[q - 2] : 0.0);
+        }
+        // d/dr1 of (cc - x^2)/((r + s r1)^2 + x^2) = -2 r1 v - 2 s (r + s r1) (cc - x^2) v^2
+        for (int sgn = 0; sgn < 2; ++sgn) {
+            const double *v = sgn == 0 ? vp : vm;
+            double s = sgn == 0 ? 1.0 : -1.0, aa = r + s * r1;
+            double *d = sgn == 0 ? dhp : dhm;
+            for (int q = 0; q <= P; ++q) {
+                // (cc - x^2) v^2 Taylor coefficient q, via w = v*v
+                double wq = 0, wq1 = 0, wq2 = 0;
+                for (int t = 0; t <= q; ++t) wq += v[t] * v[q - t];
+                if (q >= 1)
+                    for (int t = 0; t <= q - 1; ++t) wq1 += v[t] * v[q - 1 - t];
+                if (q >= 2)
+                    for (int t = 0; t <= q - 2; ++t) wq2 += v[t] * v[q - 2 - t];
+                double cw = (cc - x * x) * wq - 2.0 * x * wq1 - wq2;
+                d[q] = -2.0 * r1 * v[q] - 2.0 * s * aa * cw;
+            }
+        }
+    }
+    __syncthreads();
+    const double *fxp = tv + 2 * Q, *fxm = tv + 3 * Q, *hp = tv + 4 * Q, *hm = tv + 5 * Q;
+    const double *hp1 = tv + 6 * Q, *hm1 = tv + 7 * Q, *dhp = tv + 8 * Q, *dhm = tv + 9 * Q;
+    for (int n = threadIdx.x; n <= Nw; n += blockDim.x) g00[n * Q] = G[n];
+    __syncthreads();
+    // 3a. x-recursion, coupled in n (G^(-1) = G^(1))
+    for (int k = 0; k < P; ++k) {
+        for (int n = threadIdx.x; n <= Nw; n += blockDim.x) {
+            int m = n == 0 ? 1 : n - 1;
+            double acc = 0.0;
+            for (int q = 0; q <= k; ++q) {
+                double gp = g00[n * Q + k - q], gm = g00[m * Q + k - q];
+                acc = fma(gp + gm, fxp[q], acc);
+                acc = fma(gp - gm, fxm[q], acc);
+            }
+            g00[n * Q + k + 1] = (n - 0.5) / (k + 1) * acc;
+        }
+        __syncthreads();
+    }
+    // 3b. first r and r1 derivatives
+    for (int n = threadIdx.x; n <= Nw; n += blockDim.x) {
+        int m = n == 0 ? 1 : n - 1;
+        double nu = n - 0.5;
+        for (int k = 0; k + 1 <= P; ++k) {
+            double a1 = 0.0, a2 = 0.0;
+            for (int q = 0; q <= k; ++q) {
+                double gp = g00[n * Q + k - q], gm = g00[m * Q + k - q];
+                a1 += (gp + gm) * hp[q] + (gp - gm) * hm[q];
+                a2 += (gp + gm) * hp1[q] + (gp - gm) * hm1[q];
+            }
+            g10[n * Q + k] = (-g00[n * Q + k] + nu * a1) / (2.0 * r);
+            g01[n * Q + k] = (-g00[n * Q + k] + nu * a2) / (2.0 * r1);
+        }
+    }
+    __syncthreads();
+    // 3c. mixed
+    for (int n = threadIdx.x; n <= Nw; n += blockDim.x) {
+        int m = n == 0 ? 1 : n - 1;
+        double nu = n - 0.5;
+        for (int k = 0; k + 2 <= P; ++k) {
+            double acc = 0.0;
+            for (int q = 0; q <= k; ++q) {
+                double g0p = g00[n * Q + k - q], g0m = g00[m * Q + k - q];
+                double g1p = g01[n * Q + k - q], g1m = g01[m * Q + k - q];
+                acc += (g0p + g0m) * dhp[q] + (g1p + g1m) * hp[q] + (g0p - g0m) * dhm[q] + (g1p - g1m) * hm[q];
+            }
+            g11[n * Q + k] = (-g01[n * Q + k] + nu * acc) / (2.0 * r);
+        }
+    }
+    __syncthreads();
+    // 4. Laplace recursions, one mode per thread, into the output slab
+    const int SA = (Bm + 1) * Q;  // stride of a
+    for (int n = threadIdx.x; n <= N; n += blockDim.x) {
+        double *E = out + (size_t)n * (A + 1) * SA;
+        double n2 = (double)n * n;
+#define EI(a_, b_, c_) E[(size_t)(a_) * SA + (b_) * Q + (c_)]
+        for (int c = 0; c <= P; ++c) EI(0, 0, c) = g00[n * Q + c];
+        if (A >= 1)
+            for (int c = 0; c + 1 <= P; ++c) EI(1, 0, c) = g10[n * Q + c];
+        if (Bm >= 1)
+            for (int c = 0; c + 1 <= P; ++c) EI(0, 1, c) = g01[n * Q + c];
+        if (A >= 1 && Bm >= 1)
+            for (int c = 0; c + 2 <= P; ++c) EI(1, 1, c) = g11[n * Q + c];
+        double r1s = r1 * r1, ir1s = 1.0 / r1s, rs = r * r, irs = 1.0 / rs;
+        for (int a = 0; a <= 1 && a <= A; ++a)
+            for (int b = 0; b + 2 <= Bm && a + b + 2 <= P; ++b) {
+                double den = ir1s / ((b + 1.0) * (b + 2.0));
+                for (int c = 0; a + b + 2 + c <= P; ++c) {
+                    double s = (b + 1.0) * (2.0 * b + 1.0) * r1 * EI(a, b + 1, c) + (b * (double)b - n2) * EI(a, b, c);
+                    double t = r1s * EI(a, b, c + 2);
+                    if (b >= 1) t += 2.0 * r1 * EI(a, b - 1, c + 2);
+                    if (b >= 2) t += EI(a, b - 2, c + 2);
+                    s += (c + 1.0) * (c + 2.0) * t;
+                    EI(a, b + 2, c) = -s * den;
+                }
+            }
+        for (int a = 0; a + 2 <= A; ++a)
+            for (int b = 0; b <= Bm && a + 2 + b <= P; ++b) {
+                double den = irs / ((a + 1.0) * (a + 2.0));
+                for (int c = 0; a + 2 + b + c <= P; ++c) {
+                    double s = (a + 1.0) * (2.0 * a + 1.0) * r * EI(a + 1, b, c) + (a * (double)a - n2) * EI(a, b, c);
+                    double t = rs * EI(a, b, c + 2);
+                    if (a >= 1) t += 2.0 * r * EI(a - 1, b, c + 2);
+                    if (a >= 2) t += EI(a - 2, b, c + 2);
+                    s += (c + 1.0) * (c + 2.0) * t;
+                    EI(a + 2, b, c) = -s * den;
+                }
+            }
+        if (fact || scale != 1.0) {
+            for (int a = 0; a <= A; ++a)
+                for (int b = 0; b <= Bm && a + b <= P; ++b) {
+                    double f = scale;
+                    for (int c = 0; a + b + c <= P; ++c) {
+                        if (fact && c > 0) f *= c;
+                        EI(a, b, c) *= f;
+                    }
+                }
+        }
+#undef EI
+    }
+}
+
+static size_t gbar_smem(int N, int P)
+{
+    int nmw = (N < 1 ? 1 : N) + 1;
+    return sizeof(double) * ((size_t)AFMM_REC_TAB + (size_t)nmw * 32 + 10 * (size_t)(P + 1) + 4 * (size_t)nmw * (P + 1) + nmw);
+}
+
+// unit entry point: one point per block, dense (P+1)^3 per mode
+__global__ void k_gbar_points(int64_t np, const double *__restrict__ r, const double *__restrict__ r1,
+                              const double *__restrict__ x, int nm, int P, const RecTab tab, PairParams pp, double *out)
+{
+    extern __shared__ double sm[];
+    int64_t pidx = blockIdx.x;
+    if (pidx >= np) return;
+    size_t per = (size_t)nm * (P + 1) * (P + 1) * (P + 1);
+    gbar_block(r[pidx], r1[pidx], fabs(x[pidx]), nm - 1, P, P, P, tab, pp, sm, out + pidx * per, 1.0, 0);
+    // odd x-derivatives change sign for x < 0 (G even in x)
+    if (x[pidx] < 0.0) {
+        __syncthreads();
+        for (size_t i = threadIdx.x; i < per; i += blockDim.x)
+            if ((i % (P + 1)) & 1) out[pidx * per + i] = -out[pidx * per + i];
+    }
+}
+
+// S2L expansions of one level: block = (station, slot a*4+b)
+__global__ void k_gexp_level(const int32_t *__restrict__ col_of_station, const int32_t *__restrict__ station_of_col,
+                             int nstation, int level, double r0h, double h, int nm, int M, const RecTab tab,
+                             PairParams pp, double *gexp)
+{
+    extern __shared__ double sm[];
+    int st = blockIdx.x / 16, slot = blockIdx.x % 16;
+    int a = slot / 4, b = slot % 4;
+    if (st >= nstation || (a <= 1 && b <= 1)) return;
+    int col = col_of_station[st];
+    int nl = 1 << level;
+    if (col + a >= nl || station_of_col[col + a] < 0) return;
+    double Rs = r0h + col + 0.5, Rb = Rs + a;
+    size_t slab = (size_t)(M + 1) * (M + 1) * (2 * M + 1);
+    double *out = gexp + ((size_t)st * 16 + slot) * nm * slab;
+    gbar_block(Rb, Rs, (double)b, nm - 1, 2 * M, M, M, tab, pp, sm, out, 1.0 / h, 1);
+}
+
+afmm_status launch_green_expansion(int64_t npts, const double *r, const double *r1, const double *x, int n_modes, int P,
+                                   double *out, cudaStream_t st)
+{
+    RecTab tab;
+    make_rec_tab(&tab);
+    PairParams pp;
+    pp.fwd_switch = 9.0;
+    pp.miller_extra = 15.0;
+    size_t per = (size_t)n_modes * (P + 1) * (P + 1) * (P + 1);
+    AFMM_CUDA(cudaMemsetAsync(out, 0, per * npts * sizeof(double), st));
+    size_t sm = gbar_smem(n_modes - 1, P);
+    AFMM_CUDA(cudaFuncSetAttribute(k_gbar_points, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_gbar_points<<<(unsigned)npts, 128, sm, st>>>(npts, r, r1, x, n_modes, P, tab, pp, out);
+    AFMM_LAUNCH_CHECK();
+    return AFMM_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// S2L: one block per (unit of <= 32 field boxes of one column and axial parity, mode).
+// For each of the 27 list slots the expansion slab (oriented FO/BO/FI/BI) and the 32
+// source moment vectors are staged in shared memory; each thread owns one box (lane) and
+// a strided subset of the output coefficients (warp), accumulated in registers.
+// ------------------------------------------------------------------------------------
+__host__ __device__ inline void s2l_offset_ff(int pr, int pz, int slot, int *dr, int *dz)
+{
+    int s = 0;
+    for (int a = -2 - pr; a <= 3 - pr; ++a)
+        for (int b = -2 - pz; b <= 3 - pz; ++b) {
+            if (a >= -1 && a <= 1 && b >= -1 && b <= 1) continue;
+            if (s == slot) {
+                *dr = a;
+                *dz = b;
+                return;
+            }
+            ++s;
+        }
+    *dr = 0;
+    *dz = 0;
+}
+
+struct S2LArgs {
+    const int32_t *unit_box, *unit_col, *s2l, *station_of_col;
+    int64_t nunit;
+    int level, nm, M, nc;
+    const double *gexp;
+    const double *mom_re, *mom_im;
+    double *loc_re, *loc_im;
+};
+
+template <int KPT>
+__global__ void __launch_bounds__(128) k_s2l(const S2LArgs a)
+{
+    extern __shared__ double sm[];
+    const int M = a.M, nc = a.nc, W = M + 1, C2 = 2 * M + 1;
+    const int slab = W * W * C2;
+    double *S = sm;                  // [W][W][C2] oriented expansion
+    double *Ir = S + slab;           // [nc][32]
+    double *Ii = Ir + (size_t)nc * 32;
+    __shared__ int bx[32];
+    __shared__ int src[32];
+    __shared__ int any;
+    const int64_t u = blockIdx.x;
+    const int n = blockIdx.y;
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    if (threadIdx.x < 32) bx[threadIdx.x] = a.unit_box[u * 32 + threadIdx.x];
+    const int ucol = a.unit_col[u];
+    const int col = ucol & 0xffff, pz = (ucol >> 30) & 1, pr = col & 1;
+    const int nl = 1 << a.level;
+    double accr[KPT], acci[KPT];
+    int base[KPT];
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+        accr[q] = 0.0;
+        acci[q] = 0.0;
+        int kl = grp + 4 * q;
+        int k = 0, rem = kl < nc ? kl : 0;
+        while (rem >= M + 1 - k) { rem -= M + 1 - k; ++k; }
+        base[q] = (k * W) * C2 + rem;  // + i*C2 + j
+    }
+    const size_t slabn = (size_t)slab;
+    for (int slot = 0; slot < 27; ++slot) {
+        int dr, dz;
+        s2l_offset_ff(pr, pz, slot, &dr, &dz);
+        int scol = col + dr;
+        if (scol < 0 || scol >= nl) continue;
+        __syncthreads();
+        if (threadIdx.x == 0) any = 0;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int b = bx[threadIdx.x];
+            int s = b >= 0 ? a.s2l[(size_t)b * 27 + slot] : -1;
+            src[threadIdx.x] = s;
+            if (s >= 0) any = 1;
+        }
+        __syncthreads();
+        if (!any) continue;
+        int station = dr < 0 ? scol : col;  // the smaller radius
+        int sidx = a.station_of_col[station];
+        int ea = dr < 0 ? -dr : dr, eb = dz < 0 ? -dz : dz;
+        bool inward = dr > 0, backward = dz > 0;
+        const double *E = a.gexp + (((size_t)sidx * 16 + ea * 4 + eb) * a.nm + n) * slabn;
+        for (int i = threadIdx.x; i < slab; i += blockDim.x) {
+            int c = i % C2, ki = i / C2;
+            int k = ki / W, ii = ki % W;
+            if (k + ii + c > 2 * M) continue;
+            double v = inward ? E[((size_t)ii * W + k) * C2 + c] : E[i];
+            S[i] = (backward && (c & 1)) ? -v : v;
+        }
+        for (int i = threadIdx.x; i < nc * 32; i += blockDim.x) {
+            int c = i / 32, m = i % 32;
+            int s = src[m];
+            Ir[i] = s >= 0 ? a.mom_re[((size_t)s * a.nm + n) * nc + c] : 0.0;
+            Ii[i] = s >= 0 ? a.mom_im[((size_t)s * a.nm + n) * nc + c] : 0.0;
+        }
+        __syncthreads();
+        int ij = 0;
+        for (int i = 0; i <= M; ++i) {
+            for (int j = 0; i + j <= M; ++j, ++ij) {
+                double xr = Ir[ij * 32 + lane], xi = Ii[ij * 32 + lane];
+                int off = i * C2 + j;
+#pragma unroll
+                for (int q = 0; q < KPT; ++q) {
+                    double e = S[base[q] + off];
+                    accr[q] = fma(e, xr, accr[q]);
+                    acci[q] = fma(e, xi, acci[q]);
+                }
+            }
+        }
+    }
+    int b = bx[lane];
+    if (b < 0) return;
+    // F_kl += acc / l!
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+        int kl = grp + 4 * q;
+        if (kl < nc) {
+            int k = 0, rem = kl;
+            while (rem >= M + 1 - k) { rem -= M + 1 - k; ++k; }
+            double f = 1.0;
+            for (int t = 2; t <= rem; ++t) f *= t;
+            size_t o = ((size_t)b * a.nm + n) * nc + kl;
+            a.loc_re[o] += accr[q] / f;
+            a.loc_im[o] += acci[q] / f;
+        }
+    }
+}
+
+static inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b > 0 ? (n + b - 1) / b : 1); }
+
+template <int KPT>
+static afmm_status launch_s2l_k(const S2LArgs &a, cudaStream_t st, size_t sm)
+{
+    AFMM_CUDA(cudaFuncSetAttribute(k_s2l<KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    dim3 grid((unsigned)a.nunit, (unsigned)a.nm);
+    k_s2l<KPT><<<grid, 128, sm, st>>>(a);
+    AFMM_LAUNCH_CHECK();
+    return AFMM_OK;
+}
+
+static afmm_status launch_s2l(afmm_plan p, int l, const double *mre, const double *mim, double *lre, double *lim)
+{
+    Level &v = p->lv[l];
+    if (v.nunit == 0) return AFMM_OK;
+    S2LArgs a;
+    a.unit_box = v.unit_box;
+    a.unit_col = v.unit_col;
+    a.s2l = v.s2l;
+    a.station_of_col = v.station_of_col;
+    a.nunit = v.nunit;
+    a.level = l;
+    a.nm = p->nmodes;
+    a.M = p->M;
+    a.nc = p->ncoef;
+    a.gexp = p->gexp;
+    a.mom_re = mre;
+    a.mom_im = mim;
+    a.loc_re = lre;
+    a.loc_im = lim;
+    int W = p->M + 1;
+    size_t sm = sizeof(double) * ((size_t)W * W * (2 * p->M + 1) + 2 * (size_t)p->ncoef * 32);
+    int kpt = (p->ncoef + 3) / 4;
+    if (kpt <= 4) return launch_s2l_k<4>(a, p->stream, sm);
+    if (kpt <= 8) return launch_s2l_k<8>(a, p->stream, sm);
+    if (kpt <= 12) return launch_s2l_k<12>(a, p->stream, sm);
+    if (kpt <= 16) return launch_s2l_k<16>(a, p->stream, sm);
+    if (kpt <= 24) return launch_s2l_k<24>(a, p->stream, sm);
+    if (kpt <= 32) return launch_s2l_k<32>(a, p->stream, sm);
+    if (kpt <= 40) return launch_s2l_k<40>(a, p->stream, sm);
+    return AFMM_EUNSUPPORTED;
+}
+
+static void tmark(afmm_plan p, int idx)
+{
+    if (p->timing && idx < 16) cudaEventRecord(p->ev[idx], p->stream);
+}
+
+// Far field for direction dir (0: sources -> field points, 1: transposed).  Uses the
+// strengths already permuted into p->qs_*; leaves the leaf-level locals in lv[d].loc_*.
+afmm_status far_field(afmm_plan p, int dir)
+{
+    const int d = p->d, M = p->M, nm = p->nmodes, nc = p->ncoef;
+    cudaStream_t st = p->stream;
+    const bool fw = dir == 0;
+    const double *sr = fw ? p->s_r : p->t_r, *sz = fw ? p->s_z : p->t_z;
+    int64_t nsrc = fw ? p->ns : p->nf;
+    // P2M at the leaves
+    {
+        Level &v = p->lv[d];
+        double h = p->L / (double)(1 << d);
+        size_t sm = sizeof(double) * (32 * (size_t)nc + 2 * (size_t)nm * nc + M + 1);
+        AFMM_CUDA(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_p2m<<<(unsigned)v.nbox, 128, sm, st>>>(v.key, fw ? v.srng : v.trng, v.nbox, sr, sz, p->qs_re, p->qs_im,
+                                                 nsrc, nm, M, p->r0, p->z0, h, *p->rec, v.mom_re, v.mom_im);
+        AFMM_LAUNCH_CHECK();
+    }
+    tmark(p, 2);
+    // upward pass
+    for (int l = d - 1; l >= 2; --l) {
+        Level &v = p->lv[l];
+        size_t sm = sizeof(double) * (2 * (size_t)nc + 4 * (size_t)(M + 1) * (M + 1));
+        k_m2m<<<(unsigned)v.nbox, 128, sm, st>>>(v.child, p->lv[l + 1].key, v.nbox, nm, M, p->m2m_tab,
+                                                 p->lv[l + 1].mom_re, p->lv[l + 1].mom_im, v.mom_re, v.mom_im);
+        AFMM_LAUNCH_CHECK();
+    }
+    tmark(p, 3);
+    // downward pass
+    size_t gsm = gbar_smem(p->N, 2 * M);
+    AFMM_CUDA(cudaFuncSetAttribute(k_gexp_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+    float t_gexp = 0, t_s2l = 0, t_l2l = 0;
+    for (int l = 2; l <= d; ++l) {
+        Level &v = p->lv[l];
+        size_t sm = sizeof(double) * (2 * (size_t)nc + 4 * (size_t)(M + 1) * (M + 1));
+        tmark(p, 4);
+        k_l2l<<<(unsigned)v.nbox, 128, sm, st>>>(l >= 3 ? v.parent : nullptr, v.key, v.nbox, nm, M, p->l2l_tab,
+                                                 l >= 3 ? p->lv[l - 1].loc_re : nullptr,
+                                                 l >= 3 ? p->lv[l - 1].loc_im : nullptr, v.loc_re, v.loc_im);
+        AFMM_LAUNCH_CHECK();
+        tmark(p, 5);
+        double h = p->L / (double)(1 << l);
+        if (v.nstation > 0) {
+            k_gexp_level<<<(unsigned)(v.nstation * 16), 128, gsm, st>>>(v.col_of_station, v.station_of_col, v.nstation,
+                                                                        l, p->r0 / h, h, nm, M, *p->rec, p->pp,
+                                                                        p->gexp);
+            AFMM_LAUNCH_CHECK();
+        }
+        tmark(p, 6);
+        AFMM_TRY(launch_s2l(p, l, v.mom_re, v.mom_im, v.loc_re, v.loc_im));
+        tmark(p, 7);
+        if (p->timing) {
+            float a = 0, b = 0, c = 0;
+            cudaEventSynchronize(p->ev[7]);
+            cudaEventElapsedTime(&a, p->ev[4], p->ev[5]);
+            cudaEventElapsedTime(&b, p->ev[5], p->ev[6]);
+            cudaEventElapsedTime(&c, p->ev[6], p->ev[7]);
+            t_l2l += a;
+            t_gexp += b;
+            t_s2l += c;
+        }
+    }
+    if (p->timing) {
+        p->t_ms[3] = t_gexp;
+        p->t_ms[4] = t_s2l;
+        p->t_ms[5] = t_l2l;
+    }
+    return AFMM_OK;
+}
+
+}  // namespace afmm

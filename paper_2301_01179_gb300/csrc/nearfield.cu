@@ -1,0 +1,428 @@
+// nearfield.cu -- direct sums of S^(n) G^(n) over (field point, source) pairs (Eq.
+// analysis:sum): the FMM's near field over the 3x3 neighbour leaves (the D list, Sec. 2.2;
+// Algorithm 1 last step, together with the local expansion of Eq. analysis:local), and the
+// all-pairs direct evaluation.
+//
+// Layout: one thread per field point, one warp per work unit (<= 32 field points of one
+// leaf, or of the sorted field array for direct sums); the warp walks the unit's sources
+// in lockstep so each source's coordinates and amplitudes are warp-broadcast loads.  The
+// per-mode accumulators and each lane's Legendre sequence live in shared memory
+// ([mode][lane] planes, conflict-free); on GB300 the FP64 pipe, not shared memory, bounds
+// the kernel (FP64 issues at 1/64 of FP32).
+#include <cstring>
+#include "common.cuh"
+#include "pair.cuh"
+
+namespace afmm {
+
+struct NearArgs {
+    // field role (sorted)
+    const double *fr, *fz;
+    int64_t nfield;
+    // source role (sorted), amplitudes [nmodes][nsrc] pre-multiplied by c_n
+    const double *sr, *sz, *q_re, *q_im;
+    int64_t nsrc;
+    int nmodes, N;
+    // work
+    const NearUnit *units;
+    int64_t nunits;
+    const int32_t *nbr;  // [nbox][9] (near mode)
+    const int2 *srng;    // source-role ranges per leaf (near mode)
+    int direct;          // 1: all sources, split into nsplit chunks
+    int nsplit;
+    int64_t split_len;
+    // local expansion at the leaves (near mode, optional)
+    const double *loc_re, *loc_im;
+    const uint32_t *leaf_key;
+    int M, ncoef;
+    double r0, z0, h;
+    // outputs (caller layout [nmodes][nfield] through out_perm, or split partials)
+    const int32_t *out_perm;
+    double *o_re, *o_im, *o_dr_re, *o_dr_im, *o_dz_re, *o_dz_im;
+    double *part;  // split partials [nsplit][ncomp][nmodes][nfield]
+    PairParams pp;
+};
+
+// Local expansion value and gradient at offset (u, v) in box units (locals stored as plain
+// scaled Taylor coefficients F_kl = h^{k+l} Phi_kl, index k(M+1) - k(k-1)/2 + l).
+template <bool GRAD>
+__device__ __forceinline__ void l2p_eval(const double *__restrict__ F, int M, double u, double v, double &val,
+                                         double &du, double &dv)
+{
+    double pu = 0.0, pdu = 0.0, pdv = 0.0;
+    for (int k = M; k >= 0; --k) {
+        int base = k * (M + 1) - k * (k - 1) / 2;
+        double pk = 0.0, pkd = 0.0;
+        for (int l = M - k; l >= 0; --l) {
+            if (GRAD) pkd = fma(pkd, v, pk);
+            pk = fma(pk, v, F[base + l]);
+        }
+        if (GRAD) {
+            pdu = fma(pdu, u, pu);
+            pdv = fma(pdv, u, pkd);
+        }
+        pu = fma(pu, u, pk);
+    }
+    val = pu;
+    du = pdu;
+    dv = pdv;
+}
+
+template <bool GRAD>
+__global__ void __launch_bounds__(AFMM_NEAR_WARPS * 32) k_near(const NearArgs a, const RecTab tab)
+{
+    extern __shared__ double smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    const int nm = a.nmodes, N = a.N;
+    double *gam = smem;                    // [AFMM_REC_TAB]
+    double *rho = gam + AFMM_REC_TAB;      // [nm] c_{n-1}/c_n
+    const int ncomp = GRAD ? 6 : 2;
+    double *wbase = rho + AFMM_MAX_MODES + (size_t)warp * ((ncomp + 1) * nm + 1) * 32;
+    double *acc = wbase;                   // [ncomp][nm][32]
+    double *ys = wbase + (size_t)ncomp * nm * 32;  // [nm + 1][32]
+    const int Nq = GRAD && N < 1 ? 1 : N;          // the gradient of mode 0 needs G^(1)
+    for (int i = threadIdx.x; i < AFMM_REC_TAB; i += blockDim.x) gam[i] = tab.gam[i];
+    for (int i = threadIdx.x; i < nm; i += blockDim.x) rho[i] = i == 0 ? 1.0 : tab.c[i - 1] / tab.c[i];
+    __syncthreads();
+
+    const int64_t unit = (int64_t)blockIdx.x * nw + warp;
+    if (unit >= a.nunits) return;
+    int64_t t0, t1, split = 0;
+    int box = -1;
+    if (a.direct) {
+        int64_t tu = unit / a.nsplit;
+        split = unit % a.nsplit;
+        t0 = tu * 32;
+        t1 = min(t0 + 32, a.nfield);
+    } else {
+        NearUnit u = a.units[unit];
+        box = u.box;
+        t0 = u.begin;
+        t1 = u.end;
+    }
+    const int64_t t = t0 + lane;
+    const bool active = t < t1;
+    const int64_t tc = active ? t : t0;
+    const double rt = a.fr[tc], zt = a.fz[tc];
+    const double inv2r = 0.5 / rt;
+
+    for (int c = 0; c < ncomp; ++c)
+        for (int n = 0; n < nm; ++n) acc[((size_t)c * nm + n) * 32 + lane] = 0.0;
+
+    // source ranges: 9 neighbour leaves, or one split of all sources
+    int nrange = a.direct ? 1 : 9;
+    for (int rg = 0; rg < nrange; ++rg) {
+        int64_t s0, s1;
+        if (a.direct) {
+            s0 = split * a.split_len;
+            s1 = min(s0 + a.split_len, a.nsrc);
+        } else {
+            int32_t nb = a.nbr[(int64_t)box * 9 + rg];
+            if (nb < 0) continue;
+            int2 r = a.srng[nb];
+            s0 = r.x;
+            s1 = r.y;
+        }
+        for (int64_t s = s0; s < s1; ++s) {
+            const double r1 = a.sr[s], z1 = a.sz[s];
+            const double inv2w = inv2r / r1;
+            PairGeom g;
+            pair_geom(rt, zt, r1, z1, inv2w, active, g);
+            double sc = pair_sequence(g, inv2w, Nq, a.pp, gam, ys + lane, 32);
+            if (!GRAD) {
+                for (int n = 0; n < nm; ++n) {
+                    double gn = sc * ys[n * 32 + lane];
+                    double qr = a.q_re[(size_t)n * a.nsrc + s], qi = a.q_im[(size_t)n * a.nsrc + s];
+                    acc[(size_t)n * 32 + lane] = fma(qr, gn, acc[(size_t)n * 32 + lane]);
+                    acc[((size_t)nm + n) * 32 + lane] = fma(qi, gn, acc[((size_t)nm + n) * 32 + lane]);
+                }
+            } else {
+                // dG_n/dx = nu_n x W_n, dG_n/dr = -G_n/(2r) + nu_n (r^2 - r1^2 - x^2)/(2r) W_n,
+                // W_n = G_n A + G_{n-1} B, A = 1/rho_+^2 + 1/rho_-^2, B = 1/rho_+^2 - 1/rho_-^2,
+                // G_{-1} = G_1 (Appendix A).  nu_n and 1/(2r) are applied per field point.
+                double inv = 1.0 / (g.rp2 * g.rm2);
+                double ip = g.rm2 * inv, im = g.rp2 * inv;
+                double A = ip + im, B = ip - im;
+                double qfac = fma(rt - r1, rt + r1, -g.x * g.x);
+                double yprev = ys[32 + lane];  // y_{-1} := y_1 (G^(-1) = G^(1), c_1 = 1)
+                for (int n = 0; n < nm; ++n) {
+                    double yn = ys[n * 32 + lane];
+                    double gn = sc * yn;
+                    double wt = sc * fma(yn, A, rho[n] * yprev * B);
+                    yprev = yn;
+                    double xw = g.x * wt, qw = qfac * wt;
+                    double qr = a.q_re[(size_t)n * a.nsrc + s], qi = a.q_im[(size_t)n * a.nsrc + s];
+                    size_t o = (size_t)n * 32 + lane, st = (size_t)nm * 32;
+                    acc[o] = fma(qr, gn, acc[o]);
+                    acc[o + st] = fma(qi, gn, acc[o + st]);
+                    acc[o + 2 * st] = fma(qr, qw, acc[o + 2 * st]);
+                    acc[o + 3 * st] = fma(qi, qw, acc[o + 3 * st]);
+                    acc[o + 4 * st] = fma(qr, xw, acc[o + 4 * st]);
+                    acc[o + 5 * st] = fma(qi, xw, acc[o + 5 * st]);
+                }
+            }
+        }
+    }
+    if (!active) return;
+    // local expansion at the field point (far field)
+    double u = 0.0, v = 0.0;
+    if (a.loc_re) {
+        uint32_t k = a.leaf_key[box];
+        double cr = a.r0 + ((double)morton_ir(k) + 0.5) * a.h, cz = a.z0 + ((double)morton_iz(k) + 0.5) * a.h;
+        u = (rt - cr) / a.h;
+        v = (zt - cz) / a.h;
+    }
+    const int64_t dst = a.out_perm ? a.out_perm[t] : t;
+    const size_t st = (size_t)nm * 32;
+    for (int n = 0; n < nm; ++n) {
+        // (amplitudes carry c_n and the sequence is G_n / c_n, so the sums are plain)
+        size_t o = (size_t)n * 32 + lane;
+        double pr = acc[o], pi = acc[o + st];
+        double dr_r = 0, dr_i = 0, dz_r = 0, dz_i = 0;
+        if (GRAD) {
+            double nu = n - 0.5;
+            dr_r = (nu * acc[o + 2 * st] - pr) * inv2r;
+            dr_i = (nu * acc[o + 3 * st] - pi) * inv2r;
+            dz_r = nu * acc[o + 4 * st];
+            dz_i = nu * acc[o + 5 * st];
+        }
+        if (a.loc_re) {
+            const double *Fr = a.loc_re + ((size_t)box * nm + n) * a.ncoef;
+            const double *Fi = a.loc_im + ((size_t)box * nm + n) * a.ncoef;
+            double vr, dur, dvr, vi, dui, dvi;
+            l2p_eval<GRAD>(Fr, a.M, u, v, vr, dur, dvr);
+            l2p_eval<GRAD>(Fi, a.M, u, v, vi, dui, dvi);
+            pr += vr;
+            pi += vi;
+            if (GRAD) {
+                double ih = 1.0 / a.h;
+                dr_r += dur * ih;
+                dr_i += dui * ih;
+                dz_r += dvr * ih;
+                dz_i += dvi * ih;
+            }
+        }
+        if (a.part) {
+            size_t base = (size_t)split * ncomp;
+            size_t nfm = (size_t)a.nfield;
+            a.part[((base + 0) * nm + n) * nfm + t] = pr;
+            a.part[((base + 1) * nm + n) * nfm + t] = pi;
+            if (GRAD) {
+                a.part[((base + 2) * nm + n) * nfm + t] = dr_r;
+                a.part[((base + 3) * nm + n) * nfm + t] = dr_i;
+                a.part[((base + 4) * nm + n) * nfm + t] = dz_r;
+                a.part[((base + 5) * nm + n) * nfm + t] = dz_i;
+            }
+        } else {
+            size_t od = (size_t)n * a.nfield + dst;
+            if (a.o_re) a.o_re[od] = pr;
+            if (a.o_im) a.o_im[od] = pi;
+            if (GRAD) {
+                a.o_dr_re[od] = dr_r;
+                a.o_dr_im[od] = dr_i;
+                a.o_dz_re[od] = dz_r;
+                a.o_dz_im[od] = dz_i;
+            }
+        }
+    }
+}
+
+// sum of split partials into the caller layout
+__global__ void k_split_reduce(const double *__restrict__ part, int nsplit, int ncomp, int nm, int64_t nfield,
+                               const int32_t *__restrict__ perm, double *o0, double *o1, double *o2, double *o3,
+                               double *o4, double *o5)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t tot = (int64_t)ncomp * nm * nfield;
+    if (i >= tot) return;
+    int comp = (int)(i / ((int64_t)nm * nfield));
+    int64_t rem = i % ((int64_t)nm * nfield);
+    int n = (int)(rem / nfield);
+    int64_t t = rem % nfield;
+    double s = 0.0;
+    for (int k = 0; k < nsplit; ++k) s += part[(((size_t)k * ncomp + comp) * nm + n) * nfield + t];
+    double *o = comp == 0 ? o0 : comp == 1 ? o1 : comp == 2 ? o2 : comp == 3 ? o3 : comp == 4 ? o4 : o5;
+    if (o) o[(size_t)n * nfield + (perm ? perm[t] : t)] = s;
+}
+
+// strengths into sorted order, times c_n: qs[n][i] = q[n][perm[i]] * c_n
+__global__ void k_permute(const double *__restrict__ q_re, const double *__restrict__ q_im,
+                          const int32_t *__restrict__ perm, int64_t n, int nm, const RecTab tab,
+                          double *__restrict__ qs_re, double *__restrict__ qs_im)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n * nm) return;
+    int m = (int)(i / n);
+    int64_t j = i % n;
+    size_t src = (size_t)m * n + perm[j];
+    double c = tab.c[m];
+    qs_re[i] = q_re[src] * c;
+    qs_im[i] = q_im[src] * c;
+}
+
+// unit evaluator: thread per pair, G (and gradient) for all modes
+__global__ void k_green(int64_t np, const double *__restrict__ r, const double *__restrict__ r1,
+                        const double *__restrict__ x, int nm, const RecTab tab, PairParams pp, double *G, double *Gr,
+                        double *Gx)
+{
+    extern __shared__ double smem[];
+    double *gam = smem;
+    double *ys = gam + AFMM_REC_TAB;  // [max(nm, 2)][blockDim]
+    for (int i = threadIdx.x; i < AFMM_REC_TAB; i += blockDim.x) gam[i] = tab.gam[i];
+    __syncthreads();
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool active = p < np;
+    int64_t pc = active ? p : 0;
+    double rt = r[pc], rs = r1[pc], xx = x[pc];
+    double inv2w = 0.5 / (rt * rs);
+    PairGeom g;
+    pair_geom(rt, xx, rs, 0.0, inv2w, active, g);
+    int N = nm - 1;
+    int Nq = N < 1 ? 1 : N;  // the gradient of mode 0 needs G^(1)
+    double sc = pair_sequence(g, inv2w, Nq, pp, gam, ys + threadIdx.x, blockDim.x);
+    if (!active) return;
+    const int B = blockDim.x;
+    for (int n = 0; n < nm; ++n) G[(size_t)n * np + p] = sc * tab.c[n] * ys[n * B + threadIdx.x];
+    if (Gr) {
+        double inv = 1.0 / (g.rp2 * g.rm2);
+        double ip = g.rm2 * inv, im = g.rp2 * inv;
+        double A = ip + im, Bc = ip - im;
+        double qf = fma(rt - rs, rt + rs, -xx * xx);
+        for (int n = 0; n < nm; ++n) {
+            double gn = sc * tab.c[n] * ys[n * B + threadIdx.x];
+            int m = n == 0 ? 1 : n - 1;
+            double gm = sc * tab.c[m] * ys[m * B + threadIdx.x];
+            double wv = gn * A + gm * Bc;
+            double nu = n - 0.5;
+            Gx[(size_t)n * np + p] = nu * xx * wv;
+            Gr[(size_t)n * np + p] = (-gn + nu * qf * wv) / (2.0 * rt);
+        }
+    }
+}
+
+static size_t near_smem(int nm, int grad, int warps)
+{
+    int ncomp = grad ? 6 : 2;
+    return sizeof(double) * ((size_t)AFMM_REC_TAB + AFMM_MAX_MODES + (size_t)warps * ((ncomp + 1) * nm + 1) * 32);
+}
+
+static int near_warps(int nm, int grad)
+{
+    for (int w = AFMM_NEAR_WARPS; w >= 1; --w)
+        if (near_smem(nm, grad, w) <= 227 * 1024) return w;
+    return 0;
+}
+
+static inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b > 0 ? (n + b - 1) / b : 1); }
+
+afmm_status launch_permute(afmm_plan p, int dir, const double *q_re, const double *q_im)
+{
+    int64_t n = dir == 0 ? p->ns : p->nf;
+    const int32_t *perm = dir == 0 ? p->s_perm : p->t_perm;
+    k_permute<<<nblk(n * p->nmodes), 256, 0, p->stream>>>(q_re, q_im, perm, n, p->nmodes, *p->rec, p->qs_re,
+                                                           p->qs_im);
+    AFMM_LAUNCH_CHECK();
+    return AFMM_OK;
+}
+
+// dir 0: field points <- sources; dir 1: sources <- field points (transposed problem).
+// direct = 1: all pairs (split over sources when the field set is small).
+afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *phi_re, double *phi_im, double *dr_re,
+                        double *dr_im, double *dz_re, double *dz_im, int direct)
+{
+    NearArgs a;
+    memset(&a, 0, sizeof(a));
+    const bool fw = dir == 0;
+    a.fr = fw ? p->t_r : p->s_r;
+    a.fz = fw ? p->t_z : p->s_z;
+    a.nfield = fw ? p->nf : p->ns;
+    a.sr = fw ? p->s_r : p->t_r;
+    a.sz = fw ? p->s_z : p->t_z;
+    a.nsrc = fw ? p->ns : p->nf;
+    a.q_re = p->qs_re;
+    a.q_im = p->qs_im;
+    a.nmodes = p->nmodes;
+    a.N = p->N;
+    a.pp = p->pp;
+    a.out_perm = fw ? p->t_perm : p->s_perm;
+    a.o_re = phi_re;
+    a.o_im = phi_im;
+    a.o_dr_re = dr_re;
+    a.o_dr_im = dr_im;
+    a.o_dz_re = dz_re;
+    a.o_dz_im = dz_im;
+    int d = p->d;
+    if (direct) {
+        int64_t tunits = (a.nfield + 31) / 32;
+        int64_t want = 152 * 8;  // warps in flight to fill the GPU
+        int nsplit = 1;
+        if (tunits < want) {
+            int64_t ns_ = (want + tunits - 1) / tunits;
+            int64_t maxs = (a.nsrc + 63) / 64;
+            int64_t room = p->part_cap / ((int64_t)(grad ? 6 : 2) * a.nmodes * a.nfield);
+            if (ns_ > maxs) ns_ = maxs;
+            if (ns_ > room) ns_ = room;
+            nsplit = ns_ < 1 ? 1 : (int)ns_;
+        }
+        a.direct = 1;
+        a.nsplit = nsplit;
+        a.split_len = (a.nsrc + nsplit - 1) / nsplit;
+        a.nunits = tunits * nsplit;
+        a.part = nsplit > 1 ? p->part_buf : nullptr;
+    } else {
+        a.units = p->near_unit[dir];
+        a.nunits = p->n_near_unit[dir];
+        a.nbr = p->lv[d].nbr;
+        a.srng = fw ? p->lv[d].srng : p->lv[d].trng;
+        if (with_local) {
+            a.loc_re = p->lv[d].loc_re;
+            a.loc_im = p->lv[d].loc_im;
+            a.leaf_key = p->lv[d].key;
+            a.M = p->M;
+            a.ncoef = p->ncoef;
+            a.r0 = p->r0;
+            a.z0 = p->z0;
+            a.h = p->L / (double)(1 << d);
+        }
+    }
+    if (a.nunits == 0) return AFMM_OK;
+    int w = near_warps(p->nmodes, grad);
+    if (w == 0) return AFMM_EUNSUPPORTED;
+    size_t sm = near_smem(p->nmodes, grad, w);
+    unsigned grid = (unsigned)((a.nunits + w - 1) / w);
+    if (grad) {
+        AFMM_CUDA(cudaFuncSetAttribute(k_near<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_near<true><<<grid, w * 32, sm, p->stream>>>(a, *p->rec);
+    } else {
+        AFMM_CUDA(cudaFuncSetAttribute(k_near<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_near<false><<<grid, w * 32, sm, p->stream>>>(a, *p->rec);
+    }
+    AFMM_LAUNCH_CHECK();
+    if (a.part) {
+        int ncomp = grad ? 6 : 2;
+        int64_t tot = (int64_t)ncomp * a.nmodes * a.nfield;
+        k_split_reduce<<<nblk(tot), 256, 0, p->stream>>>(a.part, a.nsplit, ncomp, a.nmodes, a.nfield, a.out_perm,
+                                                         phi_re, phi_im, dr_re, dr_im, dz_re, dz_im);
+        AFMM_LAUNCH_CHECK();
+    }
+    return AFMM_OK;
+}
+
+afmm_status launch_green(int64_t npairs, const double *r, const double *r1, const double *x, int n_modes, double *G,
+                         double *Gr, double *Gx, cudaStream_t st)
+{
+    RecTab tab;
+    make_rec_tab(&tab);
+    PairParams pp;
+    pp.fwd_switch = 9.0;
+    pp.miller_extra = 15.0;
+    const int B = 64;
+    size_t sm = sizeof(double) * ((size_t)AFMM_REC_TAB + (size_t)(n_modes < 2 ? 2 : n_modes) * B);
+    AFMM_CUDA(cudaFuncSetAttribute(k_green, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_green<<<nblk(npairs, B), B, sm, st>>>(npairs, r, r1, x, n_modes, tab, pp, G, Gr, Gx);
+    AFMM_LAUNCH_CHECK();
+    return AFMM_OK;
+}
+
+}  // namespace afmm

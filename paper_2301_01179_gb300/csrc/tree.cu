@@ -1,0 +1,737 @@
+// tree.cu -- uniform quadtree over (r, z) (Sec. 2.1; Algorithm 1, first two steps).
+//
+// Domain: the square anchored at (min r, min z) over sources and field points with side
+// L = max(r extent, z extent) (the paper's square 0 <= r, z <= r_max, moved to the data).
+// A point's box at level l is floor((v - v0) * 2^l / L), clamped to 2^l - 1.  Keys are
+// computed once at level 16; 2^l / L is a power-of-two multiple of 2^16 / L, so a level-l
+// index is exactly the level-16 index shifted right by 16 - l.
+// Depth: the smallest d >= 2 whose non-empty source leaves hold at most leaf_size sources
+// on average, unless overridden.
+// All steps are device kernels; the host reads back a handful of counts.
+#include "common.cuh"
+#include <vector>
+#include <algorithm>
+
+namespace afmm {
+
+// ------------------------------------------------------------------------------------
+// validation and bounding square
+// ------------------------------------------------------------------------------------
+__global__ void k_minmax(const double *__restrict__ r1, const double *__restrict__ z1, int64_t n1,
+                         const double *__restrict__ r2, const double *__restrict__ z2, int64_t n2,
+                         double *__restrict__ part)
+{
+    double rmin = INFINITY, rmax = -INFINITY, zmin = INFINITY, zmax = -INFINITY, bad = 0.0;
+    int64_t n = n1 + n2;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double r = i < n1 ? r1[i] : r2[i - n1];
+        double z = i < n1 ? z1[i] : z2[i - n1];
+        if (!(r > 0.0) || !isfinite(r) || !isfinite(z)) {
+            bad += 1.0;
+            continue;
+        }
+        rmin = fmin(rmin, r);
+        rmax = fmax(rmax, r);
+        zmin = fmin(zmin, z);
+        zmax = fmax(zmax, z);
+    }
+    __shared__ double sh[5][32];
+    for (int o = 16; o > 0; o >>= 1) {
+        rmin = fmin(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+        rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+        zmin = fmin(zmin, __shfl_xor_sync(0xffffffffu, zmin, o));
+        zmax = fmax(zmax, __shfl_xor_sync(0xffffffffu, zmax, o));
+        bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    if (ln == 0) {
+        sh[0][w] = rmin; sh[1][w] = rmax; sh[2][w] = zmin; sh[3][w] = zmax; sh[4][w] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int nw = blockDim.x >> 5;
+        for (int k = 1; k < nw; ++k) {
+            sh[0][0] = fmin(sh[0][0], sh[0][k]);
+            sh[1][0] = fmax(sh[1][0], sh[1][k]);
+            sh[2][0] = fmin(sh[2][0], sh[2][k]);
+            sh[3][0] = fmax(sh[3][0], sh[3][k]);
+            sh[4][0] += sh[4][k];
+        }
+        for (int k = 0; k < 5; ++k) part[blockIdx.x * 5 + k] = sh[k][0];
+    }
+}
+
+__global__ void k_minmax_final(const double *__restrict__ part, int nblk, double *__restrict__ out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double v[5] = {INFINITY, -INFINITY, INFINITY, -INFINITY, 0.0};
+    for (int b = 0; b < nblk; ++b) {
+        v[0] = fmin(v[0], part[b * 5 + 0]);
+        v[1] = fmax(v[1], part[b * 5 + 1]);
+        v[2] = fmin(v[2], part[b * 5 + 2]);
+        v[3] = fmax(v[3], part[b * 5 + 3]);
+        v[4] += part[b * 5 + 4];
+    }
+    for (int k = 0; k < 5; ++k) out[k] = v[k];
+}
+
+// ------------------------------------------------------------------------------------
+// keys and sort
+// ------------------------------------------------------------------------------------
+__device__ inline uint32_t box_coord16(double v, double v0, double s16)
+{
+    double f = floor((v - v0) * s16);
+    if (f < 0.0) f = 0.0;
+    if (f > 65535.0) f = 65535.0;
+    return (uint32_t)f;
+}
+
+__global__ void k_keys(const double *__restrict__ r, const double *__restrict__ z, int64_t n, int64_t npad,
+                       double r0, double z0, double s16, unsigned long long *__restrict__ out)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= npad) return;
+    if (i >= n) {
+        out[i] = ~0ull;
+        return;
+    }
+    uint32_t ir = box_coord16(r[i], r0, s16), iz = box_coord16(z[i], z0, s16);
+    out[i] = ((unsigned long long)morton_key(ir, iz) << 32) | (unsigned long long)i;
+}
+
+// Bitonic sort of 64-bit keys, ascending; npad a power of two >= 2048.
+#define BITONIC_TILE 2048
+__global__ void k_bitonic_tile(unsigned long long *__restrict__ a, int64_t k_start, int merge_only)
+{
+    __shared__ unsigned long long s[BITONIC_TILE];
+    int64_t base = (int64_t)blockIdx.x * BITONIC_TILE;
+    for (int t = threadIdx.x; t < BITONIC_TILE; t += blockDim.x) s[t] = a[base + t];
+    __syncthreads();
+    int64_t kfirst = merge_only ? k_start : 2;
+    int64_t klast = merge_only ? k_start : BITONIC_TILE;
+    for (int64_t k = kfirst; k <= klast; k <<= 1) {
+        int jstart = (int)((k >> 1) < (BITONIC_TILE >> 1) ? (k >> 1) : (BITONIC_TILE >> 1));
+        for (int j = jstart; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < BITONIC_TILE / 2; t += blockDim.x) {
+                int i = 2 * j * (t / j) + (t % j);
+                int pr = i + j;
+                int64_t gi = base + i;
+                bool up = (gi & k) == 0;
+                unsigned long long x = s[i], y = s[pr];
+                if ((x > y) == up) {
+                    s[i] = y;
+                    s[pr] = x;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int t = threadIdx.x; t < BITONIC_TILE; t += blockDim.x) a[base + t] = s[t];
+}
+
+__global__ void k_bitonic_global(unsigned long long *__restrict__ a, int64_t npad, int64_t j, int64_t k)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= npad / 2) return;
+    int64_t i = 2 * j * (t / j) + (t % j);
+    int64_t pr = i + j;
+    bool up = (i & k) == 0;
+    unsigned long long x = a[i], y = a[pr];
+    if ((x > y) == up) {
+        a[i] = y;
+        a[pr] = x;
+    }
+}
+
+static afmm_status bitonic_sort(unsigned long long *a, int64_t npad, cudaStream_t st)
+{
+    int64_t tiles = npad / BITONIC_TILE;
+    k_bitonic_tile<<<(unsigned)tiles, 1024, 0, st>>>(a, 2, 0);
+    AFMM_LAUNCH_CHECK();
+    for (int64_t k = 2 * BITONIC_TILE; k <= npad; k <<= 1) {
+        for (int64_t j = k >> 1; j >= BITONIC_TILE; j >>= 1) {
+            int64_t half = npad / 2;
+            k_bitonic_global<<<(unsigned)((half + 255) / 256), 256, 0, st>>>(a, npad, j, k);
+            AFMM_LAUNCH_CHECK();
+        }
+        k_bitonic_tile<<<(unsigned)tiles, 1024, 0, st>>>(a, k, 1);
+        AFMM_LAUNCH_CHECK();
+    }
+    return AFMM_OK;
+}
+
+static int64_t pow2_at_least(int64_t n)
+{
+    int64_t p = BITONIC_TILE;
+    while (p < n) p <<= 1;
+    return p;
+}
+
+// ------------------------------------------------------------------------------------
+// scans (exclusive, int32 / int64 counts) for stream compaction
+// ------------------------------------------------------------------------------------
+__global__ void k_scan_block(const int64_t *__restrict__ in, int64_t *__restrict__ out, int64_t n,
+                             int64_t *__restrict__ bsum)
+{
+    __shared__ int64_t ws[32];
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t v = i < n ? in[i] : 0;
+    int ln = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (ln >= o) x += y;
+    }
+    if (ln == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int64_t s = ln < (int)(blockDim.x >> 5) ? ws[ln] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (ln >= o) s += y;
+        }
+        ws[ln] = s;
+    }
+    __syncthreads();
+    int64_t pre = (w > 0 ? ws[w - 1] : 0) + x - v;  // exclusive
+    if (i < n) out[i] = pre;
+    if (threadIdx.x == blockDim.x - 1) bsum[blockIdx.x] = pre + v;
+}
+
+__global__ void k_scan_add(int64_t *__restrict__ out, int64_t n, const int64_t *__restrict__ boff)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] += boff[blockIdx.x];
+}
+
+// exclusive scan of in[0..n) into out[0..n); total written to out[n] (out holds n+1).
+// tmp must hold >= 2 * ceil(n/1024) + 64 int64.
+static afmm_status scan_excl(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t st)
+{
+    const int B = 1024;
+    int64_t nb = (n + B - 1) / B;
+    if (nb < 1) nb = 1;
+    int64_t *bsum = tmp, *boff = tmp + nb + 1;
+    k_scan_block<<<(unsigned)nb, B, 0, st>>>(in, out, n, bsum);
+    AFMM_LAUNCH_CHECK();
+    if (nb == 1) {
+        // total = bsum[0]
+        cudaMemcpyAsync(out + n, bsum, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+        return AFMM_OK;
+    }
+    AFMM_TRY(scan_excl(bsum, boff, nb, tmp + 2 * nb + 2, st));
+    k_scan_add<<<(unsigned)nb, B, 0, st>>>(out, n, boff);
+    AFMM_LAUNCH_CHECK();
+    cudaMemcpyAsync(out + n, boff + nb, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+    return AFMM_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// per-point outputs of the sort
+// ------------------------------------------------------------------------------------
+__global__ void k_gather_sorted(const unsigned long long *__restrict__ srt, int64_t n, const double *__restrict__ r,
+                                const double *__restrict__ z, double *__restrict__ rs, double *__restrict__ zs,
+                                int32_t *__restrict__ perm, uint32_t *__restrict__ key)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned long long v = srt[i];
+    int32_t idx = (int32_t)(v & 0xffffffffull);
+    perm[i] = idx;
+    key[i] = (uint32_t)(v >> 32);
+    rs[i] = r[idx];
+    zs[i] = z[idx];
+}
+
+// number of distinct level-l prefixes among sorted level-16 keys, l = 2..16
+__global__ void k_depth_counts(const uint32_t *__restrict__ key, int64_t n, unsigned long long *__restrict__ cnt)
+{
+    __shared__ unsigned int c[17];
+    if (threadIdx.x < 17) c[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        for (int l = 2; l <= 16; ++l) {
+            int sh = 2 * (16 - l);
+            if (i == 0 || (key[i] >> sh) != (key[i - 1] >> sh)) atomicAdd(&c[l], 1u);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 17 && c[threadIdx.x]) atomicAdd(&cnt[threadIdx.x], (unsigned long long)c[threadIdx.x]);
+}
+
+// leaf keys of both point sets, packed for a union sort (key << 32)
+__global__ void k_leaf_union(const uint32_t *__restrict__ ks, int64_t ns, const uint32_t *__restrict__ kt, int64_t nf,
+                             int sh, int64_t npad, unsigned long long *__restrict__ out)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= npad) return;
+    unsigned long long v = ~0ull;
+    if (i < ns)
+        v = (unsigned long long)(ks[i] >> sh) << 32;
+    else if (i < ns + nf)
+        v = (unsigned long long)(kt[i - ns] >> sh) << 32;
+    out[i] = v;
+}
+
+// flags[i] = 1 where a new distinct key starts (keys from a sorted 64-bit array, value >> 32,
+// further shifted right by `extra` bits); invalid (~0) entries get 0
+__global__ void k_unique_flags(const unsigned long long *__restrict__ a, int64_t n, int extra, int64_t *__restrict__ f)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned long long v = a[i];
+    if (v == ~0ull) {
+        f[i] = 0;
+        return;
+    }
+    uint32_t k = (uint32_t)(v >> 32) >> extra;
+    f[i] = (i == 0 || ((uint32_t)(a[i - 1] >> 32) >> extra) != k) ? 1 : 0;
+}
+
+__global__ void k_unique_scatter(const unsigned long long *__restrict__ a, int64_t n, int extra,
+                                 const int64_t *__restrict__ f, const int64_t *__restrict__ pos,
+                                 uint32_t *__restrict__ keys)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (f[i]) keys[pos[i]] = (uint32_t)(a[i] >> 32) >> extra;
+}
+
+// keys of level l-1 from keys of level l (>> 2), written into a 64-bit array for uniq
+__global__ void k_parent_keys(const uint32_t *__restrict__ k, int64_t n, unsigned long long *__restrict__ out)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (unsigned long long)(k[i] >> 2) << 32;
+}
+
+__device__ inline int64_t lower_bound_u32(const uint32_t *__restrict__ a, int64_t n, unsigned long long v)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if ((unsigned long long)a[mid] < v)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__device__ inline int64_t find_key(const uint32_t *__restrict__ a, int64_t n, uint32_t v)
+{
+    int64_t i = lower_bound_u32(a, n, v);
+    return (i < n && a[i] == v) ? i : -1;
+}
+
+__global__ void k_box_ranges(const uint32_t *__restrict__ bkey, int64_t nbox, int sh, const uint32_t *__restrict__ sk,
+                             int64_t ns, const uint32_t *__restrict__ tk, int64_t nf, int2 *__restrict__ srng,
+                             int2 *__restrict__ trng)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    unsigned long long lo = (unsigned long long)bkey[b] << sh, hi = ((unsigned long long)bkey[b] + 1) << sh;
+    srng[b] = make_int2((int)lower_bound_u32(sk, ns, lo), (int)lower_bound_u32(sk, ns, hi));
+    trng[b] = make_int2((int)lower_bound_u32(tk, nf, lo), (int)lower_bound_u32(tk, nf, hi));
+}
+
+__global__ void k_parents(const uint32_t *__restrict__ bkey, int64_t nbox, const uint32_t *__restrict__ pkey,
+                          int64_t npbox, int32_t *__restrict__ parent)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    parent[b] = (int32_t)find_key(pkey, npbox, bkey[b] >> 2);
+}
+
+__global__ void k_child_ranges(const int32_t *__restrict__ parent, int64_t nbox, int2 *__restrict__ child)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    int32_t p = parent[b];
+    if (b == 0 || parent[b - 1] != p) child[p].x = (int)b;
+    if (b == nbox - 1 || parent[b + 1] != p) child[p].y = (int)(b + 1);
+}
+
+// S2L list offsets for a field box with radial parity pr and axial parity pz: children of
+// the parent's 3x3 neighbours that are not neighbours of the box (Sec. 2.2).  Slot order:
+// dr from -2-pr to 3-pr, dz from -2-pz to 3-pz, skipping |dr|,|dz| <= 1.
+__host__ __device__ inline void s2l_offset(int pr, int pz, int slot, int *dr, int *dz)
+{
+    int s = 0;
+    for (int a = -2 - pr; a <= 3 - pr; ++a)
+        for (int b = -2 - pz; b <= 3 - pz; ++b) {
+            if (a >= -1 && a <= 1 && b >= -1 && b <= 1) continue;
+            if (s == slot) {
+                *dr = a;
+                *dz = b;
+                return;
+            }
+            ++s;
+        }
+    *dr = 0;
+    *dz = 0;
+}
+
+__global__ void k_s2l_table(const uint32_t *__restrict__ bkey, int64_t nbox, int level, int32_t *__restrict__ tab)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nbox * 27) return;
+    int64_t b = t / 27;
+    int slot = (int)(t % 27);
+    uint32_t k = bkey[b];
+    int ti = (int)morton_ir(k), tj = (int)morton_iz(k);
+    int dr, dz;
+    s2l_offset(ti & 1, tj & 1, slot, &dr, &dz);
+    int si = ti + dr, sj = tj + dz, nl = 1 << level;
+    int32_t v = -1;
+    if (si >= 0 && sj >= 0 && si < nl && sj < nl) v = (int32_t)find_key(bkey, nbox, morton_key(si, sj));
+    tab[t] = v;
+}
+
+__global__ void k_nbr_table(const uint32_t *__restrict__ bkey, int64_t nbox, int level, int32_t *__restrict__ tab)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nbox * 9) return;
+    int64_t b = t / 9;
+    int slot = (int)(t % 9);
+    uint32_t k = bkey[b];
+    int ti = (int)morton_ir(k) + slot / 3 - 1, tj = (int)morton_iz(k) + slot % 3 - 1, nl = 1 << level;
+    int32_t v = -1;
+    if (ti >= 0 && tj >= 0 && ti < nl && tj < nl) v = (int32_t)find_key(bkey, nbox, morton_key(ti, tj));
+    tab[t] = v;
+}
+
+__global__ void k_station_flags(const uint32_t *__restrict__ bkey, int64_t nbox, int32_t *__restrict__ flag)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b < nbox) flag[morton_ir(bkey[b])] = 1;
+}
+
+__global__ void k_station_map(const int32_t *__restrict__ flag, int ncol, const int64_t *__restrict__ pos,
+                              int32_t *__restrict__ st_of_col, int32_t *__restrict__ col_of_st)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncol) return;
+    if (flag[c]) {
+        st_of_col[c] = (int32_t)pos[c];
+        col_of_st[pos[c]] = c;
+    } else {
+        st_of_col[c] = -1;
+    }
+}
+
+__global__ void k_i32_to_i64(const int32_t *__restrict__ a, int64_t n, int64_t *__restrict__ b)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i];
+}
+
+// S2L units: boxes sorted by (column, axial parity, axial index); groups of 32
+__global__ void k_unit_keys(const uint32_t *__restrict__ bkey, int64_t nbox, int64_t npad,
+                            unsigned long long *__restrict__ out)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= npad) return;
+    if (b >= nbox) {
+        out[b] = ~0ull;
+        return;
+    }
+    uint32_t k = bkey[b];
+    unsigned long long ir = morton_ir(k), iz = morton_iz(k);
+    out[b] = (ir << 48) | ((iz & 1ull) << 47) | (iz << 24) | (unsigned long long)b;
+}
+
+__device__ inline unsigned long long unit_group(unsigned long long v) { return v >> 47; }
+
+__global__ void k_unit_flags(const unsigned long long *__restrict__ u, int64_t nbox, int64_t *__restrict__ f)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nbox) return;
+    unsigned long long g = unit_group(u[i]);
+    int64_t lo = 0, hi = i;  // first index with the same group
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (unit_group(u[mid]) < g)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    f[i] = ((i - lo) % 32 == 0) ? 1 : 0;
+}
+
+__global__ void k_unit_fill(const unsigned long long *__restrict__ u, int64_t nbox, const int64_t *__restrict__ pos,
+                            int32_t *__restrict__ ubox, int32_t *__restrict__ ucol)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nbox) return;
+    unsigned long long v = u[i], g = unit_group(v);
+    int64_t lo = 0, hi = i;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (unit_group(u[mid]) < g)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    int64_t rank = i - lo;
+    int64_t unit = pos[i - (rank % 32)];
+    ubox[unit * 32 + rank % 32] = (int32_t)(v & 0xffffffull);
+    if (rank % 32 == 0) ucol[unit] = (int32_t)((v >> 48) | ((v >> 47 & 1ull) << 30));
+}
+
+// near-field units: ceil(count/32) per leaf box with field-role points
+__global__ void k_near_counts(const int2 *__restrict__ rng, int64_t nbox, int64_t *__restrict__ cnt)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b < nbox) cnt[b] = (rng[b].y - rng[b].x + 31) / 32;
+}
+
+__global__ void k_near_fill(const int2 *__restrict__ rng, int64_t nbox, const int64_t *__restrict__ pos,
+                            NearUnit *__restrict__ u)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    int64_t p = pos[b];
+    for (int s = rng[b].x; s < rng[b].y; s += 32) {
+        NearUnit x;
+        x.box = (int32_t)b;
+        x.begin = s;
+        x.end = min(s + 32, rng[b].y);
+        u[p++] = x;
+    }
+}
+
+// statistics: near-field pairs and S2L applications
+__global__ void k_near_pairs(const int2 *__restrict__ trng, const int2 *__restrict__ srng, const int32_t *__restrict__ nbr,
+                             int64_t nbox, unsigned long long *__restrict__ acc)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    long long nt = trng[b].y - trng[b].x, s = 0;
+    for (int k = 0; k < 9; ++k) {
+        int32_t q = nbr[b * 9 + k];
+        if (q >= 0) s += srng[q].y - srng[q].x;
+    }
+    atomicAdd(acc, (unsigned long long)(nt * s));
+}
+
+__global__ void k_s2l_count(const int32_t *__restrict__ tab, int64_t nbox, unsigned long long *__restrict__ acc)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    unsigned long long s = 0;
+    for (int k = 0; k < 27; ++k) s += tab[b * 27 + k] >= 0;
+    atomicAdd(acc, s);
+}
+
+static inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b > 0 ? (n + b - 1) / b : 1); }
+
+// compaction helper: distinct keys of a sorted 64-bit array (value >> 32 >> extra) -> keys
+static afmm_status uniq_keys(afmm_plan p, const unsigned long long *a, int64_t n, int extra, int64_t *f,
+                             int64_t *pos, int64_t *tmp, uint32_t **keys_out, int64_t *count)
+{
+    cudaStream_t st = p->stream;
+    k_unique_flags<<<nblk(n), 256, 0, st>>>(a, n, extra, f);
+    AFMM_LAUNCH_CHECK();
+    AFMM_TRY(scan_excl(f, pos, n, tmp, st));
+    int64_t c = 0;
+    AFMM_CUDA(cudaMemcpyAsync(&c, pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    AFMM_CUDA(cudaStreamSynchronize(st));
+    uint32_t *k = nullptr;
+    AFMM_TRY(dalloc_t(p, &k, c > 0 ? c : 1));
+    k_unique_scatter<<<nblk(n), 256, 0, st>>>(a, n, extra, f, pos, k);
+    AFMM_LAUNCH_CHECK();
+    *keys_out = k;
+    *count = c;
+    return AFMM_OK;
+}
+
+afmm_status build_tree(afmm_plan p, const double *src_r, const double *src_z, const double *tgt_r,
+                       const double *tgt_z)
+{
+    cudaStream_t st = p->stream;
+    const int64_t ns = p->ns, nf = p->nf;
+    // ---- validation and bounding square
+    const int mmb = 304;
+    double *part = nullptr, *mm = nullptr;
+    AFMM_TRY(dalloc_t(p, &part, mmb * 5 + 8));
+    mm = part + mmb * 5;
+    k_minmax<<<mmb, 256, 0, st>>>(src_r, src_z, ns, tgt_r, tgt_z, nf, part);
+    AFMM_LAUNCH_CHECK();
+    k_minmax_final<<<1, 32, 0, st>>>(part, mmb, mm);
+    AFMM_LAUNCH_CHECK();
+    double h_mm[5];
+    AFMM_CUDA(cudaMemcpyAsync(h_mm, mm, sizeof(h_mm), cudaMemcpyDeviceToHost, st));
+    AFMM_CUDA(cudaStreamSynchronize(st));
+    if (h_mm[4] != 0.0) return AFMM_EINVAL;
+    p->r0 = h_mm[0];
+    p->z0 = h_mm[2];
+    double L = fmax(h_mm[1] - h_mm[0], h_mm[3] - h_mm[2]);
+    if (!(L > 0.0)) L = 1.0;
+    p->L = L;
+    const double s16 = 65536.0 / L;
+
+    // ---- keys and sorts
+    int64_t nmax = ns > nf ? ns : nf;
+    int64_t npad_max = pow2_at_least(ns + nf);
+    unsigned long long *srt = nullptr;
+    AFMM_TRY(dalloc_t(p, &srt, npad_max));
+    int64_t *f = nullptr, *pos = nullptr, *tmp = nullptr;
+    // flags/scans run over points, boxes and the 2^l columns of a level (l <= 16)
+    int64_t nflag = (npad_max > 65536 ? npad_max : 65536) + 64;
+    AFMM_TRY(dalloc_t(p, &f, nflag));
+    AFMM_TRY(dalloc_t(p, &pos, nflag + 1));
+    AFMM_TRY(dalloc_t(p, &tmp, 2 * (nflag / 1024 + 64) + 256));
+    AFMM_TRY(dalloc_t(p, &p->s_r, ns));
+    AFMM_TRY(dalloc_t(p, &p->s_z, ns));
+    AFMM_TRY(dalloc_t(p, &p->s_perm, ns));
+    AFMM_TRY(dalloc_t(p, &p->s_key, ns));
+    AFMM_TRY(dalloc_t(p, &p->t_r, nf));
+    AFMM_TRY(dalloc_t(p, &p->t_z, nf));
+    AFMM_TRY(dalloc_t(p, &p->t_perm, nf));
+    AFMM_TRY(dalloc_t(p, &p->t_key, nf));
+    for (int set = 0; set < 2; ++set) {
+        int64_t n = set == 0 ? ns : nf;
+        int64_t npad = pow2_at_least(n);
+        const double *r = set == 0 ? src_r : tgt_r, *z = set == 0 ? src_z : tgt_z;
+        k_keys<<<nblk(npad), 256, 0, st>>>(r, z, n, npad, p->r0, p->z0, s16, srt);
+        AFMM_LAUNCH_CHECK();
+        AFMM_TRY(bitonic_sort(srt, npad, st));
+        if (set == 0)
+            k_gather_sorted<<<nblk(n), 256, 0, st>>>(srt, n, r, z, p->s_r, p->s_z, p->s_perm, p->s_key);
+        else
+            k_gather_sorted<<<nblk(n), 256, 0, st>>>(srt, n, r, z, p->t_r, p->t_z, p->t_perm, p->t_key);
+        AFMM_LAUNCH_CHECK();
+    }
+    // ---- depth
+    int d = p->opt.depth_override;
+    if (d <= 0) {
+        unsigned long long *cnt = nullptr;
+        AFMM_TRY(dalloc_t(p, &cnt, 17));
+        AFMM_CUDA(cudaMemsetAsync(cnt, 0, 17 * sizeof(unsigned long long), st));
+        k_depth_counts<<<nblk(ns), 256, 0, st>>>(p->s_key, ns, cnt);
+        AFMM_LAUNCH_CHECK();
+        unsigned long long hc[17];
+        AFMM_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
+        AFMM_CUDA(cudaStreamSynchronize(st));
+        d = -1;
+        for (int l = 2; l <= 16; ++l)
+            if (hc[l] > 0 && (double)ns <= (double)p->opt.leaf_size * (double)hc[l]) {
+                d = l;
+                break;
+            }
+        if (d < 0) d = 16;
+    }
+    if (d < 2 || d > AFMM_MAX_LEVEL) return AFMM_EUNSUPPORTED;
+    p->d = d;
+
+    // ---- boxes per level: union of leaf keys, then parents
+    {
+        int64_t npad = pow2_at_least(ns + nf);
+        k_leaf_union<<<nblk(npad), 256, 0, st>>>(p->s_key, ns, p->t_key, nf, 2 * (16 - d), npad, srt);
+        AFMM_LAUNCH_CHECK();
+        AFMM_TRY(bitonic_sort(srt, npad, st));
+        AFMM_TRY(uniq_keys(p, srt, ns + nf, 0, f, pos, tmp, &p->lv[d].key, &p->lv[d].nbox));
+        for (int l = d - 1; l >= 2; --l) {
+            int64_t nc = p->lv[l + 1].nbox;
+            k_parent_keys<<<nblk(nc), 256, 0, st>>>(p->lv[l + 1].key, nc, srt);
+            AFMM_LAUNCH_CHECK();
+            AFMM_TRY(uniq_keys(p, srt, nc, 0, f, pos, tmp, &p->lv[l].key, &p->lv[l].nbox));
+        }
+    }
+    // ---- per-level tables
+    for (int l = 2; l <= d; ++l) {
+        Level &v = p->lv[l];
+        int64_t nb = v.nbox;
+        if (nb >= (1 << 24)) return AFMM_EUNSUPPORTED;  // S2L unit keys hold 24-bit box indices
+        AFMM_TRY(dalloc_t(p, &v.srng, nb));
+        AFMM_TRY(dalloc_t(p, &v.trng, nb));
+        k_box_ranges<<<nblk(nb), 256, 0, st>>>(v.key, nb, 2 * (16 - l), p->s_key, ns, p->t_key, nf, v.srng, v.trng);
+        AFMM_LAUNCH_CHECK();
+        if (l >= 3) {
+            AFMM_TRY(dalloc_t(p, &v.parent, nb));
+            k_parents<<<nblk(nb), 256, 0, st>>>(v.key, nb, p->lv[l - 1].key, p->lv[l - 1].nbox, v.parent);
+            AFMM_LAUNCH_CHECK();
+            AFMM_TRY(dalloc_t(p, &p->lv[l - 1].child, p->lv[l - 1].nbox));
+            k_child_ranges<<<nblk(nb), 256, 0, st>>>(v.parent, nb, p->lv[l - 1].child);
+            AFMM_LAUNCH_CHECK();
+        }
+        AFMM_TRY(dalloc_t(p, &v.s2l, nb * 27));
+        k_s2l_table<<<nblk(nb * 27), 256, 0, st>>>(v.key, nb, l, v.s2l);
+        AFMM_LAUNCH_CHECK();
+        // stations (occupied columns)
+        int ncol = 1 << l;
+        int32_t *flag = nullptr;
+        AFMM_TRY(dalloc_t(p, &flag, ncol));
+        AFMM_TRY(dalloc_t(p, &v.station_of_col, ncol));
+        AFMM_CUDA(cudaMemsetAsync(flag, 0, ncol * sizeof(int32_t), st));
+        k_station_flags<<<nblk(nb), 256, 0, st>>>(v.key, nb, flag);
+        AFMM_LAUNCH_CHECK();
+        k_i32_to_i64<<<nblk(ncol), 256, 0, st>>>(flag, ncol, f);
+        AFMM_LAUNCH_CHECK();
+        AFMM_TRY(scan_excl(f, pos, ncol, tmp, st));
+        int64_t nst = 0;
+        AFMM_CUDA(cudaMemcpyAsync(&nst, pos + ncol, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        AFMM_CUDA(cudaStreamSynchronize(st));
+        v.nstation = (int)nst;
+        AFMM_TRY(dalloc_t(p, &v.col_of_station, nst > 0 ? nst : 1));
+        k_station_map<<<nblk(ncol), 256, 0, st>>>(flag, ncol, pos, v.station_of_col, v.col_of_station);
+        AFMM_LAUNCH_CHECK();
+        // S2L units
+        int64_t npad = pow2_at_least(nb);
+        k_unit_keys<<<nblk(npad), 256, 0, st>>>(v.key, nb, npad, srt);
+        AFMM_LAUNCH_CHECK();
+        AFMM_TRY(bitonic_sort(srt, npad, st));
+        k_unit_flags<<<nblk(nb), 256, 0, st>>>(srt, nb, f);
+        AFMM_LAUNCH_CHECK();
+        AFMM_TRY(scan_excl(f, pos, nb, tmp, st));
+        int64_t nu = 0;
+        AFMM_CUDA(cudaMemcpyAsync(&nu, pos + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        AFMM_CUDA(cudaStreamSynchronize(st));
+        v.nunit = nu;
+        AFMM_TRY(dalloc_t(p, &v.unit_box, (nu > 0 ? nu : 1) * 32));
+        AFMM_TRY(dalloc_t(p, &v.unit_col, nu > 0 ? nu : 1));
+        AFMM_CUDA(cudaMemsetAsync(v.unit_box, 0xff, (nu > 0 ? nu : 1) * 32 * sizeof(int32_t), st));
+        k_unit_fill<<<nblk(nb), 256, 0, st>>>(srt, nb, pos, v.unit_box, v.unit_col);
+        AFMM_LAUNCH_CHECK();
+    }
+    // ---- leaf neighbours and near-field units for both directions
+    {
+        Level &v = p->lv[d];
+        int64_t nb = v.nbox;
+        AFMM_TRY(dalloc_t(p, &v.nbr, nb * 9));
+        k_nbr_table<<<nblk(nb * 9), 256, 0, st>>>(v.key, nb, d, v.nbr);
+        AFMM_LAUNCH_CHECK();
+        for (int dir = 0; dir < 2; ++dir) {
+            const int2 *rng = dir == 0 ? v.trng : v.srng;
+            k_near_counts<<<nblk(nb), 256, 0, st>>>(rng, nb, f);
+            AFMM_LAUNCH_CHECK();
+            AFMM_TRY(scan_excl(f, pos, nb, tmp, st));
+            int64_t nu = 0;
+            AFMM_CUDA(cudaMemcpyAsync(&nu, pos + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            AFMM_CUDA(cudaStreamSynchronize(st));
+            p->n_near_unit[dir] = nu;
+            AFMM_TRY(dalloc_t(p, &p->near_unit[dir], nu > 0 ? nu : 1));
+            k_near_fill<<<nblk(nb), 256, 0, st>>>(rng, nb, pos, p->near_unit[dir]);
+            AFMM_LAUNCH_CHECK();
+        }
+        unsigned long long *acc = nullptr;
+        AFMM_TRY(dalloc_t(p, &acc, 2));
+        AFMM_CUDA(cudaMemsetAsync(acc, 0, 2 * sizeof(unsigned long long), st));
+        k_near_pairs<<<nblk(nb), 256, 0, st>>>(v.trng, v.srng, v.nbr, nb, acc);
+        AFMM_LAUNCH_CHECK();
+        for (int l = 2; l <= d; ++l) {
+            k_s2l_count<<<nblk(p->lv[l].nbox), 256, 0, st>>>(p->lv[l].s2l, p->lv[l].nbox, acc + 1);
+            AFMM_LAUNCH_CHECK();
+        }
+        unsigned long long h[2];
+        AFMM_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
+        AFMM_CUDA(cudaStreamSynchronize(st));
+        p->near_pairs = (int64_t)h[0];
+        p->s2l_pairs = (int64_t)h[1];
+    }
+    p->n_max = nmax;
+    return AFMM_OK;
+}
+
+}  // namespace afmm
