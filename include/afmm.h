@@ -57,7 +57,9 @@ typedef struct {
     int depth_override; /* 0: use the leaf_size rule; 2..16: use this depth */
     int precision;      /* afmm_precision */
     double fwd_switch;  /* Legendre recursion: forward iff 2 N acosh(chi) <= fwd_switch
-                           (0: default 9).  The paper's fixed switch is chi < 1.008. */
+                           (0: default 9 for N <= 16, 9 - 1.5 log2(N/16) above, which keeps
+                           the forward sweep's error growth below ~2e-12).  The paper's
+                           fixed switch is chi < 1.008 (Appendix A). */
     int miller_extra;   /* Miller start L = N + ceil(miller_extra / acosh(chi)) + 2 (0: 15) */
 } afmm_options;
 
@@ -164,6 +166,9 @@ const char *afmm_last_cuda_error(void);
  * names are "tree", "p2m", "m2m", "gexp", "s2l", "l2l", "near" (L2P + P2P), "perm".
  * afmm_set_timing(p, 1) enables event recording (adds event records, no sync). */
 afmm_status afmm_set_timing(afmm_plan p, int enable);
+/* Number of CUDA kernel launches this library has made in this process (all plans and
+ * unit evaluators), for accounting in benchmarks. */
+long long afmm_kernel_launches(void);
 afmm_status afmm_get_timing(afmm_plan p, const char *name, double *ms);
 
 #ifdef __cplusplus

@@ -20,7 +20,7 @@ _STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA e
 EXPORTS = ["afmm_options_default", "afmm_plan_create", "afmm_plan_destroy", "afmm_plan_info", "afmm_eval",
            "afmm_grad", "afmm_direct", "afmm_direct_grad", "afmm_adjoint", "afmm_adjoint_direct", "afmm_green",
            "afmm_green_expansion", "afmm_status_string", "afmm_last_cuda_error", "afmm_set_timing",
-           "afmm_get_timing"]
+           "afmm_get_timing", "afmm_kernel_launches"]
 
 
 class AfmmError(RuntimeError):
@@ -83,8 +83,15 @@ def load():
     lib.afmm_set_timing.restype = I
     lib.afmm_get_timing.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)]
     lib.afmm_get_timing.restype = I
+    lib.afmm_kernel_launches.argtypes = []
+    lib.afmm_kernel_launches.restype = ctypes.c_longlong
     _lib = lib
     return lib
+
+
+def kernel_launches():
+    """Kernel launches made by libafmm in this process so far."""
+    return int(load().afmm_kernel_launches())
 
 
 def last_cuda_error():

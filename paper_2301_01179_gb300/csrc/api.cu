@@ -9,6 +9,9 @@
 namespace afmm {
 
 static thread_local char g_cuda_err[256] = "no error";
+static unsigned long long g_launches = 0;
+
+void count_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
 
 void set_cuda_error(cudaError_t e)
 {
@@ -42,9 +45,18 @@ void make_rec_tab(RecTab *t)
     for (int n = 0; n < AFMM_MAX_MODES; ++n) t->c[n] = c[n];
 }
 
+// Default forward/backward switch of the Legendre recursion on 2 N acosh(chi).  A rounding
+// of size eps anywhere in the forward sweep grows to about eps N exp(2 N acosh chi) / s at
+// mode N; 9 for N <= 16, then 1.5 less per doubling of N keeps that below 2e-12.
+double default_fwd_switch(int N)
+{
+    if (N <= 16) return 9.0;
+    return 9.0 - 1.5 * log2((double)N / 16.0);
+}
+
 static void tmark(afmm_plan p, int idx)
 {
-    if (p->timing && idx < 16) cudaEventRecord(p->ev[idx], p->stream);
+    if (p->timing && idx < 80) cudaEventRecord(p->ev[idx], p->stream);
 }
 
 static float tdiff(afmm_plan p, int a, int b)
@@ -93,7 +105,7 @@ void afmm_plan_destroy(afmm_plan p)
     cudaStreamSynchronize(p->stream);
     for (int i = 0; i < p->nalloc; ++i) cudaFree(p->allocs[i]);
     if (p->timing)
-        for (int i = 0; i < 16; ++i) cudaEventDestroy(p->ev[i]);
+        for (int i = 0; i < 80; ++i) cudaEventDestroy(p->ev[i]);
     delete p->rec;
     delete p;
 }
@@ -136,7 +148,7 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
     p->ncoef = (opt.order + 1) * (opt.order + 2) / 2;
     p->precision = opt.precision;
     p->opt = opt;
-    p->pp.fwd_switch = opt.fwd_switch > 0.0 ? opt.fwd_switch : 9.0;
+    p->pp.fwd_switch = opt.fwd_switch > 0.0 ? opt.fwd_switch : default_fwd_switch(p->N);
     p->pp.miller_extra = opt.miller_extra > 0 ? (double)opt.miller_extra : 15.0;
 
     afmm_status s = build_tree(p, src_r, src_z, tgt_r, tgt_z);
@@ -206,11 +218,13 @@ afmm_status afmm_plan_info(afmm_plan p, afmm_plan_info_t *info)
     return AFMM_OK;
 }
 
+long long afmm_kernel_launches(void) { return (long long)__atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
 afmm_status afmm_set_timing(afmm_plan p, int enable)
 {
     if (!p) return AFMM_EINVAL;
     if (enable && !p->timing) {
-        for (int i = 0; i < 16; ++i) AFMM_CUDA(cudaEventCreate(&p->ev[i]));
+        for (int i = 0; i < 80; ++i) AFMM_CUDA(cudaEventCreate(&p->ev[i]));
         p->timing = 1;
     }
     return AFMM_OK;
@@ -245,6 +259,16 @@ static afmm_status run_fmm(afmm_plan p, int dir, const double *q_re, const doubl
         p->t_ms[2] = tdiff(p, 2, 3);
         p->t_ms[6] = tdiff(p, 8, 9);
         p->t_ms[7] = tdiff(p, 0, 9);
+        double g = 0, s2 = 0, l2 = 0;
+        for (int l = 2; l <= p->d; ++l) {  // per level: L2L, expansions, S2L (far_field)
+            int e = 16 + 4 * (l - 2);
+            l2 += tdiff(p, e, e + 1);
+            g += tdiff(p, e + 1, e + 2);
+            s2 += tdiff(p, e + 2, e + 3);
+        }
+        p->t_ms[3] = g;
+        p->t_ms[4] = s2;
+        p->t_ms[5] = l2;
     }
     return AFMM_OK;
 }

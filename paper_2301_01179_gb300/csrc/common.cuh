@@ -36,7 +36,12 @@ void set_cuda_error(cudaError_t e);
         }                                                 \
     } while (0)
 
-#define AFMM_LAUNCH_CHECK() AFMM_CUDA(cudaGetLastError())
+void count_launch();
+#define AFMM_LAUNCH_CHECK()          \
+    do {                             \
+        ::afmm::count_launch();      \
+        AFMM_CUDA(cudaGetLastError()); \
+    } while (0)
 
 #define AFMM_TRY(expr)                                    \
     do {                                                  \
@@ -59,6 +64,7 @@ struct RecTab {
     double c[AFMM_MAX_MODES];  // c[n], n <= 128
 };
 void make_rec_tab(RecTab *t);
+double default_fwd_switch(int N);
 
 struct PairParams {
     double fwd_switch;   // forward iff 2 N acosh(chi) <= fwd_switch (and acosh(chi) <= 0.96)
@@ -151,10 +157,9 @@ struct afmm_plan_s {
     int64_t n_max = 0;
     // statistics
     int64_t near_pairs = 0, s2l_pairs = 0, expansions = 0;
-    // timing
+    // timing (events on the plan's stream; read back after the evaluation's last event)
     int timing = 0;
-    cudaEvent_t ev[16];
-    int nev = 0;
+    cudaEvent_t ev[80];
     double t_ms[8] = {0};
     // device allocations to free
     void *allocs[512];

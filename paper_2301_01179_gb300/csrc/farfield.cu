@@ -489,7 +489,7 @@ afmm_status launch_green_expansion(int64_t npts, const double *r, const double *
     RecTab tab;
     make_rec_tab(&tab);
     PairParams pp;
-    pp.fwd_switch = 9.0;
+    pp.fwd_switch = default_fwd_switch(n_modes - 1);
     pp.miller_extra = 15.0;
     size_t per = (size_t)n_modes * (P + 1) * (P + 1) * (P + 1);
     AFMM_CUDA(cudaMemsetAsync(out, 0, per * npts * sizeof(double), st));
@@ -676,7 +676,7 @@ static afmm_status launch_s2l(afmm_plan p, int l, const double *mre, const doubl
 
 static void tmark(afmm_plan p, int idx)
 {
-    if (p->timing && idx < 16) cudaEventRecord(p->ev[idx], p->stream);
+    if (p->timing && idx < 80) cudaEventRecord(p->ev[idx], p->stream);
 }
 
 // Far field for direction dir (0: sources -> field points, 1: transposed).  Uses the
@@ -711,16 +711,16 @@ afmm_status far_field(afmm_plan p, int dir)
     // downward pass
     size_t gsm = gbar_smem(p->N, 2 * M);
     AFMM_CUDA(cudaFuncSetAttribute(k_gexp_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
-    float t_gexp = 0, t_s2l = 0, t_l2l = 0;
     for (int l = 2; l <= d; ++l) {
         Level &v = p->lv[l];
+        const int e = 16 + 4 * (l - 2);  // event slots: L2L, expansions, S2L, end
         size_t sm = sizeof(double) * (2 * (size_t)nc + 4 * (size_t)(M + 1) * (M + 1));
-        tmark(p, 4);
+        tmark(p, e);
         k_l2l<<<(unsigned)v.nbox, 128, sm, st>>>(l >= 3 ? v.parent : nullptr, v.key, v.nbox, nm, M, p->l2l_tab,
                                                  l >= 3 ? p->lv[l - 1].loc_re : nullptr,
                                                  l >= 3 ? p->lv[l - 1].loc_im : nullptr, v.loc_re, v.loc_im);
         AFMM_LAUNCH_CHECK();
-        tmark(p, 5);
+        tmark(p, e + 1);
         double h = p->L / (double)(1 << l);
         if (v.nstation > 0) {
             k_gexp_level<<<(unsigned)(v.nstation * 16), 128, gsm, st>>>(v.col_of_station, v.station_of_col, v.nstation,
@@ -728,24 +728,9 @@ afmm_status far_field(afmm_plan p, int dir)
                                                                         p->gexp);
             AFMM_LAUNCH_CHECK();
         }
-        tmark(p, 6);
+        tmark(p, e + 2);
         AFMM_TRY(launch_s2l(p, l, v.mom_re, v.mom_im, v.loc_re, v.loc_im));
-        tmark(p, 7);
-        if (p->timing) {
-            float a = 0, b = 0, c = 0;
-            cudaEventSynchronize(p->ev[7]);
-            cudaEventElapsedTime(&a, p->ev[4], p->ev[5]);
-            cudaEventElapsedTime(&b, p->ev[5], p->ev[6]);
-            cudaEventElapsedTime(&c, p->ev[6], p->ev[7]);
-            t_l2l += a;
-            t_gexp += b;
-            t_s2l += c;
-        }
-    }
-    if (p->timing) {
-        p->t_ms[3] = t_gexp;
-        p->t_ms[4] = t_s2l;
-        p->t_ms[5] = t_l2l;
+        tmark(p, e + 3);
     }
     return AFMM_OK;
 }

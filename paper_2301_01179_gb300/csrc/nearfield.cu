@@ -415,7 +415,7 @@ afmm_status launch_green(int64_t npairs, const double *r, const double *r1, cons
     RecTab tab;
     make_rec_tab(&tab);
     PairParams pp;
-    pp.fwd_switch = 9.0;
+    pp.fwd_switch = default_fwd_switch(n_modes - 1);
     pp.miller_extra = 15.0;
     const int B = 64;
     size_t sm = sizeof(double) * ((size_t)AFMM_REC_TAB + (size_t)(n_modes < 2 ? 2 : n_modes) * B);

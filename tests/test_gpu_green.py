@@ -40,7 +40,9 @@ def test_green_matches_oracle(N):
         g, gr, gx = oracle.green_grad(a, b, c, N)
         scale = abs(g[0]) + 1e-300
         for n in range(N + 1):
-            tol = 1e-12 * abs(g[n]) + 1e-15 * scale
+            # forward recursion is used while its error growth exp(2 N acosh chi) <= e^9:
+            # about 1e-12 relative on the highest modes
+            tol = 1e-11 * abs(g[n]) + 1e-15 * scale
             assert abs(G[n, p] - g[n]) <= tol, (p, n, G[n, p], g[n])
             dist = math.hypot(a - b, c) + 1e-300
             gscale = scale / min(a, dist)
@@ -60,4 +62,4 @@ def test_green_expansion_matches_oracle():
         i, j, k = np.meshgrid(np.arange(P + 1), np.arange(P + 1), np.arange(P + 1), indexing="ij")
         sc = np.abs(g[:, 0, 0, 0]).max() * dist ** (-(i + j + k)).astype(float)
         err = np.abs(E[p] - g) / sc[None]
-        assert err.max() < 1e-12, (p, err.max(), np.unravel_index(err.argmax(), err.shape))
+        assert err.max() < 1e-11, (p, err.max(), np.unravel_index(err.argmax(), err.shape))
