@@ -156,6 +156,32 @@ afmm_status afmm_green(int64_t npairs, const double *r, const double *r1, const 
 afmm_status afmm_green_expansion(int64_t npts, const double *r, const double *r1, const double *x,
                                  int n_modes, int P, double *out, void *stream);
 
+/* afmm_direct_static: the direct sum of afmm_direct for callers that cannot allocate
+ * device memory.  The paper has no counterpart; this entry point exists because some
+ * callers may not call cudaMalloc: services that must keep a fixed device-memory
+ * footprint after start-up, code running while another framework's caching allocator has
+ * reserved nearly all device memory, and code that must avoid the device synchronisation
+ * cudaMalloc/cudaFree can imply.
+ *  - No plan, no allocation: the caller passes sources (src_r, src_z)[ns], field points
+ *    (tgt_r, tgt_z)[nf], amplitudes q [n_modes][ns] and outputs phi [n_modes][nf] (device
+ *    pointers, caller's order, same layouts as afmm_direct); the result equals
+ *    afmm_direct's to rounding.
+ *  - Scratch comes from one file-scope device array of AFMM_STATIC_SCRATCH_DOUBLES doubles
+ *    (16 MiB) that every GPU loading this library holds until the process exits.  Requests
+ *    with 2 * n_modes * ns > AFMM_STATIC_SCRATCH_DOUBLES return AFMM_EINVAL.
+ *  - The first call on a device looks the array's device address up (cudaGetSymbolAddress,
+ *    with that device current); make that first call before any stream capture.
+ *  - Every call shares the array and leaves its contents behind; nothing is read before
+ *    this call writes it.  Calls whose work overlaps on the GPU (other streams, other host
+ *    threads) race on the array: serialise them.
+ *  - Coordinates are not validated (radii must be finite and > 0).  Work is enqueued on
+ *    `stream`. */
+#define AFMM_STATIC_SCRATCH_DOUBLES 2097152
+afmm_status afmm_direct_static(int64_t ns, const double *src_r, const double *src_z, int64_t nf,
+                               const double *tgt_r, const double *tgt_z, int n_modes,
+                               const double *q_re, const double *q_im, double *phi_re,
+                               double *phi_im, void *stream);
+
 /* Human-readable status; afmm_last_cuda_error: the last CUDA error string seen by this
  * thread's calls (static storage; "no error" if none). */
 const char *afmm_status_string(afmm_status s);

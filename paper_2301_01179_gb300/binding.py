@@ -20,7 +20,7 @@ _STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA e
 EXPORTS = ["afmm_options_default", "afmm_plan_create", "afmm_plan_destroy", "afmm_plan_info", "afmm_eval",
            "afmm_grad", "afmm_direct", "afmm_direct_grad", "afmm_adjoint", "afmm_adjoint_direct", "afmm_green",
            "afmm_green_expansion", "afmm_status_string", "afmm_last_cuda_error", "afmm_set_timing",
-           "afmm_get_timing", "afmm_kernel_launches"]
+           "afmm_get_timing", "afmm_kernel_launches", "afmm_direct_static"]
 
 
 class AfmmError(RuntimeError):
@@ -83,6 +83,8 @@ def load():
     lib.afmm_set_timing.restype = I
     lib.afmm_get_timing.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double)]
     lib.afmm_get_timing.restype = I
+    lib.afmm_direct_static.argtypes = [I64, P, P, I64, P, P, I, P, P, P, P, P]
+    lib.afmm_direct_static.restype = I
     lib.afmm_kernel_launches.argtypes = []
     lib.afmm_kernel_launches.restype = ctypes.c_longlong
     _lib = lib
@@ -246,3 +248,16 @@ def green_expansion(r, r1, x, n_modes, P):
     _check(lib.afmm_green_expansion(n, _ptr(r), _ptr(r1), _ptr(x), int(n_modes), int(P), _ptr(out), _stream()),
            "afmm_green_expansion")
     return out
+
+
+def direct_static(src_r, src_z, tgt_r, tgt_z, q_re, q_im):
+    """All-pairs potentials without any device allocation inside the library
+    (afmm_direct_static): scratch comes from the library's fixed device array."""
+    lib = load()
+    ns, nf = int(src_r.numel()), int(tgt_r.numel())
+    nm = int(q_re.shape[0])
+    o_re = _empty(nm, nf, like=src_r)
+    o_im = _empty(nm, nf, like=src_r)
+    _check(lib.afmm_direct_static(ns, _ptr(src_r), _ptr(src_z), nf, _ptr(tgt_r), _ptr(tgt_z), nm, _ptr(q_re),
+                                  _ptr(q_im), _ptr(o_re), _ptr(o_im), _stream()), "afmm_direct_static")
+    return o_re, o_im

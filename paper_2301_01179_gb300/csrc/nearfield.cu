@@ -10,6 +10,7 @@
 // ([mode][lane] planes, conflict-free); on GB300 the FP64 pipe, not shared memory, bounds
 // the kernel (FP64 issues at 1/64 of FP32).
 #include <cstring>
+#include <mutex>
 #include "common.cuh"
 #include "pair.cuh"
 
@@ -426,3 +427,123 @@ afmm_status launch_green(int64_t npairs, const double *r, const double *r1, cons
 }
 
 }  // namespace afmm
+
+namespace afmm {
+
+// ------------------------------------------------------------------------------------
+// afmm_direct_static: the all-pairs direct sum without any device allocation.
+//
+// Some callers cannot call cudaMalloc: a service that must keep a fixed device-memory
+// footprint after start-up, code that runs while another framework's caching allocator
+// has reserved almost all device memory, and code that must not risk the implicit device
+// synchronisation cudaMalloc/cudaFree can cause.  For them the direct sum takes its
+// scratch (the strengths scaled by the recursion constants, and the per-split partial
+// sums when the field set is small) from one file-scope device array of fixed size.
+// Every GPU that loads this library holds that array until the process exits.
+// ------------------------------------------------------------------------------------
+static __device__ __align__(256) double g_static_scratch[AFMM_STATIC_SCRATCH_DOUBLES];
+
+static double *g_static_addr[64];
+static bool g_static_ready[64];
+static std::mutex g_static_mu;
+
+// Host code may not take the address of g_static_scratch directly (it names a host-side
+// stand-in); the device address comes from cudaGetSymbolAddress, once per device, with
+// that device current.
+static afmm_status static_scratch(double **out)
+{
+    int dev = 0;
+    AFMM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return AFMM_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ready[dev]) {
+        void *ptr = nullptr;
+        AFMM_CUDA(cudaGetSymbolAddress(&ptr, g_static_scratch));
+        g_static_addr[dev] = (double *)ptr;
+        g_static_ready[dev] = true;
+    }
+    *out = g_static_addr[dev];
+    return AFMM_OK;
+}
+
+// qs[n][i] = q[n][i] * c_n (caller order, no permutation)
+__global__ void k_scale_strengths(const double *__restrict__ q_re, const double *__restrict__ q_im, int64_t n, int nm,
+                                  const RecTab tab, double *__restrict__ qs_re, double *__restrict__ qs_im)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n * nm) return;
+    double c = tab.c[i / n];
+    qs_re[i] = q_re[i] * c;
+    qs_im[i] = q_im[i] * c;
+}
+
+}  // namespace afmm
+
+extern "C" afmm_status afmm_direct_static(int64_t ns, const double *src_r, const double *src_z, int64_t nf,
+                                          const double *tgt_r, const double *tgt_z, int n_modes, const double *q_re,
+                                          const double *q_im, double *phi_re, double *phi_im, void *stream)
+{
+    using namespace afmm;
+    if (ns < 1 || nf < 1 || n_modes < 1 || n_modes > AFMM_MAX_MODES) return AFMM_EINVAL;
+    if (!src_r || !src_z || !tgt_r || !tgt_z || !q_re || !q_im || !phi_re || !phi_im) return AFMM_EINVAL;
+    const int64_t need = 2 * (int64_t)n_modes * ns;  // scaled strengths
+    if (need > AFMM_STATIC_SCRATCH_DOUBLES) return AFMM_EINVAL;
+    double *scr = nullptr;
+    AFMM_TRY(static_scratch(&scr));
+    cudaStream_t st = (cudaStream_t)stream;
+    RecTab tab;
+    make_rec_tab(&tab);
+    double *qs_re = scr, *qs_im = scr + (size_t)n_modes * ns;
+    k_scale_strengths<<<nblk(ns * n_modes), 256, 0, st>>>(q_re, q_im, ns, n_modes, tab, qs_re, qs_im);
+    AFMM_LAUNCH_CHECK();
+
+    NearArgs a;
+    memset(&a, 0, sizeof(a));
+    a.fr = tgt_r;
+    a.fz = tgt_z;
+    a.nfield = nf;
+    a.sr = src_r;
+    a.sz = src_z;
+    a.nsrc = ns;
+    a.q_re = qs_re;
+    a.q_im = qs_im;
+    a.nmodes = n_modes;
+    a.N = n_modes - 1;
+    a.pp.fwd_switch = default_fwd_switch(n_modes - 1);
+    a.pp.miller_extra = 15.0;
+    a.out_perm = nullptr;
+    a.o_re = phi_re;
+    a.o_im = phi_im;
+    // split the sources when the field set is too small to fill the GPU, as far as the
+    // rest of the array holds the partial sums (every partial is written, none is read
+    // before it is written, so nothing has to start at zero)
+    int64_t tunits = (nf + 31) / 32, want = 152 * 8;
+    int64_t room = (AFMM_STATIC_SCRATCH_DOUBLES - need) / (2 * (int64_t)n_modes * nf);
+    int64_t nsplit = 1;
+    if (tunits < want) {
+        nsplit = (want + tunits - 1) / tunits;
+        int64_t maxs = (ns + 63) / 64;
+        if (nsplit > maxs) nsplit = maxs;
+        if (nsplit > room) nsplit = room;
+        if (nsplit < 1) nsplit = 1;
+    }
+    a.direct = 1;
+    a.nsplit = (int)nsplit;
+    a.split_len = (ns + nsplit - 1) / nsplit;
+    a.nunits = tunits * nsplit;
+    a.part = nsplit > 1 ? scr + need : nullptr;
+    int w = near_warps(n_modes, 0);
+    if (w == 0) return AFMM_EUNSUPPORTED;
+    size_t sm = near_smem(n_modes, 0, w);
+    AFMM_CUDA(cudaFuncSetAttribute(k_near<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_near<false><<<(unsigned)((a.nunits + w - 1) / w), w * 32, sm, st>>>(a, tab);
+    AFMM_LAUNCH_CHECK();
+    if (a.part) {
+        int64_t tot = (int64_t)2 * n_modes * nf;
+        k_split_reduce<<<nblk(tot), 256, 0, st>>>(a.part, a.nsplit, 2, n_modes, nf, nullptr, phi_re, phi_im, nullptr,
+                                                  nullptr, nullptr, nullptr);
+        AFMM_LAUNCH_CHECK();
+    }
+    return AFMM_OK;
+}
+
