@@ -114,6 +114,13 @@ def max_over_ranks(ws, v, device):
     return float(t.item())
 
 
+def aggregate(ws, units_per_rank_step, t_ms_local, device):
+    """Whole-job throughput: each rank processes its own replica of the workload; the job's
+    step time is the slowest rank's.  Returns (value, ms_per_step)."""
+    t = max_over_ranks(ws, t_ms_local, device)
+    return ws * units_per_rank_step / (t / 1e3), t
+
+
 def cpu_baseline(w, budget_s=15.0):
     """The oracle (CPU FP64 direct sum, OpenMP on all host cores) on a bounded sample of
     field points against all sources; rate in modal interactions/s."""
@@ -142,7 +149,7 @@ def run_reference(args):
         return 0
     from paper_2301_01179_gb300 import workloads as W
     import oracle
-    w = W.make(WORKLOAD)
+    w = W.make(WORKLOAD, ns=args.ns, nf=args.nf)
     nf = w["tgt_r"].size
     # size one step to about 5 s of CPU work
     idx = W.subset(nf, 4, seed=7)
@@ -231,9 +238,7 @@ def run_ours(args):
     barrier(ws)
     launches = binding.kernel_launches() - l0
     clocks = clk.stop()
-    t_ms = e0.elapsed_time(e1) / args.steps
-    t_ms = max_over_ranks(ws, t_ms, dev)
-    value = ws * units_per_step / (t_ms / 1e3)
+    value, t_ms = aggregate(ws, units_per_step, e0.elapsed_time(e1) / args.steps, dev)
 
     # ---- roofline of the dominant kernel (S2L: plain FP64 FMA contraction)
     nc = (M + 1) * (M + 2) // 2

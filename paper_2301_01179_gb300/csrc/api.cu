@@ -129,7 +129,6 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
         return AFMM_EINVAL;
     if (opt.precision != AFMM_FP64 && opt.precision != AFMM_MIXED) return AFMM_EINVAL;
     if (opt.order > AFMM_MAX_ORDER) return AFMM_EUNSUPPORTED;
-    if (opt.precision == AFMM_MIXED) return AFMM_EUNSUPPORTED;
 
     afmm_plan p = new (std::nothrow) afmm_plan_s();
     if (!p) return AFMM_ENOMEM;
@@ -156,17 +155,27 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
     // evaluation scratch: nothing is allocated by the evaluation calls
     const int nm = p->nmodes, nc = p->ncoef;
     const int64_t nmax = p->n_max;
-    if (s == AFMM_OK) s = dalloc_t(p, &p->qs_re, (size_t)nm * nmax);
-    if (s == AFMM_OK) s = dalloc_t(p, &p->qs_im, (size_t)nm * nmax);
+    const bool mix = p->precision == AFMM_MIXED;
+    if (s == AFMM_OK && !mix) s = dalloc_t(p, &p->qs_re, (size_t)nm * nmax);
+    if (s == AFMM_OK && !mix) s = dalloc_t(p, &p->qs_im, (size_t)nm * nmax);
+    if (s == AFMM_OK && mix) s = dalloc_t(p, &p->qs32_re, (size_t)nm * nmax);
+    if (s == AFMM_OK && mix) s = dalloc_t(p, &p->qs32_im, (size_t)nm * nmax);
     if (s == AFMM_OK) s = dalloc_t(p, &p->acc_buf, (size_t)6 * nm * p->ns);
     int64_t gcap = 0, nexp = 0;
     for (int l = 2; s == AFMM_OK && l <= p->d; ++l) {
         Level &v = p->lv[l];
         size_t per = (size_t)v.nbox * nm * nc;
-        s = dalloc_t(p, &v.mom_re, per);
-        if (s == AFMM_OK) s = dalloc_t(p, &v.mom_im, per);
-        if (s == AFMM_OK) s = dalloc_t(p, &v.loc_re, per);
-        if (s == AFMM_OK) s = dalloc_t(p, &v.loc_im, per);
+        if (mix) {
+            s = dalloc_t(p, &v.mom32_re, per);
+            if (s == AFMM_OK) s = dalloc_t(p, &v.mom32_im, per);
+            if (s == AFMM_OK) s = dalloc_t(p, &v.loc32_re, per);
+            if (s == AFMM_OK) s = dalloc_t(p, &v.loc32_im, per);
+        } else {
+            s = dalloc_t(p, &v.mom_re, per);
+            if (s == AFMM_OK) s = dalloc_t(p, &v.mom_im, per);
+            if (s == AFMM_OK) s = dalloc_t(p, &v.loc_re, per);
+            if (s == AFMM_OK) s = dalloc_t(p, &v.loc_im, per);
+        }
         int64_t g = (int64_t)v.nstation * 16 * nm * (p->M + 1) * (p->M + 1) * (2 * p->M + 1);
         if (g > gcap) gcap = g;
         nexp += (int64_t)v.nstation * 12;

@@ -117,7 +117,8 @@ struct Level {
     int32_t *col_of_station = nullptr;  // [nstation]
     double *mom_re = nullptr, *mom_im = nullptr;  // [nbox][nmodes][ncoef]
     double *loc_re = nullptr, *loc_im = nullptr;  // [nbox][nmodes][ncoef]
-    float *mom32 = nullptr, *loc32 = nullptr;     // MIXED: [nbox][nmodes][2][ncoef]
+    float *mom32_re = nullptr, *mom32_im = nullptr;  // MIXED: [nbox][nmodes][ncoef]
+    float *loc32_re = nullptr, *loc32_im = nullptr;
 };
 
 struct NearUnit {       // one warp of near-field work: up to 32 field points of one leaf
@@ -147,6 +148,7 @@ struct afmm_plan_s {
     afmm::NearUnit *dir_unit[2] = {nullptr, nullptr};
     // eval scratch
     double *qs_re = nullptr, *qs_im = nullptr;  // [nmodes][max(ns,nf)] strengths, sorted, * c_n
+    float *qs32_re = nullptr, *qs32_im = nullptr;  // MIXED: the same in FP32
     double *gexp = nullptr;                     // expansions of one level
     int64_t gexp_cap = 0;                       // doubles
     double *m2m_tab = nullptr;                  // [4][2][(M+1)^2] shift tables (see farfield.cu)

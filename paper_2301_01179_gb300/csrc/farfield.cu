@@ -70,24 +70,26 @@ afmm_status make_shift_tables(afmm_plan p)
 // ------------------------------------------------------------------------------------
 // P2M: hat moments of every leaf box (zero for boxes without source-role points)
 // ------------------------------------------------------------------------------------
+template <typename T>
 __global__ void k_p2m(const uint32_t *__restrict__ key, const int2 *__restrict__ rng, int64_t nbox,
-                      const double *__restrict__ sr, const double *__restrict__ sz, const double *__restrict__ q_re,
-                      const double *__restrict__ q_im, int64_t nsrc, int nm, int M, double r0, double z0, double h,
-                      const RecTab tab, double *__restrict__ mom_re, double *__restrict__ mom_im)
+                      const double *__restrict__ sr, const double *__restrict__ sz, const T *__restrict__ q_re,
+                      const T *__restrict__ q_im, int64_t nsrc, int nm, int M, double r0, double z0, double h,
+                      const RecTab tab, T *__restrict__ mom_re, T *__restrict__ mom_im)
 {
-    extern __shared__ double sm[];
+    extern __shared__ double sm_raw[];
+    T *sm = reinterpret_cast<T *>(sm_raw);
     const int nc = (M + 1) * (M + 2) / 2;
-    double *mono = sm;                       // [32][nc]
-    double *acc = mono + 32 * nc;            // [2][nm][nc]
-    double *invf = acc + 2 * (size_t)nm * nc;  // [M+1] 1/j!
+    T *mono = sm;                        // [32][nc]
+    T *acc = mono + 32 * nc;             // [2][nm][nc]
+    T *invf = acc + 2 * (size_t)nm * nc;  // [M+1] 1/j!
     int64_t b = blockIdx.x;
     if (b >= nbox) return;
-    for (int i = threadIdx.x; i < 2 * nm * nc; i += blockDim.x) acc[i] = 0.0;
+    for (int i = threadIdx.x; i < 2 * nm * nc; i += blockDim.x) acc[i] = (T)0;
     if (threadIdx.x == 0) {
         double f = 1.0;
         for (int j = 0; j <= M; ++j) {
             if (j > 0) f *= j;
-            invf[j] = 1.0 / f;
+            invf[j] = (T)(1.0 / f);
         }
     }
     uint32_t k = key[b];
@@ -98,10 +100,10 @@ __global__ void k_p2m(const uint32_t *__restrict__ key, const int2 *__restrict__
         int cnt = min(32, R.y - s0);
         // monomials U^i W^j / j! of the chunk's points
         for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-            double U = (sr[s0 + t] - cr) / h, Wv = -(sz[s0 + t] - cz) / h;
-            double ui = 1.0;
+            T U = (T)((sr[s0 + t] - cr) / h), Wv = (T)(-(sz[s0 + t] - cz) / h);
+            T ui = (T)1;
             for (int i = 0; i <= M; ++i) {
-                double wj = ui;
+                T wj = ui;
                 for (int j = 0; i + j <= M; ++j) {
                     mono[t * nc + cix(i, j, M)] = wj * invf[j];
                     wj *= Wv;
@@ -112,9 +114,9 @@ __global__ void k_p2m(const uint32_t *__restrict__ key, const int2 *__restrict__
         __syncthreads();
         for (int o = threadIdx.x; o < nm * nc; o += blockDim.x) {
             int n = o / nc, c = o % nc;
-            double ar = acc[o], ai = acc[nm * nc + o];
+            T ar = acc[o], ai = acc[nm * nc + o];
             for (int t = 0; t < cnt; ++t) {
-                double m = mono[t * nc + c];
+                T m = mono[t * nc + c];
                 ar = fma(q_re[(size_t)n * nsrc + s0 + t], m, ar);
                 ai = fma(q_im[(size_t)n * nsrc + s0 + t], m, ai);
             }
@@ -126,7 +128,7 @@ __global__ void k_p2m(const uint32_t *__restrict__ key, const int2 *__restrict__
     // amplitudes carry the recursion constant c_n: divide it out
     for (int o = threadIdx.x; o < nm * nc; o += blockDim.x) {
         int n = o / nc;
-        double ic = 1.0 / tab.c[n];
+        T ic = (T)(1.0 / tab.c[n]);
         mom_re[(size_t)b * nm * nc + o] = acc[o] * ic;
         mom_im[(size_t)b * nm * nc + o] = acc[nm * nc + o] * ic;
     }
@@ -135,34 +137,36 @@ __global__ void k_p2m(const uint32_t *__restrict__ key, const int2 *__restrict__
 // ------------------------------------------------------------------------------------
 // M2M: parent hat moments from the children (separable radial then axial shift)
 // ------------------------------------------------------------------------------------
+template <typename R>
 __global__ void k_m2m(const int2 *__restrict__ child, const uint32_t *__restrict__ ckey, int64_t npar, int nm, int M,
-                      const double *__restrict__ tab, const double *__restrict__ cre, const double *__restrict__ cim,
-                      double *__restrict__ pre, double *__restrict__ pim)
+                      const double *__restrict__ tab, const R *__restrict__ cre, const R *__restrict__ cim,
+                      R *__restrict__ pre, R *__restrict__ pim)
 {
-    extern __shared__ double sm[];
+    extern __shared__ double sm_raw[];
+    R *sm = reinterpret_cast<R *>(sm_raw);
     const int nc = (M + 1) * (M + 2) / 2, W = M + 1;
-    double *X = sm;          // [2][nc]
-    double *T = X + 2 * nc;  // [4][W][W] tables
-    for (int i = threadIdx.x; i < 4 * W * W; i += blockDim.x) T[i] = tab[i];
+    R *X = sm;          // [2][nc]
+    R *T = X + 2 * nc;  // [4][W][W] tables
+    for (int i = threadIdx.x; i < 4 * W * W; i += blockDim.x) T[i] = (R)tab[i];
     int64_t P = blockIdx.x;
     __syncthreads();
     if (P >= npar) return;
     int2 ch = child[P];
     for (int n = 0; n < nm; ++n) {
-        double accr[2] = {0, 0}, acci[2] = {0, 0};  // outputs o = tid, tid + blockDim (nc <= 2 * blockDim)
+        R accr[2] = {0, 0}, acci[2] = {0, 0};  // outputs o = tid, tid + blockDim (nc <= 2 * blockDim)
         for (int c = ch.x; c < ch.y; ++c) {
             uint32_t k = ckey[c];
             int br = morton_ir(k) & 1, bz = morton_iz(k) & 1;
-            const double *Ar = T + (0 * 2 + br) * W * W, *Bz = T + (1 * 2 + bz) * W * W;
-            const double *sr_ = cre + ((size_t)c * nm + n) * nc, *si_ = cim + ((size_t)c * nm + n) * nc;
+            const R *Ar = T + (0 * 2 + br) * W * W, *Bz = T + (1 * 2 + bz) * W * W;
+            const R *sr_ = cre + ((size_t)c * nm + n) * nc, *si_ = cim + ((size_t)c * nm + n) * nc;
             // X_{i,j} = sum_q Ar[i][q] S_{i-q, j}
             for (int o = threadIdx.x; o < nc; o += blockDim.x) {
                 int i = 0, rem = o;
                 while (rem >= M + 1 - i) { rem -= M + 1 - i; ++i; }
                 int j = rem;
-                double xr = 0, xi = 0;
+                R xr = 0, xi = 0;
                 for (int q = 0; q <= i; ++q) {
-                    double a = Ar[i * W + q];
+                    R a = Ar[i * W + q];
                     int s = cix(i - q, j, M);
                     xr = fma(a, sr_[s], xr);
                     xi = fma(a, si_[s], xi);
@@ -178,7 +182,7 @@ __global__ void k_m2m(const int2 *__restrict__ child, const uint32_t *__restrict
                 while (rem >= M + 1 - i) { rem -= M + 1 - i; ++i; }
                 int j = rem;
                 for (int v = 0; v <= j; ++v) {
-                    double bcoef = Bz[j * W + v];
+                    R bcoef = Bz[j * W + v];
                     int s = cix(i, j - v, M);
                     accr[h] = fma(bcoef, X[s], accr[h]);
                     acci[h] = fma(bcoef, X[nc + s], acci[h]);
@@ -198,37 +202,39 @@ __global__ void k_m2m(const int2 *__restrict__ child, const uint32_t *__restrict
 // ------------------------------------------------------------------------------------
 // L2L: child locals from the parent (overwrites; level-2 locals start at zero)
 // ------------------------------------------------------------------------------------
+template <typename R>
 __global__ void k_l2l(const int32_t *__restrict__ parent, const uint32_t *__restrict__ key, int64_t nbox, int nm, int M,
-                      const double *__restrict__ tab, const double *__restrict__ fre_p, const double *__restrict__ fim_p,
-                      double *__restrict__ fre, double *__restrict__ fim)
+                      const double *__restrict__ tab, const R *__restrict__ fre_p, const R *__restrict__ fim_p,
+                      R *__restrict__ fre, R *__restrict__ fim)
 {
-    extern __shared__ double sm[];
+    extern __shared__ double sm_raw[];
+    R *sm = reinterpret_cast<R *>(sm_raw);
     const int nc = (M + 1) * (M + 2) / 2, W = M + 1;
-    double *Y = sm;          // [2][nc]
-    double *T = Y + 2 * nc;  // [4][W][W]
-    for (int i = threadIdx.x; i < 4 * W * W; i += blockDim.x) T[i] = tab[i];
+    R *Y = sm;          // [2][nc]
+    R *T = Y + 2 * nc;  // [4][W][W]
+    for (int i = threadIdx.x; i < 4 * W * W; i += blockDim.x) T[i] = (R)tab[i];
     int64_t b = blockIdx.x;
     __syncthreads();
     if (b >= nbox) return;
     int32_t P = parent ? parent[b] : -1;
     uint32_t k = key[b];
     int br = morton_ir(k) & 1, bz = morton_iz(k) & 1;
-    const double *Lr = T + (0 * 2 + br) * W * W, *Lz = T + (1 * 2 + bz) * W * W;
+    const R *Lr = T + (0 * 2 + br) * W * W, *Lz = T + (1 * 2 + bz) * W * W;
     for (int n = 0; n < nm; ++n) {
-        double *or_ = fre + ((size_t)b * nm + n) * nc, *oi_ = fim + ((size_t)b * nm + n) * nc;
+        R *or_ = fre + ((size_t)b * nm + n) * nc, *oi_ = fim + ((size_t)b * nm + n) * nc;
         if (P < 0) {
-            for (int o = threadIdx.x; o < nc; o += blockDim.x) or_[o] = oi_[o] = 0.0;
+            for (int o = threadIdx.x; o < nc; o += blockDim.x) or_[o] = oi_[o] = (R)0;
             continue;
         }
-        const double *pr = fre_p + ((size_t)P * nm + n) * nc, *pi = fim_p + ((size_t)P * nm + n) * nc;
+        const R *pr = fre_p + ((size_t)P * nm + n) * nc, *pi = fim_p + ((size_t)P * nm + n) * nc;
         // Y_{k,m} = sum_{l >= m} Lz[m][l] F_{k,l}
         for (int o = threadIdx.x; o < nc; o += blockDim.x) {
             int kk = 0, rem = o;
             while (rem >= M + 1 - kk) { rem -= M + 1 - kk; ++kk; }
             int m = rem;
-            double yr = 0, yi = 0;
+            R yr = 0, yi = 0;
             for (int l = m; kk + l <= M; ++l) {
-                double c = Lz[m * W + l];
+                R c = Lz[m * W + l];
                 int s = cix(kk, l, M);
                 yr = fma(c, pr[s], yr);
                 yi = fma(c, pi[s], yi);
@@ -242,9 +248,9 @@ __global__ void k_l2l(const int32_t *__restrict__ parent, const uint32_t *__rest
             int i = 0, rem = o;
             while (rem >= M + 1 - i) { rem -= M + 1 - i; ++i; }
             int m = rem;
-            double fr = 0, fi = 0;
+            R fr = 0, fi = 0;
             for (int kk = i; kk + m <= M; ++kk) {
-                double c = Lr[i * W + kk];
+                R c = Lr[i * W + kk];
                 int s = cix(kk, m, M);
                 fr = fma(c, Y[s], fr);
                 fi = fma(c, Y[nc + s], fi);
@@ -523,24 +529,26 @@ __host__ __device__ inline void s2l_offset_ff(int pr, int pz, int slot, int *dr,
     *dz = 0;
 }
 
+template <typename R>
 struct S2LArgs {
     const int32_t *unit_box, *unit_col, *s2l, *station_of_col;
     int64_t nunit;
     int level, nm, M, nc;
     const double *gexp;
-    const double *mom_re, *mom_im;
-    double *loc_re, *loc_im;
+    const R *mom_re, *mom_im;
+    R *loc_re, *loc_im;
 };
 
-template <int KPT>
-__global__ void __launch_bounds__(128) k_s2l(const S2LArgs a)
+template <typename R, int KPT>
+__global__ void __launch_bounds__(128) k_s2l(const S2LArgs<R> a)
 {
-    extern __shared__ double sm[];
+    extern __shared__ double sm_raw[];
+    R *sm = reinterpret_cast<R *>(sm_raw);
     const int M = a.M, nc = a.nc, W = M + 1, C2 = 2 * M + 1;
     const int slab = W * W * C2;
-    double *S = sm;                  // [W][W][C2] oriented expansion
-    double *Ir = S + slab;           // [nc][32]
-    double *Ii = Ir + (size_t)nc * 32;
+    R *S = sm;                  // [W][W][C2] oriented expansion
+    R *Ir = S + slab;           // [nc][32]
+    R *Ii = Ir + (size_t)nc * 32;
     __shared__ int bx[32];
     __shared__ int src[32];
     __shared__ int any;
@@ -551,12 +559,12 @@ __global__ void __launch_bounds__(128) k_s2l(const S2LArgs a)
     const int ucol = a.unit_col[u];
     const int col = ucol & 0xffff, pz = (ucol >> 30) & 1, pr = col & 1;
     const int nl = 1 << a.level;
-    double accr[KPT], acci[KPT];
+    R accr[KPT], acci[KPT];
     int base[KPT];
 #pragma unroll
     for (int q = 0; q < KPT; ++q) {
-        accr[q] = 0.0;
-        acci[q] = 0.0;
+        accr[q] = (R)0;
+        acci[q] = (R)0;
         int kl = grp + 4 * q;
         int k = 0, rem = kl < nc ? kl : 0;
         while (rem >= M + 1 - k) { rem -= M + 1 - k; ++k; }
@@ -588,24 +596,24 @@ __global__ void __launch_bounds__(128) k_s2l(const S2LArgs a)
             int c = i % C2, ki = i / C2;
             int k = ki / W, ii = ki % W;
             if (k + ii + c > 2 * M) continue;
-            double v = inward ? E[((size_t)ii * W + k) * C2 + c] : E[i];
+            R v = (R)(inward ? E[((size_t)ii * W + k) * C2 + c] : E[i]);
             S[i] = (backward && (c & 1)) ? -v : v;
         }
         for (int i = threadIdx.x; i < nc * 32; i += blockDim.x) {
             int c = i / 32, m = i % 32;
             int s = src[m];
-            Ir[i] = s >= 0 ? a.mom_re[((size_t)s * a.nm + n) * nc + c] : 0.0;
-            Ii[i] = s >= 0 ? a.mom_im[((size_t)s * a.nm + n) * nc + c] : 0.0;
+            Ir[i] = s >= 0 ? a.mom_re[((size_t)s * a.nm + n) * nc + c] : (R)0;
+            Ii[i] = s >= 0 ? a.mom_im[((size_t)s * a.nm + n) * nc + c] : (R)0;
         }
         __syncthreads();
         int ij = 0;
         for (int i = 0; i <= M; ++i) {
             for (int j = 0; i + j <= M; ++j, ++ij) {
-                double xr = Ir[ij * 32 + lane], xi = Ii[ij * 32 + lane];
+                R xr = Ir[ij * 32 + lane], xi = Ii[ij * 32 + lane];
                 int off = i * C2 + j;
 #pragma unroll
                 for (int q = 0; q < KPT; ++q) {
-                    double e = S[base[q] + off];
+                    R e = S[base[q] + off];
                     accr[q] = fma(e, xr, accr[q]);
                     acci[q] = fma(e, xi, acci[q]);
                 }
@@ -623,30 +631,32 @@ __global__ void __launch_bounds__(128) k_s2l(const S2LArgs a)
             while (rem >= M + 1 - k) { rem -= M + 1 - k; ++k; }
             double f = 1.0;
             for (int t = 2; t <= rem; ++t) f *= t;
+            R invf = (R)(1.0 / f);
             size_t o = ((size_t)b * a.nm + n) * nc + kl;
-            a.loc_re[o] += accr[q] / f;
-            a.loc_im[o] += acci[q] / f;
+            a.loc_re[o] += accr[q] * invf;
+            a.loc_im[o] += acci[q] * invf;
         }
     }
 }
 
 static inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b > 0 ? (n + b - 1) / b : 1); }
 
-template <int KPT>
-static afmm_status launch_s2l_k(const S2LArgs &a, cudaStream_t st, size_t sm)
+template <typename R, int KPT>
+static afmm_status launch_s2l_k(const S2LArgs<R> &a, cudaStream_t st, size_t sm)
 {
-    AFMM_CUDA(cudaFuncSetAttribute(k_s2l<KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    AFMM_CUDA(cudaFuncSetAttribute(k_s2l<R, KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     dim3 grid((unsigned)a.nunit, (unsigned)a.nm);
-    k_s2l<KPT><<<grid, 128, sm, st>>>(a);
+    k_s2l<R, KPT><<<grid, 128, sm, st>>>(a);
     AFMM_LAUNCH_CHECK();
     return AFMM_OK;
 }
 
-static afmm_status launch_s2l(afmm_plan p, int l, const double *mre, const double *mim, double *lre, double *lim)
+template <typename R>
+static afmm_status launch_s2l(afmm_plan p, int l, const R *mre, const R *mim, R *lre, R *lim)
 {
     Level &v = p->lv[l];
     if (v.nunit == 0) return AFMM_OK;
-    S2LArgs a;
+    S2LArgs<R> a;
     a.unit_box = v.unit_box;
     a.unit_col = v.unit_col;
     a.s2l = v.s2l;
@@ -662,15 +672,15 @@ static afmm_status launch_s2l(afmm_plan p, int l, const double *mre, const doubl
     a.loc_re = lre;
     a.loc_im = lim;
     int W = p->M + 1;
-    size_t sm = sizeof(double) * ((size_t)W * W * (2 * p->M + 1) + 2 * (size_t)p->ncoef * 32);
+    size_t sm = sizeof(R) * ((size_t)W * W * (2 * p->M + 1) + 2 * (size_t)p->ncoef * 32);
     int kpt = (p->ncoef + 3) / 4;
-    if (kpt <= 4) return launch_s2l_k<4>(a, p->stream, sm);
-    if (kpt <= 8) return launch_s2l_k<8>(a, p->stream, sm);
-    if (kpt <= 12) return launch_s2l_k<12>(a, p->stream, sm);
-    if (kpt <= 16) return launch_s2l_k<16>(a, p->stream, sm);
-    if (kpt <= 24) return launch_s2l_k<24>(a, p->stream, sm);
-    if (kpt <= 32) return launch_s2l_k<32>(a, p->stream, sm);
-    if (kpt <= 40) return launch_s2l_k<40>(a, p->stream, sm);
+    if (kpt <= 4) return launch_s2l_k<R, 4>(a, p->stream, sm);
+    if (kpt <= 8) return launch_s2l_k<R, 8>(a, p->stream, sm);
+    if (kpt <= 12) return launch_s2l_k<R, 12>(a, p->stream, sm);
+    if (kpt <= 16) return launch_s2l_k<R, 16>(a, p->stream, sm);
+    if (kpt <= 24) return launch_s2l_k<R, 24>(a, p->stream, sm);
+    if (kpt <= 32) return launch_s2l_k<R, 32>(a, p->stream, sm);
+    if (kpt <= 40) return launch_s2l_k<R, 40>(a, p->stream, sm);
     return AFMM_EUNSUPPORTED;
 }
 
@@ -679,32 +689,42 @@ static void tmark(afmm_plan p, int idx)
     if (p->timing && idx < 80) cudaEventRecord(p->ev[idx], p->stream);
 }
 
-// Far field for direction dir (0: sources -> field points, 1: transposed).  Uses the
-// strengths already permuted into p->qs_*; leaves the leaf-level locals in lv[d].loc_*.
-afmm_status far_field(afmm_plan p, int dir)
+// Far field for direction dir (0: sources -> field points, 1: transposed), in the real
+// type R of the plan's precision.  Uses the strengths already permuted into p->qs_*;
+// leaves the leaf-level locals in lv[d].loc_* (or loc32_* for the mixed precision).
+template <typename R>
+static afmm_status far_field_t(afmm_plan p, int dir)
 {
+    const bool mix = sizeof(R) == sizeof(float);
     const int d = p->d, M = p->M, nm = p->nmodes, nc = p->ncoef;
     cudaStream_t st = p->stream;
     const bool fw = dir == 0;
     const double *sr = fw ? p->s_r : p->t_r, *sz = fw ? p->s_z : p->t_z;
     int64_t nsrc = fw ? p->ns : p->nf;
+    auto MR = [&](int l) { return mix ? (R *)p->lv[l].mom32_re : (R *)p->lv[l].mom_re; };
+    auto MI = [&](int l) { return mix ? (R *)p->lv[l].mom32_im : (R *)p->lv[l].mom_im; };
+    auto LR = [&](int l) { return mix ? (R *)p->lv[l].loc32_re : (R *)p->lv[l].loc_re; };
+    auto LI = [&](int l) { return mix ? (R *)p->lv[l].loc32_im : (R *)p->lv[l].loc_im; };
+    const R *q_re = mix ? (const R *)p->qs32_re : (const R *)p->qs_re;
+    const R *q_im = mix ? (const R *)p->qs32_im : (const R *)p->qs_im;
     // P2M at the leaves
     {
         Level &v = p->lv[d];
         double h = p->L / (double)(1 << d);
-        size_t sm = sizeof(double) * (32 * (size_t)nc + 2 * (size_t)nm * nc + M + 1);
-        AFMM_CUDA(cudaFuncSetAttribute(k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_p2m<<<(unsigned)v.nbox, 128, sm, st>>>(v.key, fw ? v.srng : v.trng, v.nbox, sr, sz, p->qs_re, p->qs_im,
-                                                 nsrc, nm, M, p->r0, p->z0, h, *p->rec, v.mom_re, v.mom_im);
+        size_t sm = sizeof(R) * (32 * (size_t)nc + 2 * (size_t)nm * nc + M + 1);
+        if (sm > 227 * 1024) return AFMM_EUNSUPPORTED;
+        AFMM_CUDA(cudaFuncSetAttribute(k_p2m<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_p2m<R><<<(unsigned)v.nbox, 128, sm, st>>>(v.key, fw ? v.srng : v.trng, v.nbox, sr, sz, q_re, q_im, nsrc,
+                                                    nm, M, p->r0, p->z0, h, *p->rec, MR(d), MI(d));
         AFMM_LAUNCH_CHECK();
     }
     tmark(p, 2);
     // upward pass
     for (int l = d - 1; l >= 2; --l) {
         Level &v = p->lv[l];
-        size_t sm = sizeof(double) * (2 * (size_t)nc + 4 * (size_t)(M + 1) * (M + 1));
-        k_m2m<<<(unsigned)v.nbox, 128, sm, st>>>(v.child, p->lv[l + 1].key, v.nbox, nm, M, p->m2m_tab,
-                                                 p->lv[l + 1].mom_re, p->lv[l + 1].mom_im, v.mom_re, v.mom_im);
+        size_t sm = sizeof(R) * (2 * (size_t)nc + 4 * (size_t)(M + 1) * (M + 1));
+        k_m2m<R><<<(unsigned)v.nbox, 128, sm, st>>>(v.child, p->lv[l + 1].key, v.nbox, nm, M, p->m2m_tab, MR(l + 1),
+                                                    MI(l + 1), MR(l), MI(l));
         AFMM_LAUNCH_CHECK();
     }
     tmark(p, 3);
@@ -714,11 +734,11 @@ afmm_status far_field(afmm_plan p, int dir)
     for (int l = 2; l <= d; ++l) {
         Level &v = p->lv[l];
         const int e = 16 + 4 * (l - 2);  // event slots: L2L, expansions, S2L, end
-        size_t sm = sizeof(double) * (2 * (size_t)nc + 4 * (size_t)(M + 1) * (M + 1));
+        size_t sm = sizeof(R) * (2 * (size_t)nc + 4 * (size_t)(M + 1) * (M + 1));
         tmark(p, e);
-        k_l2l<<<(unsigned)v.nbox, 128, sm, st>>>(l >= 3 ? v.parent : nullptr, v.key, v.nbox, nm, M, p->l2l_tab,
-                                                 l >= 3 ? p->lv[l - 1].loc_re : nullptr,
-                                                 l >= 3 ? p->lv[l - 1].loc_im : nullptr, v.loc_re, v.loc_im);
+        k_l2l<R><<<(unsigned)v.nbox, 128, sm, st>>>(l >= 3 ? v.parent : nullptr, v.key, v.nbox, nm, M, p->l2l_tab,
+                                                    l >= 3 ? LR(l - 1) : nullptr, l >= 3 ? LI(l - 1) : nullptr, LR(l),
+                                                    LI(l));
         AFMM_LAUNCH_CHECK();
         tmark(p, e + 1);
         double h = p->L / (double)(1 << l);
@@ -729,10 +749,16 @@ afmm_status far_field(afmm_plan p, int dir)
             AFMM_LAUNCH_CHECK();
         }
         tmark(p, e + 2);
-        AFMM_TRY(launch_s2l(p, l, v.mom_re, v.mom_im, v.loc_re, v.loc_im));
+        AFMM_TRY(launch_s2l<R>(p, l, MR(l), MI(l), LR(l), LI(l)));
         tmark(p, e + 3);
     }
     return AFMM_OK;
+}
+
+afmm_status far_field(afmm_plan p, int dir)
+{
+    if (p->precision == AFMM_MIXED) return far_field_t<float>(p, dir);
+    return far_field_t<double>(p, dir);
 }
 
 }  // namespace afmm

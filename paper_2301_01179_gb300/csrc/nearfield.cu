@@ -32,6 +32,9 @@ struct NearArgs {
     int direct;          // 1: all sources, split into nsplit chunks
     int nsplit;
     int64_t split_len;
+    // MIXED precision: FP32 amplitudes and local expansions, compensated FP32 sums
+    const float *q32_re, *q32_im;
+    const float *loc32_re, *loc32_im;
     // local expansion at the leaves (near mode, optional)
     const double *loc_re, *loc_im;
     const uint32_t *leaf_key;
@@ -70,6 +73,38 @@ __device__ __forceinline__ void l2p_eval(const double *__restrict__ F, int M, do
 }
 
 template <bool GRAD>
+__device__ __forceinline__ void l2p_eval32(const float *__restrict__ F, int M, float u, float v, float &val, float &du,
+                                           float &dv)
+{
+    float pu = 0.f, pdu = 0.f, pdv = 0.f;
+    for (int k = M; k >= 0; --k) {
+        int base = k * (M + 1) - k * (k - 1) / 2;
+        float pk = 0.f, pkd = 0.f;
+        for (int l = M - k; l >= 0; --l) {
+            if (GRAD) pkd = fmaf(pkd, v, pk);
+            pk = fmaf(pk, v, F[base + l]);
+        }
+        if (GRAD) {
+            pdu = fmaf(pdu, u, pu);
+            pdv = fmaf(pdv, u, pkd);
+        }
+        pu = fmaf(pu, u, pk);
+    }
+    val = pu;
+    du = pdu;
+    dv = pdv;
+}
+
+// Kahan-compensated FP32 accumulation: (sum, running compensation) in a float2
+__device__ __forceinline__ void kadd(float2 &a, float v)
+{
+    float y = v - a.y;
+    float t = a.x + y;
+    a.y = (t - a.x) - y;
+    a.x = t;
+}
+
+template <bool GRAD, bool MIX>
 __global__ void __launch_bounds__(AFMM_NEAR_WARPS * 32) k_near(const NearArgs a, const RecTab tab)
 {
     extern __shared__ double smem[];
@@ -109,7 +144,8 @@ __global__ void __launch_bounds__(AFMM_NEAR_WARPS * 32) k_near(const NearArgs a,
     const double inv2r = 0.5 / rt;
 
     for (int c = 0; c < ncomp; ++c)
-        for (int n = 0; n < nm; ++n) acc[((size_t)c * nm + n) * 32 + lane] = 0.0;
+        for (int n = 0; n < nm; ++n) acc[((size_t)c * nm + n) * 32 + lane] = 0.0;  // also (0.f, 0.f) pairs
+    float2 *acc2 = reinterpret_cast<float2 *>(acc);
 
     // source ranges: 9 neighbour leaves, or one split of all sources
     int nrange = a.direct ? 1 : 9;
@@ -131,7 +167,40 @@ __global__ void __launch_bounds__(AFMM_NEAR_WARPS * 32) k_near(const NearArgs a,
             PairGeom g;
             pair_geom(rt, zt, r1, z1, inv2w, active, g);
             double sc = pair_sequence(g, inv2w, Nq, a.pp, gam, ys + lane, 32);
-            if (!GRAD) {
+            if (MIX) {
+                // FP64 sequence, FP32 products, Kahan-compensated FP32 sums
+                const size_t st = (size_t)nm * 32;
+                if (!GRAD) {
+                    for (int n = 0; n < nm; ++n) {
+                        float gn = (float)(sc * ys[n * 32 + lane]);
+                        float qr = a.q32_re[(size_t)n * a.nsrc + s], qi = a.q32_im[(size_t)n * a.nsrc + s];
+                        size_t o = (size_t)n * 32 + lane;
+                        kadd(acc2[o], qr * gn);
+                        kadd(acc2[o + st], qi * gn);
+                    }
+                } else {
+                    double inv = 1.0 / (g.rp2 * g.rm2);
+                    double ip = g.rm2 * inv, im = g.rp2 * inv;
+                    double A = ip + im, B = ip - im;
+                    float qfac = (float)fma(rt - r1, rt + r1, -g.x * g.x), x32 = (float)g.x;
+                    double yprev = ys[32 + lane];
+                    for (int n = 0; n < nm; ++n) {
+                        double yn = ys[n * 32 + lane];
+                        float gn = (float)(sc * yn);
+                        float wt = (float)(sc * fma(yn, A, rho[n] * yprev * B));
+                        yprev = yn;
+                        float xw = x32 * wt, qw = qfac * wt;
+                        float qr = a.q32_re[(size_t)n * a.nsrc + s], qi = a.q32_im[(size_t)n * a.nsrc + s];
+                        size_t o = (size_t)n * 32 + lane;
+                        kadd(acc2[o], qr * gn);
+                        kadd(acc2[o + st], qi * gn);
+                        kadd(acc2[o + 2 * st], qr * qw);
+                        kadd(acc2[o + 3 * st], qi * qw);
+                        kadd(acc2[o + 4 * st], qr * xw);
+                        kadd(acc2[o + 5 * st], qi * xw);
+                    }
+                }
+            } else if (!GRAD) {
                 for (int n = 0; n < nm; ++n) {
                     double gn = sc * ys[n * 32 + lane];
                     double qr = a.q_re[(size_t)n * a.nsrc + s], qi = a.q_im[(size_t)n * a.nsrc + s];
@@ -168,7 +237,7 @@ __global__ void __launch_bounds__(AFMM_NEAR_WARPS * 32) k_near(const NearArgs a,
     if (!active) return;
     // local expansion at the field point (far field)
     double u = 0.0, v = 0.0;
-    if (a.loc_re) {
+    if (a.loc_re || a.loc32_re) {
         uint32_t k = a.leaf_key[box];
         double cr = a.r0 + ((double)morton_ir(k) + 0.5) * a.h, cz = a.z0 + ((double)morton_iz(k) + 0.5) * a.h;
         u = (rt - cr) / a.h;
@@ -179,16 +248,52 @@ __global__ void __launch_bounds__(AFMM_NEAR_WARPS * 32) k_near(const NearArgs a,
     for (int n = 0; n < nm; ++n) {
         // (amplitudes carry c_n and the sequence is G_n / c_n, so the sums are plain)
         size_t o = (size_t)n * 32 + lane;
-        double pr = acc[o], pi = acc[o + st];
+        double c0, c1, c2 = 0, c3 = 0, c4 = 0, c5 = 0;
+        if (MIX) {
+            c0 = (double)acc2[o].x - (double)acc2[o].y;
+            c1 = (double)acc2[o + st].x - (double)acc2[o + st].y;
+            if (GRAD) {
+                c2 = (double)acc2[o + 2 * st].x - (double)acc2[o + 2 * st].y;
+                c3 = (double)acc2[o + 3 * st].x - (double)acc2[o + 3 * st].y;
+                c4 = (double)acc2[o + 4 * st].x - (double)acc2[o + 4 * st].y;
+                c5 = (double)acc2[o + 5 * st].x - (double)acc2[o + 5 * st].y;
+            }
+        } else {
+            c0 = acc[o];
+            c1 = acc[o + st];
+            if (GRAD) {
+                c2 = acc[o + 2 * st];
+                c3 = acc[o + 3 * st];
+                c4 = acc[o + 4 * st];
+                c5 = acc[o + 5 * st];
+            }
+        }
+        double pr = c0, pi = c1;
         double dr_r = 0, dr_i = 0, dz_r = 0, dz_i = 0;
         if (GRAD) {
             double nu = n - 0.5;
-            dr_r = (nu * acc[o + 2 * st] - pr) * inv2r;
-            dr_i = (nu * acc[o + 3 * st] - pi) * inv2r;
-            dz_r = nu * acc[o + 4 * st];
-            dz_i = nu * acc[o + 5 * st];
+            dr_r = (nu * c2 - pr) * inv2r;
+            dr_i = (nu * c3 - pi) * inv2r;
+            dz_r = nu * c4;
+            dz_i = nu * c5;
         }
-        if (a.loc_re) {
+        if (MIX && a.loc32_re) {
+            const float *Fr = a.loc32_re + ((size_t)box * nm + n) * a.ncoef;
+            const float *Fi = a.loc32_im + ((size_t)box * nm + n) * a.ncoef;
+            float vr, dur, dvr, vi, dui, dvi;
+            l2p_eval32<GRAD>(Fr, a.M, (float)u, (float)v, vr, dur, dvr);
+            l2p_eval32<GRAD>(Fi, a.M, (float)u, (float)v, vi, dui, dvi);
+            pr += vr;
+            pi += vi;
+            if (GRAD) {
+                double ih = 1.0 / a.h;
+                dr_r += dur * ih;
+                dr_i += dui * ih;
+                dz_r += dvr * ih;
+                dz_i += dvi * ih;
+            }
+        }
+        if (!MIX && a.loc_re) {
             const double *Fr = a.loc_re + ((size_t)box * nm + n) * a.ncoef;
             const double *Fi = a.loc_im + ((size_t)box * nm + n) * a.ncoef;
             double vr, dur, dvr, vi, dui, dvi;
@@ -317,12 +422,31 @@ static int near_warps(int nm, int grad)
 
 static inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b > 0 ? (n + b - 1) / b : 1); }
 
+// strengths into sorted order, times c_n, rounded to FP32 (MIXED precision)
+__global__ void k_permute32(const double *__restrict__ q_re, const double *__restrict__ q_im,
+                            const int32_t *__restrict__ perm, int64_t n, int nm, const RecTab tab,
+                            float *__restrict__ qs_re, float *__restrict__ qs_im)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n * nm) return;
+    int m = (int)(i / n);
+    int64_t j = i % n;
+    size_t src = (size_t)m * n + perm[j];
+    double c = tab.c[m];
+    qs_re[i] = (float)(q_re[src] * c);
+    qs_im[i] = (float)(q_im[src] * c);
+}
+
 afmm_status launch_permute(afmm_plan p, int dir, const double *q_re, const double *q_im)
 {
     int64_t n = dir == 0 ? p->ns : p->nf;
     const int32_t *perm = dir == 0 ? p->s_perm : p->t_perm;
-    k_permute<<<nblk(n * p->nmodes), 256, 0, p->stream>>>(q_re, q_im, perm, n, p->nmodes, *p->rec, p->qs_re,
-                                                           p->qs_im);
+    if (p->precision == AFMM_MIXED)
+        k_permute32<<<nblk(n * p->nmodes), 256, 0, p->stream>>>(q_re, q_im, perm, n, p->nmodes, *p->rec, p->qs32_re,
+                                                                 p->qs32_im);
+    else
+        k_permute<<<nblk(n * p->nmodes), 256, 0, p->stream>>>(q_re, q_im, perm, n, p->nmodes, *p->rec, p->qs_re,
+                                                               p->qs_im);
     AFMM_LAUNCH_CHECK();
     return AFMM_OK;
 }
@@ -341,8 +465,11 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
     a.sr = fw ? p->s_r : p->t_r;
     a.sz = fw ? p->s_z : p->t_z;
     a.nsrc = fw ? p->ns : p->nf;
+    const bool mix = p->precision == AFMM_MIXED;
     a.q_re = p->qs_re;
     a.q_im = p->qs_im;
+    a.q32_re = p->qs32_re;
+    a.q32_im = p->qs32_im;
     a.nmodes = p->nmodes;
     a.N = p->N;
     a.pp = p->pp;
@@ -377,8 +504,10 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
         a.nbr = p->lv[d].nbr;
         a.srng = fw ? p->lv[d].srng : p->lv[d].trng;
         if (with_local) {
-            a.loc_re = p->lv[d].loc_re;
-            a.loc_im = p->lv[d].loc_im;
+            a.loc_re = mix ? nullptr : p->lv[d].loc_re;
+            a.loc_im = mix ? nullptr : p->lv[d].loc_im;
+            a.loc32_re = mix ? p->lv[d].loc32_re : nullptr;
+            a.loc32_im = mix ? p->lv[d].loc32_im : nullptr;
             a.leaf_key = p->lv[d].key;
             a.M = p->M;
             a.ncoef = p->ncoef;
@@ -392,12 +521,18 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
     if (w == 0) return AFMM_EUNSUPPORTED;
     size_t sm = near_smem(p->nmodes, grad, w);
     unsigned grid = (unsigned)((a.nunits + w - 1) / w);
-    if (grad) {
-        AFMM_CUDA(cudaFuncSetAttribute(k_near<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_near<true><<<grid, w * 32, sm, p->stream>>>(a, *p->rec);
+    if (grad && mix) {
+        AFMM_CUDA(cudaFuncSetAttribute(k_near<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_near<true, true><<<grid, w * 32, sm, p->stream>>>(a, *p->rec);
+    } else if (grad) {
+        AFMM_CUDA(cudaFuncSetAttribute(k_near<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_near<true, false><<<grid, w * 32, sm, p->stream>>>(a, *p->rec);
+    } else if (mix) {
+        AFMM_CUDA(cudaFuncSetAttribute(k_near<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_near<false, true><<<grid, w * 32, sm, p->stream>>>(a, *p->rec);
     } else {
-        AFMM_CUDA(cudaFuncSetAttribute(k_near<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_near<false><<<grid, w * 32, sm, p->stream>>>(a, *p->rec);
+        AFMM_CUDA(cudaFuncSetAttribute(k_near<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_near<false, false><<<grid, w * 32, sm, p->stream>>>(a, *p->rec);
     }
     AFMM_LAUNCH_CHECK();
     if (a.part) {
@@ -535,8 +670,8 @@ extern "C" afmm_status afmm_direct_static(int64_t ns, const double *src_r, const
     int w = near_warps(n_modes, 0);
     if (w == 0) return AFMM_EUNSUPPORTED;
     size_t sm = near_smem(n_modes, 0, w);
-    AFMM_CUDA(cudaFuncSetAttribute(k_near<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_near<false><<<(unsigned)((a.nunits + w - 1) / w), w * 32, sm, st>>>(a, tab);
+    AFMM_CUDA(cudaFuncSetAttribute(k_near<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_near<false, false><<<(unsigned)((a.nunits + w - 1) / w), w * 32, sm, st>>>(a, tab);
     AFMM_LAUNCH_CHECK();
     if (a.part) {
         int64_t tot = (int64_t)2 * n_modes * nf;
