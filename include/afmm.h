@@ -42,10 +42,13 @@ typedef enum {
 } afmm_status;
 
 typedef enum {
-    AFMM_FP64 = 0,  /* every stage in FP64 */
-    AFMM_MIXED = 1  /* FP64 Legendre recursion and elliptic start values; FP32 bulk
-                       accumulation (compensated) and FP32 expansions (Sec. 2 with scaled
-                       coordinates, Eq. gfunc:scaled) */
+    AFMM_FP64 = 0,        /* FP64-accurate results (parity 1e-10 with an FP64 reference): FP64
+                             where precision demands it, FP32-pair ("double-float") arithmetic
+                             where it is exact enough and faster on GB300 (the S2L contraction) */
+    AFMM_MIXED = 1,       /* FP64 Legendre recursion and elliptic start values; FP32 bulk
+                             accumulation (compensated) and FP32 expansions (Sec. 2 with scaled
+                             coordinates, Eq. gfunc:scaled) */
+    AFMM_FP64_NATIVE = 2  /* every floating-point operation of the path in native FP64 */
 } afmm_precision;
 
 /* Options of the FMM (Sec. 3, Algorithm 1).  Zero-initialise and set what you need;

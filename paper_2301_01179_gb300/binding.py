@@ -15,6 +15,8 @@ LIB_PATH = os.path.join(HERE, "libafmm.so")
 
 AFMM_FP64 = 0
 AFMM_MIXED = 1
+AFMM_FP64_NATIVE = 2
+_PREC = {"fp64": AFMM_FP64, "mixed": AFMM_MIXED, "fp64_native": AFMM_FP64_NATIVE}
 _STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA error",
            4: "device wait timed out", 5: "unsupported request"}
 EXPORTS = ["afmm_options_default", "afmm_plan_create", "afmm_plan_destroy", "afmm_plan_info", "afmm_eval",
@@ -127,7 +129,7 @@ class Plan:
     """A quadtree plan over sources and field points (afmm_plan_create).
 
     Parameters mirror ``afmm_options``: ``order`` (M), ``leaf_size``, ``depth`` (0 = rule),
-    ``precision`` ("fp64" or "mixed"), ``fwd_switch``, ``miller_extra``.  The plan is bound
+    ``precision`` ("fp64", "mixed" or "fp64_native"), ``fwd_switch``, ``miller_extra``.  The plan is bound
     to the current torch stream at creation.
     """
 
@@ -144,7 +146,7 @@ class Plan:
         opt.order = int(order)
         opt.leaf_size = int(leaf_size)
         opt.depth_override = int(depth)
-        opt.precision = AFMM_MIXED if precision == "mixed" else AFMM_FP64
+        opt.precision = _PREC[precision]
         opt.fwd_switch = float(fwd_switch)
         opt.miller_extra = int(miller_extra)
         h = ctypes.c_void_p()

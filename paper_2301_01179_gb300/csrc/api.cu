@@ -127,7 +127,8 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
     if (opt.order < 0 || opt.leaf_size < 1 || opt.depth_override < 0 || opt.depth_override == 1 ||
         opt.depth_override > AFMM_MAX_LEVEL || opt.fwd_switch < 0.0 || opt.miller_extra < 0)
         return AFMM_EINVAL;
-    if (opt.precision != AFMM_FP64 && opt.precision != AFMM_MIXED) return AFMM_EINVAL;
+    if (opt.precision != AFMM_FP64 && opt.precision != AFMM_MIXED && opt.precision != AFMM_FP64_NATIVE)
+        return AFMM_EINVAL;
     if (opt.order > AFMM_MAX_ORDER) return AFMM_EUNSUPPORTED;
 
     afmm_plan p = new (std::nothrow) afmm_plan_s();

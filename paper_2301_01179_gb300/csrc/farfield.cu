@@ -639,7 +639,143 @@ __global__ void __launch_bounds__(128) k_s2l(const S2LArgs<R> a)
     }
 }
 
+// ------------------------------------------------------------------------------------
+// S2L in FP32-pair ("double-float") arithmetic for the FP64 path.  On GB300 an FP32 FMA
+// issues 61x faster than an FP64 FMA, so each FP64 operand is held as hi + lo floats and
+// each complex multiply-add is an exact FP32 two-product (hi*hi by FMA, plus the cross
+// terms) folded into a (sum, error) pair by an exact two-sum: ~24 FP32 operations in
+// place of two FP64 FMAs, relative accuracy ~1e-14.  Round-to-nearest intrinsics keep
+// the compiler from contracting the error-free transformations.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 split_df(double v)
+{
+    float h = __double2float_rn(v);
+    float l = __double2float_rn(v - (double)h);
+    return make_float2(h, l);
+}
+
+// acc (S, E) += a * b, a = (ah, al), b = (bh, bl)
+__device__ __forceinline__ void df_fma_acc(float &S, float &E, float2 a, float2 b)
+{
+    float p = __fmul_rn(a.x, b.x);
+    float pe = __fmaf_rn(a.x, b.x, -p);
+    pe = __fmaf_rn(a.x, b.y, pe);
+    pe = __fmaf_rn(a.y, b.x, pe);
+    float s = __fadd_rn(S, p);
+    float v = __fsub_rn(s, S);
+    float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, v)), __fsub_rn(p, v));
+    E = __fadd_rn(E, __fadd_rn(err, pe));
+    S = s;
+}
+
+template <int KPT>
+__global__ void __launch_bounds__(128) k_s2l_df(const S2LArgs<double> a)
+{
+    extern __shared__ double sm_raw[];
+    float2 *sm = reinterpret_cast<float2 *>(sm_raw);
+    const int M = a.M, nc = a.nc, W = M + 1, C2 = 2 * M + 1;
+    const int slab = W * W * C2;
+    float2 *S = sm;                 // [W][W][C2] oriented expansion, hi/lo
+    float2 *Ir = S + slab;          // [nc][32]
+    float2 *Ii = Ir + (size_t)nc * 32;
+    __shared__ int bx[32];
+    __shared__ int src[32];
+    __shared__ int any;
+    const int64_t u = blockIdx.x;
+    const int n = blockIdx.y;
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    if (threadIdx.x < 32) bx[threadIdx.x] = a.unit_box[u * 32 + threadIdx.x];
+    const int ucol = a.unit_col[u];
+    const int col = ucol & 0xffff, pz = (ucol >> 30) & 1, pr = col & 1;
+    const int nl = 1 << a.level;
+    float aSr[KPT], aEr[KPT], aSi[KPT], aEi[KPT];
+    int base[KPT];
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+        aSr[q] = aEr[q] = aSi[q] = aEi[q] = 0.f;
+        int kl = grp + 4 * q;
+        int k = 0, rem = kl < nc ? kl : 0;
+        while (rem >= M + 1 - k) { rem -= M + 1 - k; ++k; }
+        base[q] = (k * W) * C2 + rem;
+    }
+    const size_t slabn = (size_t)slab;
+    for (int slot = 0; slot < 27; ++slot) {
+        int dr, dz;
+        s2l_offset_ff(pr, pz, slot, &dr, &dz);
+        int scol = col + dr;
+        if (scol < 0 || scol >= nl) continue;
+        __syncthreads();
+        if (threadIdx.x == 0) any = 0;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int b = bx[threadIdx.x];
+            int s2 = b >= 0 ? a.s2l[(size_t)b * 27 + slot] : -1;
+            src[threadIdx.x] = s2;
+            if (s2 >= 0) any = 1;
+        }
+        __syncthreads();
+        if (!any) continue;
+        int station = dr < 0 ? scol : col;
+        int sidx = a.station_of_col[station];
+        int ea = dr < 0 ? -dr : dr, eb = dz < 0 ? -dz : dz;
+        bool inward = dr > 0, backward = dz > 0;
+        const double *E = a.gexp + (((size_t)sidx * 16 + ea * 4 + eb) * a.nm + n) * slabn;
+        for (int i = threadIdx.x; i < slab; i += blockDim.x) {
+            int c = i % C2, ki = i / C2;
+            int k = ki / W, ii = ki % W;
+            if (k + ii + c > 2 * M) continue;
+            double v = inward ? E[((size_t)ii * W + k) * C2 + c] : E[i];
+            S[i] = split_df((backward && (c & 1)) ? -v : v);
+        }
+        for (int i = threadIdx.x; i < nc * 32; i += blockDim.x) {
+            int c = i / 32, m = i % 32;
+            int s2 = src[m];
+            Ir[i] = s2 >= 0 ? split_df(a.mom_re[((size_t)s2 * a.nm + n) * nc + c]) : make_float2(0.f, 0.f);
+            Ii[i] = s2 >= 0 ? split_df(a.mom_im[((size_t)s2 * a.nm + n) * nc + c]) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        int ij = 0;
+        for (int i = 0; i <= M; ++i) {
+            for (int j = 0; i + j <= M; ++j, ++ij) {
+                float2 xr = Ir[ij * 32 + lane], xi = Ii[ij * 32 + lane];
+                int off = i * C2 + j;
+#pragma unroll
+                for (int q = 0; q < KPT; ++q) {
+                    float2 e = S[base[q] + off];
+                    df_fma_acc(aSr[q], aEr[q], e, xr);
+                    df_fma_acc(aSi[q], aEi[q], e, xi);
+                }
+            }
+        }
+    }
+    int b = bx[lane];
+    if (b < 0) return;
+#pragma unroll
+    for (int q = 0; q < KPT; ++q) {
+        int kl = grp + 4 * q;
+        if (kl < nc) {
+            int k = 0, rem = kl;
+            while (rem >= M + 1 - k) { rem -= M + 1 - k; ++k; }
+            double f = 1.0;
+            for (int t = 2; t <= rem; ++t) f *= t;
+            size_t o = ((size_t)b * a.nm + n) * nc + kl;
+            a.loc_re[o] += ((double)aSr[q] + (double)aEr[q]) / f;
+            a.loc_im[o] += ((double)aSi[q] + (double)aEi[q]) / f;
+        }
+    }
+}
+
 static inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b > 0 ? (n + b - 1) / b : 1); }
+
+template <int KPT>
+static afmm_status launch_s2l_df_k(const S2LArgs<double> &a, cudaStream_t st, size_t sm)
+{
+    AFMM_CUDA(cudaFuncSetAttribute(k_s2l_df<KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    dim3 grid((unsigned)a.nunit, (unsigned)a.nm);
+    k_s2l_df<KPT><<<grid, 128, sm, st>>>(a);
+    AFMM_LAUNCH_CHECK();
+    return AFMM_OK;
+}
 
 template <typename R, int KPT>
 static afmm_status launch_s2l_k(const S2LArgs<R> &a, cudaStream_t st, size_t sm)
@@ -674,6 +810,17 @@ static afmm_status launch_s2l(afmm_plan p, int l, const R *mre, const R *mim, R 
     int W = p->M + 1;
     size_t sm = sizeof(R) * ((size_t)W * W * (2 * p->M + 1) + 2 * (size_t)p->ncoef * 32);
     int kpt = (p->ncoef + 3) / 4;
+    if (sizeof(R) == sizeof(double) && p->precision == AFMM_FP64) {
+        // FP64 path: FP32-pair arithmetic (same shared-memory size: float2 per entry)
+        const S2LArgs<double> &ad = reinterpret_cast<const S2LArgs<double> &>(a);
+        if (kpt <= 4) return launch_s2l_df_k<4>(ad, p->stream, sm);
+        if (kpt <= 8) return launch_s2l_df_k<8>(ad, p->stream, sm);
+        if (kpt <= 12) return launch_s2l_df_k<12>(ad, p->stream, sm);
+        if (kpt <= 16) return launch_s2l_df_k<16>(ad, p->stream, sm);
+        if (kpt <= 24) return launch_s2l_df_k<24>(ad, p->stream, sm);
+        if (kpt <= 32) return launch_s2l_df_k<32>(ad, p->stream, sm);
+        return AFMM_EUNSUPPORTED;
+    }
     if (kpt <= 4) return launch_s2l_k<R, 4>(a, p->stream, sm);
     if (kpt <= 8) return launch_s2l_k<R, 8>(a, p->stream, sm);
     if (kpt <= 12) return launch_s2l_k<R, 12>(a, p->stream, sm);
@@ -758,7 +905,7 @@ static afmm_status far_field_t(afmm_plan p, int dir)
 afmm_status far_field(afmm_plan p, int dir)
 {
     if (p->precision == AFMM_MIXED) return far_field_t<float>(p, dir);
-    return far_field_t<double>(p, dir);
+    return far_field_t<double>(p, dir);  // AFMM_FP64 (FP32-pair S2L) and AFMM_FP64_NATIVE
 }
 
 }  // namespace afmm

@@ -334,6 +334,255 @@ __global__ void __launch_bounds__(AFMM_NEAR_WARPS * 32) k_near(const NearArgs a,
     }
 }
 
+// ------------------------------------------------------------------------------------
+// Cooperative near-field kernel: the WB warps of a block share one unit of <= 32 field
+// points.  Sources are taken WB at a time: in phase 1 warp w evaluates the pair sequence of
+// source w of the chunk for all 32 field points and leaves it in shared memory; in phase 2
+// warp w accumulates its contiguous share of the modes over the chunk's sources.  Each lane
+// thus holds accumulators for nm / WB modes instead of nm, which lifts occupancy from 3 to
+// 8 warps per SM (FP64 with gradient, N = 32) so the FP64 pipe stays busy.
+// ------------------------------------------------------------------------------------
+#define NEAR2_WB 4
+
+template <bool GRAD, bool MIX>
+__global__ void __launch_bounds__(NEAR2_WB * 32) k_near2(const NearArgs a, const RecTab tab)
+{
+    extern __shared__ double smem[];
+    constexpr int WB = NEAR2_WB;
+    constexpr int NPP = GRAD ? 5 : 1;  // per-pair scalars: scale (, x, qfac, A, B)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nm = a.nmodes, N = a.N;
+    const int Nq = GRAD && N < 1 ? 1 : N;
+    const int nmq = Nq + 1;                     // sequence rows per pair
+    const int ncomp = GRAD ? 6 : 2;
+    const int mper = (nm + WB - 1) / WB;        // modes per warp
+    double *gam = smem;                         // [AFMM_REC_TAB]
+    double *rho = gam + AFMM_REC_TAB;           // [AFMM_MAX_MODES] c_{n-1}/c_n
+    double *ys = rho + AFMM_MAX_MODES;          // [WB][nmq][32]
+    double *pp = ys + (size_t)WB * nmq * 32;    // [WB][NPP][32]
+    double *acc = pp + (size_t)WB * NPP * 32;   // [WB][ncomp][mper][32]
+    __shared__ int rb[10], rcum[10];
+    for (int i = threadIdx.x; i < AFMM_REC_TAB; i += blockDim.x) gam[i] = tab.gam[i];
+    for (int i = threadIdx.x; i < nm; i += blockDim.x) rho[i] = i == 0 ? 1.0 : tab.c[i - 1] / tab.c[i];
+
+    const int64_t unit = blockIdx.x;
+    int64_t t0, t1, split = 0;
+    int box = -1;
+    if (a.direct) {
+        int64_t tu = unit / a.nsplit;
+        split = unit % a.nsplit;
+        t0 = tu * 32;
+        t1 = min(t0 + 32, a.nfield);
+    } else {
+        NearUnit u = a.units[unit];
+        box = u.box;
+        t0 = u.begin;
+        t1 = u.end;
+    }
+    // source ranges (flattened): 9 neighbour leaves, or one split of all sources
+    if (threadIdx.x == 0) {
+        int cum = 0;
+        if (a.direct) {
+            int64_t s0 = split * a.split_len, s1 = min(s0 + a.split_len, a.nsrc);
+            rb[0] = (int)s0;
+            rcum[0] = 0;
+            cum = (int)(s1 > s0 ? s1 - s0 : 0);
+            for (int k = 1; k < 10; ++k) {
+                rb[k] = 0;
+                rcum[k] = cum;
+            }
+        } else {
+            for (int k = 0; k < 9; ++k) {
+                int32_t nb = a.nbr[(int64_t)box * 9 + k];
+                int2 r = nb >= 0 ? a.srng[nb] : make_int2(0, 0);
+                rb[k] = r.x;
+                rcum[k] = cum;
+                cum += r.y - r.x;
+            }
+            rb[9] = 0;
+            rcum[9] = cum;
+        }
+    }
+    const int64_t t = t0 + lane;
+    const bool active = t < t1;
+    const int64_t tc = active ? t : t0;
+    const double rt = a.fr[tc], zt = a.fz[tc];
+    const double inv2r = 0.5 / rt;
+    double *myacc = acc + (size_t)warp * ncomp * mper * 32;
+    for (int i = lane; i < ncomp * mper * 32; i += 32) myacc[i] = 0.0;
+    float2 *myacc2 = reinterpret_cast<float2 *>(myacc);
+    const int n0 = warp * mper, n1 = min(nm, n0 + mper);
+    __syncthreads();
+    const int total = rcum[9];
+    for (int c0 = 0; c0 < total; c0 += WB) {
+        // ---- phase 1: warp w evaluates source c0 + w for the unit's field points
+        const int k = c0 + warp;
+        if (k < total) {
+            int rg = 0;
+            while (rg < 8 && rcum[rg + 1] <= k) ++rg;
+            const int64_t s = rb[rg] + (k - rcum[rg]);
+            const double r1 = a.sr[s], z1 = a.sz[s];
+            const double inv2w = inv2r / r1;
+            PairGeom g;
+            pair_geom(rt, zt, r1, z1, inv2w, active, g);
+            double *yw = ys + (size_t)warp * nmq * 32;
+            double sc = pair_sequence(g, inv2w, Nq, a.pp, gam, yw + lane, 32);
+            double *pw = pp + (size_t)warp * NPP * 32;
+            pw[lane] = sc;
+            if (GRAD) {
+                double inv = 1.0 / (g.rp2 * g.rm2);
+                double ip = g.rm2 * inv, im = g.rp2 * inv;
+                pw[32 + lane] = g.x;
+                pw[64 + lane] = fma(rt - r1, rt + r1, -g.x * g.x);
+                pw[96 + lane] = sc * (ip + im);  // scaled A
+                pw[128 + lane] = sc * (ip - im); // scaled B
+            }
+        }
+        __syncthreads();
+        // ---- phase 2: warp w accumulates modes [n0, n1) over the chunk's sources
+        const int kmax = min(WB, total - c0);
+        for (int kk = 0; kk < kmax; ++kk) {
+            const int kq = c0 + kk;
+            int rg = 0;
+            while (rg < 8 && rcum[rg + 1] <= kq) ++rg;
+            const int64_t s = rb[rg] + (kq - rcum[rg]);
+            const double *yk = ys + (size_t)kk * nmq * 32;
+            const double *pk = pp + (size_t)kk * NPP * 32;
+            const double sc = pk[lane];
+            double gx = 0, qf = 0, As = 0, Bs = 0, yprev = 0;
+            if (GRAD) {
+                gx = pk[32 + lane];
+                qf = pk[64 + lane];
+                As = pk[96 + lane];
+                Bs = pk[128 + lane];
+                yprev = n0 == 0 ? yk[32 + lane] : yk[(n0 - 1) * 32 + lane];  // y_{-1} := y_1
+            }
+            for (int n = n0; n < n1; ++n) {
+                const double yn = yk[n * 32 + lane];
+                const size_t o = (size_t)(n - n0) * 32 + lane, st = (size_t)mper * 32;
+                if (MIX) {
+                    float qr = a.q32_re[(size_t)n * a.nsrc + s], qi = a.q32_im[(size_t)n * a.nsrc + s];
+                    float gn = (float)(sc * yn);
+                    kadd(myacc2[o], qr * gn);
+                    kadd(myacc2[o + st], qi * gn);
+                    if (GRAD) {
+                        float wt = (float)fma(yn, As, rho[n] * yprev * Bs);
+                        yprev = yn;
+                        float xw = (float)gx * wt, qw = (float)qf * wt;
+                        kadd(myacc2[o + 2 * st], qr * qw);
+                        kadd(myacc2[o + 3 * st], qi * qw);
+                        kadd(myacc2[o + 4 * st], qr * xw);
+                        kadd(myacc2[o + 5 * st], qi * xw);
+                    }
+                } else {
+                    double qr = a.q_re[(size_t)n * a.nsrc + s], qi = a.q_im[(size_t)n * a.nsrc + s];
+                    double gn = sc * yn;
+                    myacc[o] = fma(qr, gn, myacc[o]);
+                    myacc[o + st] = fma(qi, gn, myacc[o + st]);
+                    if (GRAD) {
+                        double wt = fma(yn, As, rho[n] * yprev * Bs);
+                        yprev = yn;
+                        double xw = gx * wt, qw = qf * wt;
+                        myacc[o + 2 * st] = fma(qr, qw, myacc[o + 2 * st]);
+                        myacc[o + 3 * st] = fma(qi, qw, myacc[o + 3 * st]);
+                        myacc[o + 4 * st] = fma(qr, xw, myacc[o + 4 * st]);
+                        myacc[o + 5 * st] = fma(qi, xw, myacc[o + 5 * st]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (!active) return;
+    double u = 0.0, v = 0.0;
+    if (a.loc_re || a.loc32_re) {
+        uint32_t kk = a.leaf_key[box];
+        double cr = a.r0 + ((double)morton_ir(kk) + 0.5) * a.h, cz = a.z0 + ((double)morton_iz(kk) + 0.5) * a.h;
+        u = (rt - cr) / a.h;
+        v = (zt - cz) / a.h;
+    }
+    const int64_t dst = a.out_perm ? a.out_perm[t] : t;
+    const size_t st = (size_t)mper * 32;
+    for (int n = n0; n < n1; ++n) {
+        size_t o = (size_t)(n - n0) * 32 + lane;
+        double c[6] = {0, 0, 0, 0, 0, 0};
+        for (int q = 0; q < ncomp; ++q)
+            c[q] = MIX ? (double)myacc2[o + q * st].x - (double)myacc2[o + q * st].y : myacc[o + q * st];
+        double pr = c[0], pi = c[1];
+        double dr_r = 0, dr_i = 0, dz_r = 0, dz_i = 0;
+        if (GRAD) {
+            double nu = n - 0.5;
+            dr_r = (nu * c[2] - pr) * inv2r;
+            dr_i = (nu * c[3] - pi) * inv2r;
+            dz_r = nu * c[4];
+            dz_i = nu * c[5];
+        }
+        if (MIX && a.loc32_re) {
+            const float *Fr = a.loc32_re + ((size_t)box * nm + n) * a.ncoef;
+            const float *Fi = a.loc32_im + ((size_t)box * nm + n) * a.ncoef;
+            float vr, dur, dvr, vi, dui, dvi;
+            l2p_eval32<GRAD>(Fr, a.M, (float)u, (float)v, vr, dur, dvr);
+            l2p_eval32<GRAD>(Fi, a.M, (float)u, (float)v, vi, dui, dvi);
+            pr += vr;
+            pi += vi;
+            if (GRAD) {
+                double ih = 1.0 / a.h;
+                dr_r += dur * ih;
+                dr_i += dui * ih;
+                dz_r += dvr * ih;
+                dz_i += dvi * ih;
+            }
+        }
+        if (!MIX && a.loc_re) {
+            const double *Fr = a.loc_re + ((size_t)box * nm + n) * a.ncoef;
+            const double *Fi = a.loc_im + ((size_t)box * nm + n) * a.ncoef;
+            double vr, dur, dvr, vi, dui, dvi;
+            l2p_eval<GRAD>(Fr, a.M, u, v, vr, dur, dvr);
+            l2p_eval<GRAD>(Fi, a.M, u, v, vi, dui, dvi);
+            pr += vr;
+            pi += vi;
+            if (GRAD) {
+                double ih = 1.0 / a.h;
+                dr_r += dur * ih;
+                dr_i += dui * ih;
+                dz_r += dvr * ih;
+                dz_i += dvi * ih;
+            }
+        }
+        if (a.part) {
+            size_t base = (size_t)split * ncomp;
+            size_t nfm = (size_t)a.nfield;
+            a.part[((base + 0) * nm + n) * nfm + t] = pr;
+            a.part[((base + 1) * nm + n) * nfm + t] = pi;
+            if (GRAD) {
+                a.part[((base + 2) * nm + n) * nfm + t] = dr_r;
+                a.part[((base + 3) * nm + n) * nfm + t] = dr_i;
+                a.part[((base + 4) * nm + n) * nfm + t] = dz_r;
+                a.part[((base + 5) * nm + n) * nfm + t] = dz_i;
+            }
+        } else {
+            size_t od = (size_t)n * a.nfield + dst;
+            if (a.o_re) a.o_re[od] = pr;
+            if (a.o_im) a.o_im[od] = pi;
+            if (GRAD) {
+                a.o_dr_re[od] = dr_r;
+                a.o_dr_im[od] = dr_i;
+                a.o_dz_re[od] = dz_r;
+                a.o_dz_im[od] = dz_i;
+            }
+        }
+    }
+}
+
+static size_t near2_smem(int nm, int grad)
+{
+    int Nq = (grad && nm < 2) ? 1 : nm - 1;
+    int ncomp = grad ? 6 : 2, npp = grad ? 5 : 1;
+    int mper = (nm + NEAR2_WB - 1) / NEAR2_WB;
+    return sizeof(double) * ((size_t)AFMM_REC_TAB + AFMM_MAX_MODES + (size_t)NEAR2_WB * (Nq + 1) * 32 +
+                             (size_t)NEAR2_WB * npp * 32 + (size_t)NEAR2_WB * ncomp * mper * 32);
+}
+
 // sum of split partials into the caller layout
 __global__ void k_split_reduce(const double *__restrict__ part, int nsplit, int ncomp, int nm, int64_t nfield,
                                const int32_t *__restrict__ perm, double *o0, double *o1, double *o2, double *o3,
@@ -517,22 +766,22 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
         }
     }
     if (a.nunits == 0) return AFMM_OK;
-    int w = near_warps(p->nmodes, grad);
-    if (w == 0) return AFMM_EUNSUPPORTED;
-    size_t sm = near_smem(p->nmodes, grad, w);
-    unsigned grid = (unsigned)((a.nunits + w - 1) / w);
+    size_t sm = near2_smem(p->nmodes, grad);
+    if (sm > 227 * 1024) return AFMM_EUNSUPPORTED;
+    unsigned grid = (unsigned)a.nunits;
+    const int T = NEAR2_WB * 32;
     if (grad && mix) {
-        AFMM_CUDA(cudaFuncSetAttribute(k_near<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_near<true, true><<<grid, w * 32, sm, p->stream>>>(a, *p->rec);
+        AFMM_CUDA(cudaFuncSetAttribute(k_near2<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_near2<true, true><<<grid, T, sm, p->stream>>>(a, *p->rec);
     } else if (grad) {
-        AFMM_CUDA(cudaFuncSetAttribute(k_near<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_near<true, false><<<grid, w * 32, sm, p->stream>>>(a, *p->rec);
+        AFMM_CUDA(cudaFuncSetAttribute(k_near2<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_near2<true, false><<<grid, T, sm, p->stream>>>(a, *p->rec);
     } else if (mix) {
-        AFMM_CUDA(cudaFuncSetAttribute(k_near<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_near<false, true><<<grid, w * 32, sm, p->stream>>>(a, *p->rec);
+        AFMM_CUDA(cudaFuncSetAttribute(k_near2<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_near2<false, true><<<grid, T, sm, p->stream>>>(a, *p->rec);
     } else {
-        AFMM_CUDA(cudaFuncSetAttribute(k_near<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_near<false, false><<<grid, w * 32, sm, p->stream>>>(a, *p->rec);
+        AFMM_CUDA(cudaFuncSetAttribute(k_near2<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_near2<false, false><<<grid, T, sm, p->stream>>>(a, *p->rec);
     }
     AFMM_LAUNCH_CHECK();
     if (a.part) {
