@@ -150,6 +150,9 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
     p->opt = opt;
     p->pp.fwd_switch = opt.fwd_switch > 0.0 ? opt.fwd_switch : default_fwd_switch(p->N);
     p->pp.miller_extra = opt.miller_extra > 0 ? (double)opt.miller_extra : 15.0;
+    // FP32-pair recursion (AFMM_FP64): rounding ~2^-47 instead of 2^-53, so the forward
+    // sweep is used only while its growth e^s N / s keeps the error below ~5e-12
+    p->df_fwd_switch = opt.fwd_switch > 0.0 ? (opt.fwd_switch < 4.5 ? opt.fwd_switch : 4.5) : 4.5;
 
     afmm_status s = build_tree(p, src_r, src_z, tgt_r, tgt_z);
     if (s == AFMM_OK) s = make_shift_tables(p);
@@ -184,6 +187,16 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
     p->expansions = nexp;
     if (s == AFMM_OK && gcap > 0) s = dalloc_t(p, &p->gexp, gcap);
     p->gexp_cap = gcap;
+    if (s == AFMM_OK && p->precision == AFMM_FP64) {
+        s = dalloc_t(p, &p->qsdf, (size_t)2 * nm * nmax);
+        if (s == AFMM_OK) s = dalloc_t(p, &p->locdf, (size_t)2 * p->lv[p->d].nbox * nm * nc);
+    }
+    if (s == AFMM_OK && p->precision == AFMM_FP64) {
+        int64_t mmax = 0;
+        for (int l = 2; l <= p->d; ++l) mmax = p->lv[l].nbox > mmax ? p->lv[l].nbox : mmax;
+        if (gcap > 0) s = dalloc_t(p, &p->gexp_df, gcap);
+        if (s == AFMM_OK) s = dalloc_t(p, &p->mom_df, (size_t)2 * mmax * nm * nc);
+    }
     // direct sums over few field points are split over sources: room for the partials
     // of up to 64 splits of the smaller point set, at most 1 GB
     if (s == AFMM_OK) {
@@ -259,6 +272,7 @@ static afmm_status run_fmm(afmm_plan p, int dir, const double *q_re, const doubl
     AFMM_TRY(launch_permute(p, dir, q_re, q_im));
     tmark(p, 1);
     AFMM_TRY(far_field(p, dir));
+    if (p->precision == AFMM_FP64) AFMM_TRY(split_leaf_locals(p));
     tmark(p, 8);
     AFMM_TRY(launch_near(p, dir, 1, grad, o_re, o_im, dr_re, dr_im, dz_re, dz_im, 0));
     tmark(p, 9);

@@ -149,7 +149,12 @@ struct afmm_plan_s {
     // eval scratch
     double *qs_re = nullptr, *qs_im = nullptr;  // [nmodes][max(ns,nf)] strengths, sorted, * c_n
     float *qs32_re = nullptr, *qs32_im = nullptr;  // MIXED: the same in FP32
+    float2 *qsdf = nullptr;                     // FP64 path: the same as FP32 pairs [2][nmodes][n]
+    float2 *locdf = nullptr;                    // FP64 path: leaf locals as FP32 pairs [2][nbox][nmodes][ncoef]
+    double df_fwd_switch = 4.5;                 // forward switch of the FP32-pair recursion
     double *gexp = nullptr;                     // expansions of one level
+    float2 *gexp_df = nullptr;                  // FP64 path: the same as FP32 pairs
+    float2 *mom_df = nullptr;                   // FP64 path: moments of one level as FP32 pairs [2][...]
     int64_t gexp_cap = 0;                       // doubles
     double *m2m_tab = nullptr;                  // [4][2][(M+1)^2] shift tables (see farfield.cu)
     double *l2l_tab = nullptr;
@@ -190,4 +195,5 @@ afmm_status far_field(afmm_plan p, int dir);
 afmm_status launch_green_expansion(int64_t npts, const double *r, const double *r1, const double *x,
                                    int n_modes, int P, double *out, cudaStream_t st);
 afmm_status make_shift_tables(afmm_plan p);
+afmm_status split_leaf_locals(afmm_plan p);
 }  // namespace afmm

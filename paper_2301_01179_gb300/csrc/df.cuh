@@ -1,0 +1,159 @@
+// df.cuh -- FP32-pair ("double-float") arithmetic for FP64-class accuracy on the FP32 pipe.
+//
+// A value is hi + lo with two floats, |lo| <= ulp(hi)/2: 48 significant bits, relative
+// rounding ~2^-47 per operation.  On GB300 an FP32 operation issues 61x faster than an
+// FP64 one, so a df multiply (6 FP32 ops) or add (~10) costs a fraction of one FP64
+// instruction.  The error-free transformations (Knuth's two-sum, the FMA two-product)
+// use round-to-nearest intrinsics so the compiler cannot contract or reassociate them.
+// The exponent range is FP32's; callers keep magnitudes well inside 1e-30..1e30.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace afmm {
+
+struct dfv {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dfv df_make(float h, float l)
+{
+    dfv r;
+    r.hi = h;
+    r.lo = l;
+    return r;
+}
+
+__device__ __forceinline__ dfv two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float v = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
+    return df_make(s, e);
+}
+
+__device__ __forceinline__ dfv quick_two_sum(float a, float b)  // |a| >= |b|
+{
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return df_make(s, e);
+}
+
+__device__ __forceinline__ dfv df_add(dfv a, dfv b)
+{
+    dfv s = two_sum(a.hi, b.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return quick_two_sum(s.hi, e);
+}
+
+__device__ __forceinline__ dfv df_neg(dfv a) { return df_make(-a.hi, -a.lo); }
+__device__ __forceinline__ dfv df_sub(dfv a, dfv b) { return df_add(a, df_neg(b)); }
+
+__device__ __forceinline__ dfv df_mul(dfv a, dfv b)
+{
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return quick_two_sum(p, e);
+}
+
+__device__ __forceinline__ dfv df_mulf(dfv a, float b)
+{
+    float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    return quick_two_sum(p, e);
+}
+
+// a * 2^k exactly (k small): scale both parts
+__device__ __forceinline__ dfv df_scale2(dfv a, float p2) { return df_make(a.hi * p2, a.lo * p2); }
+
+// a / b: FP32 quotient from the hardware reciprocal (MUFU, ~1 ulp), then one df residual
+// correction; the residual step removes the approximation error of the first quotient
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ dfv df_div(dfv a, dfv b)
+{
+    float rb = rcp_approx(b.hi);
+    float q1 = __fmul_rn(a.hi, rb);
+    dfv r = df_sub(a, df_mulf(b, q1));
+    float q2 = __fmul_rn(r.hi, rb);
+    dfv q = quick_two_sum(q1, q2);
+    // second correction for full df accuracy
+    dfv r2 = df_sub(a, df_mul(b, q));
+    return df_add(q, df_make(__fmul_rn(r2.hi, rb), 0.f));
+}
+
+// sqrt by one correction of an FP32 seed from the hardware reciprocal square root (Karp):
+// x = rsqrt(a_hi), y = a_hi x, sqrt(a) ~ y + (a - y^2) x / 2
+__device__ __forceinline__ dfv df_sqrt(dfv a)
+{
+    if (!(a.hi > 0.f)) return df_make(0.f, 0.f);
+    float x = rsqrtf(a.hi);
+    float y = __fmul_rn(a.hi, x);
+    float p = __fmul_rn(y, y);
+    float pe = __fmaf_rn(y, y, -p);
+    float d = __fsub_rn(__fsub_rn(a.hi, p), pe);
+    d = __fadd_rn(d, a.lo);
+    return two_sum(y, __fmul_rn(d, __fmul_rn(0.5f, x)));
+}
+
+__device__ __forceinline__ double df_to_double(dfv a) { return (double)a.hi + (double)a.lo; }
+
+// FP64 -> df with integer operations (the FP64<->FP32 conversions run on the FP64 pipe on
+// GB300): hi keeps the top 24 bits of the significand (rounded), lo = v - hi is exact in
+// FP64 and keeps the next 24.  Values outside the normal FP32 range fall back to the
+// conversion instructions.
+__device__ __forceinline__ float f64_to_f32_bits(double v, double &back)
+{
+    long long b = __double_as_longlong(v);
+    int e = (int)((b >> 52) & 0x7ff) - 1023;
+    if (e < -125 || e > 126) {
+        float f = __double2float_rn(v);
+        back = (double)f;
+        return f;
+    }
+    unsigned long long sgn = (unsigned long long)b & 0x8000000000000000ull;
+    unsigned long long m = (unsigned long long)b & 0x000fffffffffffffull;
+    unsigned long long m23 = (m + (1ull << 28)) >> 29;  // round to 23 fraction bits
+    if (m23 == (1ull << 23)) {
+        m23 = 0;
+        ++e;
+    }
+    unsigned int fb = (unsigned int)(sgn >> 32) | ((unsigned int)(e + 127) << 23) | (unsigned int)m23;
+    back = __longlong_as_double((long long)(sgn | ((unsigned long long)(e + 1023) << 52) | (m23 << 29)));
+    return __uint_as_float(fb);
+}
+
+__device__ __forceinline__ dfv df_from_double(double v)
+{
+    if (v == 0.0) return df_make(0.f, 0.f);
+    double hb;
+    float h = f64_to_f32_bits(v, hb);
+    double r = v - hb;  // exact
+    double lb;
+    float l = r == 0.0 ? 0.f : f64_to_f32_bits(r, lb);
+    return df_make(h, l);
+}
+
+// accumulate a * b into the (sum, error) pair (S, E): exact two-product and two-sum
+__device__ __forceinline__ void df_acc(float &S, float &E, dfv a, dfv b)
+{
+    float p = __fmul_rn(a.hi, b.hi);
+    float pe = __fmaf_rn(a.hi, b.hi, -p);
+    pe = __fmaf_rn(a.hi, b.lo, pe);
+    pe = __fmaf_rn(a.lo, b.hi, pe);
+    float s = __fadd_rn(S, p);
+    float v = __fsub_rn(s, S);
+    float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, v)), __fsub_rn(p, v));
+    E = __fadd_rn(E, __fadd_rn(err, pe));
+    S = s;
+}
+
+}  // namespace afmm

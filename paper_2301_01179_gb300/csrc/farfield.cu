@@ -537,6 +537,7 @@ struct S2LArgs {
     const double *gexp;
     const R *mom_re, *mom_im;
     R *loc_re, *loc_im;
+    const float2 *gexp_df, *mom_df_re, *mom_df_im;  // FP32-pair copies (FP64 path)
 };
 
 template <typename R, int KPT>
@@ -668,6 +669,13 @@ __device__ __forceinline__ void df_fma_acc(float &S, float &E, float2 a, float2 
     S = s;
 }
 
+// hi/lo split of an FP64 array into FP32 pairs (once per level, ahead of the S2L)
+__global__ void k_split_df(const double *__restrict__ in, int64_t n, float2 *__restrict__ out)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = split_df(in[i]);
+}
+
 template <int KPT>
 __global__ void __launch_bounds__(128) k_s2l_df(const S2LArgs<double> a)
 {
@@ -719,19 +727,19 @@ __global__ void __launch_bounds__(128) k_s2l_df(const S2LArgs<double> a)
         int sidx = a.station_of_col[station];
         int ea = dr < 0 ? -dr : dr, eb = dz < 0 ? -dz : dz;
         bool inward = dr > 0, backward = dz > 0;
-        const double *E = a.gexp + (((size_t)sidx * 16 + ea * 4 + eb) * a.nm + n) * slabn;
+        const float2 *E = a.gexp_df + (((size_t)sidx * 16 + ea * 4 + eb) * a.nm + n) * slabn;
         for (int i = threadIdx.x; i < slab; i += blockDim.x) {
             int c = i % C2, ki = i / C2;
             int k = ki / W, ii = ki % W;
             if (k + ii + c > 2 * M) continue;
-            double v = inward ? E[((size_t)ii * W + k) * C2 + c] : E[i];
-            S[i] = split_df((backward && (c & 1)) ? -v : v);
+            float2 v = inward ? E[((size_t)ii * W + k) * C2 + c] : E[i];
+            S[i] = (backward && (c & 1)) ? make_float2(-v.x, -v.y) : v;
         }
         for (int i = threadIdx.x; i < nc * 32; i += blockDim.x) {
             int c = i / 32, m = i % 32;
             int s2 = src[m];
-            Ir[i] = s2 >= 0 ? split_df(a.mom_re[((size_t)s2 * a.nm + n) * nc + c]) : make_float2(0.f, 0.f);
-            Ii[i] = s2 >= 0 ? split_df(a.mom_im[((size_t)s2 * a.nm + n) * nc + c]) : make_float2(0.f, 0.f);
+            Ir[i] = s2 >= 0 ? a.mom_df_re[((size_t)s2 * a.nm + n) * nc + c] : make_float2(0.f, 0.f);
+            Ii[i] = s2 >= 0 ? a.mom_df_im[((size_t)s2 * a.nm + n) * nc + c] : make_float2(0.f, 0.f);
         }
         __syncthreads();
         int ij = 0;
@@ -807,6 +815,9 @@ static afmm_status launch_s2l(afmm_plan p, int l, const R *mre, const R *mim, R 
     a.mom_im = mim;
     a.loc_re = lre;
     a.loc_im = lim;
+    a.gexp_df = p->gexp_df;
+    a.mom_df_re = p->mom_df;
+    a.mom_df_im = p->mom_df ? p->mom_df + (size_t)v.nbox * p->nmodes * p->ncoef : nullptr;
     int W = p->M + 1;
     size_t sm = sizeof(R) * ((size_t)W * W * (2 * p->M + 1) + 2 * (size_t)p->ncoef * 32);
     int kpt = (p->ncoef + 3) / 4;
@@ -895,10 +906,34 @@ static afmm_status far_field_t(afmm_plan p, int dir)
                                                                         p->gexp);
             AFMM_LAUNCH_CHECK();
         }
+        if (!mix && p->precision == AFMM_FP64) {
+            int64_t ng = (int64_t)v.nstation * 16 * nm * (M + 1) * (M + 1) * (2 * M + 1);
+            int64_t nmom = (int64_t)v.nbox * nm * nc;
+            if (ng > 0) {
+                k_split_df<<<nblk(ng), 256, 0, st>>>(p->gexp, ng, p->gexp_df);
+                AFMM_LAUNCH_CHECK();
+            }
+            k_split_df<<<nblk(nmom), 256, 0, st>>>((const double *)MR(l), nmom, p->mom_df);
+            AFMM_LAUNCH_CHECK();
+            k_split_df<<<nblk(nmom), 256, 0, st>>>((const double *)MI(l), nmom, p->mom_df + nmom);
+            AFMM_LAUNCH_CHECK();
+        }
         tmark(p, e + 2);
         AFMM_TRY(launch_s2l<R>(p, l, MR(l), MI(l), LR(l), LI(l)));
         tmark(p, e + 3);
     }
+    return AFMM_OK;
+}
+
+// FP64 path: leaf-level locals as FP32 pairs for the double-float local evaluation
+afmm_status split_leaf_locals(afmm_plan p)
+{
+    Level &v = p->lv[p->d];
+    int64_t n = v.nbox * (int64_t)p->nmodes * p->ncoef;
+    k_split_df<<<nblk(n), 256, 0, p->stream>>>(v.loc_re, n, p->locdf);
+    AFMM_LAUNCH_CHECK();
+    k_split_df<<<nblk(n), 256, 0, p->stream>>>(v.loc_im, n, p->locdf + n);
+    AFMM_LAUNCH_CHECK();
     return AFMM_OK;
 }
 

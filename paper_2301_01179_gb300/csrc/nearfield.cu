@@ -13,6 +13,7 @@
 #include <mutex>
 #include "common.cuh"
 #include "pair.cuh"
+#include "pair_df.cuh"
 
 namespace afmm {
 
@@ -32,6 +33,10 @@ struct NearArgs {
     int direct;          // 1: all sources, split into nsplit chunks
     int nsplit;
     int64_t split_len;
+    // FP64 path in FP32 pairs: amplitudes and leaf locals as (hi, lo)
+    const float2 *qdf_re, *qdf_im;
+    const float2 *locdf_re, *locdf_im;
+    float df_fwd_switch;
     // MIXED precision: FP32 amplitudes and local expansions, compensated FP32 sums
     const float *q32_re, *q32_im;
     const float *loc32_re, *loc32_im;
@@ -583,6 +588,301 @@ static size_t near2_smem(int nm, int grad)
                              (size_t)NEAR2_WB * npp * 32 + (size_t)NEAR2_WB * ncomp * mper * 32);
 }
 
+// ------------------------------------------------------------------------------------
+// FP64-path near field in FP32-pair arithmetic: the cooperative layout of k_near2 with the
+// pair sequence, the gradient factors, the accumulation and the local-expansion
+// evaluation all in double-float.  Per pair only the three coordinate differences touch
+// the FP64 pipe; the rest runs on the FP32 pipe at ~48-bit precision.
+// ------------------------------------------------------------------------------------
+template <bool GRAD>
+__device__ __forceinline__ void l2p_eval_df(const float2 *__restrict__ F, int M, dfv u, dfv v, dfv &val, dfv &du,
+                                            dfv &dv)
+{
+    dfv pu = df_make(0.f, 0.f), pdu = pu, pdv = pu;
+    for (int k = M; k >= 0; --k) {
+        int base = k * (M + 1) - k * (k - 1) / 2;
+        dfv pk = df_make(0.f, 0.f), pkd = pk;
+        for (int l = M - k; l >= 0; --l) {
+            if (GRAD) pkd = df_add(df_mul(pkd, v), pk);
+            float2 f = F[base + l];
+            pk = df_add(df_mul(pk, v), df_make(f.x, f.y));
+        }
+        if (GRAD) {
+            pdu = df_add(df_mul(pdu, u), pu);
+            pdv = df_add(df_mul(pdv, u), pkd);
+        }
+        pu = df_add(df_mul(pu, u), pk);
+    }
+    val = pu;
+    du = pdu;
+    dv = pdv;
+}
+
+#define NEARDF_WB 8
+
+// MPER: modes per warp (compile time), accumulators in registers
+template <bool GRAD, int MPER>
+__global__ void __launch_bounds__(NEARDF_WB * 32, 1) k_near_df(const NearArgs a, const RecTab tab)
+{
+    extern __shared__ double smem[];
+    constexpr int WB = NEARDF_WB;
+    constexpr int NPP = GRAD ? 5 : 1;  // per-pair df scalars: scale (, x, qfac, A, B)
+    constexpr int NC = GRAD ? 6 : 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nm = a.nmodes, N = a.N;
+    const int Nq = GRAD && N < 1 ? 1 : N;
+    const int nmq = Nq + 1;
+    float2 *gam2 = reinterpret_cast<float2 *>(smem);  // [AFMM_REC_TAB]
+    float2 *rho2 = gam2 + AFMM_REC_TAB;               // [AFMM_MAX_MODES]
+    float2 *ys = rho2 + AFMM_MAX_MODES;               // [WB][nmq][32]
+    float2 *pp = ys + (size_t)WB * nmq * 32;          // [WB][NPP][32]
+    __shared__ int rb[10], rcum[10];
+    for (int i = threadIdx.x; i < AFMM_REC_TAB; i += blockDim.x) {
+        dfv g = df_from_double(tab.gam[i]);
+        gam2[i] = make_float2(g.hi, g.lo);
+    }
+    for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+        dfv r = df_from_double(i == 0 ? 1.0 : tab.c[i - 1] / tab.c[i]);
+        rho2[i] = make_float2(r.hi, r.lo);
+    }
+    const int64_t unit = blockIdx.x;
+    int64_t t0, t1, split = 0;
+    int box = -1;
+    if (a.direct) {
+        int64_t tu = unit / a.nsplit;
+        split = unit % a.nsplit;
+        t0 = tu * 32;
+        t1 = min(t0 + 32, a.nfield);
+    } else {
+        NearUnit u = a.units[unit];
+        box = u.box;
+        t0 = u.begin;
+        t1 = u.end;
+    }
+    if (threadIdx.x == 0) {
+        int cum = 0;
+        if (a.direct) {
+            int64_t s0 = split * a.split_len, s1 = min(s0 + a.split_len, a.nsrc);
+            rb[0] = (int)s0;
+            rcum[0] = 0;
+            cum = (int)(s1 > s0 ? s1 - s0 : 0);
+            for (int k = 1; k < 10; ++k) {
+                rb[k] = 0;
+                rcum[k] = cum;
+            }
+        } else {
+            for (int k = 0; k < 9; ++k) {
+                int32_t nb = a.nbr[(int64_t)box * 9 + k];
+                int2 r = nb >= 0 ? a.srng[nb] : make_int2(0, 0);
+                rb[k] = r.x;
+                rcum[k] = cum;
+                cum += r.y - r.x;
+            }
+            rb[9] = 0;
+            rcum[9] = cum;
+        }
+    }
+    const int64_t t = t0 + lane;
+    const bool active = t < t1;
+    const int64_t tc = active ? t : t0;
+    const double rt = a.fr[tc], zt = a.fz[tc];
+    const dfv inv2r = df_from_double(0.5 / rt);
+    float aS[NC][MPER], aE[NC][MPER];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int j = 0; j < MPER; ++j) aS[c][j] = aE[c][j] = 0.f;
+    const int n0 = warp * MPER;
+    __syncthreads();
+    const int total = rcum[9];
+    for (int c0 = 0; c0 < total; c0 += WB) {
+        const int k = c0 + warp;
+        if (k < total) {
+            int rg = 0;
+            while (rg < 8 && rcum[rg + 1] <= k) ++rg;
+            const int64_t s = rb[rg] + (k - rcum[rg]);
+            const double r1 = a.sr[s], z1 = a.sz[s];
+            const dfv inv2w = df_div(inv2r, df_from_double(r1));
+            PairDF g;
+            pair_geom_df(rt, zt, r1, z1, inv2w, active, g);
+            float2 *yw = ys + (size_t)warp * nmq * 32;
+            dfv sc = pair_sequence_df(g, inv2w, Nq, a.df_fwd_switch, (float)a.pp.miller_extra, gam2, yw + lane, 32);
+            float2 *pw = pp + (size_t)warp * NPP * 32;
+            pw[lane] = make_float2(sc.hi, sc.lo);
+            if (GRAD) {
+                dfv inv = df_div(df_make(1.f, 0.f), df_mul(g.rp2, g.rm2));
+                dfv ip = df_mul(g.rm2, inv), im = df_mul(g.rp2, inv);
+                dfv As = df_mul(sc, df_add(ip, im)), Bs = df_mul(sc, df_sub(ip, im));
+                dfv qf = df_sub(df_mul(g.dr, g.sr), df_mul(g.x, g.x));
+                pw[32 + lane] = make_float2(g.x.hi, g.x.lo);
+                pw[64 + lane] = make_float2(qf.hi, qf.lo);
+                pw[96 + lane] = make_float2(As.hi, As.lo);
+                pw[128 + lane] = make_float2(Bs.hi, Bs.lo);
+            }
+        }
+        __syncthreads();
+        const int kmax = min(WB, total - c0);
+        for (int kk = 0; kk < kmax; ++kk) {
+            const int kq = c0 + kk;
+            int rg = 0;
+            while (rg < 8 && rcum[rg + 1] <= kq) ++rg;
+            const int64_t s = rb[rg] + (kq - rcum[rg]);
+            const float2 *yk = ys + (size_t)kk * nmq * 32;
+            const float2 *pk = pp + (size_t)kk * NPP * 32;
+            const dfv sc = df_make(pk[lane].x, pk[lane].y);
+            dfv gx = sc, qf = sc, As = sc, Bs = sc, yprev = sc;
+            if (GRAD) {
+                gx = df_make(pk[32 + lane].x, pk[32 + lane].y);
+                qf = df_make(pk[64 + lane].x, pk[64 + lane].y);
+                As = df_make(pk[96 + lane].x, pk[96 + lane].y);
+                Bs = df_make(pk[128 + lane].x, pk[128 + lane].y);
+                float2 yp = n0 == 0 ? yk[32 + lane] : yk[(n0 - 1) * 32 + lane];  // y_{-1} := y_1
+                yprev = df_make(yp.x, yp.y);
+            }
+#pragma unroll
+            for (int j = 0; j < MPER; ++j) {
+                const int n = n0 + j;
+                if (n < nm) {
+                    const float2 yv = yk[n * 32 + lane];
+                    const dfv yn = df_make(yv.x, yv.y);
+                    const float2 q2r = a.qdf_re[(size_t)n * a.nsrc + s], q2i = a.qdf_im[(size_t)n * a.nsrc + s];
+                    const dfv qr = df_make(q2r.x, q2r.y), qi = df_make(q2i.x, q2i.y);
+                    const dfv gn = df_mul(sc, yn);
+                    df_acc(aS[0][j], aE[0][j], qr, gn);
+                    df_acc(aS[1][j], aE[1][j], qi, gn);
+                    if (GRAD) {
+                        float2 rr = rho2[n];
+                        dfv wt = df_add(df_mul(yn, As), df_mul(df_mul(df_make(rr.x, rr.y), yprev), Bs));
+                        yprev = yn;
+                        dfv xw = df_mul(gx, wt), qw = df_mul(qf, wt);
+                        df_acc(aS[2 % NC][j], aE[2 % NC][j], qr, qw);
+                        df_acc(aS[3 % NC][j], aE[3 % NC][j], qi, qw);
+                        df_acc(aS[4 % NC][j], aE[4 % NC][j], qr, xw);
+                        df_acc(aS[5 % NC][j], aE[5 % NC][j], qi, xw);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (!active) return;
+    dfv u = df_make(0.f, 0.f), v = u;
+    if (a.locdf_re) {
+        uint32_t kk = a.leaf_key[box];
+        double cr = a.r0 + ((double)morton_ir(kk) + 0.5) * a.h, cz = a.z0 + ((double)morton_iz(kk) + 0.5) * a.h;
+        u = df_from_double((rt - cr) / a.h);
+        v = df_from_double((zt - cz) / a.h);
+    }
+    const int64_t dst = a.out_perm ? a.out_perm[t] : t;
+#pragma unroll
+    for (int j = 0; j < MPER; ++j) {
+        const int n = n0 + j;
+        if (n >= nm) continue;
+        double pr = (double)aS[0][j] + (double)aE[0][j];
+        double pi = (double)aS[1][j] + (double)aE[1][j];
+        double dr_r = 0, dr_i = 0, dz_r = 0, dz_i = 0;
+        if (GRAD) {
+            double nu = n - 0.5;
+            dr_r = (nu * ((double)aS[2 % NC][j] + (double)aE[2 % NC][j]) - pr) * (0.5 / rt);
+            dr_i = (nu * ((double)aS[3 % NC][j] + (double)aE[3 % NC][j]) - pi) * (0.5 / rt);
+            dz_r = nu * ((double)aS[4 % NC][j] + (double)aE[4 % NC][j]);
+            dz_i = nu * ((double)aS[5 % NC][j] + (double)aE[5 % NC][j]);
+        }
+        if (a.locdf_re) {
+            const float2 *Fr = a.locdf_re + ((size_t)box * nm + n) * a.ncoef;
+            const float2 *Fi = a.locdf_im + ((size_t)box * nm + n) * a.ncoef;
+            dfv vr, dur, dvr, vi, dui, dvi;
+            l2p_eval_df<GRAD>(Fr, a.M, u, v, vr, dur, dvr);
+            l2p_eval_df<GRAD>(Fi, a.M, u, v, vi, dui, dvi);
+            pr += df_to_double(vr);
+            pi += df_to_double(vi);
+            if (GRAD) {
+                double ih = 1.0 / a.h;
+                dr_r += df_to_double(dur) * ih;
+                dr_i += df_to_double(dui) * ih;
+                dz_r += df_to_double(dvr) * ih;
+                dz_i += df_to_double(dvi) * ih;
+            }
+        }
+        if (a.part) {
+            size_t base = (size_t)split * NC;
+            size_t nfm = (size_t)a.nfield;
+            a.part[((base + 0) * nm + n) * nfm + t] = pr;
+            a.part[((base + 1) * nm + n) * nfm + t] = pi;
+            if (GRAD) {
+                a.part[((base + 2) * nm + n) * nfm + t] = dr_r;
+                a.part[((base + 3) * nm + n) * nfm + t] = dr_i;
+                a.part[((base + 4) * nm + n) * nfm + t] = dz_r;
+                a.part[((base + 5) * nm + n) * nfm + t] = dz_i;
+            }
+        } else {
+            size_t od = (size_t)n * a.nfield + dst;
+            if (a.o_re) a.o_re[od] = pr;
+            if (a.o_im) a.o_im[od] = pi;
+            if (GRAD) {
+                a.o_dr_re[od] = dr_r;
+                a.o_dr_im[od] = dr_i;
+                a.o_dz_re[od] = dz_r;
+                a.o_dz_im[od] = dz_i;
+            }
+        }
+    }
+}
+
+static size_t neardf_smem(int nm, int grad)
+{
+    int Nq = (grad && nm < 2) ? 1 : nm - 1;
+    int npp = grad ? 5 : 1;
+    return sizeof(double) * ((size_t)AFMM_REC_TAB + AFMM_MAX_MODES + (size_t)NEARDF_WB * (Nq + 1) * 32 +
+                             (size_t)NEARDF_WB * npp * 32);
+}
+
+template <bool GRAD, int MPER>
+static afmm_status launch_near_df_k(const NearArgs &a, const RecTab &tab, cudaStream_t st)
+{
+    size_t sm = neardf_smem(a.nmodes, GRAD);
+    if (sm > 227 * 1024) return AFMM_EUNSUPPORTED;
+    AFMM_CUDA(cudaFuncSetAttribute(k_near_df<GRAD, MPER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_near_df<GRAD, MPER><<<(unsigned)a.nunits, NEARDF_WB * 32, sm, st>>>(a, tab);
+    AFMM_LAUNCH_CHECK();
+    return AFMM_OK;
+}
+
+template <bool GRAD>
+static afmm_status launch_near_df(const NearArgs &a, const RecTab &tab, cudaStream_t st)
+{
+    int mper = (a.nmodes + NEARDF_WB - 1) / NEARDF_WB;
+    if (mper <= 1) return launch_near_df_k<GRAD, 1>(a, tab, st);
+    if (mper <= 2) return launch_near_df_k<GRAD, 2>(a, tab, st);
+    if (mper <= 3) return launch_near_df_k<GRAD, 3>(a, tab, st);
+    if (mper <= 4) return launch_near_df_k<GRAD, 4>(a, tab, st);
+    if (mper <= 5) return launch_near_df_k<GRAD, 5>(a, tab, st);
+    if (mper <= 9) return launch_near_df_k<GRAD, 9>(a, tab, st);
+    if (mper <= 17) return launch_near_df_k<GRAD, 17>(a, tab, st);
+    return AFMM_EUNSUPPORTED;
+}
+
+// strengths into sorted order, times c_n, as FP32 pairs (FP64 path; the FP64 copy feeds the
+// far field)
+__global__ void k_permute_df(const double *__restrict__ q_re, const double *__restrict__ q_im,
+                             const int32_t *__restrict__ perm, int64_t n, int nm, const RecTab tab,
+                             double *__restrict__ qs_re, double *__restrict__ qs_im, float2 *__restrict__ qd_re,
+                             float2 *__restrict__ qd_im)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n * nm) return;
+    int m = (int)(i / n);
+    int64_t j = i % n;
+    size_t src = (size_t)m * n + perm[j];
+    double c = tab.c[m];
+    double vr = q_re[src] * c, vi = q_im[src] * c;
+    qs_re[i] = vr;
+    qs_im[i] = vi;
+    dfv a = df_from_double(vr), b = df_from_double(vi);
+    qd_re[i] = make_float2(a.hi, a.lo);
+    qd_im[i] = make_float2(b.hi, b.lo);
+}
+
 // sum of split partials into the caller layout
 __global__ void k_split_reduce(const double *__restrict__ part, int nsplit, int ncomp, int nm, int64_t nfield,
                                const int32_t *__restrict__ perm, double *o0, double *o1, double *o2, double *o3,
@@ -693,6 +993,9 @@ afmm_status launch_permute(afmm_plan p, int dir, const double *q_re, const doubl
     if (p->precision == AFMM_MIXED)
         k_permute32<<<nblk(n * p->nmodes), 256, 0, p->stream>>>(q_re, q_im, perm, n, p->nmodes, *p->rec, p->qs32_re,
                                                                  p->qs32_im);
+    else if (p->precision == AFMM_FP64)
+        k_permute_df<<<nblk(n * p->nmodes), 256, 0, p->stream>>>(q_re, q_im, perm, n, p->nmodes, *p->rec, p->qs_re,
+                                                                  p->qs_im, p->qsdf, p->qsdf + (size_t)p->nmodes * p->n_max);
     else
         k_permute<<<nblk(n * p->nmodes), 256, 0, p->stream>>>(q_re, q_im, perm, n, p->nmodes, *p->rec, p->qs_re,
                                                                p->qs_im);
@@ -767,10 +1070,24 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
     }
     if (a.nunits == 0) return AFMM_OK;
     size_t sm = near2_smem(p->nmodes, grad);
-    if (sm > 227 * 1024) return AFMM_EUNSUPPORTED;
     unsigned grid = (unsigned)a.nunits;
     const int T = NEAR2_WB * 32;
-    if (grad && mix) {
+    if (p->precision != AFMM_FP64 && sm > 227 * 1024) return AFMM_EUNSUPPORTED;
+    if (p->precision == AFMM_FP64) {
+        a.qdf_re = p->qsdf;
+        a.qdf_im = p->qsdf + (size_t)p->nmodes * p->n_max;
+        if (a.loc_re) {
+            a.locdf_re = p->locdf;
+            a.locdf_im = p->locdf + (size_t)p->lv[d].nbox * p->nmodes * p->ncoef;
+            a.loc_re = nullptr;
+            a.loc_im = nullptr;
+        }
+        a.df_fwd_switch = (float)p->df_fwd_switch;
+        if (grad)
+            AFMM_TRY(launch_near_df<true>(a, *p->rec, p->stream));
+        else
+            AFMM_TRY(launch_near_df<false>(a, *p->rec, p->stream));
+    } else if (grad && mix) {
         AFMM_CUDA(cudaFuncSetAttribute(k_near2<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_near2<true, true><<<grid, T, sm, p->stream>>>(a, *p->rec);
     } else if (grad) {
@@ -783,7 +1100,7 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
         AFMM_CUDA(cudaFuncSetAttribute(k_near2<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_near2<false, false><<<grid, T, sm, p->stream>>>(a, *p->rec);
     }
-    AFMM_LAUNCH_CHECK();
+    if (p->precision != AFMM_FP64) AFMM_LAUNCH_CHECK();
     if (a.part) {
         int ncomp = grad ? 6 : 2;
         int64_t tot = (int64_t)ncomp * a.nmodes * a.nfield;

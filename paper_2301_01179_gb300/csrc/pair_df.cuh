@@ -1,0 +1,116 @@
+// pair_df.cuh -- the per-pair modal Green's function sequence of pair.cuh, in FP32-pair
+// (double-float) arithmetic: same start values (G^(0) = 1/(2 AGM(rho_+, rho_-)), G^(1) from
+// the AGM half-difference sum), same scaled Legendre recursion (Eq. gfunc:recursion), same
+// forward / Miller choice, ~48-bit precision.  Only the cancelling coordinate differences
+// r - r1 and z - z1 (and r + r1) are formed in FP64 and split exactly.
+//
+// Precision budget: the forward sweep amplifies rounding by about exp(2 N acosh chi); with
+// df rounding ~2^-47 the forward switch is lowered (df_fwd_switch) so that this stays
+// below ~5e-12, and pairs beyond it use Miller's sweep, which is cheap in FP32 pairs.
+#pragma once
+#include "common.cuh"
+#include "df.cuh"
+
+namespace afmm {
+
+struct PairDF {
+    dfv x;     // z_field - z_source
+    dfv dr;    // r - r1
+    dfv sr;    // r + r1
+    dfv rm2;   // rho_-^2 (rho_+^2 for coincident / inactive pairs)
+    dfv rp2;   // rho_+^2
+    dfv chi;   // 1 + rho_-^2 / (2 r r1)
+    float t;   // chi - 1 (FP32, regime decision only)
+    float zero;
+};
+
+__device__ __forceinline__ void pair_geom_df(double rt, double zt, double r1, double z1, dfv inv2w, bool active,
+                                             PairDF &g)
+{
+    g.x = df_from_double(zt - z1);
+    g.dr = df_from_double(rt - r1);
+    g.sr = df_from_double(rt + r1);
+    dfv x2 = df_mul(g.x, g.x);
+    dfv rm2 = df_add(df_mul(g.dr, g.dr), x2);
+    dfv rp2 = df_add(df_mul(g.sr, g.sr), x2);
+    bool coinc = !(rm2.hi > 0.f) || !active;
+    g.zero = coinc ? 0.f : 1.f;
+    if (coinc) rm2 = rp2;
+    g.rm2 = rm2;
+    g.rp2 = rp2;
+    dfv t = df_mul(rm2, inv2w);
+    g.t = t.hi;
+    g.chi = df_add(df_make(1.f, 0.f), t);
+}
+
+// Writes y_n (n = 0..N) as FP32 pairs to ys[n * stride] and returns the df factor s with
+// G_n = s * c_n * y_n.  gam2: recursion constants gam_n as FP32 pairs (shared memory).
+__device__ __forceinline__ dfv pair_sequence_df(const PairDF &g, dfv inv2w, int N, float fwd_switch, float extra,
+                                                const float2 *__restrict__ gam2, float2 *ys, int stride)
+{
+    float tf = g.t;
+    float af = log1pf(tf + sqrtf(tf * (tf + 2.0f)));  // acosh(chi)
+    int Nr = N < 1 ? 1 : N;
+    bool fwd = (2.0f * (float)Nr * af <= fwd_switch) && (af <= 0.96f);
+    // AGM of (rho_+, rho_-) with the half-difference sum for G^(1)
+    dfv a = df_sqrt(g.rp2), b = df_sqrt(g.rm2);
+    dfv csum = df_make(0.f, 0.f);
+    float w = 1.f;
+    for (int it = 0; it < 40; ++it) {
+        dfv c = df_scale2(df_sub(a, b), 0.5f);
+        csum = df_add(csum, df_scale2(df_mul(c, c), w));
+        w *= 2.f;
+        dfv an = df_scale2(df_add(a, b), 0.5f);
+        b = df_sqrt(df_mul(a, b));
+        a = an;
+        if (c.hi <= 1e-7f * a.hi) break;
+    }
+    dfv G0 = df_div(df_make(0.5f, 0.f), a);
+    int L = N + 2;
+    if (!fwd) {
+        float lf = ceilf(extra / fmaxf(af, 1e-6f));
+        int ext = lf > (float)AFMM_REC_TAB ? AFMM_REC_TAB : (int)lf;
+        L = N + ext + 2;
+        if (L > AFMM_REC_TAB - 1) L = AFMM_REC_TAB - 1;
+    }
+    dfv y0, y1;
+    if (fwd) {
+        y0 = G0;
+        y1 = df_mul(df_mul(G0, csum), inv2w);
+        ys[0] = make_float2(y0.hi, y0.lo);
+        if (N >= 1) ys[stride] = make_float2(y1.hi, y1.lo);
+    } else {
+        y0 = df_make(0.f, 0.f);           // y_L
+        y1 = df_make(7.8886091e-31f, 0.f); // y_{L-1} = 2^-100
+    }
+    int steps = fwd ? N - 1 : L - 1;
+    int smax = steps;
+    for (int o = 16; o > 0; o >>= 1) smax = max(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+    for (int s = 0; s < smax; ++s) {
+        if (s < steps) {
+            int n = fwd ? s + 2 : L - s;
+            float2 gm = gam2[n];
+            dfv yn = df_sub(df_mul(df_mul(df_make(gm.x, gm.y), g.chi), y1), y0);
+            y0 = y1;
+            y1 = yn;
+            int idx = fwd ? n : n - 2;
+            if (idx <= N) ys[idx * stride] = make_float2(yn.hi, yn.lo);
+            if (!fwd && fabsf(yn.hi) > 1.2676506e30f) {  // > 2^100: rescale by 2^-100 (exact)
+                const float s100 = 7.8886091e-31f;
+                y0 = df_scale2(y0, s100);
+                y1 = df_scale2(y1, s100);
+                for (int m = idx; m <= N; ++m)
+                    if (m >= 0) {
+                        float2 v = ys[m * stride];
+                        ys[m * stride] = make_float2(v.x * s100, v.y * s100);
+                    }
+            }
+        }
+    }
+    if (fwd) return df_make(g.zero, 0.f);
+    float2 y0s = ys[0];
+    dfv sc = df_div(G0, df_make(y0s.x, y0s.y));
+    return df_make(sc.hi * g.zero, sc.lo * g.zero);
+}
+
+}  // namespace afmm
