@@ -622,7 +622,7 @@ __device__ __forceinline__ void l2p_eval_df(const float2 *__restrict__ F, int M,
 
 // MPER: modes per warp (compile time), accumulators in registers
 template <bool GRAD, int MPER>
-__global__ void __launch_bounds__(NEARDF_WB * 32, 1) k_near_df(const NearArgs a, const RecTab tab)
+__global__ void __launch_bounds__(NEARDF_WB * 32, (MPER <= 5 ? 2 : 1)) k_near_df(const NearArgs a, const RecTab tab)
 {
     extern __shared__ double smem[];
     constexpr int WB = NEARDF_WB;
@@ -637,6 +637,7 @@ __global__ void __launch_bounds__(NEARDF_WB * 32, 1) k_near_df(const NearArgs a,
     float2 *ys = rho2 + AFMM_MAX_MODES;               // [WB][nmq][32]
     float2 *pp = ys + (size_t)WB * nmq * 32;          // [WB][NPP][32]
     __shared__ int rb[10], rcum[10];
+    __shared__ int sidx[WB * 32];  // source of each (warp, lane) pair of the chunk
     for (int i = threadIdx.x; i < AFMM_REC_TAB; i += blockDim.x) {
         dfv g = df_from_double(tab.gam[i]);
         gam2[i] = make_float2(g.hi, g.lo);
@@ -682,7 +683,13 @@ __global__ void __launch_bounds__(NEARDF_WB * 32, 1) k_near_df(const NearArgs a,
             rcum[9] = cum;
         }
     }
-    const int64_t t = t0 + lane;
+    // lane packing: the unit's c targets take T = 2^ceil(log2 c) lanes, and the 32 / T lane
+    // groups (slices) take interleaved sources; the slices are summed at the end
+    const int cnt = (int)(t1 - t0);
+    const int lgT = cnt <= 1 ? 0 : 32 - __clz(cnt - 1);
+    const int S = 32 >> lgT;
+    const int tl = lane & ((1 << lgT) - 1), slice = lane >> lgT;
+    const int64_t t = t0 + tl;
     const bool active = t < t1;
     const int64_t tc = active ? t : t0;
     const double rt = a.fr[tc], zt = a.fz[tc];
@@ -695,20 +702,24 @@ __global__ void __launch_bounds__(NEARDF_WB * 32, 1) k_near_df(const NearArgs a,
     const int n0 = warp * MPER;
     __syncthreads();
     const int total = rcum[9];
-    for (int c0 = 0; c0 < total; c0 += WB) {
-        const int k = c0 + warp;
-        if (k < total) {
+    const int per_chunk = WB * S;
+    for (int c0 = 0; c0 < total; c0 += per_chunk) {
+        if (c0 + warp * S < total) {  // warp-uniform
+            int k = c0 + warp * S + slice;
+            const bool valid = k < total;
+            if (!valid) k = total - 1;
             int rg = 0;
             while (rg < 8 && rcum[rg + 1] <= k) ++rg;
             const int64_t s = rb[rg] + (k - rcum[rg]);
             const double r1 = a.sr[s], z1 = a.sz[s];
             const dfv inv2w = df_div(inv2r, df_from_double(r1));
             PairDF g;
-            pair_geom_df(rt, zt, r1, z1, inv2w, active, g);
+            pair_geom_df(rt, zt, r1, z1, inv2w, active && valid, g);
             float2 *yw = ys + (size_t)warp * nmq * 32;
             dfv sc = pair_sequence_df(g, inv2w, Nq, a.df_fwd_switch, (float)a.pp.miller_extra, gam2, yw + lane, 32);
             float2 *pw = pp + (size_t)warp * NPP * 32;
             pw[lane] = make_float2(sc.hi, sc.lo);
+            sidx[warp * 32 + lane] = (int)s;
             if (GRAD) {
                 dfv inv = df_div(df_make(1.f, 0.f), df_mul(g.rp2, g.rm2));
                 dfv ip = df_mul(g.rm2, inv), im = df_mul(g.rp2, inv);
@@ -721,12 +732,9 @@ __global__ void __launch_bounds__(NEARDF_WB * 32, 1) k_near_df(const NearArgs a,
             }
         }
         __syncthreads();
-        const int kmax = min(WB, total - c0);
+        const int kmax = min(WB, (total - c0 + S - 1) / S);
         for (int kk = 0; kk < kmax; ++kk) {
-            const int kq = c0 + kk;
-            int rg = 0;
-            while (rg < 8 && rcum[rg + 1] <= kq) ++rg;
-            const int64_t s = rb[rg] + (kq - rcum[rg]);
+            const int64_t s = sidx[kk * 32 + lane];
             const float2 *yk = ys + (size_t)kk * nmq * 32;
             const float2 *pk = pp + (size_t)kk * NPP * 32;
             const dfv sc = df_make(pk[lane].x, pk[lane].y);
@@ -765,7 +773,17 @@ __global__ void __launch_bounds__(NEARDF_WB * 32, 1) k_near_df(const NearArgs a,
         }
         __syncthreads();
     }
-    if (!active) return;
+    // sum the slices in FP64: cs[q][j] on every lane of target tl
+    double cs[NC][MPER];
+#pragma unroll
+    for (int q = 0; q < NC; ++q)
+#pragma unroll
+        for (int j = 0; j < MPER; ++j) {
+            double v = (double)aS[q][j] + (double)aE[q][j];
+            for (int o = 1 << lgT; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            cs[q][j] = v;
+        }
+    if (!active || slice != 0) return;
     dfv u = df_make(0.f, 0.f), v = u;
     if (a.locdf_re) {
         uint32_t kk = a.leaf_key[box];
@@ -778,15 +796,15 @@ __global__ void __launch_bounds__(NEARDF_WB * 32, 1) k_near_df(const NearArgs a,
     for (int j = 0; j < MPER; ++j) {
         const int n = n0 + j;
         if (n >= nm) continue;
-        double pr = (double)aS[0][j] + (double)aE[0][j];
-        double pi = (double)aS[1][j] + (double)aE[1][j];
+        double pr = cs[0][j];
+        double pi = cs[1][j];
         double dr_r = 0, dr_i = 0, dz_r = 0, dz_i = 0;
         if (GRAD) {
             double nu = n - 0.5;
-            dr_r = (nu * ((double)aS[2 % NC][j] + (double)aE[2 % NC][j]) - pr) * (0.5 / rt);
-            dr_i = (nu * ((double)aS[3 % NC][j] + (double)aE[3 % NC][j]) - pi) * (0.5 / rt);
-            dz_r = nu * ((double)aS[4 % NC][j] + (double)aE[4 % NC][j]);
-            dz_i = nu * ((double)aS[5 % NC][j] + (double)aE[5 % NC][j]);
+            dr_r = (nu * cs[2 % NC][j] - pr) * (0.5 / rt);
+            dr_i = (nu * cs[3 % NC][j] - pi) * (0.5 / rt);
+            dz_r = nu * cs[4 % NC][j];
+            dz_i = nu * cs[5 % NC][j];
         }
         if (a.locdf_re) {
             const float2 *Fr = a.locdf_re + ((size_t)box * nm + n) * a.ncoef;
