@@ -37,14 +37,19 @@ typedef enum {
     AFMM_EINVAL = 1,       /* bad size, option, NULL pointer, r <= 0 or non-finite coordinate */
     AFMM_ENOMEM = 2,       /* device allocation failed */
     AFMM_ECUDA = 3,        /* a CUDA call or kernel launch failed (see afmm_last_cuda_error) */
-    AFMM_ETIMEOUT = 4,     /* reserved: a bounded device-side wait ran out */
+    AFMM_ETIMEOUT = 4,     /* a bounded device-side wait (the completion barrier of the
+                              tensor-core S2L) ran out during an earlier evaluation on this
+                              plan; that evaluation's results are invalid.  Reported once, by
+                              the next call on the plan. */
     AFMM_EUNSUPPORTED = 5  /* valid request the library does not implement (e.g. depth > 16) */
 } afmm_status;
 
 typedef enum {
     AFMM_FP64 = 0,        /* FP64-accurate results (parity 1e-10 with an FP64 reference): FP64
                              where precision demands it, FP32-pair ("double-float") arithmetic
-                             where it is exact enough and faster on GB300 (the S2L contraction) */
+                             where it is exact enough and faster on GB300 (near field, L2P), and
+                             the S2L contraction on the bf16 tensor cores by exact 8-bit digit
+                             slicing (48-bit operands, see s2l_engine) */
     AFMM_MIXED = 1,       /* FP64 Legendre recursion and elliptic start values; FP32 bulk
                              accumulation (compensated) and FP32 expansions (Sec. 2 with scaled
                              coordinates, Eq. gfunc:scaled) */
@@ -64,6 +69,9 @@ typedef struct {
                            the forward sweep's error growth below ~2e-12).  The paper's
                            fixed switch is chi < 1.008 (Appendix A). */
     int miller_extra;   /* Miller start L = N + ceil(miller_extra / acosh(chi)) + 2 (0: 15) */
+    int s2l_engine;     /* AFMM_FP64 only. 0: S2L (Eq. analysis:s2l) on the tcgen05 tensor
+                           cores when order <= 12, else on CUDA cores; 1: always on CUDA
+                           cores in FP32-pair arithmetic */
 } afmm_options;
 
 typedef struct afmm_plan_s *afmm_plan;

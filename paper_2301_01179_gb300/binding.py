@@ -33,7 +33,8 @@ class AfmmError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("leaf_size", ctypes.c_int), ("depth_override", ctypes.c_int),
-                ("precision", ctypes.c_int), ("fwd_switch", ctypes.c_double), ("miller_extra", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("fwd_switch", ctypes.c_double), ("miller_extra", ctypes.c_int),
+                ("s2l_engine", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -129,12 +130,13 @@ class Plan:
     """A quadtree plan over sources and field points (afmm_plan_create).
 
     Parameters mirror ``afmm_options``: ``order`` (M), ``leaf_size``, ``depth`` (0 = rule),
-    ``precision`` ("fp64", "mixed" or "fp64_native"), ``fwd_switch``, ``miller_extra``.  The plan is bound
+    ``precision`` ("fp64", "mixed" or "fp64_native"), ``fwd_switch``, ``miller_extra``,
+    ``s2l_engine`` ("auto": tensor cores where supported, "cuda_cores").  The plan is bound
     to the current torch stream at creation.
     """
 
     def __init__(self, src_r, src_z, tgt_r, tgt_z, n_modes, order=8, leaf_size=32, depth=0, precision="fp64",
-                 fwd_switch=0.0, miller_extra=0):
+                 fwd_switch=0.0, miller_extra=0, s2l_engine="auto"):
         lib = load()
         self._lib = lib
         self.ns = int(src_r.numel())
@@ -149,6 +151,7 @@ class Plan:
         opt.precision = _PREC[precision]
         opt.fwd_switch = float(fwd_switch)
         opt.miller_extra = int(miller_extra)
+        opt.s2l_engine = {"auto": 0, "cuda_cores": 1}[s2l_engine]
         h = ctypes.c_void_p()
         st = lib.afmm_plan_create(ctypes.byref(h), self.ns, _ptr(src_r), _ptr(src_z), self.nf, _ptr(tgt_r),
                                   _ptr(tgt_z), self.n_modes, ctypes.byref(opt), _stream())

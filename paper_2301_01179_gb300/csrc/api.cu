@@ -82,6 +82,7 @@ void afmm_options_default(afmm_options *opt)
     opt->precision = AFMM_FP64;
     opt->fwd_switch = 0.0;
     opt->miller_extra = 0;
+    opt->s2l_engine = 0;
 }
 
 const char *afmm_status_string(afmm_status s)
@@ -104,6 +105,8 @@ void afmm_plan_destroy(afmm_plan p)
     if (!p) return;
     cudaStreamSynchronize(p->stream);
     for (int i = 0; i < p->nalloc; ++i) cudaFree(p->allocs[i]);
+    if (p->err_host) cudaFreeHost(p->err_host);
+    delete p->tct;
     if (p->timing)
         for (int i = 0; i < 80; ++i) cudaEventDestroy(p->ev[i]);
     delete p->rec;
@@ -125,7 +128,8 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
     if (n_modes < 1 || n_modes > AFMM_MAX_MODES) return AFMM_EINVAL;
     if (!src_r || !src_z || !tgt_r || !tgt_z) return AFMM_EINVAL;
     if (opt.order < 0 || opt.leaf_size < 1 || opt.depth_override < 0 || opt.depth_override == 1 ||
-        opt.depth_override > AFMM_MAX_LEVEL || opt.fwd_switch < 0.0 || opt.miller_extra < 0)
+        opt.depth_override > AFMM_MAX_LEVEL || opt.fwd_switch < 0.0 || opt.miller_extra < 0 ||
+        (opt.s2l_engine != 0 && opt.s2l_engine != 1))
         return AFMM_EINVAL;
     if (opt.precision != AFMM_FP64 && opt.precision != AFMM_MIXED && opt.precision != AFMM_FP64_NATIVE)
         return AFMM_EINVAL;
@@ -195,7 +199,24 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
         int64_t mmax = 0;
         for (int l = 2; l <= p->d; ++l) mmax = p->lv[l].nbox > mmax ? p->lv[l].nbox : mmax;
         if (gcap > 0) s = dalloc_t(p, &p->gexp_df, gcap);
-        if (s == AFMM_OK) s = dalloc_t(p, &p->mom_df, (size_t)2 * mmax * nm * nc);
+        if (s2l_tc_enabled(p)) {
+            if (s == AFMM_OK) s = dalloc_t(p, &p->asl, (size_t)s2l_tc_slice_elems(p, mmax));
+            if (s == AFMM_OK) s = make_tc_tables(p);
+        } else if (s == AFMM_OK) {
+            s = dalloc_t(p, &p->mom_df, (size_t)2 * mmax * nm * nc);
+        }
+    }
+    // device-side error word in mapped host memory (set by kernels whose bounded waits run out)
+    if (s == AFMM_OK) {
+        cudaError_t e = cudaHostAlloc((void **)&p->err_host, sizeof(int), cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&p->err_dev, p->err_host, 0);
+        if (e != cudaSuccess) {
+            set_cuda_error(e);
+            cudaGetLastError();
+            s = AFMM_ECUDA;
+        } else {
+            *(volatile int *)p->err_host = 0;
+        }
     }
     // direct sums over few field points are split over sources: room for the partials
     // of up to 64 splits of the smaller point set, at most 1 GB
@@ -265,9 +286,20 @@ afmm_status afmm_get_timing(afmm_plan p, const char *name, double *ms)
     return AFMM_EINVAL;
 }
 
+// a bounded device-side wait of an earlier evaluation ran out: report it once
+static afmm_status take_device_error(afmm_plan p)
+{
+    if (p->err_host && *(volatile int *)p->err_host) {
+        *(volatile int *)p->err_host = 0;
+        return AFMM_ETIMEOUT;
+    }
+    return AFMM_OK;
+}
+
 static afmm_status run_fmm(afmm_plan p, int dir, const double *q_re, const double *q_im, int grad, double *o_re,
                            double *o_im, double *dr_re, double *dr_im, double *dz_re, double *dz_im)
 {
+    AFMM_TRY(take_device_error(p));
     tmark(p, 0);
     AFMM_TRY(launch_permute(p, dir, q_re, q_im));
     tmark(p, 1);
@@ -293,6 +325,7 @@ static afmm_status run_fmm(afmm_plan p, int dir, const double *q_re, const doubl
         p->t_ms[3] = g;
         p->t_ms[4] = s2;
         p->t_ms[5] = l2;
+        AFMM_TRY(take_device_error(p));
     }
     return AFMM_OK;
 }

@@ -100,6 +100,26 @@ __host__ __device__ inline uint32_t morton_key(uint32_t ir, uint32_t iz)
 __host__ __device__ inline uint32_t morton_ir(uint32_t k) { return morton_compact(k >> 1); }
 __host__ __device__ inline uint32_t morton_iz(uint32_t k) { return morton_compact(k); }
 
+// S2L list offsets for a field box with radial parity pr and axial parity pz: children of
+// the parent's 3x3 neighbours that are not neighbours of the box (Sec. 2.2).  Slot order:
+// dr from -2-pr to 3-pr, dz from -2-pz to 3-pz, skipping |dr|,|dz| <= 1.
+__host__ __device__ inline void s2l_offset(int pr, int pz, int slot, int *dr, int *dz)
+{
+    int s = 0;
+    for (int a = -2 - pr; a <= 3 - pr; ++a)
+        for (int b = -2 - pz; b <= 3 - pz; ++b) {
+            if (a >= -1 && a <= 1 && b >= -1 && b <= 1) continue;
+            if (s == slot) {
+                *dr = a;
+                *dz = b;
+                return;
+            }
+            ++s;
+        }
+    *dr = 0;
+    *dz = 0;
+}
+
 struct Level {
     int64_t nbox = 0;
     uint32_t *key = nullptr;     // [nbox] Morton key at this level (2l bits), sorted
@@ -112,6 +132,9 @@ struct Level {
     int64_t nunit = 0;           // S2L work units: up to 32 boxes of one column and parity
     int32_t *unit_box = nullptr; // [nunit][32] box indices (-1 pad)
     int32_t *unit_col = nullptr; // [nunit] column (radial index) | axial parity << 30
+    int64_t nunit64 = 0;           // the same in groups of up to 64 boxes (tensor-core S2L)
+    int32_t *unit64_box = nullptr; // [nunit64][64]
+    int32_t *unit64_col = nullptr; // [nunit64]
     int nstation = 0;            // occupied columns
     int32_t *station_of_col = nullptr;  // [2^l] compact station index or -1
     int32_t *col_of_station = nullptr;  // [nstation]
@@ -119,6 +142,13 @@ struct Level {
     double *loc_re = nullptr, *loc_im = nullptr;  // [nbox][nmodes][ncoef]
     float *mom32_re = nullptr, *mom32_im = nullptr;  // MIXED: [nbox][nmodes][ncoef]
     float *loc32_re = nullptr, *loc32_im = nullptr;
+};
+
+// tensor-core S2L: factor tables and coefficient-index maps (host-built, passed by value)
+struct TcTables {
+    float2 rjl[14 * 14];      // 1 / (j! l!) as FP32 pairs, j, l <= 13
+    float jfact[14];          // j! (exact in FP32 up to 13!)
+    int8_t ci[128], cj[128];  // coefficient index -> (first, second) exponent
 };
 
 struct NearUnit {       // one warp of near-field work: up to 32 field points of one leaf
@@ -155,6 +185,9 @@ struct afmm_plan_s {
     double *gexp = nullptr;                     // expansions of one level
     float2 *gexp_df = nullptr;                  // FP64 path: the same as FP32 pairs
     float2 *mom_df = nullptr;                   // FP64 path: moments of one level as FP32 pairs [2][...]
+    uint16_t *asl = nullptr;                    // tensor-core S2L: bf16 digit slices of the moments of one level
+    afmm::TcTables *tct = nullptr;              // tensor-core S2L tables (host)
+    int *err_host = nullptr, *err_dev = nullptr;  // device-side error word (mapped host memory)
     int64_t gexp_cap = 0;                       // doubles
     double *m2m_tab = nullptr;                  // [4][2][(M+1)^2] shift tables (see farfield.cu)
     double *l2l_tab = nullptr;
@@ -196,4 +229,9 @@ afmm_status launch_green_expansion(int64_t npts, const double *r, const double *
                                    int n_modes, int P, double *out, cudaStream_t st);
 afmm_status make_shift_tables(afmm_plan p);
 afmm_status split_leaf_locals(afmm_plan p);
+// s2l_tc.cu
+bool s2l_tc_enabled(afmm_plan p);
+int64_t s2l_tc_slice_elems(afmm_plan p, int64_t nbox);
+afmm_status make_tc_tables(afmm_plan p);
+afmm_status launch_s2l_tc(afmm_plan p, int l, const double *mre, const double *mim, double *lre, double *lim);
 }  // namespace afmm

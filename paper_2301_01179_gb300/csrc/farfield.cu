@@ -506,28 +506,6 @@ afmm_status launch_green_expansion(int64_t npts, const double *r, const double *
     return AFMM_OK;
 }
 
-// ------------------------------------------------------------------------------------
-// S2L: one block per (unit of <= 32 field boxes of one column and axial parity, mode).
-// For each of the 27 list slots the expansion slab (oriented FO/BO/FI/BI) and the 32
-// source moment vectors are staged in shared memory; each thread owns one box (lane) and
-// a strided subset of the output coefficients (warp), accumulated in registers.
-// ------------------------------------------------------------------------------------
-__host__ __device__ inline void s2l_offset_ff(int pr, int pz, int slot, int *dr, int *dz)
-{
-    int s = 0;
-    for (int a = -2 - pr; a <= 3 - pr; ++a)
-        for (int b = -2 - pz; b <= 3 - pz; ++b) {
-            if (a >= -1 && a <= 1 && b >= -1 && b <= 1) continue;
-            if (s == slot) {
-                *dr = a;
-                *dz = b;
-                return;
-            }
-            ++s;
-        }
-    *dr = 0;
-    *dz = 0;
-}
 
 template <typename R>
 struct S2LArgs {
@@ -574,7 +552,7 @@ __global__ void __launch_bounds__(128) k_s2l(const S2LArgs<R> a)
     const size_t slabn = (size_t)slab;
     for (int slot = 0; slot < 27; ++slot) {
         int dr, dz;
-        s2l_offset_ff(pr, pz, slot, &dr, &dz);
+        s2l_offset(pr, pz, slot, &dr, &dz);
         int scol = col + dr;
         if (scol < 0 || scol >= nl) continue;
         __syncthreads();
@@ -709,7 +687,7 @@ __global__ void __launch_bounds__(128) k_s2l_df(const S2LArgs<double> a)
     const size_t slabn = (size_t)slab;
     for (int slot = 0; slot < 27; ++slot) {
         int dr, dz;
-        s2l_offset_ff(pr, pz, slot, &dr, &dz);
+        s2l_offset(pr, pz, slot, &dr, &dz);
         int scol = col + dr;
         if (scol < 0 || scol >= nl) continue;
         __syncthreads();
@@ -821,6 +799,8 @@ static afmm_status launch_s2l(afmm_plan p, int l, const R *mre, const R *mim, R 
     int W = p->M + 1;
     size_t sm = sizeof(R) * ((size_t)W * W * (2 * p->M + 1) + 2 * (size_t)p->ncoef * 32);
     int kpt = (p->ncoef + 3) / 4;
+    if (sizeof(R) == sizeof(double) && s2l_tc_enabled(p))
+        return launch_s2l_tc(p, l, (const double *)mre, (const double *)mim, (double *)lre, (double *)lim);
     if (sizeof(R) == sizeof(double) && p->precision == AFMM_FP64) {
         // FP64 path: FP32-pair arithmetic (same shared-memory size: float2 per entry)
         const S2LArgs<double> &ad = reinterpret_cast<const S2LArgs<double> &>(a);
@@ -913,10 +893,12 @@ static afmm_status far_field_t(afmm_plan p, int dir)
                 k_split_df<<<nblk(ng), 256, 0, st>>>(p->gexp, ng, p->gexp_df);
                 AFMM_LAUNCH_CHECK();
             }
-            k_split_df<<<nblk(nmom), 256, 0, st>>>((const double *)MR(l), nmom, p->mom_df);
-            AFMM_LAUNCH_CHECK();
-            k_split_df<<<nblk(nmom), 256, 0, st>>>((const double *)MI(l), nmom, p->mom_df + nmom);
-            AFMM_LAUNCH_CHECK();
+            if (!s2l_tc_enabled(p)) {  // the tensor-core S2L slices the FP64 moments itself
+                k_split_df<<<nblk(nmom), 256, 0, st>>>((const double *)MR(l), nmom, p->mom_df);
+                AFMM_LAUNCH_CHECK();
+                k_split_df<<<nblk(nmom), 256, 0, st>>>((const double *)MI(l), nmom, p->mom_df + nmom);
+                AFMM_LAUNCH_CHECK();
+            }
         }
         tmark(p, e + 2);
         AFMM_TRY(launch_s2l<R>(p, l, MR(l), MI(l), LR(l), LI(l)));

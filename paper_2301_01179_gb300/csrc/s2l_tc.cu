@@ -1,0 +1,537 @@
+// s2l_tc.cu -- the source-to-local operator (Eq. analysis:s2l, the S2L step of Algorithm 1)
+// of the FP64 path on the fifth-generation tensor cores (tcgen05.mma, bf16 in, FP32 out).
+//
+// Per interaction-list slot, a unit of up to 64 boxes of one column and axial parity needs
+//     F_kl += sum_ij  A_ij * B_kl,ij,     A_ij = j! S_ij = sum q U^i W^j,
+//                                         B_kl,ij = E_{k,i,j+l} / (j! l!),
+// with E the box-scaled, oriented Taylor coefficients (FO/BO/FI/BI of Sec. 2.2).  Moving
+// the factorials onto B balances both operands: A decays like 2^-(i+j), and each column of
+// B varies by a bounded binomial factor instead of (j+l)!.  The contraction is a GEMM:
+// 128 rows (box x {re, im}) x K = ij x N = kl, padded to KP = 16 ceil(ncoef / 16) <= 96.
+//
+// FP64-class accuracy from bf16 tensor cores by exact digit slicing (the Ozaki scheme):
+// every row of A and every column of B is written as six signed 8-bit digits on a common
+// power-of-two grid of its own, a = sum_s a_s, a_s a multiple of 2^(e - 8 - 8s), with
+// |a_s| <= 128 grid units (256 for s = 3, where the low FP32 word joins).  A digit is exact
+// in bf16 and a digit product exact in FP32.  Level L of the product expansion, the sum of
+// a_s b_t over s + t = L, is a sum of at most 4 KP products on one grid of at most 2^15
+// units each: below 2^24 units for KP <= 96, so its FP32 accumulation is EXACT.
+//     L0 .. L3  one accumulator per level, exact, drained after every slot into FP32-pair
+//               (double-float) registers (L3, of weight 2^-24, joins the low word)
+//     L4        levels 4 and 5 (weight <= 2^-32), FP32 over all slots
+// An FP32 accumulation of level 2 alone would already cost ~2^-40 per product, amplified
+// by the thousands of products per output; the exact levels keep the contraction at the
+// FP32-pair level.  Dropped products (s + t >= 6) are below 2^-48 of the row and column
+// maxima.
+//
+// Operands in shared memory use the no-swizzle K-major layout of 8-row x 16-byte core
+// matrices; the five accumulators live in tensor memory (TMEM) columns [lv KP, (lv+1) KP).  One thread issues the MMAs; completion is tracked with mbarriers whose waits
+// are bounded: a wait that runs out sets the plan's error word and the block ends cleanly.
+#include <cuda_bf16.h>
+
+#include <new>
+
+#include "common.cuh"
+#include "df.cuh"
+
+namespace afmm {
+
+namespace {
+
+constexpr int TC_SLICES = 6;
+constexpr int TC_THREADS = 256;
+constexpr long TC_WAIT_LIMIT = 1l << 26;  // mbarrier polls before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start address, leading (K) and stride (M/N) byte offsets
+// between core matrices, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: D FP32, A and B bf16, both K-major, M x N
+__host__ __device__ constexpr uint32_t umma_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dtmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *mbar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 lanes x 8 consecutive FP32 columns of TMEM
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8])
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// e with 2^(e-1) <= m < 2^e for normal m > 0
+__device__ __forceinline__ int grid_exp(float m) { return (int)((__float_as_uint(m) >> 23) & 0xff) - 126; }
+
+// 1.5 * 2^(23 + e): (a + c) - c rounds a to a multiple of 2^e (|a| < 2^(e + 22))
+__device__ __forceinline__ float round_magic(int e) { return __uint_as_float((uint32_t)(127 + 23 + e) << 23 | 0x400000u); }
+
+// the six digits of v = hi + lo on the grid 2^E > |v|: digit s is a multiple of 2^(E-8-8s)
+// with at most 8 significant bits; the digits of hi are exact, lo joins at the fourth digit
+// with one FP32 rounding (below 2^(E-48))
+__device__ __forceinline__ void digits6(float hi, float lo, int E, float d[TC_SLICES])
+{
+    float a = hi;
+#pragma unroll
+    for (int s = 0; s < TC_SLICES; ++s) {
+        if (s == 3) a = __fadd_rn(a, lo);
+        const float c = round_magic(E - 8 - 8 * s);
+        const float t = __fsub_rn(__fadd_rn(a, c), c);
+        d[s] = t;
+        a = __fsub_rn(a, t);
+    }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float x, float y)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+}  // namespace
+
+struct S2LTcArgs {
+    const int32_t *unit_box, *unit_col, *s2l, *station_of_col;
+    int level, nm, M, nc;
+    const float2 *gexp_df;        // [station][16][mode][(M+1)^2 (2M+1)] FP32 pairs
+    const __nv_bfloat16 *asl;     // [box][mode][re, im][6][KP] digit slices of A
+    double *loc_re, *loc_im;      // [box][mode][ncoef], += F
+    int *err;                     // set to 1 when a bounded wait runs out
+};
+
+// ---- A operand: digit slices of j! S_ij per (box, mode, re/im) row, one warp per row
+template <int KP>
+__global__ void __launch_bounds__(256) k_slice_moments(const double *__restrict__ mre, const double *__restrict__ mim,
+                                                       int64_t nbox, int nm, int nc, const TcTables tt,
+                                                       __nv_bfloat16 *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (row >= nbox * nm * 2) return;
+    const int reim = (int)(row & 1);
+    const int64_t bm = row >> 1;  // box * nm + mode
+    const double *src = (reim ? mim : mre) + bm * nc;
+    constexpr int PER = (KP + 31) / 32;
+    dfv v[PER];
+    float m = 0.f;
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+        const int ij = lane + 32 * t;
+        v[t] = df_make(0.f, 0.f);
+        if (ij < nc) {
+            v[t] = df_mulf(df_from_double(src[ij]), tt.jfact[tt.cj[ij]]);
+            m = fmaxf(m, fabsf(v[t].hi));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const bool live = m >= 1e-30f && m < 1e30f;
+    const int E = live ? grid_exp(m) + 1 : 0;
+    __nv_bfloat16 *dst = out + row * (TC_SLICES * KP);
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+        const int ij = lane + 32 * t;
+        if (ij < KP) {
+            float d[TC_SLICES];
+            if (live && ij < nc)
+                digits6(v[t].hi, v[t].lo, E, d);
+            else
+#pragma unroll
+                for (int s = 0; s < TC_SLICES; ++s) d[s] = 0.f;
+#pragma unroll
+            for (int s = 0; s < TC_SLICES; ++s) dst[s * KP + ij] = __float2bfloat16_rn(d[s]);
+        }
+    }
+}
+
+// ---- the operator: one block per (unit of up to 64 boxes, mode)
+template <int KP>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, const TcTables tt)
+{
+    constexpr int KG = KP / 8;              // core matrices along K
+    constexpr int BT = KP * KP * 2;         // bytes of one B slice (N = KP rows)
+    constexpr int AT = 128 * KP * 2;        // bytes of one A slice buffer
+    constexpr int HALF = KP / 2;            // accumulator columns drained per thread
+    constexpr uint32_t IDESC = umma_idesc(128, KP);
+    constexpr int NACC = 5;  // accumulators: levels 0, 1, 2, 3 (exact) and 4 + 5
+    static_assert(NACC * KP <= 512, "TMEM holds 512 FP32 columns");
+    constexpr uint32_t NCOL = NACC * KP <= 32 ? 32 : NACC * KP <= 64 ? 64 : NACC * KP <= 128 ? 128 : NACC * KP <= 256 ? 256 : 512;
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint8_t *sB = smem;                     // [6][KP rows][KP]
+    uint8_t *sA = smem + TC_SLICES * BT;    // [2][128 rows][KP]
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tbase;
+    __shared__ int src[64], bx[64];
+    __shared__ int colE[KP];
+    __shared__ int wait_ok;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t u = blockIdx.x;
+    const int n = blockIdx.y;
+    const int M = a.M, nc = a.nc, nm = a.nm, W = M + 1, C2 = 2 * M + 1;
+    const size_t slab = (size_t)W * W * C2;
+    if (tid < 64) bx[tid] = a.unit_box[u * 64 + tid];
+    const int ucol = a.unit_col[u];
+    const int col = ucol & 0xffff, pz = (ucol >> 30) & 1, pr = col & 1;
+    const int nl = 1 << a.level;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tbase)),
+                     "r"(NCOL));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tbase;
+    // accumulator lv (0 .. 4) at TMEM columns [lv KP, (lv + 1) KP)
+
+    // thread 0 polls the mbarrier (bounded); the block learns the outcome at the barrier
+    uint32_t nphase[2] = {0, 0};
+    bool pend[2] = {false, false};
+    bool abort_ = false;
+    auto wait_buf = [&](int b) {
+        if (!pend[b] || abort_) return;
+        if (tid == 0) {
+            const uint32_t par = (nphase[b] - 1) & 1;
+            bool ok = false;
+            for (long it = 0; it < TC_WAIT_LIMIT && !ok; ++it) ok = mbar_try(&mbar[b], par);
+            wait_ok = ok;
+            if (!ok) atomicExch(a.err, 1);
+        }
+        __syncthreads();
+        pend[b] = false;
+        if (!wait_ok) abort_ = true;
+    };
+
+    // double-float accumulators of the exact levels: row (lane quadrant) x HALF columns
+    const int q = warp & 3, h = warp >> 2;
+    const int row = 32 * q + lane, c0 = h * HALF;
+    float accS[HALF], accE[HALF];
+#pragma unroll
+    for (int t = 0; t < HALF; ++t) accS[t] = accE[t] = 0.f;
+    bool any_work = false;
+    bool l4_init = false;  // thread 0: the level-4 accumulator holds a sum
+
+    const int ntaskB = KP * KG;          // 16-byte chunks of one B slice
+    const int ntaskA = 128 * KG;         // 16-byte chunks of one A slice
+    for (int slot = 0; slot < 27 && !abort_; ++slot) {
+        int dr, dz;
+        s2l_offset(pr, pz, slot, &dr, &dz);
+        const int scol = col + dr;
+        if (scol < 0 || scol >= nl) continue;
+        __syncthreads();  // src[] of the previous slot is no longer read
+        int has = 0;
+        if (tid < 64) {
+            const int b = bx[tid];
+            const int s2 = b >= 0 ? a.s2l[(size_t)b * 27 + slot] : -1;
+            src[tid] = s2;
+            has = s2 >= 0;
+        }
+        if (!__syncthreads_or(has)) continue;
+        any_work = true;
+        const int station = dr < 0 ? scol : col;
+        const int sidx = a.station_of_col[station];
+        const int ea = dr < 0 ? -dr : dr, eb = dz < 0 ? -dz : dz;
+        const bool inward = dr > 0, backward = dz > 0;
+        const float2 *Eg = a.gexp_df + (((size_t)sidx * 16 + ea * 4 + eb) * nm + n) * slab;
+
+        // A slice s -> buffer b (rows without a source box read zeros)
+        auto load_A = [&](int s, int b) {
+            uint8_t *dstb = sA + b * AT;
+            for (int T = tid; T < ntaskA; T += TC_THREADS) {
+                const int rg = T / (KG * 8), kc = (T >> 3) % KG, r8 = T & 7;
+                const int r = rg * 8 + r8;
+                const int s2 = src[r & 63];
+                const __nv_bfloat16 *g = a.asl;
+                int bytes = 0;
+                if (s2 >= 0) {
+                    g = a.asl + ((((size_t)s2 * nm + n) * 2 + (r >> 6)) * TC_SLICES + s) * KP + kc * 8;
+                    bytes = 16;
+                }
+                cp_async16(dstb + T * 16, g, bytes);
+            }
+            cp_async_commit();
+        };
+        wait_buf(0);
+        if (abort_) break;
+        load_A(0, 0);
+
+        // B: pass 1, the grid exponent of every column kl
+        for (int kl = warp; kl < KP; kl += TC_THREADS / 32) {
+            float m = 0.f;
+            if (kl < nc) {
+                const int k = tt.ci[kl], l = tt.cj[kl];
+                for (int ij = lane; ij < nc; ij += 32) {
+                    const int i = tt.ci[ij], j = tt.cj[ij], c = j + l;
+                    const size_t idx = inward ? ((size_t)i * W + k) * C2 + c : ((size_t)k * W + i) * C2 + c;
+                    m = fmaxf(m, fabsf(Eg[idx].x) * tt.rjl[j * 14 + l].x);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0) colE[kl] = (m >= 1e-30f && m < 1e30f) ? grid_exp(m) + 1 : -1000;
+        }
+        __syncthreads();
+        // B: pass 2, digits into the six slices (thread T writes byte offset 16 T of each)
+        for (int T = tid; T < ntaskB; T += TC_THREADS) {
+            const int rg = T / (KG * 8), kc = (T >> 3) % KG, r8 = T & 7;
+            const int kl = rg * 8 + r8;
+            uint32_t w[TC_SLICES][4];
+#pragma unroll
+            for (int s = 0; s < TC_SLICES; ++s) w[s][0] = w[s][1] = w[s][2] = w[s][3] = 0u;
+            const int Ec = kl < nc ? colE[kl] : -1000;
+            if (Ec > -1000) {
+                const int k = tt.ci[kl], l = tt.cj[kl];
+#pragma unroll
+                for (int e2 = 0; e2 < 4; ++e2) {
+                    float dd[2][TC_SLICES];
+#pragma unroll
+                    for (int e1 = 0; e1 < 2; ++e1) {
+                        const int ij = kc * 8 + e2 * 2 + e1;
+                        if (ij < nc) {
+                            const int i = tt.ci[ij], j = tt.cj[ij], c = j + l;
+                            const size_t idx = inward ? ((size_t)i * W + k) * C2 + c : ((size_t)k * W + i) * C2 + c;
+                            float2 ev = Eg[idx];
+                            if (backward && (c & 1)) ev = make_float2(-ev.x, -ev.y);
+                            const float2 rf = tt.rjl[j * 14 + l];
+                            const dfv v = df_mul(df_make(ev.x, ev.y), df_make(rf.x, rf.y));
+                            digits6(v.hi, v.lo, Ec, dd[e1]);
+                        } else {
+#pragma unroll
+                            for (int s = 0; s < TC_SLICES; ++s) dd[e1][s] = 0.f;
+                        }
+                    }
+#pragma unroll
+                    for (int s = 0; s < TC_SLICES; ++s) w[s][e2] = pack_bf16(dd[0][s], dd[1][s]);
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < TC_SLICES; ++s)
+                *reinterpret_cast<uint4 *>(sB + s * BT + T * 16) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+        }
+
+        // slices of A in turn, double-buffered; slice i meets B slices 0 .. 5 - i
+        for (int i = 0; i < TC_SLICES; ++i) {
+            const int b = i & 1;
+            if (i + 1 < TC_SLICES) {
+                wait_buf(b ^ 1);
+                if (abort_) break;
+                load_A(i + 1, b ^ 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            fence_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t abase = smem_u32(sA + b * AT), bbase = smem_u32(sB);
+                for (int j = 0; j + i < TC_SLICES; ++j) {
+                    const int lv = i + j < 4 ? i + j : 4;
+                    for (int ks = 0; ks < KP / 16; ++ks) {
+                        const uint64_t ad = umma_desc(abase + ks * 256, 128, KG * 128);
+                        const uint64_t bd = umma_desc(bbase + j * BT + ks * 256, 128, KG * 128);
+                        // levels 0..3 restart every slot with the pair (0, lv); level 4 spans all slots
+                        const uint32_t acc = lv < 4 ? (ks > 0 || i > 0) : (ks > 0 || l4_init);
+                        umma_bf16(tmem + (uint32_t)(KP * lv), ad, bd, IDESC, acc);
+                        if (lv == 4) l4_init = true;
+                    }
+                }
+                umma_commit(&mbar[b]);
+            }
+            ++nphase[b];
+            pend[b] = true;
+        }
+        if (abort_) break;
+        // all MMAs of the slot complete -> drain the exact levels (two-sum into the pair;
+        // level 3 is small enough to join the low word with one rounding)
+        wait_buf(1);
+        wait_buf(0);
+        if (abort_) break;
+        tc_fence_after();
+#pragma unroll
+        for (int lv = 0; lv < 4; ++lv) {
+#pragma unroll
+            for (int c = 0; c < HALF / 8; ++c) {
+                float v[8];
+                tmem_ld8(tmem + (uint32_t)(KP * lv) + ((uint32_t)(32 * q) << 16) + c0 + 8 * c, v);
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    float &S = accS[8 * c + t], &Er = accE[8 * c + t];
+                    if (lv == 3) {
+                        Er = __fadd_rn(Er, v[t]);
+                    } else {
+                        const float s = __fadd_rn(S, v[t]);
+                        const float bb = __fsub_rn(s, S);
+                        const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bb)), __fsub_rn(v[t], bb));
+                        Er = __fadd_rn(Er, err);
+                        S = s;
+                    }
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+
+    // levels 4 and 5 (accumulated over all slots) and the write-back
+    if (!abort_ && any_work) {
+        tc_fence_after();
+        const int bl = row & 63, reim = row >> 6;
+        const int box = bx[bl];
+        double *dst = box >= 0 ? (reim ? a.loc_im : a.loc_re) + ((size_t)box * nm + n) * nc : nullptr;
+#pragma unroll
+        for (int c = 0; c < HALF / 8; ++c) {
+            float v[8];
+            tmem_ld8(tmem + (uint32_t)(4 * KP) + ((uint32_t)(32 * q) << 16) + c0 + 8 * c, v);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int kl = c0 + 8 * c + t;
+                if (dst && kl < nc) dst[kl] += ((double)accS[8 * c + t] + (double)accE[8 * c + t]) + (double)v[t];
+            }
+        }
+    }
+    cp_async_wait<0>();  // no copy of this block is still in flight
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOL));
+}
+
+// ---- host side
+static int tc_kp(int nc) { return (nc + 15) / 16 * 16; }
+
+bool s2l_tc_enabled(afmm_plan p)
+{
+    return p->precision == AFMM_FP64 && p->opt.s2l_engine == 0 && p->ncoef <= 96;
+}
+
+int64_t s2l_tc_slice_elems(afmm_plan p, int64_t nbox)
+{
+    return nbox * p->nmodes * 2 * TC_SLICES * (int64_t)tc_kp(p->ncoef);
+}
+
+afmm_status make_tc_tables(afmm_plan p)
+{
+    TcTables *t = new (std::nothrow) TcTables();
+    if (!t) return AFMM_ENOMEM;
+    double f[14];
+    f[0] = 1.0;
+    for (int i = 1; i < 14; ++i) f[i] = f[i - 1] * i;
+    for (int j = 0; j < 14; ++j) {
+        t->jfact[j] = (float)f[j];
+        for (int l = 0; l < 14; ++l) {
+            double x = 1.0 / (f[j] * f[l]);
+            float hi = (float)x;
+            t->rjl[j * 14 + l] = make_float2(hi, (float)(x - (double)hi));
+        }
+    }
+    for (int i = 0; i < 128; ++i) t->ci[i] = t->cj[i] = -1;
+    int idx = 0;
+    for (int a = 0; a <= p->M; ++a)
+        for (int b = 0; a + b <= p->M; ++b, ++idx) {
+            t->ci[idx] = (int8_t)a;
+            t->cj[idx] = (int8_t)b;
+        }
+    p->tct = t;
+    return AFMM_OK;
+}
+
+template <int KP>
+static afmm_status launch_tc_k(afmm_plan p, int l, const double *mre, const double *mim, double *lre, double *lim)
+{
+    Level &v = p->lv[l];
+    cudaStream_t st = p->stream;
+    const int nm = p->nmodes, nc = p->ncoef;
+    __nv_bfloat16 *asl = reinterpret_cast<__nv_bfloat16 *>(p->asl);
+    const int64_t rows = v.nbox * nm * 2;
+    k_slice_moments<KP><<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(mre, mim, v.nbox, nm, nc, *p->tct, asl);
+    AFMM_LAUNCH_CHECK();
+    S2LTcArgs a;
+    a.unit_box = v.unit64_box;
+    a.unit_col = v.unit64_col;
+    a.s2l = v.s2l;
+    a.station_of_col = v.station_of_col;
+    a.level = l;
+    a.nm = nm;
+    a.M = p->M;
+    a.nc = nc;
+    a.gexp_df = p->gexp_df;
+    a.asl = asl;
+    a.loc_re = lre;
+    a.loc_im = lim;
+    a.err = p->err_dev;
+    const size_t sm = (size_t)TC_SLICES * KP * KP * 2 + (size_t)2 * 128 * KP * 2;
+    AFMM_CUDA(cudaFuncSetAttribute(k_s2l_tc<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_s2l_tc<KP><<<dim3((unsigned)v.nunit64, (unsigned)nm), TC_THREADS, sm, st>>>(a, *p->tct);
+    AFMM_LAUNCH_CHECK();
+    return AFMM_OK;
+}
+
+afmm_status launch_s2l_tc(afmm_plan p, int l, const double *mre, const double *mim, double *lre, double *lim)
+{
+    if (p->lv[l].nunit64 == 0) return AFMM_OK;
+    if (!p->asl || !p->tct || !p->err_dev || !p->gexp_df) return AFMM_EINVAL;
+    switch (tc_kp(p->ncoef)) {
+    case 16: return launch_tc_k<16>(p, l, mre, mim, lre, lim);
+    case 32: return launch_tc_k<32>(p, l, mre, mim, lre, lim);
+    case 48: return launch_tc_k<48>(p, l, mre, mim, lre, lim);
+    case 64: return launch_tc_k<64>(p, l, mre, mim, lre, lim);
+    case 80: return launch_tc_k<80>(p, l, mre, mim, lre, lim);
+    case 96: return launch_tc_k<96>(p, l, mre, mim, lre, lim);
+    }
+    return AFMM_EUNSUPPORTED;
+}
+
+}  // namespace afmm

@@ -352,26 +352,6 @@ __global__ void k_child_ranges(const int32_t *__restrict__ parent, int64_t nbox,
     if (b == nbox - 1 || parent[b + 1] != p) child[p].y = (int)(b + 1);
 }
 
-// S2L list offsets for a field box with radial parity pr and axial parity pz: children of
-// the parent's 3x3 neighbours that are not neighbours of the box (Sec. 2.2).  Slot order:
-// dr from -2-pr to 3-pr, dz from -2-pz to 3-pz, skipping |dr|,|dz| <= 1.
-__host__ __device__ inline void s2l_offset(int pr, int pz, int slot, int *dr, int *dz)
-{
-    int s = 0;
-    for (int a = -2 - pr; a <= 3 - pr; ++a)
-        for (int b = -2 - pz; b <= 3 - pz; ++b) {
-            if (a >= -1 && a <= 1 && b >= -1 && b <= 1) continue;
-            if (s == slot) {
-                *dr = a;
-                *dz = b;
-                return;
-            }
-            ++s;
-        }
-    *dr = 0;
-    *dz = 0;
-}
-
 __global__ void k_s2l_table(const uint32_t *__restrict__ bkey, int64_t nbox, int level, int32_t *__restrict__ tab)
 {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -426,7 +406,8 @@ __global__ void k_i32_to_i64(const int32_t *__restrict__ a, int64_t n, int64_t *
     if (i < n) b[i] = a[i];
 }
 
-// S2L units: boxes sorted by (column, axial parity, axial index); groups of 32
+// S2L units: boxes sorted by (column, axial parity, axial index); groups of us (32 for the
+// CUDA-core operators, 64 for the tensor-core operator)
 __global__ void k_unit_keys(const uint32_t *__restrict__ bkey, int64_t nbox, int64_t npad,
                             unsigned long long *__restrict__ out)
 {
@@ -443,7 +424,7 @@ __global__ void k_unit_keys(const uint32_t *__restrict__ bkey, int64_t nbox, int
 
 __device__ inline unsigned long long unit_group(unsigned long long v) { return v >> 47; }
 
-__global__ void k_unit_flags(const unsigned long long *__restrict__ u, int64_t nbox, int64_t *__restrict__ f)
+__global__ void k_unit_flags(const unsigned long long *__restrict__ u, int64_t nbox, int us, int64_t *__restrict__ f)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= nbox) return;
@@ -456,11 +437,11 @@ __global__ void k_unit_flags(const unsigned long long *__restrict__ u, int64_t n
         else
             hi = mid;
     }
-    f[i] = ((i - lo) % 32 == 0) ? 1 : 0;
+    f[i] = ((i - lo) % us == 0) ? 1 : 0;
 }
 
-__global__ void k_unit_fill(const unsigned long long *__restrict__ u, int64_t nbox, const int64_t *__restrict__ pos,
-                            int32_t *__restrict__ ubox, int32_t *__restrict__ ucol)
+__global__ void k_unit_fill(const unsigned long long *__restrict__ u, int64_t nbox, int us,
+                            const int64_t *__restrict__ pos, int32_t *__restrict__ ubox, int32_t *__restrict__ ucol)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= nbox) return;
@@ -474,9 +455,9 @@ __global__ void k_unit_fill(const unsigned long long *__restrict__ u, int64_t nb
             hi = mid;
     }
     int64_t rank = i - lo;
-    int64_t unit = pos[i - (rank % 32)];
-    ubox[unit * 32 + rank % 32] = (int32_t)(v & 0xffffffull);
-    if (rank % 32 == 0) ucol[unit] = (int32_t)((v >> 48) | ((v >> 47 & 1ull) << 30));
+    int64_t unit = pos[i - (rank % us)];
+    ubox[unit * us + rank % us] = (int32_t)(v & 0xffffffull);
+    if (rank % us == 0) ucol[unit] = (int32_t)((v >> 48) | ((v >> 47 & 1ull) << 30));
 }
 
 // near-field units: ceil(count/32) per leaf box with field-role points
@@ -682,18 +663,22 @@ afmm_status build_tree(afmm_plan p, const double *src_r, const double *src_z, co
         k_unit_keys<<<nblk(npad), 256, 0, st>>>(v.key, nb, npad, srt);
         AFMM_LAUNCH_CHECK();
         AFMM_TRY(bitonic_sort(srt, npad, st));
-        k_unit_flags<<<nblk(nb), 256, 0, st>>>(srt, nb, f);
-        AFMM_LAUNCH_CHECK();
-        AFMM_TRY(scan_excl(f, pos, nb, tmp, st));
-        int64_t nu = 0;
-        AFMM_CUDA(cudaMemcpyAsync(&nu, pos + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        AFMM_CUDA(cudaStreamSynchronize(st));
-        v.nunit = nu;
-        AFMM_TRY(dalloc_t(p, &v.unit_box, (nu > 0 ? nu : 1) * 32));
-        AFMM_TRY(dalloc_t(p, &v.unit_col, nu > 0 ? nu : 1));
-        AFMM_CUDA(cudaMemsetAsync(v.unit_box, 0xff, (nu > 0 ? nu : 1) * 32 * sizeof(int32_t), st));
-        k_unit_fill<<<nblk(nb), 256, 0, st>>>(srt, nb, pos, v.unit_box, v.unit_col);
-        AFMM_LAUNCH_CHECK();
+        for (int us = 32; us <= 64; us += 32) {
+            if (us == 64 && p->precision != AFMM_FP64) break;  // tensor-core units: FP64 path only
+            k_unit_flags<<<nblk(nb), 256, 0, st>>>(srt, nb, us, f);
+            AFMM_LAUNCH_CHECK();
+            AFMM_TRY(scan_excl(f, pos, nb, tmp, st));
+            int64_t nu = 0;
+            AFMM_CUDA(cudaMemcpyAsync(&nu, pos + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            AFMM_CUDA(cudaStreamSynchronize(st));
+            int32_t **ub = us == 32 ? &v.unit_box : &v.unit64_box, **uc = us == 32 ? &v.unit_col : &v.unit64_col;
+            (us == 32 ? v.nunit : v.nunit64) = nu;
+            AFMM_TRY(dalloc_t(p, ub, (nu > 0 ? nu : 1) * us));
+            AFMM_TRY(dalloc_t(p, uc, nu > 0 ? nu : 1));
+            AFMM_CUDA(cudaMemsetAsync(*ub, 0xff, (nu > 0 ? nu : 1) * us * sizeof(int32_t), st));
+            k_unit_fill<<<nblk(nb), 256, 0, st>>>(srt, nb, us, pos, *ub, *uc);
+            AFMM_LAUNCH_CHECK();
+        }
     }
     // ---- leaf neighbours and near-field units for both directions
     {
