@@ -39,7 +39,7 @@ namespace afmm {
 namespace {
 
 constexpr int TC_SLICES = 6;
-constexpr int TC_THREADS = 256;
+constexpr int TC_THREADS = 512;
 constexpr long TC_WAIT_LIMIT = 1l << 26;  // mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -107,6 +107,18 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8])
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 lanes x 4 consecutive FP32 columns of TMEM
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float v[4])
+{
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // e with 2^(e-1) <= m < 2^e for normal m > 0
 __device__ __forceinline__ int grid_exp(float m) { return (int)((__float_as_uint(m) >> 23) & 0xff) - 126; }
 
@@ -135,6 +147,15 @@ __device__ __forceinline__ uint32_t pack_bf16(float x, float y)
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
+// the tables are indexed per lane: read them from shared memory (a kernel parameter lives
+// in the constant bank, where divergent indices serialise)
+__device__ __forceinline__ void stage_tables(const TcTables &src, TcTables &dst)
+{
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(&src);
+    uint32_t *d = reinterpret_cast<uint32_t *>(&dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(TcTables) / 4); i += blockDim.x) d[i] = s[i];
+}
+
 }  // namespace
 
 struct S2LTcArgs {
@@ -149,9 +170,12 @@ struct S2LTcArgs {
 // ---- A operand: digit slices of j! S_ij per (box, mode, re/im) row, one warp per row
 template <int KP>
 __global__ void __launch_bounds__(256) k_slice_moments(const double *__restrict__ mre, const double *__restrict__ mim,
-                                                       int64_t nbox, int nm, int nc, const TcTables tt,
+                                                       int64_t nbox, int nm, int nc, const TcTables tp,
                                                        __nv_bfloat16 *__restrict__ out)
 {
+    __shared__ TcTables tt;
+    stage_tables(tp, tt);
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (row >= nbox * nm * 2) return;
@@ -191,33 +215,61 @@ __global__ void __launch_bounds__(256) k_slice_moments(const double *__restrict_
     }
 }
 
-// ---- the operator: one block per (unit of up to 64 boxes, mode)
+// ---- the operator: one block of 16 warps per (unit of up to 64 boxes, mode)
+//
+// Per slot: stage the slot's Taylor-coefficient cube (FP32 pairs) in shared memory, build the
+// six digit slices of B from it (column grids first), then stream the six digit slices of A
+// through two buffers while thread 0 issues the 21 slice-pair MMAs per K step, and finally
+// drain the four exact levels into the FP32-pair registers.  Thread (warp w, lane) owns TMEM
+// lane 32 (w % 4) + lane (box (w % 2) 32 + lane, re/im w % 4 / 2) and a quarter of the columns.
 template <int KP>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, const TcTables tt)
+__global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, const TcTables tp)
 {
     constexpr int KG = KP / 8;              // core matrices along K
     constexpr int BT = KP * KP * 2;         // bytes of one B slice (N = KP rows)
     constexpr int AT = 128 * KP * 2;        // bytes of one A slice buffer
-    constexpr int HALF = KP / 2;            // accumulator columns drained per thread
+    constexpr int QC = KP / 4;              // accumulator columns drained per thread
     constexpr uint32_t IDESC = umma_idesc(128, KP);
-    constexpr int NACC = 5;  // accumulators: levels 0, 1, 2, 3 (exact) and 4 + 5
+    constexpr int NACC = 5;                 // accumulators: levels 0, 1, 2, 3 (exact) and 4 + 5
     static_assert(NACC * KP <= 512, "TMEM holds 512 FP32 columns");
     constexpr uint32_t NCOL = NACC * KP <= 32 ? 32 : NACC * KP <= 64 ? 64 : NACC * KP <= 128 ? 128 : NACC * KP <= 256 ? 256 : 512;
+    constexpr int NW = TC_THREADS / 32;
     extern __shared__ __align__(128) uint8_t smem[];
-    uint8_t *sB = smem;                     // [6][KP rows][KP]
-    uint8_t *sA = smem + TC_SLICES * BT;    // [2][128 rows][KP]
+    uint8_t *sB = smem;                                       // [6][KP rows][KP] bf16
+    uint8_t *sA = smem + TC_SLICES * BT;                      // [2][128 rows][KP] bf16
+    float2 *sE = reinterpret_cast<float2 *>(sA + 2 * AT);     // the slot's cube [(M+1)^2 (2M+1)]
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tbase;
-    __shared__ int src[64], bx[64];
+    __shared__ int bx[64];
+    __shared__ long long rbase[128];        // element offset of each A row's slices, or -1
     __shared__ int colE[KP];
+    __shared__ int offK[2][KP], offI[2][KP];  // cube offsets (outward, inward) of kl and ij
+    __shared__ float2 rj[14];               // 1 / j! as FP32 pairs
     __shared__ int wait_ok;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t u = blockIdx.x;
     const int n = blockIdx.y;
     const int M = a.M, nc = a.nc, nm = a.nm, W = M + 1, C2 = 2 * M + 1;
-    const size_t slab = (size_t)W * W * C2;
+    const int slab = W * W * C2;
     if (tid < 64) bx[tid] = a.unit_box[u * 64 + tid];
+    // separable cube offsets: outward (k W + i) C2 + j + l, inward (i W + k) C2 + j + l;
+    // the low 4 bits carry l (for kl) and j (for ij)
+    for (int t = tid; t < KP; t += TC_THREADS) {
+        int oo = 0, oi = 0, po = 0, pi = 0;
+        if (t < nc) {
+            const int x = tp.ci[t], y = tp.cj[t];
+            oo = x * W * C2 + y;  // as kl: k W C2 + l
+            oi = x * C2 + y;      // as kl (inward): k C2 + l
+            po = x * C2 + y;      // as ij: i C2 + j
+            pi = x * W * C2 + y;  // as ij (inward): i W C2 + j
+        }
+        offK[0][t] = oo << 4 | (t < nc ? tp.cj[t] : 0);
+        offK[1][t] = oi << 4 | (t < nc ? tp.cj[t] : 0);
+        offI[0][t] = po << 4 | (t < nc ? tp.cj[t] : 0);
+        offI[1][t] = pi << 4 | (t < nc ? tp.cj[t] : 0);
+    }
+    if (tid < 14) rj[tid] = tp.rjl[tid * 14];
     const int ucol = a.unit_col[u];
     const int col = ucol & 0xffff, pz = (ucol >> 30) & 1, pr = col & 1;
     const int nl = 1 << a.level;
@@ -234,8 +286,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = tbase;
-    // accumulator lv (0 .. 4) at TMEM columns [lv KP, (lv + 1) KP)
+    const uint32_t tmem = tbase;  // accumulator lv (0 .. 4) at TMEM columns [lv KP, (lv + 1) KP)
 
     // thread 0 polls the mbarrier (bounded); the block learns the outcome at the barrier
     uint32_t nphase[2] = {0, 0};
@@ -248,35 +299,35 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
             bool ok = false;
             for (long it = 0; it < TC_WAIT_LIMIT && !ok; ++it) ok = mbar_try(&mbar[b], par);
             wait_ok = ok;
-            if (!ok) atomicExch(a.err, 1);
+            if (!ok) *(volatile int *)a.err = 1;
         }
         __syncthreads();
         pend[b] = false;
         if (!wait_ok) abort_ = true;
     };
 
-    // double-float accumulators of the exact levels: row (lane quadrant) x HALF columns
-    const int q = warp & 3, h = warp >> 2;
-    const int row = 32 * q + lane, c0 = h * HALF;
-    float accS[HALF], accE[HALF];
+    // FP32-pair accumulators of the exact levels: one TMEM lane x QC columns
+    const int q = warp & 3;
+    const int row = 32 * q + lane, c0 = (warp >> 2) * QC;
+    float accS[QC], accE[QC];
 #pragma unroll
-    for (int t = 0; t < HALF; ++t) accS[t] = accE[t] = 0.f;
+    for (int t = 0; t < QC; ++t) accS[t] = accE[t] = 0.f;
     bool any_work = false;
     bool l4_init = false;  // thread 0: the level-4 accumulator holds a sum
 
-    const int ntaskB = KP * KG;          // 16-byte chunks of one B slice
-    const int ntaskA = 128 * KG;         // 16-byte chunks of one A slice
+    constexpr int ntaskB = KP * KG;   // 16-byte chunks of one B slice
+    constexpr int ntaskA = 128 * KG;  // 16-byte chunks of one A slice
     for (int slot = 0; slot < 27 && !abort_; ++slot) {
         int dr, dz;
         s2l_offset(pr, pz, slot, &dr, &dz);
         const int scol = col + dr;
         if (scol < 0 || scol >= nl) continue;
-        __syncthreads();  // src[] of the previous slot is no longer read
+        __syncthreads();  // rbase[] of the previous slot is no longer read
         int has = 0;
-        if (tid < 64) {
-            const int b = bx[tid];
+        if (tid < 128) {
+            const int b = bx[tid & 63];
             const int s2 = b >= 0 ? a.s2l[(size_t)b * 27 + slot] : -1;
-            src[tid] = s2;
+            rbase[tid] = s2 >= 0 ? (((long long)s2 * nm + n) * 2 + (tid >> 6)) * TC_SLICES * KP : -1ll;
             has = s2 >= 0;
         }
         if (!__syncthreads_or(has)) continue;
@@ -284,39 +335,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
         const int station = dr < 0 ? scol : col;
         const int sidx = a.station_of_col[station];
         const int ea = dr < 0 ? -dr : dr, eb = dz < 0 ? -dz : dz;
-        const bool inward = dr > 0, backward = dz > 0;
-        const float2 *Eg = a.gexp_df + (((size_t)sidx * 16 + ea * 4 + eb) * nm + n) * slab;
+        const int inward = dr > 0 ? 1 : 0;
+        const bool backward = dz > 0;
+        const float2 *Eg = a.gexp_df + (((size_t)sidx * 16 + ea * 4 + eb) * nm + n) * (size_t)slab;
 
         // A slice s -> buffer b (rows without a source box read zeros)
         auto load_A = [&](int s, int b) {
             uint8_t *dstb = sA + b * AT;
-            for (int T = tid; T < ntaskA; T += TC_THREADS) {
-                const int rg = T / (KG * 8), kc = (T >> 3) % KG, r8 = T & 7;
-                const int r = rg * 8 + r8;
-                const int s2 = src[r & 63];
-                const __nv_bfloat16 *g = a.asl;
-                int bytes = 0;
-                if (s2 >= 0) {
-                    g = a.asl + ((((size_t)s2 * nm + n) * 2 + (r >> 6)) * TC_SLICES + s) * KP + kc * 8;
-                    bytes = 16;
+#pragma unroll
+            for (int T0 = 0; T0 < ntaskA; T0 += TC_THREADS) {
+                const int T = T0 + tid;
+                if (T < ntaskA) {
+                    const int r = (T / (KG * 8)) * 8 + (T & 7), kc = (T >> 3) % KG;
+                    const long long rb = rbase[r];
+                    const __nv_bfloat16 *g = rb >= 0 ? a.asl + rb + s * KP + kc * 8 : a.asl;
+                    cp_async16(dstb + T * 16, g, rb >= 0 ? 16 : 0);
                 }
-                cp_async16(dstb + T * 16, g, bytes);
             }
             cp_async_commit();
         };
         wait_buf(0);
         if (abort_) break;
+        // the cube (8-byte copies: its offset is a multiple of 8 bytes only), then A slice 0
+        for (int t = tid; t < slab; t += TC_THREADS)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(sE + t)), "l"(Eg + t) : "memory");
+        cp_async_commit();
         load_A(0, 0);
+        cp_async_wait<1>();
+        __syncthreads();
 
-        // B: pass 1, the grid exponent of every column kl
-        for (int kl = warp; kl < KP; kl += TC_THREADS / 32) {
+        // B: pass 1, the grid exponent of every column kl (max over ij of |E / j!|)
+        for (int kl = warp; kl < KP; kl += NW) {
             float m = 0.f;
             if (kl < nc) {
-                const int k = tt.ci[kl], l = tt.cj[kl];
+                const int ok = offK[inward][kl] >> 4;
                 for (int ij = lane; ij < nc; ij += 32) {
-                    const int i = tt.ci[ij], j = tt.cj[ij], c = j + l;
-                    const size_t idx = inward ? ((size_t)i * W + k) * C2 + c : ((size_t)k * W + i) * C2 + c;
-                    m = fmaxf(m, fabsf(Eg[idx].x) * tt.rjl[j * 14 + l].x);
+                    const int oi = offI[inward][ij];
+                    m = fmaxf(m, fabsf(sE[ok + (oi >> 4)].x) * rj[oi & 15].x);
                 }
             }
 #pragma unroll
@@ -324,16 +379,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
             if (lane == 0) colE[kl] = (m >= 1e-30f && m < 1e30f) ? grid_exp(m) + 1 : -1000;
         }
         __syncthreads();
-        // B: pass 2, digits into the six slices (thread T writes byte offset 16 T of each)
+        // B: pass 2, digits of E_{k,i,j+l} / j! into the six slices (chunk T at byte 16 T)
         for (int T = tid; T < ntaskB; T += TC_THREADS) {
-            const int rg = T / (KG * 8), kc = (T >> 3) % KG, r8 = T & 7;
-            const int kl = rg * 8 + r8;
+            const int kl = (T / (KG * 8)) * 8 + (T & 7), kc = (T >> 3) % KG;
             uint32_t w[TC_SLICES][4];
 #pragma unroll
             for (int s = 0; s < TC_SLICES; ++s) w[s][0] = w[s][1] = w[s][2] = w[s][3] = 0u;
             const int Ec = kl < nc ? colE[kl] : -1000;
             if (Ec > -1000) {
-                const int k = tt.ci[kl], l = tt.cj[kl];
+                const int okl = offK[inward][kl];
+                const int ok = okl >> 4, l = okl & 15;
 #pragma unroll
                 for (int e2 = 0; e2 < 4; ++e2) {
                     float dd[2][TC_SLICES];
@@ -341,11 +396,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
                     for (int e1 = 0; e1 < 2; ++e1) {
                         const int ij = kc * 8 + e2 * 2 + e1;
                         if (ij < nc) {
-                            const int i = tt.ci[ij], j = tt.cj[ij], c = j + l;
-                            const size_t idx = inward ? ((size_t)i * W + k) * C2 + c : ((size_t)k * W + i) * C2 + c;
-                            float2 ev = Eg[idx];
-                            if (backward && (c & 1)) ev = make_float2(-ev.x, -ev.y);
-                            const float2 rf = tt.rjl[j * 14 + l];
+                            const int oi = offI[inward][ij];
+                            const int j = oi & 15;
+                            float2 ev = sE[ok + (oi >> 4)];
+                            if (backward && ((j + l) & 1)) ev = make_float2(-ev.x, -ev.y);
+                            const float2 rf = rj[j];
                             const dfv v = df_mul(df_make(ev.x, ev.y), df_make(rf.x, rf.y));
                             digits6(v.hi, v.lo, Ec, dd[e1]);
                         } else {
@@ -404,12 +459,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
 #pragma unroll
         for (int lv = 0; lv < 4; ++lv) {
 #pragma unroll
-            for (int c = 0; c < HALF / 8; ++c) {
-                float v[8];
-                tmem_ld8(tmem + (uint32_t)(KP * lv) + ((uint32_t)(32 * q) << 16) + c0 + 8 * c, v);
+            for (int c = 0; c < QC / 4; ++c) {
+                float v[4];
+                tmem_ld4(tmem + (uint32_t)(KP * lv) + ((uint32_t)(32 * q) << 16) + c0 + 4 * c, v);
 #pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    float &S = accS[8 * c + t], &Er = accE[8 * c + t];
+                for (int t = 0; t < 4; ++t) {
+                    float &S = accS[4 * c + t], &Er = accE[4 * c + t];
                     if (lv == 3) {
                         Er = __fadd_rn(Er, v[t]);
                     } else {
@@ -426,20 +481,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
         __syncthreads();
     }
 
-    // levels 4 and 5 (accumulated over all slots) and the write-back
+    // levels 4 and 5 (accumulated over all slots), 1 / l!, and the write-back
     if (!abort_ && any_work) {
         tc_fence_after();
         const int bl = row & 63, reim = row >> 6;
         const int box = bx[bl];
         double *dst = box >= 0 ? (reim ? a.loc_im : a.loc_re) + ((size_t)box * nm + n) * nc : nullptr;
 #pragma unroll
-        for (int c = 0; c < HALF / 8; ++c) {
-            float v[8];
-            tmem_ld8(tmem + (uint32_t)(4 * KP) + ((uint32_t)(32 * q) << 16) + c0 + 8 * c, v);
+        for (int c = 0; c < QC / 4; ++c) {
+            float v[4];
+            tmem_ld4(tmem + (uint32_t)(4 * KP) + ((uint32_t)(32 * q) << 16) + c0 + 4 * c, v);
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int kl = c0 + 8 * c + t;
-                if (dst && kl < nc) dst[kl] += ((double)accS[8 * c + t] + (double)accE[8 * c + t]) + (double)v[t];
+            for (int t = 0; t < 4; ++t) {
+                const int kl = c0 + 4 * c + t;
+                if (dst && kl < nc) {
+                    const float2 rl = rj[offK[0][kl] & 15];
+                    const double f = ((double)accS[4 * c + t] + (double)accE[4 * c + t]) + (double)v[t];
+                    dst[kl] += f * ((double)rl.x + (double)rl.y);
+                }
             }
         }
     }
@@ -512,7 +571,8 @@ static afmm_status launch_tc_k(afmm_plan p, int l, const double *mre, const doub
     a.loc_re = lre;
     a.loc_im = lim;
     a.err = p->err_dev;
-    const size_t sm = (size_t)TC_SLICES * KP * KP * 2 + (size_t)2 * 128 * KP * 2;
+    const int W = p->M + 1;
+    const size_t sm = (size_t)TC_SLICES * KP * KP * 2 + (size_t)2 * 128 * KP * 2 + (size_t)W * W * (2 * p->M + 1) * 8;
     AFMM_CUDA(cudaFuncSetAttribute(k_s2l_tc<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_s2l_tc<KP><<<dim3((unsigned)v.nunit64, (unsigned)nm), TC_THREADS, sm, st>>>(a, *p->tct);
     AFMM_LAUNCH_CHECK();
