@@ -28,9 +28,26 @@ UNIT = "modal ring interactions/s"
 WORKLOAD = "cfg2"
 WORKLOAD_DESC = ("1,000,000 ring sources x 1,000,000 field points, r~U[0.05,2], z~U[-2,2], modes n=0..32, "
                  "complex N(0,1) amplitudes, FMM order 12, leaf 64, FP64")
-# FP64 FMA peak of the GB300: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-FP64_INST_T = 152 * 2 * 2.07e9 / 1e12  # FP64 instructions per second (x 1e12)
+# FP32 issue peak of the GB300, from its unit counts and clock: 152 SMs x 128 FP32 lanes x
+# 2.07 GHz (one FP32 operation per lane and clock; an FMA counts as one operation)
+FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+# near field, FP32-pair arithmetic, a-priori operation count per (field point, source) pair:
+# ~600 for the pair geometry, the AGM start values and the gradient factors, then per mode 24
+# (recursion step), 27 (scale and two compensated accumulations) and 85 (gradient terms)
+NEAR_SETUP_OPS, NEAR_MODE_OPS = 600, 24 + 27 + 85
+# S2L on the tensor cores: 21 digit-slice products per FP64-equivalent multiply-add
+S2L_SLICE_PAIRS = 21
+
+
+def measured_bf16_peak():
+    """Dense bf16 tensor peak (TFLOP/s) measured on the GB300s: the sustained figure
+    (the S2L runs inside a long step), else the documented fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["bf16_tflops_sustained"]), "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
+    except Exception:
+        return 1700.0, "fallback 1.7 PFLOP/s sustained bf16 (of fallback)"
 
 
 def read_traffic():
@@ -258,28 +275,29 @@ def run_ours(args):
     clocks = clk.stop()
     value, t_ms = aggregate(ws, units_per_step, e0.elapsed_time(e1) / args.steps, dev)
 
-    # ---- roofline of the dominant kernel, from the live phase split of the timed steps
+    # ---- roofline of the dominant kernel, from the live phase split of the timed steps (CUDA
+    # events recorded by the library on the plan's stream around each phase)
     nc = (M + 1) * (M + 2) // 2
     s2l_ms = statistics.mean(p["s2l"] for p in phases)
     near_ms = statistics.mean(p["near"] for p in phases)
     traffic_of = read_traffic()
-    # near field: algorithmic FP64 instructions per (field point, source) pair, the a-priori
-    # count (N+1) * (3 recursion + 2 accumulate + 6 gradient) + 80 setup, against the FP64
-    # issue rate (152 SMs x 2 per clock x 2.07 GHz)
-    near_inst = 80.0 + nm * (5.0 + 6.0)
-    near_ach = float(info["near_pairs"]) * near_inst / (near_ms / 1e3) / 1e12
-    near_roof = {"bound": "alu", "kernel": "k_near2 (field gradient)", "achieved": near_ach, "peak": FP64_INST_T,
-                 "unit": "FP64 Tinst/s", "frac": near_ach / FP64_INST_T, "traffic": traffic_of.get("k_near2"),
-                 "work_per_unit": "%.0f FP64 instructions per near pair (80 + 11 (N+1))" % near_inst,
-                 "peak_source": "152 SMs x 2 FP64 issue/clk x 2.07 GHz (derived; own FMA probe 0.60 TFMA/s)"}
-    # S2L: 4 ncoef^2 FP64-equivalent flop per (box pair, mode); the FP64 path evaluates it in
-    # FP32-pair arithmetic, so the FP64 peak is the reference it replaces
-    s2l_flop = float(info["s2l_pairs"]) * nm * 4.0 * nc * nc
+    near_ops = NEAR_SETUP_OPS + nm * NEAR_MODE_OPS
+    near_ach = float(info["near_pairs"]) * near_ops / (near_ms / 1e3) / 1e12
+    near_roof = {"bound": "alu", "kernel": "k_near_df (near field + L2P, potential and gradient, FP32 pairs)",
+                 "achieved": near_ach, "peak": FP32_PEAK_TOPS, "unit": "FP32 Tops/s",
+                 "frac": near_ach / FP32_PEAK_TOPS, "traffic": traffic_of.get("k_near_df"),
+                 "work_per_unit": "%d FP32 operations per near pair (%d + %d (N+1)); %d pairs per launch"
+                                  % (near_ops, NEAR_SETUP_OPS, NEAR_MODE_OPS, info["near_pairs"]),
+                 "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (derived from unit counts and clock)"}
+    bf16_peak, bf16_src = measured_bf16_peak()
+    s2l_flop = float(info["s2l_pairs"]) * nm * 4.0 * nc * nc * S2L_SLICE_PAIRS
     s2l_ach = s2l_flop / (s2l_ms / 1e3) / 1e12
-    s2l_roof = {"bound": "alu", "kernel": "k_s2l_df (FP32-pair S2L)", "achieved": s2l_ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s (FP64-equivalent)", "frac": s2l_ach / FP64_PEAK_TFLOPS,
-                "traffic": traffic_of.get("k_s2l_df"),
-                "peak_source": "FP64 FMA peak 152 x 2 x 2 x 2.07 GHz; frac > 1 is the gain of the FP32-pair form"}
+    s2l_roof = {"bound": "tensor", "kernel": "k_s2l_tc (tcgen05 bf16, exact 6-digit slicing; all levels)",
+                "achieved": s2l_ach, "peak": bf16_peak, "unit": "TFLOP/s", "frac": s2l_ach / bf16_peak,
+                "traffic": traffic_of.get("k_s2l_tc"),
+                "work_per_unit": "21 digit-slice products x 4 ncoef^2 flop per (box pair, mode); %d box pairs"
+                                 % info["s2l_pairs"],
+                "peak_source": bf16_src}
     roofline, secondary = (near_roof, s2l_roof) if near_ms >= s2l_ms else (s2l_roof, near_roof)
     phase_ms = {k: round(statistics.mean(p[k] for p in phases), 3) for k in phases[0]}
 
@@ -345,7 +363,7 @@ def run_ours(args):
         cb = cpu_baseline(w) if ws == 1 and not args.no_cpu_baseline else None
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f64-class (fp32-pair, bf16-digit tensor, f64)", "data": "synthetic",
                 "config": {"workload": WORKLOAD_DESC, "ns": ns, "nf": nf, "n_modes": nm, "order": M, "leaf": leaf,
                            "depth": info["depth"], "step": "quadtree build + FMM potential and field gradient",
                            "l2": "inputs larger than L2 (amplitudes 528 MB per step)",

@@ -189,7 +189,8 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
         nexp += (int64_t)v.nstation * 12;
     }
     p->expansions = nexp;
-    if (s == AFMM_OK && gcap > 0) s = dalloc_t(p, &p->gexp, gcap);
+    // FP64 expansions (the FP64 path generates FP32-pair expansions instead)
+    if (s == AFMM_OK && gcap > 0 && p->precision != AFMM_FP64) s = dalloc_t(p, &p->gexp, gcap);
     p->gexp_cap = gcap;
     if (s == AFMM_OK && p->precision == AFMM_FP64) {
         s = dalloc_t(p, &p->qsdf, (size_t)2 * nm * nmax);

@@ -20,6 +20,7 @@
 #include <vector>
 #include "common.cuh"
 #include "pair.cuh"
+#include "df.cuh"
 
 namespace afmm {
 
@@ -149,10 +150,11 @@ __global__ void k_m2m(const int2 *__restrict__ child, const uint32_t *__restrict
     R *T = X + 2 * nc;  // [4][W][W] tables
     for (int i = threadIdx.x; i < 4 * W * W; i += blockDim.x) T[i] = (R)tab[i];
     int64_t P = blockIdx.x;
+    const int n = blockIdx.y;  // one block per (parent, mode)
     __syncthreads();
     if (P >= npar) return;
     int2 ch = child[P];
-    for (int n = 0; n < nm; ++n) {
+    {
         R accr[2] = {0, 0}, acci[2] = {0, 0};  // outputs o = tid, tid + blockDim (nc <= 2 * blockDim)
         for (int c = ch.x; c < ch.y; ++c) {
             uint32_t k = ckey[c];
@@ -220,11 +222,12 @@ __global__ void k_l2l(const int32_t *__restrict__ parent, const uint32_t *__rest
     uint32_t k = key[b];
     int br = morton_ir(k) & 1, bz = morton_iz(k) & 1;
     const R *Lr = T + (0 * 2 + br) * W * W, *Lz = T + (1 * 2 + bz) * W * W;
-    for (int n = 0; n < nm; ++n) {
+    const int n = blockIdx.y;  // one block per (box, mode)
+    {
         R *or_ = fre + ((size_t)b * nm + n) * nc, *oi_ = fim + ((size_t)b * nm + n) * nc;
         if (P < 0) {
             for (int o = threadIdx.x; o < nc; o += blockDim.x) or_[o] = oi_[o] = (R)0;
-            continue;
+            return;
         }
         const R *pr = fre_p + ((size_t)P * nm + n) * nc, *pi = fim_p + ((size_t)P * nm + n) * nc;
         // Y_{k,m} = sum_{l >= m} Lz[m][l] F_{k,l}
@@ -281,8 +284,125 @@ struct ExpJob {
     double *out;       // slab base for this point (modes consecutive)
 };
 
+// Number types of the warp-parallel Laplace fill: FP64, or FP32 pairs (the FP64 path)
+struct NumF64 {
+    using T = double;
+    using S = double;  // storage
+    static __device__ __forceinline__ T from(double x) { return x; }
+    static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+    static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
+    static __device__ __forceinline__ T mulf(T a, float b) { return a * (double)b; }
+    static __device__ __forceinline__ T neg(T a) { return -a; }
+    static __device__ __forceinline__ T zero() { return 0.0; }
+    static __device__ __forceinline__ T down2(T a) { return __shfl_down_sync(0xffffffffu, a, 2); }
+    static __device__ __forceinline__ T ld(const S *p) { return *p; }
+    static __device__ __forceinline__ void st(S *p, T v) { *p = v; }
+};
+struct NumDF {
+    using T = dfv;
+    using S = float2;
+    static __device__ __forceinline__ T from(double x) { return df_from_double(x); }
+    static __device__ __forceinline__ T add(T a, T b) { return df_add(a, b); }
+    static __device__ __forceinline__ T mul(T a, T b) { return df_mul(a, b); }
+    static __device__ __forceinline__ T mulf(T a, float b) { return df_mulf(a, b); }
+    static __device__ __forceinline__ T neg(T a) { return df_neg(a); }
+    static __device__ __forceinline__ T zero() { return df_make(0.f, 0.f); }
+    static __device__ __forceinline__ T down2(T a)
+    {
+        return df_make(__shfl_down_sync(0xffffffffu, a.hi, 2), __shfl_down_sync(0xffffffffu, a.lo, 2));
+    }
+    static __device__ __forceinline__ T ld(const S *p)
+    {
+        const float2 v = *p;
+        return df_make(v.x, v.y);
+    }
+    static __device__ __forceinline__ void st(S *p, T v) { *p = make_float2(v.hi, v.lo); }
+};
+
+// Step 4 of gbar_block, warp-parallel (P <= 31): lane c holds the c-th Taylor coefficient of
+// one row (a, b) of one mode.  The Laplace recursion of a row needs rows b+1, b, b-1, b-2
+// (resp. a+1 .. a-2) at c and c+2 only, so a warp walks the rows with a register window and
+// a shuffle for c+2:  phase A raises b for a = 0, 1 (one warp per (mode, a)); phase B raises
+// a for each b (one warp per (mode, b)), reading the phase-A rows and writing every entry
+// scaled by scale * c!.  Same recursions and coefficients as the serial fill below.
+template <class O>
+__device__ void gbar_fill_warp(double r, double r1, int N, int P, int A, int Bm, int Q, const double *g00,
+                               const double *g10, const double *g01, const double *g11, typename O::S *out,
+                               double scale, int fact)
+{
+    using T = typename O::T;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int c = lane;
+    const int SA = (Bm + 1) * Q;
+    const T r1d = O::from(r1), r1s = O::from(r1 * r1), r1x2 = O::from(2.0 * r1);
+    const T rd = O::from(r), rs = O::from(r * r), rx2 = O::from(2.0 * r);
+    const float cc2 = (float)((c + 1) * (c + 2));
+    // phase A: rows (a, b), a <= 1, unscaled
+    const int na = A >= 1 ? 2 : 1;
+    for (int task = warp; task < (N + 1) * na; task += nw) {
+        const int n = task / na, a = task % na;
+        typename O::S *E = out + (size_t)n * (A + 1) * SA + (size_t)a * SA;
+        const float n2 = (float)(n * n);
+        const double *gb0 = a == 0 ? g00 : g10, *gb1 = a == 0 ? g01 : g11;
+        T R0 = c <= P - a ? O::from(gb0[n * Q + c]) : O::zero();                           // b = 0
+        T R1 = (Bm >= 1 && c <= P - a - 1) ? O::from(gb1[n * Q + c]) : O::zero();         // b = 1
+        T Rm1 = O::zero(), Rm2 = O::zero();                                                // b - 1, b - 2
+        if (c <= P - a) O::st(E + c, R0);
+        if (Bm >= 1 && c <= P - a - 1) O::st(E + Q + c, R1);
+        for (int b = 0; b + 2 <= Bm && a + b + 2 <= P; ++b) {
+            const T den = O::from(1.0 / (r1 * r1 * (b + 1.0) * (b + 2.0)));
+            const T d0 = O::down2(R0), dm1 = O::down2(Rm1), dm2 = O::down2(Rm2);
+            T sv = O::add(O::mulf(O::mul(r1d, R1), (float)((b + 1) * (2 * b + 1))), O::mulf(R0, (float)(b * b) - n2));
+            T t = O::mul(r1s, d0);
+            if (b >= 1) t = O::add(t, O::mul(r1x2, dm1));
+            if (b >= 2) t = O::add(t, dm2);
+            sv = O::add(sv, O::mulf(t, cc2));
+            const T R2 = O::neg(O::mul(sv, den));
+            if (a + b + 2 + c <= P) O::st(E + (size_t)(b + 2) * Q + c, R2);
+            Rm2 = Rm1;
+            Rm1 = R0;
+            R0 = R1;
+            R1 = R2;
+        }
+    }
+    __syncthreads();
+    // phase B: raise a for each (mode, b); write every entry scaled
+    double fcd = scale;
+    if (fact)
+        for (int k = 2; k <= c; ++k) fcd *= k;
+    const T fc = O::from(fcd);
+    for (int task = warp; task < (N + 1) * (Bm + 1); task += nw) {
+        const int n = task / (Bm + 1), b = task % (Bm + 1);
+        if (b > P) continue;  // warp-uniform
+        typename O::S *E = out + (size_t)n * (A + 1) * SA + (size_t)b * Q;
+        const float n2 = (float)(n * n);
+        T R0 = c <= P - b ? O::ld(E + c) : O::zero();                                       // a = 0
+        T R1 = (A >= 1 && c <= P - b - 1) ? O::ld(E + SA + c) : O::zero();                  // a = 1
+        T Rm1 = O::zero(), Rm2 = O::zero();
+        __syncwarp();
+        if (c <= P - b) O::st(E + c, O::mul(R0, fc));
+        if (A >= 1 && c <= P - b - 1) O::st(E + SA + c, O::mul(R1, fc));
+        for (int a = 0; a + 2 <= A && a + 2 + b <= P; ++a) {
+            const T den = O::from(1.0 / (r * r * (a + 1.0) * (a + 2.0)));
+            const T d0 = O::down2(R0), dm1 = O::down2(Rm1), dm2 = O::down2(Rm2);
+            T sv = O::add(O::mulf(O::mul(rd, R1), (float)((a + 1) * (2 * a + 1))), O::mulf(R0, (float)(a * a) - n2));
+            T t = O::mul(rs, d0);
+            if (a >= 1) t = O::add(t, O::mul(rx2, dm1));
+            if (a >= 2) t = O::add(t, dm2);
+            sv = O::add(sv, O::mulf(t, cc2));
+            const T R2 = O::neg(O::mul(sv, den));
+            if (a + 2 + b + c <= P) O::st(E + (size_t)(a + 2) * SA + c, O::mul(R2, fc));
+            Rm2 = Rm1;
+            Rm1 = R0;
+            R0 = R1;
+            R1 = R2;
+        }
+    }
+}
+
 __device__ void gbar_block(double r, double r1, double x, int N, int P, int A, int Bm, const RecTab &tab,
-                           const PairParams &pp, double *sm, double *out, double scale, int fact)
+                           const PairParams &pp, double *sm, double *out, double scale, int fact,
+                           float2 *dfout = nullptr)
 {
     const int Nw = N < 1 ? 1 : N;
     const int nmw = Nw + 1;
@@ -396,6 +516,14 @@ __device__ void gbar_block(double r, double r1, double x, int N, int P, int A, i
         }
     }
     __syncthreads();
+    if (P <= 31) {  // warp-parallel fill (every order a plan accepts: 2M <= 30)
+        if (dfout)
+            gbar_fill_warp<NumDF>(r, r1, N, P, A, Bm, Q, g00, g10, g01, g11, dfout, scale, fact);
+        else
+            gbar_fill_warp<NumF64>(r, r1, N, P, A, Bm, Q, g00, g10, g01, g11, out, scale, fact);
+        return;
+    }
+    if (dfout) return;  // not reached: FP32-pair expansions come from plans (P = 2M <= 30)
     // 4. Laplace recursions, one mode per thread, into the output slab
     const int SA = (Bm + 1) * Q;  // stride of a
     for (int n = threadIdx.x; n <= N; n += blockDim.x) {
@@ -474,7 +602,7 @@ __global__ void k_gbar_points(int64_t np, const double *__restrict__ r, const do
 // S2L expansions of one level: block = (station, slot a*4+b)
 __global__ void k_gexp_level(const int32_t *__restrict__ col_of_station, const int32_t *__restrict__ station_of_col,
                              int nstation, int level, double r0h, double h, int nm, int M, const RecTab tab,
-                             PairParams pp, double *gexp)
+                             PairParams pp, double *gexp, float2 *gexp_df)
 {
     extern __shared__ double sm[];
     int st = blockIdx.x / 16, slot = blockIdx.x % 16;
@@ -485,8 +613,9 @@ __global__ void k_gexp_level(const int32_t *__restrict__ col_of_station, const i
     if (col + a >= nl || station_of_col[col + a] < 0) return;
     double Rs = r0h + col + 0.5, Rb = Rs + a;
     size_t slab = (size_t)(M + 1) * (M + 1) * (2 * M + 1);
-    double *out = gexp + ((size_t)st * 16 + slot) * nm * slab;
-    gbar_block(Rb, Rs, (double)b, nm - 1, 2 * M, M, M, tab, pp, sm, out, 1.0 / h, 1);
+    double *out = gexp ? gexp + ((size_t)st * 16 + slot) * nm * slab : nullptr;
+    float2 *dout = gexp_df ? gexp_df + ((size_t)st * 16 + slot) * nm * slab : nullptr;
+    gbar_block(Rb, Rs, (double)b, nm - 1, 2 * M, M, M, tab, pp, sm, out, 1.0 / h, 1, dout);
 }
 
 afmm_status launch_green_expansion(int64_t npts, const double *r, const double *r1, const double *x, int n_modes, int P,
@@ -861,7 +990,7 @@ static afmm_status far_field_t(afmm_plan p, int dir)
     for (int l = d - 1; l >= 2; --l) {
         Level &v = p->lv[l];
         size_t sm = sizeof(R) * (2 * (size_t)nc + 4 * (size_t)(M + 1) * (M + 1));
-        k_m2m<R><<<(unsigned)v.nbox, 128, sm, st>>>(v.child, p->lv[l + 1].key, v.nbox, nm, M, p->m2m_tab, MR(l + 1),
+        k_m2m<R><<<dim3((unsigned)v.nbox, (unsigned)nm), 128, sm, st>>>(v.child, p->lv[l + 1].key, v.nbox, nm, M, p->m2m_tab, MR(l + 1),
                                                     MI(l + 1), MR(l), MI(l));
         AFMM_LAUNCH_CHECK();
     }
@@ -874,25 +1003,23 @@ static afmm_status far_field_t(afmm_plan p, int dir)
         const int e = 16 + 4 * (l - 2);  // event slots: L2L, expansions, S2L, end
         size_t sm = sizeof(R) * (2 * (size_t)nc + 4 * (size_t)(M + 1) * (M + 1));
         tmark(p, e);
-        k_l2l<R><<<(unsigned)v.nbox, 128, sm, st>>>(l >= 3 ? v.parent : nullptr, v.key, v.nbox, nm, M, p->l2l_tab,
+        k_l2l<R><<<dim3((unsigned)v.nbox, (unsigned)nm), 128, sm, st>>>(l >= 3 ? v.parent : nullptr, v.key, v.nbox, nm, M, p->l2l_tab,
                                                     l >= 3 ? LR(l - 1) : nullptr, l >= 3 ? LI(l - 1) : nullptr, LR(l),
                                                     LI(l));
         AFMM_LAUNCH_CHECK();
         tmark(p, e + 1);
         double h = p->L / (double)(1 << l);
         if (v.nstation > 0) {
+            // the FP64 path generates its expansions directly as FP32 pairs
+            const bool dfx = !mix && p->precision == AFMM_FP64;
             k_gexp_level<<<(unsigned)(v.nstation * 16), 128, gsm, st>>>(v.col_of_station, v.station_of_col, v.nstation,
                                                                         l, p->r0 / h, h, nm, M, *p->rec, p->pp,
-                                                                        p->gexp);
+                                                                        dfx ? nullptr : p->gexp,
+                                                                        dfx ? p->gexp_df : nullptr);
             AFMM_LAUNCH_CHECK();
         }
         if (!mix && p->precision == AFMM_FP64) {
-            int64_t ng = (int64_t)v.nstation * 16 * nm * (M + 1) * (M + 1) * (2 * M + 1);
             int64_t nmom = (int64_t)v.nbox * nm * nc;
-            if (ng > 0) {
-                k_split_df<<<nblk(ng), 256, 0, st>>>(p->gexp, ng, p->gexp_df);
-                AFMM_LAUNCH_CHECK();
-            }
             if (!s2l_tc_enabled(p)) {  // the tensor-core S2L slices the FP64 moments itself
                 k_split_df<<<nblk(nmom), 256, 0, st>>>((const double *)MR(l), nmom, p->mom_df);
                 AFMM_LAUNCH_CHECK();
