@@ -328,12 +328,19 @@ struct NumDF {
 template <class O>
 __device__ void gbar_fill_warp(double r, double r1, int N, int P, int A, int Bm, int Q, const double *g00,
                                const double *g10, const double *g01, const double *g11, typename O::S *out,
-                               double scale, int fact)
+                               double scale, int fact, typename O::S *dtab)
 {
     using T = typename O::T;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int c = lane;
     const int SA = (Bm + 1) * Q;
+    // 1 / (r1^2 (b+1)(b+2)) and 1 / (r^2 (a+1)(a+2)), once per block (FP64 division is slow)
+    typename O::S *denB = dtab, *denA = dtab + Q;
+    for (int i = threadIdx.x; i < Q; i += blockDim.x) {
+        O::st(denB + i, O::from(1.0 / (r1 * r1 * (i + 1.0) * (i + 2.0))));
+        O::st(denA + i, O::from(1.0 / (r * r * (i + 1.0) * (i + 2.0))));
+    }
+    __syncthreads();
     const T r1d = O::from(r1), r1s = O::from(r1 * r1), r1x2 = O::from(2.0 * r1);
     const T rd = O::from(r), rs = O::from(r * r), rx2 = O::from(2.0 * r);
     const float cc2 = (float)((c + 1) * (c + 2));
@@ -350,7 +357,7 @@ __device__ void gbar_fill_warp(double r, double r1, int N, int P, int A, int Bm,
         if (c <= P - a) O::st(E + c, R0);
         if (Bm >= 1 && c <= P - a - 1) O::st(E + Q + c, R1);
         for (int b = 0; b + 2 <= Bm && a + b + 2 <= P; ++b) {
-            const T den = O::from(1.0 / (r1 * r1 * (b + 1.0) * (b + 2.0)));
+            const T den = O::ld(denB + b);
             const T d0 = O::down2(R0), dm1 = O::down2(Rm1), dm2 = O::down2(Rm2);
             T sv = O::add(O::mulf(O::mul(r1d, R1), (float)((b + 1) * (2 * b + 1))), O::mulf(R0, (float)(b * b) - n2));
             T t = O::mul(r1s, d0);
@@ -383,7 +390,7 @@ __device__ void gbar_fill_warp(double r, double r1, int N, int P, int A, int Bm,
         if (c <= P - b) O::st(E + c, O::mul(R0, fc));
         if (A >= 1 && c <= P - b - 1) O::st(E + SA + c, O::mul(R1, fc));
         for (int a = 0; a + 2 <= A && a + 2 + b <= P; ++a) {
-            const T den = O::from(1.0 / (r * r * (a + 1.0) * (a + 2.0)));
+            const T den = O::ld(denA + a);
             const T d0 = O::down2(R0), dm1 = O::down2(Rm1), dm2 = O::down2(Rm2);
             T sv = O::add(O::mulf(O::mul(rd, R1), (float)((a + 1) * (2 * a + 1))), O::mulf(R0, (float)(a * a) - n2));
             T t = O::mul(rs, d0);
@@ -427,19 +434,23 @@ __device__ void gbar_block(double r, double r1, double x, int N, int P, int A, i
             for (int n = 0; n <= Nw; ++n) G[n] = s * tab.c[n] * ys[n * 32];
     }
     // 2. Taylor coefficients in x of 1/rho_pm^2 and the rational factors of Appendix A
-    if (threadIdx.x == 0) {
-        double *vp = tv, *vm = tv + Q, *fxp = tv + 2 * Q, *fxm = tv + 3 * Q, *hp = tv + 4 * Q, *hm = tv + 5 * Q;
-        double *hp1 = tv + 6 * Q, *hm1 = tv + 7 * Q, *dhp = tv + 8 * Q, *dhm = tv + 9 * Q;
-        for (int sgn = 0; sgn < 2; ++sgn) {
-            double aa = sgn == 0 ? r + r1 : r - r1;
-            double *v = sgn == 0 ? vp : vm;
-            double u0 = aa * aa + x * x, iu0 = 1.0 / u0;
-            v[0] = iu0;
-            if (P >= 1) v[1] = -2.0 * x * iu0 * iu0;
-            for (int q = 2; q <= P; ++q) v[q] = -(2.0 * x * v[q - 1] + v[q - 2]) * iu0;
-        }
+    //    (the recursion for v on two threads, the q-wise factors on one thread per q)
+    double *vp = tv, *vm = tv + Q, *fxp_ = tv + 2 * Q, *fxm_ = tv + 3 * Q, *hp_ = tv + 4 * Q, *hm_ = tv + 5 * Q;
+    double *hp1_ = tv + 6 * Q, *hm1_ = tv + 7 * Q, *dhp_ = tv + 8 * Q, *dhm_ = tv + 9 * Q;
+    if (threadIdx.x < 2) {
+        const int sgn = threadIdx.x;
+        double aa = sgn == 0 ? r + r1 : r - r1;
+        double *v = sgn == 0 ? vp : vm;
+        double u0 = aa * aa + x * x, iu0 = 1.0 / u0;
+        v[0] = iu0;
+        if (P >= 1) v[1] = -2.0 * x * iu0 * iu0;
+        for (int q = 2; q <= P; ++q) v[q] = -(2.0 * x * v[q - 1] + v[q - 2]) * iu0;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q <= P; q += blockDim.x) {
+        double *fxp = fxp_, *fxm = fxm_, *hp = hp_, *hm = hm_, *hp1 = hp1_, *hm1 = hm1_, *dhp = dhp_, *dhm = dhm_;
         double cc = r * r - r1 * r1;
-        for (int q = 0; q <= P; ++q) {
+        {
             fxp[q] = x * vp[q] + (q >= 1 ? vp[q - 1] : 0.0);
             fxm[q] = x * vm[q] + (q >= 1 ? vm[q - 1] : 0.0);
             double a1 = q >= 1 ? 2.0 * x : 0.0;
@@ -453,7 +464,7 @@ __device__ void gbar_block(double r, double r1, double x, int N, int P, int A, i
             const double *v = sgn == 0 ? vp : vm;
             double s = sgn == 0 ? 1.0 : -1.0, aa = r + s * r1;
             double *d = sgn == 0 ? dhp : dhm;
-            for (int q = 0; q <= P; ++q) {
+            {
                 // (cc - x^2) v^2 Taylor coefficient q, via w = v*v
                 double wq = 0, wq1 = 0, wq2 = 0;
                 for (int t = 0; t <= q; ++t) wq += v[t] * v[q - t];
@@ -475,13 +486,13 @@ __device__ void gbar_block(double r, double r1, double x, int N, int P, int A, i
     for (int k = 0; k < P; ++k) {
         for (int n = threadIdx.x; n <= Nw; n += blockDim.x) {
             int m = n == 0 ? 1 : n - 1;
-            double acc = 0.0;
+            double acc0 = 0.0, acc1 = 0.0;  // two chains: the FP64 FMA latency dominates
             for (int q = 0; q <= k; ++q) {
                 double gp = g00[n * Q + k - q], gm = g00[m * Q + k - q];
-                acc = fma(gp + gm, fxp[q], acc);
-                acc = fma(gp - gm, fxm[q], acc);
+                acc0 = fma(gp + gm, fxp[q], acc0);
+                acc1 = fma(gp - gm, fxm[q], acc1);
             }
-            g00[n * Q + k + 1] = (n - 0.5) / (k + 1) * acc;
+            g00[n * Q + k + 1] = (n - 0.5) / (k + 1) * (acc0 + acc1);
         }
         __syncthreads();
     }
@@ -489,15 +500,18 @@ __device__ void gbar_block(double r, double r1, double x, int N, int P, int A, i
     for (int n = threadIdx.x; n <= Nw; n += blockDim.x) {
         int m = n == 0 ? 1 : n - 1;
         double nu = n - 0.5;
+        const double i2r = 1.0 / (2.0 * r), i2r1 = 1.0 / (2.0 * r1);
         for (int k = 0; k + 1 <= P; ++k) {
-            double a1 = 0.0, a2 = 0.0;
+            double a1p = 0.0, a1m = 0.0, a2p = 0.0, a2m = 0.0;
             for (int q = 0; q <= k; ++q) {
                 double gp = g00[n * Q + k - q], gm = g00[m * Q + k - q];
-                a1 += (gp + gm) * hp[q] + (gp - gm) * hm[q];
-                a2 += (gp + gm) * hp1[q] + (gp - gm) * hm1[q];
+                a1p = fma(gp + gm, hp[q], a1p);
+                a1m = fma(gp - gm, hm[q], a1m);
+                a2p = fma(gp + gm, hp1[q], a2p);
+                a2m = fma(gp - gm, hm1[q], a2m);
             }
-            g10[n * Q + k] = (-g00[n * Q + k] + nu * a1) / (2.0 * r);
-            g01[n * Q + k] = (-g00[n * Q + k] + nu * a2) / (2.0 * r1);
+            g10[n * Q + k] = (-g00[n * Q + k] + nu * (a1p + a1m)) * i2r;
+            g01[n * Q + k] = (-g00[n * Q + k] + nu * (a2p + a2m)) * i2r1;
         }
     }
     __syncthreads();
@@ -505,22 +519,28 @@ __device__ void gbar_block(double r, double r1, double x, int N, int P, int A, i
     for (int n = threadIdx.x; n <= Nw; n += blockDim.x) {
         int m = n == 0 ? 1 : n - 1;
         double nu = n - 0.5;
+        const double i2r = 1.0 / (2.0 * r);
         for (int k = 0; k + 2 <= P; ++k) {
-            double acc = 0.0;
+            double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
             for (int q = 0; q <= k; ++q) {
                 double g0p = g00[n * Q + k - q], g0m = g00[m * Q + k - q];
                 double g1p = g01[n * Q + k - q], g1m = g01[m * Q + k - q];
-                acc += (g0p + g0m) * dhp[q] + (g1p + g1m) * hp[q] + (g0p - g0m) * dhm[q] + (g1p - g1m) * hm[q];
+                c0 = fma(g0p + g0m, dhp[q], c0);
+                c1 = fma(g1p + g1m, hp[q], c1);
+                c2 = fma(g0p - g0m, dhm[q], c2);
+                c3 = fma(g1p - g1m, hm[q], c3);
             }
-            g11[n * Q + k] = (-g01[n * Q + k] + nu * acc) / (2.0 * r);
+            g11[n * Q + k] = (-g01[n * Q + k] + nu * ((c0 + c1) + (c2 + c3))) * i2r;
         }
     }
     __syncthreads();
     if (P <= 31) {  // warp-parallel fill (every order a plan accepts: 2M <= 30)
+        double *dtab = G + nmw;  // [2 Q]
         if (dfout)
-            gbar_fill_warp<NumDF>(r, r1, N, P, A, Bm, Q, g00, g10, g01, g11, dfout, scale, fact);
+            gbar_fill_warp<NumDF>(r, r1, N, P, A, Bm, Q, g00, g10, g01, g11, dfout, scale, fact,
+                                  reinterpret_cast<float2 *>(dtab));
         else
-            gbar_fill_warp<NumF64>(r, r1, N, P, A, Bm, Q, g00, g10, g01, g11, out, scale, fact);
+            gbar_fill_warp<NumF64>(r, r1, N, P, A, Bm, Q, g00, g10, g01, g11, out, scale, fact, dtab);
         return;
     }
     if (dfout) return;  // not reached: FP32-pair expansions come from plans (P = 2M <= 30)
@@ -579,7 +599,8 @@ __device__ void gbar_block(double r, double r1, double x, int N, int P, int A, i
 static size_t gbar_smem(int N, int P)
 {
     int nmw = (N < 1 ? 1 : N) + 1;
-    return sizeof(double) * ((size_t)AFMM_REC_TAB + (size_t)nmw * 32 + 10 * (size_t)(P + 1) + 4 * (size_t)nmw * (P + 1) + nmw);
+    return sizeof(double) * ((size_t)AFMM_REC_TAB + (size_t)nmw * 32 + 10 * (size_t)(P + 1) + 4 * (size_t)nmw * (P + 1) + nmw +
+                             2 * (size_t)(P + 1));
 }
 
 // unit entry point: one point per block, dense (P+1)^3 per mode
@@ -1012,7 +1033,7 @@ static afmm_status far_field_t(afmm_plan p, int dir)
         if (v.nstation > 0) {
             // the FP64 path generates its expansions directly as FP32 pairs
             const bool dfx = !mix && p->precision == AFMM_FP64;
-            k_gexp_level<<<(unsigned)(v.nstation * 16), 128, gsm, st>>>(v.col_of_station, v.station_of_col, v.nstation,
+            k_gexp_level<<<(unsigned)(v.nstation * 16), 256, gsm, st>>>(v.col_of_station, v.station_of_col, v.nstation,
                                                                         l, p->r0 / h, h, nm, M, *p->rec, p->pp,
                                                                         dfx ? nullptr : p->gexp,
                                                                         dfx ? p->gexp_df : nullptr);
