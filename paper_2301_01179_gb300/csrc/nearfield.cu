@@ -101,6 +101,15 @@ __device__ __forceinline__ void l2p_eval32(const float *__restrict__ F, int M, f
 }
 
 // Kahan-compensated FP32 accumulation: (sum, running compensation) in a float2
+// Kahan-compensated FP32 sum: s holds the sum, c the compensation (true sum ~ s - c)
+__device__ __forceinline__ void kahan_add(float &s, float &c, float v)
+{
+    const float y = __fsub_rn(v, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
 __device__ __forceinline__ void kadd(float2 &a, float v)
 {
     float y = v - a.y;
@@ -620,8 +629,9 @@ __device__ __forceinline__ void l2p_eval_df(const float2 *__restrict__ F, int M,
 
 #define NEARDF_WB 8
 
-// MPER: modes per warp (compile time), accumulators in registers
-template <bool GRAD, int MPER>
+// MPER: modes per warp (compile time), accumulators in registers.  MIX: the MIXED precision
+// (same FP32-pair sequence, FP32 products with Kahan-compensated FP32 sums, FP32 locals)
+template <bool GRAD, int MPER, bool MIX>
 __global__ void __launch_bounds__(NEARDF_WB * 32, (MPER <= 5 ? 2 : 1)) k_near_df(const NearArgs a, const RecTab tab)
 {
     extern __shared__ double smem[];
@@ -747,6 +757,36 @@ __global__ void __launch_bounds__(NEARDF_WB * 32, (MPER <= 5 ? 2 : 1)) k_near_df
                 float2 yp = n0 == 0 ? yk[32 + lane] : yk[(n0 - 1) * 32 + lane];  // y_{-1} := y_1
                 yprev = df_make(yp.x, yp.y);
             }
+            if (MIX) {
+                // FP32 products of the pairs' high words, Kahan-compensated sums (aE: compensation)
+                const float scf = sc.hi, gxf = gx.hi, qff = qf.hi;
+#pragma unroll
+                for (int j = 0; j < MPER; ++j) {
+                    const int n = n0 + j;
+                    if (n < nm) {
+                        const float2 yv = yk[n * 32 + lane];
+                        const float yn = yv.x;
+                        const float qr = a.q32_re[(size_t)n * a.nsrc + s], qi = a.q32_im[(size_t)n * a.nsrc + s];
+                        const float gn = scf * yn;
+                        kahan_add(aS[0][j], aE[0][j], qr * gn);
+                        kahan_add(aS[1][j], aE[1][j], qi * gn);
+                        if (GRAD) {
+                            // y_n A + rho_n y_{n-1} B cancels for near pairs (A ~ -B): FP32 pairs
+                            const dfv ynd = df_make(yv.x, yv.y);
+                            const float2 rr = rho2[n];
+                            const float wt =
+                                df_add(df_mul(ynd, As), df_mul(df_mul(df_make(rr.x, rr.y), yprev), Bs)).hi;
+                            yprev = ynd;
+                            const float xw = gxf * wt, qw = qff * wt;
+                            kahan_add(aS[2 % NC][j], aE[2 % NC][j], qr * qw);
+                            kahan_add(aS[3 % NC][j], aE[3 % NC][j], qi * qw);
+                            kahan_add(aS[4 % NC][j], aE[4 % NC][j], qr * xw);
+                            kahan_add(aS[5 % NC][j], aE[5 % NC][j], qi * xw);
+                        }
+                    }
+                }
+                continue;
+            }
 #pragma unroll
             for (int j = 0; j < MPER; ++j) {
                 const int n = n0 + j;
@@ -779,17 +819,21 @@ __global__ void __launch_bounds__(NEARDF_WB * 32, (MPER <= 5 ? 2 : 1)) k_near_df
     for (int q = 0; q < NC; ++q)
 #pragma unroll
         for (int j = 0; j < MPER; ++j) {
-            double v = (double)aS[q][j] + (double)aE[q][j];
+            double v = MIX ? (double)aS[q][j] - (double)aE[q][j] : (double)aS[q][j] + (double)aE[q][j];
             for (int o = 1 << lgT; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             cs[q][j] = v;
         }
     if (!active || slice != 0) return;
     dfv u = df_make(0.f, 0.f), v = u;
-    if (a.locdf_re) {
+    double ud = 0.0, vd = 0.0;
+    const bool has_loc = MIX ? a.loc32_re != nullptr : a.locdf_re != nullptr;
+    if (has_loc) {
         uint32_t kk = a.leaf_key[box];
         double cr = a.r0 + ((double)morton_ir(kk) + 0.5) * a.h, cz = a.z0 + ((double)morton_iz(kk) + 0.5) * a.h;
-        u = df_from_double((rt - cr) / a.h);
-        v = df_from_double((zt - cz) / a.h);
+        ud = (rt - cr) / a.h;
+        vd = (zt - cz) / a.h;
+        u = df_from_double(ud);
+        v = df_from_double(vd);
     }
     const int64_t dst = a.out_perm ? a.out_perm[t] : t;
 #pragma unroll
@@ -806,7 +850,22 @@ __global__ void __launch_bounds__(NEARDF_WB * 32, (MPER <= 5 ? 2 : 1)) k_near_df
             dz_r = nu * cs[4 % NC][j];
             dz_i = nu * cs[5 % NC][j];
         }
-        if (a.locdf_re) {
+        if (has_loc && MIX) {
+            const float *Fr = a.loc32_re + ((size_t)box * nm + n) * a.ncoef;
+            const float *Fi = a.loc32_im + ((size_t)box * nm + n) * a.ncoef;
+            float vr, dur, dvr, vi, dui, dvi;
+            l2p_eval32<GRAD>(Fr, a.M, (float)ud, (float)vd, vr, dur, dvr);
+            l2p_eval32<GRAD>(Fi, a.M, (float)ud, (float)vd, vi, dui, dvi);
+            pr += vr;
+            pi += vi;
+            if (GRAD) {
+                const double ih = 1.0 / a.h;
+                dr_r += dur * ih;
+                dr_i += dui * ih;
+                dz_r += dvr * ih;
+                dz_i += dvi * ih;
+            }
+        } else if (has_loc) {
             const float2 *Fr = a.locdf_re + ((size_t)box * nm + n) * a.ncoef;
             const float2 *Fi = a.locdf_im + ((size_t)box * nm + n) * a.ncoef;
             dfv vr, dur, dvr, vi, dui, dvi;
@@ -855,28 +914,28 @@ static size_t neardf_smem(int nm, int grad)
                              (size_t)NEARDF_WB * npp * 32);
 }
 
-template <bool GRAD, int MPER>
+template <bool GRAD, int MPER, bool MIX>
 static afmm_status launch_near_df_k(const NearArgs &a, const RecTab &tab, cudaStream_t st)
 {
     size_t sm = neardf_smem(a.nmodes, GRAD);
     if (sm > 227 * 1024) return AFMM_EUNSUPPORTED;
-    AFMM_CUDA(cudaFuncSetAttribute(k_near_df<GRAD, MPER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_near_df<GRAD, MPER><<<(unsigned)a.nunits, NEARDF_WB * 32, sm, st>>>(a, tab);
+    AFMM_CUDA(cudaFuncSetAttribute(k_near_df<GRAD, MPER, MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_near_df<GRAD, MPER, MIX><<<(unsigned)a.nunits, NEARDF_WB * 32, sm, st>>>(a, tab);
     AFMM_LAUNCH_CHECK();
     return AFMM_OK;
 }
 
-template <bool GRAD>
+template <bool GRAD, bool MIX>
 static afmm_status launch_near_df(const NearArgs &a, const RecTab &tab, cudaStream_t st)
 {
     int mper = (a.nmodes + NEARDF_WB - 1) / NEARDF_WB;
-    if (mper <= 1) return launch_near_df_k<GRAD, 1>(a, tab, st);
-    if (mper <= 2) return launch_near_df_k<GRAD, 2>(a, tab, st);
-    if (mper <= 3) return launch_near_df_k<GRAD, 3>(a, tab, st);
-    if (mper <= 4) return launch_near_df_k<GRAD, 4>(a, tab, st);
-    if (mper <= 5) return launch_near_df_k<GRAD, 5>(a, tab, st);
-    if (mper <= 9) return launch_near_df_k<GRAD, 9>(a, tab, st);
-    if (mper <= 17) return launch_near_df_k<GRAD, 17>(a, tab, st);
+    if (mper <= 1) return launch_near_df_k<GRAD, 1, MIX>(a, tab, st);
+    if (mper <= 2) return launch_near_df_k<GRAD, 2, MIX>(a, tab, st);
+    if (mper <= 3) return launch_near_df_k<GRAD, 3, MIX>(a, tab, st);
+    if (mper <= 4) return launch_near_df_k<GRAD, 4, MIX>(a, tab, st);
+    if (mper <= 5) return launch_near_df_k<GRAD, 5, MIX>(a, tab, st);
+    if (mper <= 9) return launch_near_df_k<GRAD, 9, MIX>(a, tab, st);
+    if (mper <= 17) return launch_near_df_k<GRAD, 17, MIX>(a, tab, st);
     return AFMM_EUNSUPPORTED;
 }
 
@@ -1090,7 +1149,7 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
     size_t sm = near2_smem(p->nmodes, grad);
     unsigned grid = (unsigned)a.nunits;
     const int T = NEAR2_WB * 32;
-    if (p->precision != AFMM_FP64 && sm > 227 * 1024) return AFMM_EUNSUPPORTED;
+    if (p->precision == AFMM_FP64_NATIVE && sm > 227 * 1024) return AFMM_EUNSUPPORTED;
     if (p->precision == AFMM_FP64) {
         a.qdf_re = p->qsdf;
         a.qdf_im = p->qsdf + (size_t)p->nmodes * p->n_max;
@@ -1102,9 +1161,17 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
         }
         a.df_fwd_switch = (float)p->df_fwd_switch;
         if (grad)
-            AFMM_TRY(launch_near_df<true>(a, *p->rec, p->stream));
+            AFMM_TRY((launch_near_df<true, false>(a, *p->rec, p->stream)));
         else
-            AFMM_TRY(launch_near_df<false>(a, *p->rec, p->stream));
+            AFMM_TRY((launch_near_df<false, false>(a, *p->rec, p->stream)));
+    } else if (mix) {
+        // MIXED: the FP32-pair sequence with compensated FP32 sums (GB300's FP64 issues at
+        // 1/61 of FP32, so the pair arithmetic is the fast way to the FP64-class sequence)
+        a.df_fwd_switch = (float)p->df_fwd_switch;
+        if (grad)
+            AFMM_TRY((launch_near_df<true, true>(a, *p->rec, p->stream)));
+        else
+            AFMM_TRY((launch_near_df<false, true>(a, *p->rec, p->stream)));
     } else if (grad && mix) {
         AFMM_CUDA(cudaFuncSetAttribute(k_near2<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_near2<true, true><<<grid, T, sm, p->stream>>>(a, *p->rec);
@@ -1118,7 +1185,7 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
         AFMM_CUDA(cudaFuncSetAttribute(k_near2<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_near2<false, false><<<grid, T, sm, p->stream>>>(a, *p->rec);
     }
-    if (p->precision != AFMM_FP64) AFMM_LAUNCH_CHECK();
+    if (p->precision == AFMM_FP64_NATIVE) AFMM_LAUNCH_CHECK();
     if (a.part) {
         int ncomp = grad ? 6 : 2;
         int64_t tot = (int64_t)ncomp * a.nmodes * a.nfield;
