@@ -50,9 +50,10 @@ typedef enum {
                              where it is exact enough and faster on GB300 (near field, L2P), and
                              the S2L contraction on the bf16 tensor cores by exact 8-bit digit
                              slicing (48-bit operands, see s2l_engine) */
-    AFMM_MIXED = 1,       /* FP64 Legendre recursion and elliptic start values; FP32 bulk
-                             accumulation (compensated) and FP32 expansions (Sec. 2 with scaled
-                             coordinates, Eq. gfunc:scaled) */
+    AFMM_MIXED = 1,       /* FP64-class Legendre recursion and elliptic start values (FP32
+                             pairs); FP32 products with compensated FP32 sums; FP32 moments and
+                             locals (Sec. 2 with scaled coordinates, Eq. gfunc:scaled); S2L on
+                             the tensor cores with 4-digit (32-bit) slicing */
     AFMM_FP64_NATIVE = 2  /* every floating-point operation of the path in native FP64 */
 } afmm_precision;
 
@@ -70,9 +71,9 @@ typedef struct {
                            the forward sweep's error growth below ~2e-12).  The paper's
                            fixed switch is chi < 1.008 (Appendix A). */
     int miller_extra;   /* Miller start L = N + ceil(miller_extra / acosh(chi)) + 2 (0: 15) */
-    int s2l_engine;     /* AFMM_FP64 only. 0: S2L (Eq. analysis:s2l) on the tcgen05 tensor
-                           cores when order <= 12, else on CUDA cores; 1: always on CUDA
-                           cores in FP32-pair arithmetic */
+    int s2l_engine;     /* AFMM_FP64 and AFMM_MIXED. 0: S2L (Eq. analysis:s2l) on the tcgen05
+                           tensor cores when order <= 12, else on CUDA cores; 1: always on
+                           CUDA cores (FP32 pairs for AFMM_FP64, FP32 for AFMM_MIXED) */
 } afmm_options;
 
 typedef struct afmm_plan_s *afmm_plan;

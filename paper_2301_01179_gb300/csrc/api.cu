@@ -189,14 +189,15 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
         nexp += (int64_t)v.nstation * 12;
     }
     p->expansions = nexp;
-    // FP64 expansions (the FP64 path generates FP32-pair expansions instead)
-    if (s == AFMM_OK && gcap > 0 && p->precision != AFMM_FP64) s = dalloc_t(p, &p->gexp, gcap);
+    // FP64 expansions (the FP64 path and the tensor-core S2L use FP32-pair expansions instead)
+    const bool dfx = p->precision == AFMM_FP64 || s2l_tc_enabled(p);
+    if (s == AFMM_OK && gcap > 0 && !dfx) s = dalloc_t(p, &p->gexp, gcap);
     p->gexp_cap = gcap;
     if (s == AFMM_OK && p->precision == AFMM_FP64) {
         s = dalloc_t(p, &p->qsdf, (size_t)2 * nm * nmax);
         if (s == AFMM_OK) s = dalloc_t(p, &p->locdf, (size_t)2 * p->lv[p->d].nbox * nm * nc);
     }
-    if (s == AFMM_OK && p->precision == AFMM_FP64) {
+    if (s == AFMM_OK && dfx) {
         int64_t mmax = 0;
         for (int l = 2; l <= p->d; ++l) mmax = p->lv[l].nbox > mmax ? p->lv[l].nbox : mmax;
         if (gcap > 0) s = dalloc_t(p, &p->gexp_df, gcap);

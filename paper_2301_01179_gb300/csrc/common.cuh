@@ -234,4 +234,5 @@ bool s2l_tc_enabled(afmm_plan p);
 int64_t s2l_tc_slice_elems(afmm_plan p, int64_t nbox);
 afmm_status make_tc_tables(afmm_plan p);
 afmm_status launch_s2l_tc(afmm_plan p, int l, const double *mre, const double *mim, double *lre, double *lim);
+afmm_status launch_s2l_tc(afmm_plan p, int l, const float *mre, const float *mim, float *lre, float *lim);
 }  // namespace afmm

@@ -949,8 +949,7 @@ static afmm_status launch_s2l(afmm_plan p, int l, const R *mre, const R *mim, R 
     int W = p->M + 1;
     size_t sm = sizeof(R) * ((size_t)W * W * (2 * p->M + 1) + 2 * (size_t)p->ncoef * 32);
     int kpt = (p->ncoef + 3) / 4;
-    if (sizeof(R) == sizeof(double) && s2l_tc_enabled(p))
-        return launch_s2l_tc(p, l, (const double *)mre, (const double *)mim, (double *)lre, (double *)lim);
+    if (s2l_tc_enabled(p)) return launch_s2l_tc(p, l, mre, mim, lre, lim);
     if (sizeof(R) == sizeof(double) && p->precision == AFMM_FP64) {
         // FP64 path: FP32-pair arithmetic (same shared-memory size: float2 per entry)
         const S2LArgs<double> &ad = reinterpret_cast<const S2LArgs<double> &>(a);
@@ -1031,8 +1030,8 @@ static afmm_status far_field_t(afmm_plan p, int dir)
         tmark(p, e + 1);
         double h = p->L / (double)(1 << l);
         if (v.nstation > 0) {
-            // the FP64 path generates its expansions directly as FP32 pairs
-            const bool dfx = !mix && p->precision == AFMM_FP64;
+            // the FP64 path and the tensor-core S2L take their expansions directly as FP32 pairs
+            const bool dfx = (!mix && p->precision == AFMM_FP64) || s2l_tc_enabled(p);
             k_gexp_level<<<(unsigned)(v.nstation * 16), 256, gsm, st>>>(v.col_of_station, v.station_of_col, v.nstation,
                                                                         l, p->r0 / h, h, nm, M, *p->rec, p->pp,
                                                                         dfx ? nullptr : p->gexp,

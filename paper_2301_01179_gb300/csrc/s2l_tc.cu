@@ -128,11 +128,12 @@ __device__ __forceinline__ float round_magic(int e) { return __uint_as_float((ui
 // the six digits of v = hi + lo on the grid 2^E > |v|: digit s is a multiple of 2^(E-8-8s)
 // with at most 8 significant bits; the digits of hi are exact, lo joins at the fourth digit
 // with one FP32 rounding (below 2^(E-48))
-__device__ __forceinline__ void digits6(float hi, float lo, int E, float d[TC_SLICES])
+template <int NS>
+__device__ __forceinline__ void digits(float hi, float lo, int E, float d[NS])
 {
     float a = hi;
 #pragma unroll
-    for (int s = 0; s < TC_SLICES; ++s) {
+    for (int s = 0; s < NS; ++s) {
         if (s == 3) a = __fadd_rn(a, lo);
         const float c = round_magic(E - 8 - 8 * s);
         const float t = __fsub_rn(__fadd_rn(a, c), c);
@@ -162,14 +163,14 @@ struct S2LTcArgs {
     const int32_t *unit_box, *unit_col, *s2l, *station_of_col;
     int level, nm, M, nc;
     const float2 *gexp_df;        // [station][16][mode][(M+1)^2 (2M+1)] FP32 pairs
-    const __nv_bfloat16 *asl;     // [box][mode][re, im][6][KP] digit slices of A
-    double *loc_re, *loc_im;      // [box][mode][ncoef], += F
+    const __nv_bfloat16 *asl;     // [box][mode][re, im][NS][KP] digit slices of A
+    void *loc_re, *loc_im;        // [box][mode][ncoef] of the locals' type, += F
     int *err;                     // set to 1 when a bounded wait runs out
 };
 
 // ---- A operand: digit slices of j! S_ij per (box, mode, re/im) row, one warp per row
-template <int KP>
-__global__ void __launch_bounds__(256) k_slice_moments(const double *__restrict__ mre, const double *__restrict__ mim,
+template <int KP, int NS, typename MT>
+__global__ void __launch_bounds__(256) k_slice_moments(const MT *__restrict__ mre, const MT *__restrict__ mim,
                                                        int64_t nbox, int nm, int nc, const TcTables tp,
                                                        __nv_bfloat16 *__restrict__ out)
 {
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(256) k_slice_moments(const double *__restrict_
     if (row >= nbox * nm * 2) return;
     const int reim = (int)(row & 1);
     const int64_t bm = row >> 1;  // box * nm + mode
-    const double *src = (reim ? mim : mre) + bm * nc;
+    const MT *src = (reim ? mim : mre) + bm * nc;
     constexpr int PER = (KP + 31) / 32;
     dfv v[PER];
     float m = 0.f;
@@ -190,7 +191,8 @@ __global__ void __launch_bounds__(256) k_slice_moments(const double *__restrict_
         const int ij = lane + 32 * t;
         v[t] = df_make(0.f, 0.f);
         if (ij < nc) {
-            v[t] = df_mulf(df_from_double(src[ij]), tt.jfact[tt.cj[ij]]);
+            const dfv x = sizeof(MT) == sizeof(double) ? df_from_double((double)src[ij]) : df_make((float)src[ij], 0.f);
+            v[t] = df_mulf(x, tt.jfact[tt.cj[ij]]);
             m = fmaxf(m, fabsf(v[t].hi));
         }
     }
@@ -198,19 +200,19 @@ __global__ void __launch_bounds__(256) k_slice_moments(const double *__restrict_
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     const bool live = m >= 1e-30f && m < 1e30f;
     const int E = live ? grid_exp(m) + 1 : 0;
-    __nv_bfloat16 *dst = out + row * (TC_SLICES * KP);
+    __nv_bfloat16 *dst = out + row * (NS * KP);
 #pragma unroll
     for (int t = 0; t < PER; ++t) {
         const int ij = lane + 32 * t;
         if (ij < KP) {
-            float d[TC_SLICES];
+            float d[NS];
             if (live && ij < nc)
-                digits6(v[t].hi, v[t].lo, E, d);
+                digits<NS>(v[t].hi, v[t].lo, E, d);
             else
 #pragma unroll
-                for (int s = 0; s < TC_SLICES; ++s) d[s] = 0.f;
+                for (int s = 0; s < NS; ++s) d[s] = 0.f;
 #pragma unroll
-            for (int s = 0; s < TC_SLICES; ++s) dst[s * KP + ij] = __float2bfloat16_rn(d[s]);
+            for (int s = 0; s < NS; ++s) dst[s * KP + ij] = __float2bfloat16_rn(d[s]);
         }
     }
 }
@@ -222,21 +224,24 @@ __global__ void __launch_bounds__(256) k_slice_moments(const double *__restrict_
 // through two buffers while thread 0 issues the 21 slice-pair MMAs per K step, and finally
 // drain the four exact levels into the FP32-pair registers.  Thread (warp w, lane) owns TMEM
 // lane 32 (w % 4) + lane (box (w % 2) 32 + lane, re/im w % 4 / 2) and a quarter of the columns.
-template <int KP>
+template <int KP, int NS, typename LT>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, const TcTables tp)
 {
+    // NS digit slices (6: FP64 path, 4: MIXED); levels 0 .. NE-1 exact and drained per slot,
+    // level NE (and above) in FP32 over all slots
+    constexpr int NE = NS == 6 ? 4 : 2;
     constexpr int KG = KP / 8;              // core matrices along K
     constexpr int BT = KP * KP * 2;         // bytes of one B slice (N = KP rows)
     constexpr int AT = 128 * KP * 2;        // bytes of one A slice buffer
     constexpr int QC = KP / 4;              // accumulator columns drained per thread
     constexpr uint32_t IDESC = umma_idesc(128, KP);
-    constexpr int NACC = 5;                 // accumulators: levels 0, 1, 2, 3 (exact) and 4 + 5
+    constexpr int NACC = NE + 1;            // accumulators: the exact levels and the rest
     static_assert(NACC * KP <= 512, "TMEM holds 512 FP32 columns");
     constexpr uint32_t NCOL = NACC * KP <= 32 ? 32 : NACC * KP <= 64 ? 64 : NACC * KP <= 128 ? 128 : NACC * KP <= 256 ? 256 : 512;
     constexpr int NW = TC_THREADS / 32;
     extern __shared__ __align__(128) uint8_t smem[];
-    uint8_t *sB = smem;                                       // [6][KP rows][KP] bf16
-    uint8_t *sA = smem + TC_SLICES * BT;                      // [2][128 rows][KP] bf16
+    uint8_t *sB = smem;                                       // [NS][KP rows][KP] bf16
+    uint8_t *sA = smem + NS * BT;                             // [2][128 rows][KP] bf16
     float2 *sE = reinterpret_cast<float2 *>(sA + 2 * AT);     // the slot's cube [(M+1)^2 (2M+1)]
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tbase;
@@ -286,7 +291,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = tbase;  // accumulator lv (0 .. 4) at TMEM columns [lv KP, (lv + 1) KP)
+    const uint32_t tmem = tbase;  // accumulator lv (0 .. NE) at TMEM columns [lv KP, (lv + 1) KP)
 
     // thread 0 polls the mbarrier (bounded); the block learns the outcome at the barrier
     uint32_t nphase[2] = {0, 0};
@@ -313,7 +318,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
 #pragma unroll
     for (int t = 0; t < QC; ++t) accS[t] = accE[t] = 0.f;
     bool any_work = false;
-    bool l4_init = false;  // thread 0: the level-4 accumulator holds a sum
+    bool lx_init = false;  // thread 0: the inexact accumulator holds a sum
 
     constexpr int ntaskB = KP * KG;   // 16-byte chunks of one B slice
     constexpr int ntaskA = 128 * KG;  // 16-byte chunks of one A slice
@@ -327,7 +332,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
         if (tid < 128) {
             const int b = bx[tid & 63];
             const int s2 = b >= 0 ? a.s2l[(size_t)b * 27 + slot] : -1;
-            rbase[tid] = s2 >= 0 ? (((long long)s2 * nm + n) * 2 + (tid >> 6)) * TC_SLICES * KP : -1ll;
+            rbase[tid] = s2 >= 0 ? (((long long)s2 * nm + n) * 2 + (tid >> 6)) * NS * KP : -1ll;
             has = s2 >= 0;
         }
         if (!__syncthreads_or(has)) continue;
@@ -379,19 +384,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
             if (lane == 0) colE[kl] = (m >= 1e-30f && m < 1e30f) ? grid_exp(m) + 1 : -1000;
         }
         __syncthreads();
-        // B: pass 2, digits of E_{k,i,j+l} / j! into the six slices (chunk T at byte 16 T)
+        // B: pass 2, digits of E_{k,i,j+l} / j! into the NS slices (chunk T at byte 16 T)
         for (int T = tid; T < ntaskB; T += TC_THREADS) {
             const int kl = (T / (KG * 8)) * 8 + (T & 7), kc = (T >> 3) % KG;
-            uint32_t w[TC_SLICES][4];
+            uint32_t w[NS][4];
 #pragma unroll
-            for (int s = 0; s < TC_SLICES; ++s) w[s][0] = w[s][1] = w[s][2] = w[s][3] = 0u;
+            for (int s = 0; s < NS; ++s) w[s][0] = w[s][1] = w[s][2] = w[s][3] = 0u;
             const int Ec = kl < nc ? colE[kl] : -1000;
             if (Ec > -1000) {
                 const int okl = offK[inward][kl];
                 const int ok = okl >> 4, l = okl & 15;
 #pragma unroll
                 for (int e2 = 0; e2 < 4; ++e2) {
-                    float dd[2][TC_SLICES];
+                    float dd[2][NS];
 #pragma unroll
                     for (int e1 = 0; e1 < 2; ++e1) {
                         const int ij = kc * 8 + e2 * 2 + e1;
@@ -402,25 +407,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
                             if (backward && ((j + l) & 1)) ev = make_float2(-ev.x, -ev.y);
                             const float2 rf = rj[j];
                             const dfv v = df_mul(df_make(ev.x, ev.y), df_make(rf.x, rf.y));
-                            digits6(v.hi, v.lo, Ec, dd[e1]);
+                            digits<NS>(v.hi, v.lo, Ec, dd[e1]);
                         } else {
 #pragma unroll
-                            for (int s = 0; s < TC_SLICES; ++s) dd[e1][s] = 0.f;
+                            for (int s = 0; s < NS; ++s) dd[e1][s] = 0.f;
                         }
                     }
 #pragma unroll
-                    for (int s = 0; s < TC_SLICES; ++s) w[s][e2] = pack_bf16(dd[0][s], dd[1][s]);
+                    for (int s = 0; s < NS; ++s) w[s][e2] = pack_bf16(dd[0][s], dd[1][s]);
                 }
             }
 #pragma unroll
-            for (int s = 0; s < TC_SLICES; ++s)
+            for (int s = 0; s < NS; ++s)
                 *reinterpret_cast<uint4 *>(sB + s * BT + T * 16) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
         }
 
-        // slices of A in turn, double-buffered; slice i meets B slices 0 .. 5 - i
-        for (int i = 0; i < TC_SLICES; ++i) {
+        // slices of A in turn, double-buffered; slice i meets B slices 0 .. NS - 1 - i
+        for (int i = 0; i < NS; ++i) {
             const int b = i & 1;
-            if (i + 1 < TC_SLICES) {
+            if (i + 1 < NS) {
                 wait_buf(b ^ 1);
                 if (abort_) break;
                 load_A(i + 1, b ^ 1);
@@ -433,15 +438,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
             if (tid == 0) {
                 tc_fence_after();
                 const uint32_t abase = smem_u32(sA + b * AT), bbase = smem_u32(sB);
-                for (int j = 0; j + i < TC_SLICES; ++j) {
-                    const int lv = i + j < 4 ? i + j : 4;
+                for (int j = 0; j + i < NS; ++j) {
+                    const int lv = i + j < NE ? i + j : NE;
                     for (int ks = 0; ks < KP / 16; ++ks) {
                         const uint64_t ad = umma_desc(abase + ks * 256, 128, KG * 128);
                         const uint64_t bd = umma_desc(bbase + j * BT + ks * 256, 128, KG * 128);
-                        // levels 0..3 restart every slot with the pair (0, lv); level 4 spans all slots
-                        const uint32_t acc = lv < 4 ? (ks > 0 || i > 0) : (ks > 0 || l4_init);
+                        // exact levels restart every slot with the pair (0, lv); level NE spans all slots
+                        const uint32_t acc = lv < NE ? (ks > 0 || i > 0) : (ks > 0 || lx_init);
                         umma_bf16(tmem + (uint32_t)(KP * lv), ad, bd, IDESC, acc);
-                        if (lv == 4) l4_init = true;
+                        if (lv == NE) lx_init = true;
                     }
                 }
                 umma_commit(&mbar[b]);
@@ -457,7 +462,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
         if (abort_) break;
         tc_fence_after();
 #pragma unroll
-        for (int lv = 0; lv < 4; ++lv) {
+        for (int lv = 0; lv < NE; ++lv) {
 #pragma unroll
             for (int c = 0; c < QC / 4; ++c) {
                 float v[4];
@@ -481,23 +486,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
         __syncthreads();
     }
 
-    // levels 4 and 5 (accumulated over all slots), 1 / l!, and the write-back
+    // the inexact levels (accumulated over all slots), 1 / l!, and the write-back
     if (!abort_ && any_work) {
         tc_fence_after();
         const int bl = row & 63, reim = row >> 6;
         const int box = bx[bl];
-        double *dst = box >= 0 ? (reim ? a.loc_im : a.loc_re) + ((size_t)box * nm + n) * nc : nullptr;
+        LT *dst = box >= 0 ? static_cast<LT *>(reim ? a.loc_im : a.loc_re) + ((size_t)box * nm + n) * nc : nullptr;
 #pragma unroll
         for (int c = 0; c < QC / 4; ++c) {
             float v[4];
-            tmem_ld4(tmem + (uint32_t)(4 * KP) + ((uint32_t)(32 * q) << 16) + c0 + 4 * c, v);
+            tmem_ld4(tmem + (uint32_t)(NE * KP) + ((uint32_t)(32 * q) << 16) + c0 + 4 * c, v);
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 const int kl = c0 + 4 * c + t;
                 if (dst && kl < nc) {
                     const float2 rl = rj[offK[0][kl] & 15];
                     const double f = ((double)accS[4 * c + t] + (double)accE[4 * c + t]) + (double)v[t];
-                    dst[kl] += f * ((double)rl.x + (double)rl.y);
+                    dst[kl] += (LT)(f * ((double)rl.x + (double)rl.y));
                 }
             }
         }
@@ -513,12 +518,16 @@ static int tc_kp(int nc) { return (nc + 15) / 16 * 16; }
 
 bool s2l_tc_enabled(afmm_plan p)
 {
-    return p->precision == AFMM_FP64 && p->opt.s2l_engine == 0 && p->ncoef <= 96;
+    return (p->precision == AFMM_FP64 || p->precision == AFMM_MIXED) && p->opt.s2l_engine == 0 && p->ncoef <= 96;
 }
+
+// digit slices per operand: six (48 bits) for the FP64 path, four (32 bits) for MIXED (three
+// cost 24-bit truncation, 6e-6 on cfg2, above the FP32 near field's 1e-6)
+static int tc_slices(afmm_plan p) { return p->precision == AFMM_MIXED ? 4 : TC_SLICES; }
 
 int64_t s2l_tc_slice_elems(afmm_plan p, int64_t nbox)
 {
-    return nbox * p->nmodes * 2 * TC_SLICES * (int64_t)tc_kp(p->ncoef);
+    return nbox * p->nmodes * 2 * tc_slices(p) * (int64_t)tc_kp(p->ncoef);
 }
 
 afmm_status make_tc_tables(afmm_plan p)
@@ -547,15 +556,16 @@ afmm_status make_tc_tables(afmm_plan p)
     return AFMM_OK;
 }
 
-template <int KP>
-static afmm_status launch_tc_k(afmm_plan p, int l, const double *mre, const double *mim, double *lre, double *lim)
+template <int KP, int NS, typename R>
+static afmm_status launch_tc_k(afmm_plan p, int l, const R *mre, const R *mim, R *lre, R *lim)
 {
     Level &v = p->lv[l];
     cudaStream_t st = p->stream;
     const int nm = p->nmodes, nc = p->ncoef;
     __nv_bfloat16 *asl = reinterpret_cast<__nv_bfloat16 *>(p->asl);
     const int64_t rows = v.nbox * nm * 2;
-    k_slice_moments<KP><<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(mre, mim, v.nbox, nm, nc, *p->tct, asl);
+    k_slice_moments<KP, NS, R><<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(mre, mim, v.nbox, nm, nc,
+                                                                                  *p->tct, asl);
     AFMM_LAUNCH_CHECK();
     S2LTcArgs a;
     a.unit_box = v.unit64_box;
@@ -572,26 +582,39 @@ static afmm_status launch_tc_k(afmm_plan p, int l, const double *mre, const doub
     a.loc_im = lim;
     a.err = p->err_dev;
     const int W = p->M + 1;
-    const size_t sm = (size_t)TC_SLICES * KP * KP * 2 + (size_t)2 * 128 * KP * 2 + (size_t)W * W * (2 * p->M + 1) * 8;
-    AFMM_CUDA(cudaFuncSetAttribute(k_s2l_tc<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_s2l_tc<KP><<<dim3((unsigned)v.nunit64, (unsigned)nm), TC_THREADS, sm, st>>>(a, *p->tct);
+    const size_t sm = (size_t)NS * KP * KP * 2 + (size_t)2 * 128 * KP * 2 + (size_t)W * W * (2 * p->M + 1) * 8;
+    AFMM_CUDA(cudaFuncSetAttribute(k_s2l_tc<KP, NS, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_s2l_tc<KP, NS, R><<<dim3((unsigned)v.nunit64, (unsigned)nm), TC_THREADS, sm, st>>>(a, *p->tct);
     AFMM_LAUNCH_CHECK();
     return AFMM_OK;
+}
+
+template <int NS, typename R>
+static afmm_status launch_tc_ns(afmm_plan p, int l, const R *mre, const R *mim, R *lre, R *lim)
+{
+    switch (tc_kp(p->ncoef)) {
+    case 16: return launch_tc_k<16, NS, R>(p, l, mre, mim, lre, lim);
+    case 32: return launch_tc_k<32, NS, R>(p, l, mre, mim, lre, lim);
+    case 48: return launch_tc_k<48, NS, R>(p, l, mre, mim, lre, lim);
+    case 64: return launch_tc_k<64, NS, R>(p, l, mre, mim, lre, lim);
+    case 80: return launch_tc_k<80, NS, R>(p, l, mre, mim, lre, lim);
+    case 96: return launch_tc_k<96, NS, R>(p, l, mre, mim, lre, lim);
+    }
+    return AFMM_EUNSUPPORTED;
 }
 
 afmm_status launch_s2l_tc(afmm_plan p, int l, const double *mre, const double *mim, double *lre, double *lim)
 {
     if (p->lv[l].nunit64 == 0) return AFMM_OK;
     if (!p->asl || !p->tct || !p->err_dev || !p->gexp_df) return AFMM_EINVAL;
-    switch (tc_kp(p->ncoef)) {
-    case 16: return launch_tc_k<16>(p, l, mre, mim, lre, lim);
-    case 32: return launch_tc_k<32>(p, l, mre, mim, lre, lim);
-    case 48: return launch_tc_k<48>(p, l, mre, mim, lre, lim);
-    case 64: return launch_tc_k<64>(p, l, mre, mim, lre, lim);
-    case 80: return launch_tc_k<80>(p, l, mre, mim, lre, lim);
-    case 96: return launch_tc_k<96>(p, l, mre, mim, lre, lim);
-    }
-    return AFMM_EUNSUPPORTED;
+    return launch_tc_ns<TC_SLICES, double>(p, l, mre, mim, lre, lim);
+}
+
+afmm_status launch_s2l_tc(afmm_plan p, int l, const float *mre, const float *mim, float *lre, float *lim)
+{
+    if (p->lv[l].nunit64 == 0) return AFMM_OK;
+    if (!p->asl || !p->tct || !p->err_dev || !p->gexp_df) return AFMM_EINVAL;
+    return launch_tc_ns<4, float>(p, l, mre, mim, lre, lim);
 }
 
 }  // namespace afmm

@@ -664,7 +664,7 @@ afmm_status build_tree(afmm_plan p, const double *src_r, const double *src_z, co
         AFMM_LAUNCH_CHECK();
         AFMM_TRY(bitonic_sort(srt, npad, st));
         for (int us = 32; us <= 64; us += 32) {
-            if (us == 64 && p->precision != AFMM_FP64) break;  // tensor-core units: FP64 path only
+            if (us == 64 && !s2l_tc_enabled(p)) break;  // units of the tensor-core S2L
             k_unit_flags<<<nblk(nb), 256, 0, st>>>(srt, nb, us, f);
             AFMM_LAUNCH_CHECK();
             AFMM_TRY(scan_excl(f, pos, nb, tmp, st));
