@@ -178,6 +178,11 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
             if (s == AFMM_OK) s = dalloc_t(p, &v.mom32_im, per);
             if (s == AFMM_OK) s = dalloc_t(p, &v.loc32_re, per);
             if (s == AFMM_OK) s = dalloc_t(p, &v.loc32_im, per);
+        } else if (p->precision == AFMM_FP64) {  // FP32 pairs
+            s = dalloc_t(p, &v.momd_re, per);
+            if (s == AFMM_OK) s = dalloc_t(p, &v.momd_im, per);
+            if (s == AFMM_OK) s = dalloc_t(p, &v.locd_re, per);
+            if (s == AFMM_OK) s = dalloc_t(p, &v.locd_im, per);
         } else {
             s = dalloc_t(p, &v.mom_re, per);
             if (s == AFMM_OK) s = dalloc_t(p, &v.mom_im, per);
@@ -193,10 +198,7 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
     const bool dfx = p->precision == AFMM_FP64 || s2l_tc_enabled(p);
     if (s == AFMM_OK && gcap > 0 && !dfx) s = dalloc_t(p, &p->gexp, gcap);
     p->gexp_cap = gcap;
-    if (s == AFMM_OK && p->precision == AFMM_FP64) {
-        s = dalloc_t(p, &p->qsdf, (size_t)2 * nm * nmax);
-        if (s == AFMM_OK) s = dalloc_t(p, &p->locdf, (size_t)2 * p->lv[p->d].nbox * nm * nc);
-    }
+    if (s == AFMM_OK && p->precision == AFMM_FP64) s = dalloc_t(p, &p->qsdf, (size_t)2 * nm * nmax);
     if (s == AFMM_OK && dfx) {
         int64_t mmax = 0;
         for (int l = 2; l <= p->d; ++l) mmax = p->lv[l].nbox > mmax ? p->lv[l].nbox : mmax;
@@ -204,8 +206,6 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
         if (s2l_tc_enabled(p)) {
             if (s == AFMM_OK) s = dalloc_t(p, &p->asl, (size_t)s2l_tc_slice_elems(p, mmax));
             if (s == AFMM_OK) s = make_tc_tables(p);
-        } else if (s == AFMM_OK) {
-            s = dalloc_t(p, &p->mom_df, (size_t)2 * mmax * nm * nc);
         }
     }
     // device-side error word in mapped host memory (set by kernels whose bounded waits run out)
@@ -306,7 +306,6 @@ static afmm_status run_fmm(afmm_plan p, int dir, const double *q_re, const doubl
     AFMM_TRY(launch_permute(p, dir, q_re, q_im));
     tmark(p, 1);
     AFMM_TRY(far_field(p, dir));
-    if (p->precision == AFMM_FP64) AFMM_TRY(split_leaf_locals(p));
     tmark(p, 8);
     AFMM_TRY(launch_near(p, dir, 1, grad, o_re, o_im, dr_re, dr_im, dz_re, dz_im, 0));
     tmark(p, 9);

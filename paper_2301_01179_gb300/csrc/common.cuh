@@ -142,6 +142,8 @@ struct Level {
     double *loc_re = nullptr, *loc_im = nullptr;  // [nbox][nmodes][ncoef]
     float *mom32_re = nullptr, *mom32_im = nullptr;  // MIXED: [nbox][nmodes][ncoef]
     float *loc32_re = nullptr, *loc32_im = nullptr;
+    float2 *momd_re = nullptr, *momd_im = nullptr;   // FP64 path: FP32 pairs [nbox][nmodes][ncoef]
+    float2 *locd_re = nullptr, *locd_im = nullptr;
 };
 
 // tensor-core S2L: factor tables and coefficient-index maps (host-built, passed by value)
@@ -180,17 +182,16 @@ struct afmm_plan_s {
     double *qs_re = nullptr, *qs_im = nullptr;  // [nmodes][max(ns,nf)] strengths, sorted, * c_n
     float *qs32_re = nullptr, *qs32_im = nullptr;  // MIXED: the same in FP32
     float2 *qsdf = nullptr;                     // FP64 path: the same as FP32 pairs [2][nmodes][n]
-    float2 *locdf = nullptr;                    // FP64 path: leaf locals as FP32 pairs [2][nbox][nmodes][ncoef]
     double df_fwd_switch = 4.5;                 // forward switch of the FP32-pair recursion
     double *gexp = nullptr;                     // expansions of one level
     float2 *gexp_df = nullptr;                  // FP64 path: the same as FP32 pairs
-    float2 *mom_df = nullptr;                   // FP64 path: moments of one level as FP32 pairs [2][...]
     uint16_t *asl = nullptr;                    // tensor-core S2L: bf16 digit slices of the moments of one level
     afmm::TcTables *tct = nullptr;              // tensor-core S2L tables (host)
     int *err_host = nullptr, *err_dev = nullptr;  // device-side error word (mapped host memory)
     int64_t gexp_cap = 0;                       // doubles
     double *m2m_tab = nullptr;                  // [4][2][(M+1)^2] shift tables (see farfield.cu)
     double *l2l_tab = nullptr;
+    float2 *m2m_tab_df = nullptr, *l2l_tab_df = nullptr;  // the same as FP32 pairs
     double *acc_buf = nullptr;                  // [6][nmodes][max(ns,nf)] adjoint temporaries
     double *part_buf = nullptr;                 // direct sums split over sources: partials
     int64_t part_cap = 0;                       // doubles in part_buf
@@ -228,11 +229,11 @@ afmm_status far_field(afmm_plan p, int dir);
 afmm_status launch_green_expansion(int64_t npts, const double *r, const double *r1, const double *x,
                                    int n_modes, int P, double *out, cudaStream_t st);
 afmm_status make_shift_tables(afmm_plan p);
-afmm_status split_leaf_locals(afmm_plan p);
 // s2l_tc.cu
 bool s2l_tc_enabled(afmm_plan p);
 int64_t s2l_tc_slice_elems(afmm_plan p, int64_t nbox);
 afmm_status make_tc_tables(afmm_plan p);
 afmm_status launch_s2l_tc(afmm_plan p, int l, const double *mre, const double *mim, double *lre, double *lim);
 afmm_status launch_s2l_tc(afmm_plan p, int l, const float *mre, const float *mim, float *lre, float *lim);
+afmm_status launch_s2l_tc(afmm_plan p, int l, const float2 *mre, const float2 *mim, float2 *lre, float2 *lim);
 }  // namespace afmm

@@ -65,6 +65,17 @@ afmm_status make_shift_tables(afmm_plan p)
     AFMM_TRY(dalloc_t(p, &p->l2l_tab, l2l.size()));
     AFMM_CUDA(cudaMemcpy(p->m2m_tab, m2m.data(), m2m.size() * sizeof(double), cudaMemcpyHostToDevice));
     AFMM_CUDA(cudaMemcpy(p->l2l_tab, l2l.data(), l2l.size() * sizeof(double), cudaMemcpyHostToDevice));
+    // the same tables as FP32 pairs (hi = nearest float, lo = the rest) for the FP64 path
+    std::vector<float2> m2mf(m2m.size()), l2lf(l2l.size());
+    for (size_t i = 0; i < m2m.size(); ++i) {
+        float h = (float)m2m[i], g = (float)l2l[i];
+        m2mf[i] = make_float2(h, (float)(m2m[i] - (double)h));
+        l2lf[i] = make_float2(g, (float)(l2l[i] - (double)g));
+    }
+    AFMM_TRY(dalloc_t(p, &p->m2m_tab_df, m2mf.size()));
+    AFMM_TRY(dalloc_t(p, &p->l2l_tab_df, l2lf.size()));
+    AFMM_CUDA(cudaMemcpy(p->m2m_tab_df, m2mf.data(), m2mf.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    AFMM_CUDA(cudaMemcpy(p->l2l_tab_df, l2lf.data(), l2lf.size() * sizeof(float2), cudaMemcpyHostToDevice));
     return AFMM_OK;
 }
 
@@ -262,6 +273,207 @@ __global__ void k_l2l(const int32_t *__restrict__ parent, const uint32_t *__rest
             oi_[o] = fi;
         }
         __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// FP64 path: moments and locals as FP32 pairs ([re, im] arrays of float2), the same
+// operators as k_p2m / k_m2m / k_l2l above in pair arithmetic (GB300's FP64 issues at 1/61
+// of FP32).  Sums are (hi, err) pairs updated by exact two-sums.
+// ------------------------------------------------------------------------------------
+__global__ void k_p2m_df(const uint32_t *__restrict__ key, const int2 *__restrict__ rng, int64_t nbox,
+                         const double *__restrict__ sr, const double *__restrict__ sz, const float2 *__restrict__ q_re,
+                         const float2 *__restrict__ q_im, int64_t nsrc, int nm, int M, double r0, double z0, double h,
+                         const RecTab tab, float2 *__restrict__ mom_re, float2 *__restrict__ mom_im)
+{
+    extern __shared__ float2 smf[];
+    const int nc = (M + 1) * (M + 2) / 2;
+    float2 *mono = smf;                    // [32][nc] U^i W^j / j!
+    float2 *acc = mono + 32 * nc;          // [2][nm][nc] (hi, err)
+    float2 *invf = acc + 2 * (size_t)nm * nc;  // [M+1] 1/j!
+    float2 *ic = invf + (M + 1);           // [nm] 1/c_n
+    const int64_t b = blockIdx.x;
+    if (b >= nbox) return;
+    for (int i = threadIdx.x; i < 2 * nm * nc; i += blockDim.x) acc[i] = make_float2(0.f, 0.f);
+    for (int j = threadIdx.x; j <= M; j += blockDim.x) {
+        double f = 1.0;
+        for (int t = 2; t <= j; ++t) f *= t;
+        const dfv v = df_from_double(1.0 / f);
+        invf[j] = make_float2(v.hi, v.lo);
+    }
+    for (int n = threadIdx.x; n < nm; n += blockDim.x) {
+        const dfv v = df_from_double(1.0 / tab.c[n]);
+        ic[n] = make_float2(v.hi, v.lo);
+    }
+    const uint32_t k = key[b];
+    const double cr = r0 + ((double)morton_ir(k) + 0.5) * h, cz = z0 + ((double)morton_iz(k) + 0.5) * h;
+    const double ih = 1.0 / h;
+    const int2 R = rng[b];
+    __syncthreads();
+    for (int s0 = R.x; s0 < R.y; s0 += 32) {
+        const int cnt = min(32, R.y - s0);
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+            const dfv U = df_from_double((sr[s0 + t] - cr) * ih), Wv = df_from_double(-(sz[s0 + t] - cz) * ih);
+            dfv ui = df_make(1.f, 0.f);
+            for (int i = 0; i <= M; ++i) {
+                dfv wj = ui;
+                for (int j = 0; i + j <= M; ++j) {
+                    const dfv m = df_mul(wj, df_make(invf[j].x, invf[j].y));
+                    mono[t * nc + cix(i, j, M)] = make_float2(m.hi, m.lo);
+                    wj = df_mul(wj, Wv);
+                }
+                ui = df_mul(ui, U);
+            }
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < nm * nc; o += blockDim.x) {
+            const int n = o / nc, c = o % nc;
+            float2 ar = acc[o], ai = acc[nm * nc + o];
+            for (int t = 0; t < cnt; ++t) {
+                const float2 m2 = mono[t * nc + c];
+                const dfv m = df_make(m2.x, m2.y);
+                const float2 qr = q_re[(size_t)n * nsrc + s0 + t], qi = q_im[(size_t)n * nsrc + s0 + t];
+                df_acc(ar.x, ar.y, df_make(qr.x, qr.y), m);
+                df_acc(ai.x, ai.y, df_make(qi.x, qi.y), m);
+            }
+            acc[o] = ar;
+            acc[nm * nc + o] = ai;
+        }
+        __syncthreads();
+    }
+    // the amplitudes carry the recursion constant c_n: divide it out
+    for (int o = threadIdx.x; o < nm * nc; o += blockDim.x) {
+        const int n = o / nc;
+        const dfv c = df_make(ic[n].x, ic[n].y);
+        const dfv vr = df_mul(two_sum(acc[o].x, acc[o].y), c), vi = df_mul(two_sum(acc[nm * nc + o].x, acc[nm * nc + o].y), c);
+        mom_re[(size_t)b * nm * nc + o] = make_float2(vr.hi, vr.lo);
+        mom_im[(size_t)b * nm * nc + o] = make_float2(vi.hi, vi.lo);
+    }
+}
+
+#define SHIFT_MB 8  // modes per block of the FP32-pair shifts (the table is staged once)
+
+// M2M in FP32 pairs: one block per (parent, 8 modes)
+__global__ void k_m2m_df(const int2 *__restrict__ child, const uint32_t *__restrict__ ckey, int64_t npar, int nm, int M,
+                         const float2 *__restrict__ tab, const float2 *__restrict__ cre, const float2 *__restrict__ cim,
+                         float2 *__restrict__ pre, float2 *__restrict__ pim)
+{
+    extern __shared__ float2 smf[];
+    const int nc = (M + 1) * (M + 2) / 2, W = M + 1;
+    float2 *X = smf;          // [2][nc]
+    float2 *T = X + 2 * nc;   // [4][W][W]
+    for (int i = threadIdx.x; i < 4 * W * W; i += blockDim.x) T[i] = tab[i];
+    const int64_t P = blockIdx.x;
+    __syncthreads();
+    if (P >= npar) return;
+    const int2 ch = child[P];
+    for (int n = blockIdx.y * SHIFT_MB; n < nm && n < (blockIdx.y + 1) * SHIFT_MB; ++n) {
+    float2 accr[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, acci[2] = {accr[0], accr[1]};
+    for (int c = ch.x; c < ch.y; ++c) {
+        const uint32_t k = ckey[c];
+        const int br = morton_ir(k) & 1, bz = morton_iz(k) & 1;
+        const float2 *Ar = T + (0 * 2 + br) * W * W, *Bz = T + (1 * 2 + bz) * W * W;
+        const float2 *sr_ = cre + ((size_t)c * nm + n) * nc, *si_ = cim + ((size_t)c * nm + n) * nc;
+        // X_{i,j} = sum_q Ar[i][q] S_{i-q, j}
+        for (int o = threadIdx.x; o < nc; o += blockDim.x) {
+            int i = 0, rem = o;
+            while (rem >= M + 1 - i) { rem -= M + 1 - i; ++i; }
+            const int j = rem;
+            float xr = 0.f, er = 0.f, xi = 0.f, ei = 0.f;
+            for (int q = 0; q <= i; ++q) {
+                const dfv av = df_make(Ar[i * W + q].x, Ar[i * W + q].y);
+                const int s = cix(i - q, j, M);
+                df_acc(xr, er, av, df_make(sr_[s].x, sr_[s].y));
+                df_acc(xi, ei, av, df_make(si_[s].x, si_[s].y));
+            }
+            const dfv vr = two_sum(xr, er), vi = two_sum(xi, ei);
+            X[o] = make_float2(vr.hi, vr.lo);
+            X[nc + o] = make_float2(vi.hi, vi.lo);
+        }
+        __syncthreads();
+        for (int hh = 0; hh < 2; ++hh) {
+            const int o = threadIdx.x + hh * blockDim.x;
+            if (o >= nc) break;
+            int i = 0, rem = o;
+            while (rem >= M + 1 - i) { rem -= M + 1 - i; ++i; }
+            const int j = rem;
+            for (int v = 0; v <= j; ++v) {
+                const dfv bc = df_make(Bz[j * W + v].x, Bz[j * W + v].y);
+                const int s = cix(i, j - v, M);
+                df_acc(accr[hh].x, accr[hh].y, bc, df_make(X[s].x, X[s].y));
+                df_acc(acci[hh].x, acci[hh].y, bc, df_make(X[nc + s].x, X[nc + s].y));
+            }
+        }
+        __syncthreads();
+    }
+    for (int hh = 0; hh < 2; ++hh) {
+        const int o = threadIdx.x + hh * blockDim.x;
+        if (o >= nc) break;
+        const dfv vr = two_sum(accr[hh].x, accr[hh].y), vi = two_sum(acci[hh].x, acci[hh].y);
+        pre[((size_t)P * nm + n) * nc + o] = make_float2(vr.hi, vr.lo);
+        pim[((size_t)P * nm + n) * nc + o] = make_float2(vi.hi, vi.lo);
+    }
+    }
+}
+
+// L2L in FP32 pairs: one block per (box, 8 modes); overwrites (level-2 locals start at zero)
+__global__ void k_l2l_df(const int32_t *__restrict__ parent, const uint32_t *__restrict__ key, int64_t nbox, int nm,
+                         int M, const float2 *__restrict__ tab, const float2 *__restrict__ fre_p,
+                         const float2 *__restrict__ fim_p, float2 *__restrict__ fre, float2 *__restrict__ fim)
+{
+    extern __shared__ float2 smf[];
+    const int nc = (M + 1) * (M + 2) / 2, W = M + 1;
+    float2 *Y = smf;          // [2][nc]
+    float2 *T = Y + 2 * nc;   // [4][W][W]
+    for (int i = threadIdx.x; i < 4 * W * W; i += blockDim.x) T[i] = tab[i];
+    const int64_t b = blockIdx.x;
+    __syncthreads();
+    if (b >= nbox) return;
+    const int32_t P = parent ? parent[b] : -1;
+    for (int n = blockIdx.y * SHIFT_MB; n < nm && n < (blockIdx.y + 1) * SHIFT_MB; ++n) {
+    float2 *or_ = fre + ((size_t)b * nm + n) * nc, *oi_ = fim + ((size_t)b * nm + n) * nc;
+    if (P < 0) {
+        for (int o = threadIdx.x; o < nc; o += blockDim.x) or_[o] = oi_[o] = make_float2(0.f, 0.f);
+        continue;
+    }
+    const uint32_t k = key[b];
+    const int br = morton_ir(k) & 1, bz = morton_iz(k) & 1;
+    const float2 *Lr = T + (0 * 2 + br) * W * W, *Lz = T + (1 * 2 + bz) * W * W;
+    const float2 *pr = fre_p + ((size_t)P * nm + n) * nc, *pi = fim_p + ((size_t)P * nm + n) * nc;
+    // Y_{k,m} = sum_{l >= m} Lz[m][l] F_{k,l}
+    for (int o = threadIdx.x; o < nc; o += blockDim.x) {
+        int kk = 0, rem = o;
+        while (rem >= M + 1 - kk) { rem -= M + 1 - kk; ++kk; }
+        const int m = rem;
+        float yr = 0.f, er = 0.f, yi = 0.f, ei = 0.f;
+        for (int l = m; kk + l <= M; ++l) {
+            const dfv c = df_make(Lz[m * W + l].x, Lz[m * W + l].y);
+            const int s = cix(kk, l, M);
+            df_acc(yr, er, c, df_make(pr[s].x, pr[s].y));
+            df_acc(yi, ei, c, df_make(pi[s].x, pi[s].y));
+        }
+        const dfv vr = two_sum(yr, er), vi = two_sum(yi, ei);
+        Y[o] = make_float2(vr.hi, vr.lo);
+        Y[nc + o] = make_float2(vi.hi, vi.lo);
+    }
+    __syncthreads();
+    // F^c_{i,m} = sum_{k >= i} Lr[i][k] Y_{k,m}
+    for (int o = threadIdx.x; o < nc; o += blockDim.x) {
+        int i = 0, rem = o;
+        while (rem >= M + 1 - i) { rem -= M + 1 - i; ++i; }
+        const int m = rem;
+        float fr = 0.f, er = 0.f, fi = 0.f, ei = 0.f;
+        for (int kk = i; kk + m <= M; ++kk) {
+            const dfv c = df_make(Lr[i * W + kk].x, Lr[i * W + kk].y);
+            const int s = cix(kk, m, M);
+            df_acc(fr, er, c, df_make(Y[s].x, Y[s].y));
+            df_acc(fi, ei, c, df_make(Y[nc + s].x, Y[nc + s].y));
+        }
+        const dfv vr = two_sum(fr, er), vi = two_sum(fi, ei);
+        or_[o] = make_float2(vr.hi, vr.lo);
+        oi_[o] = make_float2(vi.hi, vi.lo);
+    }
+    __syncthreads();  // Y is rewritten for the next mode
     }
 }
 
@@ -665,7 +877,8 @@ struct S2LArgs {
     const double *gexp;
     const R *mom_re, *mom_im;
     R *loc_re, *loc_im;
-    const float2 *gexp_df, *mom_df_re, *mom_df_im;  // FP32-pair copies (FP64 path)
+    const float2 *gexp_df, *mom_df_re, *mom_df_im;  // FP32-pair moments and expansions (FP64 path)
+    float2 *locd_re, *locd_im;                      // FP32-pair locals (FP64 path)
 };
 
 template <typename R, int KPT>
@@ -894,9 +1107,12 @@ __global__ void __launch_bounds__(128) k_s2l_df(const S2LArgs<double> a)
             while (rem >= M + 1 - k) { rem -= M + 1 - k; ++k; }
             double f = 1.0;
             for (int t = 2; t <= rem; ++t) f *= t;
+            const dfv rf = df_from_double(1.0 / f);
             size_t o = ((size_t)b * a.nm + n) * nc + kl;
-            a.loc_re[o] += ((double)aSr[q] + (double)aEr[q]) / f;
-            a.loc_im[o] += ((double)aSi[q] + (double)aEi[q]) / f;
+            const dfv vr = df_add(df_make(a.locd_re[o].x, a.locd_re[o].y), df_mul(two_sum(aSr[q], aEr[q]), rf));
+            const dfv vi = df_add(df_make(a.locd_im[o].x, a.locd_im[o].y), df_mul(two_sum(aSi[q], aEi[q]), rf));
+            a.locd_re[o] = make_float2(vr.hi, vr.lo);
+            a.locd_im[o] = make_float2(vi.hi, vi.lo);
         }
     }
 }
@@ -943,24 +1159,13 @@ static afmm_status launch_s2l(afmm_plan p, int l, const R *mre, const R *mim, R 
     a.mom_im = mim;
     a.loc_re = lre;
     a.loc_im = lim;
-    a.gexp_df = p->gexp_df;
-    a.mom_df_re = p->mom_df;
-    a.mom_df_im = p->mom_df ? p->mom_df + (size_t)v.nbox * p->nmodes * p->ncoef : nullptr;
+    a.gexp_df = nullptr;
+    a.mom_df_re = a.mom_df_im = nullptr;
+    a.locd_re = a.locd_im = nullptr;
     int W = p->M + 1;
     size_t sm = sizeof(R) * ((size_t)W * W * (2 * p->M + 1) + 2 * (size_t)p->ncoef * 32);
     int kpt = (p->ncoef + 3) / 4;
     if (s2l_tc_enabled(p)) return launch_s2l_tc(p, l, mre, mim, lre, lim);
-    if (sizeof(R) == sizeof(double) && p->precision == AFMM_FP64) {
-        // FP64 path: FP32-pair arithmetic (same shared-memory size: float2 per entry)
-        const S2LArgs<double> &ad = reinterpret_cast<const S2LArgs<double> &>(a);
-        if (kpt <= 4) return launch_s2l_df_k<4>(ad, p->stream, sm);
-        if (kpt <= 8) return launch_s2l_df_k<8>(ad, p->stream, sm);
-        if (kpt <= 12) return launch_s2l_df_k<12>(ad, p->stream, sm);
-        if (kpt <= 16) return launch_s2l_df_k<16>(ad, p->stream, sm);
-        if (kpt <= 24) return launch_s2l_df_k<24>(ad, p->stream, sm);
-        if (kpt <= 32) return launch_s2l_df_k<32>(ad, p->stream, sm);
-        return AFMM_EUNSUPPORTED;
-    }
     if (kpt <= 4) return launch_s2l_k<R, 4>(a, p->stream, sm);
     if (kpt <= 8) return launch_s2l_k<R, 8>(a, p->stream, sm);
     if (kpt <= 12) return launch_s2l_k<R, 12>(a, p->stream, sm);
@@ -1030,22 +1235,13 @@ static afmm_status far_field_t(afmm_plan p, int dir)
         tmark(p, e + 1);
         double h = p->L / (double)(1 << l);
         if (v.nstation > 0) {
-            // the FP64 path and the tensor-core S2L take their expansions directly as FP32 pairs
-            const bool dfx = (!mix && p->precision == AFMM_FP64) || s2l_tc_enabled(p);
+            // the tensor-core S2L takes its expansions directly as FP32 pairs
+            const bool dfx = s2l_tc_enabled(p);
             k_gexp_level<<<(unsigned)(v.nstation * 16), 256, gsm, st>>>(v.col_of_station, v.station_of_col, v.nstation,
                                                                         l, p->r0 / h, h, nm, M, *p->rec, p->pp,
                                                                         dfx ? nullptr : p->gexp,
                                                                         dfx ? p->gexp_df : nullptr);
             AFMM_LAUNCH_CHECK();
-        }
-        if (!mix && p->precision == AFMM_FP64) {
-            int64_t nmom = (int64_t)v.nbox * nm * nc;
-            if (!s2l_tc_enabled(p)) {  // the tensor-core S2L slices the FP64 moments itself
-                k_split_df<<<nblk(nmom), 256, 0, st>>>((const double *)MR(l), nmom, p->mom_df);
-                AFMM_LAUNCH_CHECK();
-                k_split_df<<<nblk(nmom), 256, 0, st>>>((const double *)MI(l), nmom, p->mom_df + nmom);
-                AFMM_LAUNCH_CHECK();
-            }
         }
         tmark(p, e + 2);
         AFMM_TRY(launch_s2l<R>(p, l, MR(l), MI(l), LR(l), LI(l)));
@@ -1054,22 +1250,94 @@ static afmm_status far_field_t(afmm_plan p, int dir)
     return AFMM_OK;
 }
 
-// FP64 path: leaf-level locals as FP32 pairs for the double-float local evaluation
-afmm_status split_leaf_locals(afmm_plan p)
+// Far field of the FP64 path: moments, locals and expansions as FP32 pairs throughout (the
+// same steps as far_field_t); the leaf locals stay in lv[d].locd_* for the near kernel
+static afmm_status far_field_df(afmm_plan p, int dir)
 {
-    Level &v = p->lv[p->d];
-    int64_t n = v.nbox * (int64_t)p->nmodes * p->ncoef;
-    k_split_df<<<nblk(n), 256, 0, p->stream>>>(v.loc_re, n, p->locdf);
-    AFMM_LAUNCH_CHECK();
-    k_split_df<<<nblk(n), 256, 0, p->stream>>>(v.loc_im, n, p->locdf + n);
-    AFMM_LAUNCH_CHECK();
+    const int d = p->d, M = p->M, nm = p->nmodes, nc = p->ncoef, W = M + 1;
+    cudaStream_t st = p->stream;
+    const bool fw = dir == 0;
+    const double *sr = fw ? p->s_r : p->t_r, *sz = fw ? p->s_z : p->t_z;
+    const int64_t nsrc = fw ? p->ns : p->nf;
+    const float2 *q_re = p->qsdf, *q_im = p->qsdf + (size_t)nm * p->n_max;
+    {
+        Level &v = p->lv[d];
+        const double h = p->L / (double)(1 << d);
+        const size_t sm = sizeof(float2) * (32 * (size_t)nc + 2 * (size_t)nm * nc + M + 1 + nm);
+        if (sm > 227 * 1024) return AFMM_EUNSUPPORTED;
+        AFMM_CUDA(cudaFuncSetAttribute(k_p2m_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_p2m_df<<<(unsigned)v.nbox, 128, sm, st>>>(v.key, fw ? v.srng : v.trng, v.nbox, sr, sz, q_re, q_im, nsrc, nm,
+                                                   M, p->r0, p->z0, h, *p->rec, v.momd_re, v.momd_im);
+        AFMM_LAUNCH_CHECK();
+    }
+    tmark(p, 2);
+    const size_t ssm = sizeof(float2) * (2 * (size_t)nc + 4 * (size_t)W * W);
+    for (int l = d - 1; l >= 2; --l) {
+        Level &v = p->lv[l];
+        k_m2m_df<<<dim3((unsigned)v.nbox, (unsigned)((nm + SHIFT_MB - 1) / SHIFT_MB)), 128, ssm, st>>>(v.child, p->lv[l + 1].key, v.nbox, nm, M,
+                                                                         p->m2m_tab_df, p->lv[l + 1].momd_re,
+                                                                         p->lv[l + 1].momd_im, v.momd_re, v.momd_im);
+        AFMM_LAUNCH_CHECK();
+    }
+    tmark(p, 3);
+    const size_t gsm = gbar_smem(p->N, 2 * M);
+    AFMM_CUDA(cudaFuncSetAttribute(k_gexp_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+    for (int l = 2; l <= d; ++l) {
+        Level &v = p->lv[l];
+        const int e = 16 + 4 * (l - 2);  // event slots: L2L, expansions, S2L, end
+        tmark(p, e);
+        k_l2l_df<<<dim3((unsigned)v.nbox, (unsigned)((nm + SHIFT_MB - 1) / SHIFT_MB)), 128, ssm, st>>>(
+            l >= 3 ? v.parent : nullptr, v.key, v.nbox, nm, M, p->l2l_tab_df, l >= 3 ? p->lv[l - 1].locd_re : nullptr,
+            l >= 3 ? p->lv[l - 1].locd_im : nullptr, v.locd_re, v.locd_im);
+        AFMM_LAUNCH_CHECK();
+        tmark(p, e + 1);
+        const double h = p->L / (double)(1 << l);
+        if (v.nstation > 0) {
+            k_gexp_level<<<(unsigned)(v.nstation * 16), 256, gsm, st>>>(v.col_of_station, v.station_of_col, v.nstation,
+                                                                        l, p->r0 / h, h, nm, M, *p->rec, p->pp,
+                                                                        nullptr, p->gexp_df);
+            AFMM_LAUNCH_CHECK();
+        }
+        tmark(p, e + 2);
+        if (s2l_tc_enabled(p)) {
+            AFMM_TRY(launch_s2l_tc(p, l, v.momd_re, v.momd_im, v.locd_re, v.locd_im));
+        } else if (v.nunit > 0) {
+            S2LArgs<double> a = {};
+            a.unit_box = v.unit_box;
+            a.unit_col = v.unit_col;
+            a.s2l = v.s2l;
+            a.station_of_col = v.station_of_col;
+            a.nunit = v.nunit;
+            a.level = l;
+            a.nm = nm;
+            a.M = M;
+            a.nc = nc;
+            a.gexp_df = p->gexp_df;
+            a.mom_df_re = v.momd_re;
+            a.mom_df_im = v.momd_im;
+            a.locd_re = v.locd_re;
+            a.locd_im = v.locd_im;
+            const size_t sm = sizeof(float2) * ((size_t)W * W * (2 * M + 1) + 2 * (size_t)nc * 32);
+            const int kpt = (nc + 3) / 4;
+            afmm_status r = AFMM_EUNSUPPORTED;
+            if (kpt <= 4) r = launch_s2l_df_k<4>(a, st, sm);
+            else if (kpt <= 8) r = launch_s2l_df_k<8>(a, st, sm);
+            else if (kpt <= 12) r = launch_s2l_df_k<12>(a, st, sm);
+            else if (kpt <= 16) r = launch_s2l_df_k<16>(a, st, sm);
+            else if (kpt <= 24) r = launch_s2l_df_k<24>(a, st, sm);
+            else if (kpt <= 32) r = launch_s2l_df_k<32>(a, st, sm);
+            AFMM_TRY(r);
+        }
+        tmark(p, e + 3);
+    }
     return AFMM_OK;
 }
 
 afmm_status far_field(afmm_plan p, int dir)
 {
     if (p->precision == AFMM_MIXED) return far_field_t<float>(p, dir);
-    return far_field_t<double>(p, dir);  // AFMM_FP64 (FP32-pair S2L) and AFMM_FP64_NATIVE
+    if (p->precision == AFMM_FP64) return far_field_df(p, dir);
+    return far_field_t<double>(p, dir);  // AFMM_FP64_NATIVE
 }
 
 }  // namespace afmm

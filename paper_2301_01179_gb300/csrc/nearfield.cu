@@ -1153,9 +1153,9 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
     if (p->precision == AFMM_FP64) {
         a.qdf_re = p->qsdf;
         a.qdf_im = p->qsdf + (size_t)p->nmodes * p->n_max;
-        if (a.loc_re) {
-            a.locdf_re = p->locdf;
-            a.locdf_im = p->locdf + (size_t)p->lv[d].nbox * p->nmodes * p->ncoef;
+        if (with_local && !direct) {  // the leaf locals are kept as FP32 pairs
+            a.locdf_re = p->lv[d].locd_re;
+            a.locdf_im = p->lv[d].locd_im;
             a.loc_re = nullptr;
             a.loc_im = nullptr;
         }

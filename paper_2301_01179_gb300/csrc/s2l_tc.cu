@@ -169,6 +169,26 @@ struct S2LTcArgs {
 };
 
 // ---- A operand: digit slices of j! S_ij per (box, mode, re/im) row, one warp per row
+__device__ __forceinline__ dfv to_df(double x) { return df_from_double(x); }
+__device__ __forceinline__ dfv to_df(float x) { return df_make(x, 0.f); }
+__device__ __forceinline__ dfv to_df(float2 x) { return df_make(x.x, x.y); }
+
+// local += (S + E + v) / l!  (S, E: the exact levels' pair; v: the FP32 levels)
+__device__ __forceinline__ void add_local(double &d, float S, float E, float v, float2 rl)
+{
+    d += (((double)S + (double)E) + (double)v) * ((double)rl.x + (double)rl.y);
+}
+__device__ __forceinline__ void add_local(float &d, float S, float E, float v, float2 rl)
+{
+    d += (float)((((double)S + (double)E) + (double)v) * ((double)rl.x + (double)rl.y));
+}
+__device__ __forceinline__ void add_local(float2 &d, float S, float E, float v, float2 rl)
+{
+    const dfv f = df_mul(df_add(two_sum(S, E), df_make(v, 0.f)), df_make(rl.x, rl.y));
+    const dfv r = df_add(df_make(d.x, d.y), f);
+    d = make_float2(r.hi, r.lo);
+}
+
 template <int KP, int NS, typename MT>
 __global__ void __launch_bounds__(256) k_slice_moments(const MT *__restrict__ mre, const MT *__restrict__ mim,
                                                        int64_t nbox, int nm, int nc, const TcTables tp,
@@ -191,8 +211,7 @@ __global__ void __launch_bounds__(256) k_slice_moments(const MT *__restrict__ mr
         const int ij = lane + 32 * t;
         v[t] = df_make(0.f, 0.f);
         if (ij < nc) {
-            const dfv x = sizeof(MT) == sizeof(double) ? df_from_double((double)src[ij]) : df_make((float)src[ij], 0.f);
-            v[t] = df_mulf(x, tt.jfact[tt.cj[ij]]);
+            v[t] = df_mulf(to_df(src[ij]), tt.jfact[tt.cj[ij]]);
             m = fmaxf(m, fabsf(v[t].hi));
         }
     }
@@ -499,11 +518,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 const int kl = c0 + 4 * c + t;
-                if (dst && kl < nc) {
-                    const float2 rl = rj[offK[0][kl] & 15];
-                    const double f = ((double)accS[4 * c + t] + (double)accE[4 * c + t]) + (double)v[t];
-                    dst[kl] += (LT)(f * ((double)rl.x + (double)rl.y));
-                }
+                if (dst && kl < nc) add_local(dst[kl], accS[4 * c + t], accE[4 * c + t], v[t], rj[offK[0][kl] & 15]);
             }
         }
     }
@@ -608,6 +623,13 @@ afmm_status launch_s2l_tc(afmm_plan p, int l, const double *mre, const double *m
     if (p->lv[l].nunit64 == 0) return AFMM_OK;
     if (!p->asl || !p->tct || !p->err_dev || !p->gexp_df) return AFMM_EINVAL;
     return launch_tc_ns<TC_SLICES, double>(p, l, mre, mim, lre, lim);
+}
+
+afmm_status launch_s2l_tc(afmm_plan p, int l, const float2 *mre, const float2 *mim, float2 *lre, float2 *lim)
+{
+    if (p->lv[l].nunit64 == 0) return AFMM_OK;
+    if (!p->asl || !p->tct || !p->err_dev || !p->gexp_df) return AFMM_EINVAL;
+    return launch_tc_ns<TC_SLICES, float2>(p, l, mre, mim, lre, lim);
 }
 
 afmm_status launch_s2l_tc(afmm_plan p, int l, const float *mre, const float *mim, float *lre, float *lim)
