@@ -152,6 +152,12 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
     p->ncoef = (opt.order + 1) * (opt.order + 2) / 2;
     p->precision = opt.precision;
     p->opt = opt;
+    // failure-detection test hook: AFMM_INJECT_TC_TIMEOUT=1 makes the tensor-core S2L skip the
+    // MMAs and the completion of its first slot, so that its bounded wait runs out
+    {
+        const char *e = getenv("AFMM_INJECT_TC_TIMEOUT");
+        p->inject_tc_timeout = (e && e[0] == '1') ? 1 : 0;
+    }
     p->pp.fwd_switch = opt.fwd_switch > 0.0 ? opt.fwd_switch : default_fwd_switch(p->N);
     p->pp.miller_extra = opt.miller_extra > 0 ? (double)opt.miller_extra : 15.0;
     // FP32-pair recursion (AFMM_FP64): rounding ~2^-47 instead of 2^-53, so the forward

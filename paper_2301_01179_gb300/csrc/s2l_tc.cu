@@ -40,7 +40,7 @@ namespace {
 
 constexpr int TC_SLICES = 6;
 constexpr int TC_THREADS = 512;
-constexpr long TC_WAIT_LIMIT = 1l << 26;  // mbarrier polls before giving up
+constexpr unsigned long long TC_WAIT_NS = 1000000000ull;  // a completion wait gives up after 1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -70,6 +70,13 @@ __device__ __forceinline__ void umma_commit(uint64_t *mbar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
                  : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 __device__ __forceinline__ bool mbar_try(uint64_t *mbar, uint32_t parity)
@@ -166,6 +173,7 @@ struct S2LTcArgs {
     const __nv_bfloat16 *asl;     // [box][mode][re, im][NS][KP] digit slices of A
     void *loc_re, *loc_im;        // [box][mode][ncoef] of the locals' type, += F
     int *err;                     // set to 1 when a bounded wait runs out
+    int inject_timeout;           // test hook: the first slot with work issues no MMA and no commit
 };
 
 // ---- A operand: digit slices of j! S_ij per (box, mode, re/im) row, one warp per row
@@ -320,8 +328,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
         if (!pend[b] || abort_) return;
         if (tid == 0) {
             const uint32_t par = (nphase[b] - 1) & 1;
-            bool ok = false;
-            for (long it = 0; it < TC_WAIT_LIMIT && !ok; ++it) ok = mbar_try(&mbar[b], par);
+            bool ok = mbar_try(&mbar[b], par);
+            const unsigned long long t0 = global_ns();
+            while (!ok && global_ns() - t0 < TC_WAIT_NS) ok = mbar_try(&mbar[b], par);
             wait_ok = ok;
             if (!ok) *(volatile int *)a.err = 1;
         }
@@ -355,6 +364,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
             has = s2 >= 0;
         }
         if (!__syncthreads_or(has)) continue;
+        const bool first_slot = !any_work;
         any_work = true;
         const int station = dr < 0 ? scol : col;
         const int sidx = a.station_of_col[station];
@@ -454,7 +464,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
             }
             fence_async_smem();
             __syncthreads();
-            if (tid == 0) {
+            if (tid == 0 && !(a.inject_timeout && first_slot)) {
                 tc_fence_after();
                 const uint32_t abase = smem_u32(sA + b * AT), bbase = smem_u32(sB);
                 for (int j = 0; j + i < NS; ++j) {
@@ -596,6 +606,7 @@ static afmm_status launch_tc_k(afmm_plan p, int l, const R *mre, const R *mim, R
     a.loc_re = lre;
     a.loc_im = lim;
     a.err = p->err_dev;
+    a.inject_timeout = p->inject_tc_timeout;
     const int W = p->M + 1;
     const size_t sm = (size_t)NS * KP * KP * 2 + (size_t)2 * 128 * KP * 2 + (size_t)W * W * (2 * p->M + 1) * 8;
     AFMM_CUDA(cudaFuncSetAttribute(k_s2l_tc<KP, NS, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
