@@ -213,6 +213,52 @@ def run_reference(args):
     return 0
 
 
+def fwd_bwd(kind, precision, steps, warmup, dev):
+    """One forward (potential) and backward (adjoint of L = sum |Phi - T|^2) step of a
+    configuration, timed end to end on the device (plan creation included), plus the plan
+    creation alone.  Returns a dict for the JSON line."""
+    import numpy as np
+    import torch
+    from paper_2301_01179_gb300 import binding, workloads as W
+    w = W.make(kind, with_targets=True)
+    ns, nf, nm = w["src_r"].size, w["tgt_r"].size, w["n_modes"]
+
+    def d(a):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+
+    sr, sz, tr, tz, qr, qi, Tr, Ti = map(d, (w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], w["q_re"], w["q_im"],
+                                             w["T_re"], w["T_im"]))
+
+    def step():
+        pl = binding.Plan(sr, sz, tr, tz, nm, order=w["order"], leaf_size=w["leaf"], precision=precision)
+        pr, pi = pl.eval(qr, qi)
+        out = pl.adjoint(qr, qi, 2.0 * (pr - Tr), 2.0 * (pi - Ti))
+        return pl, out
+
+    for _ in range(warmup):
+        pl, _o = step()
+        pl.close()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        pl, _o = step()
+        pl.close()
+    e1.record()
+    torch.cuda.synchronize()
+    t_step = e0.elapsed_time(e1) / steps
+    e0.record()
+    for _ in range(steps):
+        pl = binding.Plan(sr, sz, tr, tz, nm, order=w["order"], leaf_size=w["leaf"], precision=precision)
+        pl.close()
+    e1.record()
+    torch.cuda.synchronize()
+    t_plan = e0.elapsed_time(e1) / steps
+    return {"workload": "%s: %d x %d, modes 0..%d, order %d, leaf %d" % (kind, ns, nf, nm - 1, w["order"], w["leaf"]),
+            "precision": precision, "fwd_bwd_ms": t_step, "plan_ms": t_plan, "steps": steps,
+            "modal_ring_interactions_per_s": 2.0 * ns * nf * nm / (t_step / 1e3)}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -357,6 +403,22 @@ def run_ours(args):
         eps = np.max(np.abs(fa - da), axis=1) / np.max(np.abs(da), axis=1)
         extra = {"fmm_eps_vs_direct_max": float(eps.max()), "fmm_eps_vs_direct_n0": float(eps[0]),
                  "direct_gpu_rate": len(idx) * ns * nm / tdir, "direct_sample_points": len(idx)}
+        # plan creation (quadtree build and allocation) alone, part of every timed step above
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            binding.Plan(sr, sz, tr, tz, nm, order=M, leaf_size=leaf).close()
+        e1.record()
+        torch.cuda.synchronize()
+        extra["plan_ms"] = e0.elapsed_time(e1) / 3
+        # forward + backward (adjoint) steps of the gradient configurations (not the headline)
+        fb = {}
+        for kind, prec in [("cfg4", "fp64")] + [(k, "mixed") for k in args.fwd_bwd if k == "cfg5"]:
+            try:
+                fb[kind] = fwd_bwd(kind, prec, 2 if kind == "cfg5" else 3, 1, dev)
+            except Exception as exc:  # an extra must not cost the headline line
+                fb[kind] = {"error": str(exc)[:200]}
+        extra["fwd_bwd"] = fb
 
     line = None
     if rank == 0:
@@ -387,6 +449,8 @@ def main():
     ap.add_argument("--ns", type=int, default=None, help="profiling captures: fewer sources (same laws)")
     ap.add_argument("--nf", type=int, default=None, help="profiling captures: fewer field points")
     ap.add_argument("--no-extras", action="store_true", help="profiling captures: skip e2e and accuracy legs")
+    ap.add_argument("--fwd-bwd", default="", type=lambda v: [x for x in v.split(",") if x],
+                    help="also time the forward+adjoint step of these configurations (cfg5: 4e6 x 4e6, MIXED)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
