@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstring>
 #include <cstdlib>
+#include <mutex>
 #include <new>
 #include "common.cuh"
 
@@ -18,12 +19,44 @@ void set_cuda_error(cudaError_t e)
     snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
+// Plan memory comes from a library-owned, stream-ordered pool per device: allocation and
+// release are asynchronous on the plan's stream, and up to 32 GiB of released plan memory
+// stays reserved for the next plan (plain cudaMalloc/cudaFree cost milliseconds and
+// synchronise the device).  Falls back to cudaMalloc when no pool can be made.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64];
+static int g_pool_state[64];  // 0: not tried, 1: ready, -1: unavailable
+
+static cudaMemPool_t plan_pool(int dev)
+{
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (g_pool_state[dev] == 0) {
+        cudaMemPoolProps pr;
+        memset(&pr, 0, sizeof(pr));
+        pr.allocType = cudaMemAllocationTypePinned;
+        pr.location.type = cudaMemLocationTypeDevice;
+        pr.location.id = dev;
+        cudaMemPool_t pool;
+        if (cudaMemPoolCreate(&pool, &pr) != cudaSuccess) {
+            cudaGetLastError();
+            g_pool_state[dev] = -1;
+            return nullptr;
+        }
+        uint64_t keep = 32ull << 30;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pool[dev] = pool;
+        g_pool_state[dev] = 1;
+    }
+    return g_pool_state[dev] == 1 ? g_pool[dev] : nullptr;
+}
+
 afmm_status dalloc(afmm_plan p, void **ptr, size_t bytes)
 {
     *ptr = nullptr;
     if (p->nalloc >= (int)(sizeof(p->allocs) / sizeof(p->allocs[0]))) return AFMM_ENOMEM;
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, bytes);
+    cudaError_t e = p->pool ? cudaMallocFromPoolAsync(&q, bytes, p->pool, p->stream) : cudaMalloc(&q, bytes);
     if (e != cudaSuccess) {
         set_cuda_error(e);
         cudaGetLastError();
@@ -103,8 +136,13 @@ const char *afmm_last_cuda_error(void) { return g_cuda_err; }
 void afmm_plan_destroy(afmm_plan p)
 {
     if (!p) return;
-    cudaStreamSynchronize(p->stream);
-    for (int i = 0; i < p->nalloc; ++i) cudaFree(p->allocs[i]);
+    if (p->pool) {
+        for (int i = 0; i < p->nalloc; ++i) cudaFreeAsync(p->allocs[i], p->stream);
+        cudaStreamSynchronize(p->stream);
+    } else {
+        cudaStreamSynchronize(p->stream);
+        for (int i = 0; i < p->nalloc; ++i) cudaFree(p->allocs[i]);
+    }
     if (p->err_host) cudaFreeHost(p->err_host);
     delete p->tct;
     if (p->timing)
@@ -144,6 +182,11 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
     }
     make_rec_tab(p->rec);
     p->stream = (cudaStream_t)stream;
+    {
+        int dev = 0;
+        p->pool = cudaGetDevice(&dev) == cudaSuccess ? plan_pool(dev) : nullptr;
+        cudaGetLastError();
+    }
     p->ns = ns;
     p->nf = nf;
     p->nmodes = n_modes;

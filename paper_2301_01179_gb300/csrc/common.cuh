@@ -203,7 +203,8 @@ struct afmm_plan_s {
     int timing = 0;
     cudaEvent_t ev[80];
     double t_ms[8] = {0};
-    // device allocations to free
+    // device allocations to free (from the library's stream-ordered pool when pool != null)
+    cudaMemPool_t pool = nullptr;
     void *allocs[512];
     int nalloc = 0;
 };

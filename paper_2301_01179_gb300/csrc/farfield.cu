@@ -63,8 +63,8 @@ afmm_status make_shift_tables(afmm_plan p)
     }
     AFMM_TRY(dalloc_t(p, &p->m2m_tab, m2m.size()));
     AFMM_TRY(dalloc_t(p, &p->l2l_tab, l2l.size()));
-    AFMM_CUDA(cudaMemcpy(p->m2m_tab, m2m.data(), m2m.size() * sizeof(double), cudaMemcpyHostToDevice));
-    AFMM_CUDA(cudaMemcpy(p->l2l_tab, l2l.data(), l2l.size() * sizeof(double), cudaMemcpyHostToDevice));
+    AFMM_CUDA(cudaMemcpyAsync(p->m2m_tab, m2m.data(), m2m.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    AFMM_CUDA(cudaMemcpyAsync(p->l2l_tab, l2l.data(), l2l.size() * sizeof(double), cudaMemcpyHostToDevice, p->stream));
     // the same tables as FP32 pairs (hi = nearest float, lo = the rest) for the FP64 path
     std::vector<float2> m2mf(m2m.size()), l2lf(l2l.size());
     for (size_t i = 0; i < m2m.size(); ++i) {
@@ -74,8 +74,9 @@ afmm_status make_shift_tables(afmm_plan p)
     }
     AFMM_TRY(dalloc_t(p, &p->m2m_tab_df, m2mf.size()));
     AFMM_TRY(dalloc_t(p, &p->l2l_tab_df, l2lf.size()));
-    AFMM_CUDA(cudaMemcpy(p->m2m_tab_df, m2mf.data(), m2mf.size() * sizeof(float2), cudaMemcpyHostToDevice));
-    AFMM_CUDA(cudaMemcpy(p->l2l_tab_df, l2lf.data(), l2lf.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    AFMM_CUDA(cudaMemcpyAsync(p->m2m_tab_df, m2mf.data(), m2mf.size() * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+    AFMM_CUDA(cudaMemcpyAsync(p->l2l_tab_df, l2lf.data(), l2lf.size() * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+    AFMM_CUDA(cudaStreamSynchronize(p->stream));  // the host vectors die here
     return AFMM_OK;
 }
 
