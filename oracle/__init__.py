@@ -74,6 +74,10 @@ def _load():
     lib.orc_adjoint_fmm.restype = I
     lib.orc_num_threads.argtypes = []
     lib.orc_num_threads.restype = I
+    lib.orc_fourier_analysis.argtypes = [I64, I, P, I, P, P]
+    lib.orc_fourier_analysis.restype = None
+    lib.orc_fourier_synthesis.argtypes = [I64, I, P, P, I, P]
+    lib.orc_fourier_synthesis.restype = None
     _lib = lib
     return lib
 
@@ -230,3 +234,26 @@ def adjoint_fmm(src_r, src_z, tgt_r, tgt_z, q_re, q_im, gphi_re, gphi_im, M, d, 
     if rc != 0:
         raise RuntimeError("orc_adjoint_fmm failed: %d" % rc)
     return gq_re, gq_im, g_r, g_z
+
+
+def fourier_analysis(samples, n_modes):
+    """Azimuthal Fourier coefficients (Eq. analysis:source) S^(n), n = 0..n_modes-1, of real
+    ring densities sampled at K equispaced angles: samples [K, npts] -> (S_re, S_im)
+    [n_modes, npts]."""
+    smp = _f64(samples)
+    K, npts = smp.shape
+    S_re = np.zeros((n_modes, npts))
+    S_im = np.zeros((n_modes, npts))
+    _load().orc_fourier_analysis(npts, K, _p(smp), int(n_modes), _p(S_re), _p(S_im))
+    return S_re, S_im
+
+
+def fourier_synthesis(P_re, P_im, K):
+    """phi(theta_k) = Re Phi^(0) + 2 sum_{n>=1} Re(Phi^(n) e^{i n theta_k}) (Eq. analysis:phi)
+    at theta_k = 2 pi k / K: [n_modes, npts] -> [K, npts]."""
+    P_re = _f64(P_re)
+    P_im = _f64(P_im)
+    n_modes, npts = P_re.shape
+    phi = np.zeros((int(K), npts))
+    _load().orc_fourier_synthesis(npts, n_modes, _p(P_re), _p(P_im), int(K), _p(phi))
+    return phi

@@ -934,6 +934,58 @@ int orc_adjoint_fmm(int64_t ns, const double *sr, const double *sz, int64_t nf, 
     return rc;
 }
 
+/* ---- Fourier analysis and synthesis in the azimuth (Sec. 2, Eqs. analysis:source and
+ * analysis:phi).  s(theta) = sum_{n=-N..N} S^(n) e^{i n theta} with S^(-n) = conj(S^(n)) for a
+ * real density, and phi(theta) = sum_n Phi^(n) e^{i n theta}.  Reading: the paper's
+ * intermediate step writes e^{-i n theta}; substituting u = theta_1 - theta in the ring
+ * integral gives the final e^{+i n theta} of Eq. analysis:phi, which is used.
+ * Analysis from K equispaced samples theta_k = 2 pi k / K (exact for K >= 2N + 1):
+ *   S^(n) = (1/K) sum_k s(theta_k) e^{-i n theta_k},  n = 0..n_modes-1.
+ * Synthesis at the same angles:  phi(theta_k) = Re Phi^(0) + 2 sum_{n>=1} Re(Phi^(n) e^{i n theta_k}).
+ * Layouts: samples [K][npts] (angle-major), coefficients [n_modes][npts].  Sums are plain
+ * Neumaier-compensated loops over k (analysis) and n (synthesis). */
+static void neumaier(double *s, double *c, double v)
+{
+    double t = *s + v;
+    if (fabs(*s) >= fabs(v))
+        *c += (*s - t) + v;
+    else
+        *c += (v - t) + *s;
+    *s = t;
+}
+
+void orc_fourier_analysis(int64_t npts, int K, const double *samples, int n_modes, double *S_re, double *S_im)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < npts; ++p)
+        for (int n = 0; n < n_modes; ++n) {
+            double ar = 0, cr = 0, ai = 0, ci = 0;
+            for (int k = 0; k < K; ++k) {
+                /* angle n theta_k reduced exactly: (n k mod K) / K of a turn */
+                double th = 2.0 * ORC_PI * (double)(((int64_t)n * k) % K) / (double)K;
+                double v = samples[(size_t)k * npts + p];
+                neumaier(&ar, &cr, v * cos(th));
+                neumaier(&ai, &ci, -v * sin(th));
+            }
+            S_re[(size_t)n * npts + p] = (ar + cr) / K;
+            S_im[(size_t)n * npts + p] = (ai + ci) / K;
+        }
+}
+
+void orc_fourier_synthesis(int64_t npts, int n_modes, const double *P_re, const double *P_im, int K, double *phi)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < npts; ++p)
+        for (int k = 0; k < K; ++k) {
+            double a = P_re[p], c = 0;
+            for (int n = 1; n < n_modes; ++n) {
+                double th = 2.0 * ORC_PI * (double)(((int64_t)n * k) % K) / (double)K;
+                neumaier(&a, &c, 2.0 * (P_re[(size_t)n * npts + p] * cos(th) - P_im[(size_t)n * npts + p] * sin(th)));
+            }
+            phi[(size_t)k * npts + p] = a + c;
+        }
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP
