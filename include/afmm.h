@@ -169,6 +169,26 @@ afmm_status afmm_green(int64_t npairs, const double *r, const double *r1, const 
 afmm_status afmm_green_expansion(int64_t npts, const double *r, const double *r1, const double *x,
                                  int n_modes, int P, double *out, void *stream);
 
+/* afmm_fourier_analysis: azimuthal Fourier coefficients of real ring densities (Sec. 2,
+ * Eq. analysis:source: s(theta) = sum_{n=-N..N} S^(n) e^{i n theta}, S^(-n) = conj(S^(n))),
+ * from K equispaced samples theta_k = 2 pi k / K:
+ *     S^(n) = (1/K) sum_k s(theta_k) e^{-i n theta_k},   n = 0..n_modes-1,
+ * exact for band-limited densities when K >= 2 (n_modes - 1) + 1 (higher modes alias).
+ * samples [K][npts] (angle-major, device); S_re, S_im [n_modes][npts] (device), the
+ * amplitude layout of afmm_eval.  1 <= K <= 4096, n_modes >= 1; else AFMM_EINVAL.
+ * Asynchronous on `stream`. */
+afmm_status afmm_fourier_analysis(int64_t npts, int K, const double *samples, int n_modes, double *S_re,
+                                  double *S_im, void *stream);
+
+/* afmm_fourier_synthesis: the field at K equispaced angles from its modes (Sec. 2,
+ * Eq. analysis:phi: phi(r, theta, z) = sum_{n=-N..N} Phi^(n) e^{i n theta}, Phi^(-n) =
+ * conj(Phi^(n)) for a real field):
+ *     phi(theta_k) = Re Phi^(0) + 2 sum_{n=1..n_modes-1} Re(Phi^(n) e^{i n theta_k}).
+ * phi_re, phi_im [n_modes][npts] (e.g. afmm_eval's outputs, or a gradient component of
+ * afmm_grad); phi [K][npts].  Same limits and errors as afmm_fourier_analysis. */
+afmm_status afmm_fourier_synthesis(int64_t npts, int n_modes, const double *phi_re, const double *phi_im, int K,
+                                   double *phi, void *stream);
+
 /* afmm_direct_static: the direct sum of afmm_direct for callers that cannot allocate
  * device memory.  The paper has no counterpart; this entry point exists because some
  * callers may not call cudaMalloc: services that must keep a fixed device-memory

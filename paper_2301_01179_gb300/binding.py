@@ -22,7 +22,8 @@ _STATUS = {0: "ok", 1: "invalid argument", 2: "out of device memory", 3: "CUDA e
 EXPORTS = ["afmm_options_default", "afmm_plan_create", "afmm_plan_destroy", "afmm_plan_info", "afmm_eval",
            "afmm_grad", "afmm_direct", "afmm_direct_grad", "afmm_adjoint", "afmm_adjoint_direct", "afmm_green",
            "afmm_green_expansion", "afmm_status_string", "afmm_last_cuda_error", "afmm_set_timing",
-           "afmm_get_timing", "afmm_kernel_launches", "afmm_direct_static"]
+           "afmm_get_timing", "afmm_kernel_launches", "afmm_direct_static", "afmm_fourier_analysis",
+           "afmm_fourier_synthesis"]
 
 
 class AfmmError(RuntimeError):
@@ -90,6 +91,10 @@ def load():
     lib.afmm_direct_static.restype = I
     lib.afmm_kernel_launches.argtypes = []
     lib.afmm_kernel_launches.restype = ctypes.c_longlong
+    lib.afmm_fourier_analysis.argtypes = [I64, I, P, I, P, P, P]
+    lib.afmm_fourier_analysis.restype = I
+    lib.afmm_fourier_synthesis.argtypes = [I64, I, P, P, I, P, P]
+    lib.afmm_fourier_synthesis.restype = I
     _lib = lib
     return lib
 
@@ -266,3 +271,26 @@ def direct_static(src_r, src_z, tgt_r, tgt_z, q_re, q_im):
     _check(lib.afmm_direct_static(ns, _ptr(src_r), _ptr(src_z), nf, _ptr(tgt_r), _ptr(tgt_z), nm, _ptr(q_re),
                                   _ptr(q_im), _ptr(o_re), _ptr(o_im), _stream()), "afmm_direct_static")
     return o_re, o_im
+
+
+def fourier_analysis(samples, n_modes):
+    """Azimuthal Fourier coefficients S^(n), n = 0..n_modes-1, of real ring densities sampled at
+    K equispaced angles (afmm_fourier_analysis): samples [K, npts] -> (S_re, S_im) [n_modes, npts]."""
+    lib = load()
+    K, npts = samples.shape
+    S_re = _empty(n_modes, npts, like=samples)
+    S_im = _empty(n_modes, npts, like=samples)
+    _check(lib.afmm_fourier_analysis(npts, K, _ptr(samples), int(n_modes), _ptr(S_re), _ptr(S_im), _stream()),
+           "afmm_fourier_analysis")
+    return S_re, S_im
+
+
+def fourier_synthesis(phi_re, phi_im, K):
+    """The field at K equispaced angles from its modes (afmm_fourier_synthesis):
+    [n_modes, npts] -> [K, npts]."""
+    lib = load()
+    n_modes, npts = phi_re.shape
+    out = _empty(int(K), npts, like=phi_re)
+    _check(lib.afmm_fourier_synthesis(npts, int(n_modes), _ptr(phi_re), _ptr(phi_im), int(K), _ptr(out), _stream()),
+           "afmm_fourier_synthesis")
+    return out

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libafmm.so")
 OBJDIR = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "tree.cu", "nearfield.cu", "farfield.cu", "s2l_tc.cu"]
+SOURCES = ["api.cu", "tree.cu", "nearfield.cu", "farfield.cu", "s2l_tc.cu", "fourier.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
 
