@@ -32,9 +32,18 @@ WORKLOAD_DESC = ("1,000,000 ring sources x 1,000,000 field points, r~U[0.05,2], 
 # 2.07 GHz (one FP32 operation per lane and clock; an FMA counts as one operation)
 FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 # near field, FP32-pair arithmetic, a-priori operation count per (field point, source) pair:
-# ~600 for the pair geometry, the AGM start values and the gradient factors, then per mode 24
-# (recursion step), 27 (scale and two compensated accumulations) and 85 (gradient terms)
-NEAR_SETUP_OPS, NEAR_MODE_OPS = 600, 24 + 27 + 85
+# ~600 for the pair geometry, the AGM start values and the gradient factors, then per mode 22
+# (forward recursion step: two products and a difference), 30 (scale and two compensated
+# accumulations) and 88 (derivative weight, its two factors, four compensated accumulations).
+# Miller pairs' longer sweeps are not counted.
+NEAR_SETUP_OPS, NEAR_MODE_OPS = 600, 22 + 30 + 88
+
+
+def l2p_ops(M):
+    """FP32 operations of the local-expansion evaluation (value and gradient, FP32 pairs) per
+    field point, mode and real/imaginary part: per coefficient two pair multiply-adds (32), per
+    axial degree three (48)."""
+    return 32 * (M + 1) * (M + 2) // 2 + 48 * (M + 1)
 # S2L on the tensor cores: 21 digit-slice products per FP64-equivalent multiply-add
 S2L_SLICE_PAIRS = 21
 
@@ -328,12 +337,16 @@ def run_ours(args):
     near_ms = statistics.mean(p["near"] for p in phases)
     traffic_of = read_traffic()
     near_ops = NEAR_SETUP_OPS + nm * NEAR_MODE_OPS
-    near_ach = float(info["near_pairs"]) * near_ops / (near_ms / 1e3) / 1e12
-    near_roof = {"bound": "alu", "kernel": "k_near_df (near field + L2P, potential and gradient, FP32 pairs)",
+    l2p_pt = 2 * nm * l2p_ops(M)
+    near_total = float(info["near_pairs"]) * near_ops + float(nf) * l2p_pt
+    near_ach = near_total / (near_ms / 1e3) / 1e12
+    near_roof = {"bound": "alu", "kernel": "k_near_ws (near field + L2P, potential and gradient, FP32 pairs)",
                  "achieved": near_ach, "peak": FP32_PEAK_TOPS, "unit": "FP32 Tops/s",
-                 "frac": near_ach / FP32_PEAK_TOPS, "traffic": traffic_of.get("k_near_df"),
-                 "work_per_unit": "%d FP32 operations per near pair (%d + %d (N+1)); %d pairs per launch"
-                                  % (near_ops, NEAR_SETUP_OPS, NEAR_MODE_OPS, info["near_pairs"]),
+                 "frac": near_ach / FP32_PEAK_TOPS, "traffic": traffic_of.get("k_near_ws"),
+                 "work_per_unit": "%d FP32 operations per near pair (%d + %d (N+1)) x %d pairs, plus %d per field "
+                                  "point for the local expansion (2 (N+1) x %d) x %d points"
+                                  % (near_ops, NEAR_SETUP_OPS, NEAR_MODE_OPS, info["near_pairs"], l2p_pt,
+                                     l2p_ops(M), nf),
                  "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (derived from unit counts and clock)"}
     bf16_peak, bf16_src = measured_bf16_peak()
     s2l_flop = float(info["s2l_pairs"]) * nm * 4.0 * nc * nc * S2L_SLICE_PAIRS

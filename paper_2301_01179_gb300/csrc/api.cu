@@ -203,9 +203,12 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
     }
     p->pp.fwd_switch = opt.fwd_switch > 0.0 ? opt.fwd_switch : default_fwd_switch(p->N);
     p->pp.miller_extra = opt.miller_extra > 0 ? (double)opt.miller_extra : 15.0;
-    // FP32-pair recursion (AFMM_FP64): rounding ~2^-47 instead of 2^-53, so the forward
-    // sweep is used only while its growth e^s N / s keeps the error below ~5e-12
-    p->df_fwd_switch = opt.fwd_switch > 0.0 ? (opt.fwd_switch < 4.5 ? opt.fwd_switch : 4.5) : 4.5;
+    // FP32-pair recursion (AFMM_FP64, AFMM_MIXED): rounding ~2^-47 instead of 2^-53.  The
+    // forward sweep's rounding grows like e^{n a} against the decaying Q_{n-1/2} ~ e^{-n a}
+    // (a = acosh chi), so its error measured against the pair's G^(0), the scale of the
+    // per-mode error max|Phi - Phi_ref| / max|Phi_ref|, is ~2^-47 N e^{s/2} / s <= 2e-12
+    // for s = 2 N a <= 8 (N <= 64)
+    p->df_fwd_switch = opt.fwd_switch > 0.0 ? fmin(opt.fwd_switch, 8.0) : 8.0;
 
     afmm_status s = build_tree(p, src_r, src_z, tgt_r, tgt_z);
     if (s == AFMM_OK) s = make_shift_tables(p);
@@ -215,8 +218,9 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
     const bool mix = p->precision == AFMM_MIXED;
     if (s == AFMM_OK && !mix) s = dalloc_t(p, &p->qs_re, (size_t)nm * nmax);
     if (s == AFMM_OK && !mix) s = dalloc_t(p, &p->qs_im, (size_t)nm * nmax);
-    if (s == AFMM_OK && mix) s = dalloc_t(p, &p->qs32_re, (size_t)nm * nmax);
-    if (s == AFMM_OK && mix) s = dalloc_t(p, &p->qs32_im, (size_t)nm * nmax);
+    const size_t npq = (size_t)(nm + 1) / 2;  // mode pairs of the interleaved amplitude copies
+    if (s == AFMM_OK && mix) s = dalloc_t(p, &p->qs32_re, npq * nmax);
+    if (s == AFMM_OK && mix) s = dalloc_t(p, &p->qs32_im, npq * nmax);
     if (s == AFMM_OK) s = dalloc_t(p, &p->acc_buf, (size_t)6 * nm * p->ns);
     int64_t gcap = 0, nexp = 0;
     for (int l = 2; s == AFMM_OK && l <= p->d; ++l) {
@@ -247,7 +251,7 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
     const bool dfx = p->precision == AFMM_FP64 || s2l_tc_enabled(p);
     if (s == AFMM_OK && gcap > 0 && !dfx) s = dalloc_t(p, &p->gexp, gcap);
     p->gexp_cap = gcap;
-    if (s == AFMM_OK && p->precision == AFMM_FP64) s = dalloc_t(p, &p->qsdf, (size_t)2 * nm * nmax);
+    if (s == AFMM_OK && p->precision == AFMM_FP64) s = dalloc_t(p, &p->qsdf, 2 * npq * nmax);
     if (s == AFMM_OK && dfx) {
         int64_t mmax = 0;
         for (int l = 2; l <= p->d; ++l) mmax = p->lv[l].nbox > mmax ? p->lv[l].nbox : mmax;

@@ -153,6 +153,14 @@ struct TcTables {
     int8_t ci[128], cj[128];  // coefficient index -> (first, second) exponent
 };
 
+// amplitude of mode n, source s: FP64 copies are planar [n][ns]; FP32 copies (MIXED) are
+// interleaved by mode pair, [n / 2][ns] x (q_2m, q_2m+1)
+__device__ __forceinline__ double amp_at(const double *q, int n, int64_t s, int64_t ns) { return q[(size_t)n * ns + s]; }
+__device__ __forceinline__ float amp_at(const float *q, int n, int64_t s, int64_t ns)
+{
+    return q[((size_t)(n >> 1) * ns + s) * 2 + (n & 1)];
+}
+
 struct NearUnit {       // one warp of near-field work: up to 32 field points of one leaf
     int32_t box;        // leaf box index
     int32_t begin, end; // field-point range (sorted order)
@@ -180,9 +188,12 @@ struct afmm_plan_s {
     afmm::NearUnit *dir_unit[2] = {nullptr, nullptr};
     // eval scratch
     double *qs_re = nullptr, *qs_im = nullptr;  // [nmodes][max(ns,nf)] strengths, sorted, * c_n
-    float *qs32_re = nullptr, *qs32_im = nullptr;  // MIXED: the same in FP32
-    float2 *qsdf = nullptr;                     // FP64 path: the same as FP32 pairs [2][nmodes][n]
-    double df_fwd_switch = 4.5;                 // forward switch of the FP32-pair recursion
+    // MIXED: the same in FP32, interleaved by mode pair: [n / 2][n_max] (q_2m, q_2m+1)
+    float2 *qs32_re = nullptr, *qs32_im = nullptr;
+    // FP64 path: the same as FP32 pairs interleaved by mode pair, re plane then im plane:
+    // [2][n / 2][n_max] (q_2m.hi, q_2m+1.hi, q_2m.lo, q_2m+1.lo)
+    float4 *qsdf = nullptr;
+    double df_fwd_switch = 8.0;                 // forward switch of the FP32-pair recursion
     double *gexp = nullptr;                     // expansions of one level
     float2 *gexp_df = nullptr;                  // FP64 path: the same as FP32 pairs
     uint16_t *asl = nullptr;                    // tensor-core S2L: bf16 digit slices of the moments of one level

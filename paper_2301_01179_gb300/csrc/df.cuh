@@ -156,4 +156,83 @@ __device__ __forceinline__ void df_acc(float &S, float &E, dfv a, dfv b)
     S = s;
 }
 
+// ---- two FP32-pair values per instruction (packed f32x2 arithmetic, sm_100 and later) ----
+// A df2 holds two independent FP32 pairs: (hi.x, lo.x) and (hi.y, lo.y).  Each operation
+// below performs, on both components, exactly the FP32 operations of its scalar
+// counterpart above (same order, same roundings), so packed and scalar results are
+// bitwise equal; one packed instruction issues the work of two FP32 instructions.
+struct df2 {
+    float2 hi, lo;
+};
+
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b)
+{
+    unsigned long long ra = *reinterpret_cast<unsigned long long *>(&a), rb = *reinterpret_cast<unsigned long long *>(&b),
+                       rd;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    return *reinterpret_cast<float2 *>(&rd);
+}
+__device__ __forceinline__ float2 fneg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ df2 df2_make(float2 hi, float2 lo)
+{
+    df2 r;
+    r.hi = hi;
+    r.lo = lo;
+    return r;
+}
+// (a, b) from two scalar pairs; the broadcast form (a, a)
+__device__ __forceinline__ df2 df2_pack(dfv a, dfv b) { return df2_make(make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)); }
+__device__ __forceinline__ df2 df2_bcast(dfv a) { return df2_pack(a, a); }
+// float4 (x.hi, y.hi, x.lo, y.lo) <-> df2
+__device__ __forceinline__ df2 df2_from4(float4 v) { return df2_make(make_float2(v.x, v.y), make_float2(v.z, v.w)); }
+__device__ __forceinline__ float4 df2_to4(df2 v) { return make_float4(v.hi.x, v.hi.y, v.lo.x, v.lo.y); }
+__device__ __forceinline__ dfv df2_x(df2 v) { return df_make(v.hi.x, v.lo.x); }
+__device__ __forceinline__ dfv df2_y(df2 v) { return df_make(v.hi.y, v.lo.y); }
+
+__device__ __forceinline__ void quick_two_sum2(float2 a, float2 b, float2 &s, float2 &e)
+{
+    s = fadd2(a, b);
+    e = fsub2(b, fsub2(s, a));
+}
+
+__device__ __forceinline__ df2 df2_add(df2 a, df2 b)
+{
+    const float2 s = fadd2(a.hi, b.hi);
+    const float2 v = fsub2(s, a.hi);
+    const float2 e = fadd2(fsub2(a.hi, fsub2(s, v)), fsub2(b.hi, v));
+    const float2 t = fadd2(e, fadd2(a.lo, b.lo));
+    df2 r;
+    quick_two_sum2(s, t, r.hi, r.lo);
+    return r;
+}
+
+__device__ __forceinline__ df2 df2_mul(df2 a, df2 b)
+{
+    const float2 p = fmul2(a.hi, b.hi);
+    float2 e = ffma2(a.hi, b.hi, fneg2(p));
+    e = ffma2(a.hi, b.lo, e);
+    e = ffma2(a.lo, b.hi, e);
+    df2 r;
+    quick_two_sum2(p, e, r.hi, r.lo);
+    return r;
+}
+
+// (S, E) += a * b componentwise, as df_acc
+__device__ __forceinline__ void df2_acc(float2 &S, float2 &E, df2 a, df2 b)
+{
+    const float2 p = fmul2(a.hi, b.hi);
+    float2 pe = ffma2(a.hi, b.hi, fneg2(p));
+    pe = ffma2(a.hi, b.lo, pe);
+    pe = ffma2(a.lo, b.hi, pe);
+    const float2 s = fadd2(S, p);
+    const float2 v = fsub2(s, S);
+    const float2 err = fadd2(fsub2(S, fsub2(s, v)), fsub2(p, v));
+    E = fadd2(E, fadd2(err, pe));
+    S = s;
+}
+
 }  // namespace afmm

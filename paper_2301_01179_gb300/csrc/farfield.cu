@@ -130,8 +130,8 @@ __global__ void k_p2m(const uint32_t *__restrict__ key, const int2 *__restrict__
             T ar = acc[o], ai = acc[nm * nc + o];
             for (int t = 0; t < cnt; ++t) {
                 T m = mono[t * nc + c];
-                ar = fma(q_re[(size_t)n * nsrc + s0 + t], m, ar);
-                ai = fma(q_im[(size_t)n * nsrc + s0 + t], m, ai);
+                ar = fma(amp_at(q_re, n, s0 + t, nsrc), m, ar);
+                ai = fma(amp_at(q_im, n, s0 + t, nsrc), m, ai);
             }
             acc[o] = ar;
             acc[nm * nc + o] = ai;
@@ -283,8 +283,8 @@ __global__ void k_l2l(const int32_t *__restrict__ parent, const uint32_t *__rest
 // of FP32).  Sums are (hi, err) pairs updated by exact two-sums.
 // ------------------------------------------------------------------------------------
 __global__ void k_p2m_df(const uint32_t *__restrict__ key, const int2 *__restrict__ rng, int64_t nbox,
-                         const double *__restrict__ sr, const double *__restrict__ sz, const float2 *__restrict__ q_re,
-                         const float2 *__restrict__ q_im, int64_t nsrc, int nm, int M, double r0, double z0, double h,
+                         const double *__restrict__ sr, const double *__restrict__ sz, const float4 *__restrict__ q_re,
+                         const float4 *__restrict__ q_im, int64_t nsrc, int nm, int M, double r0, double z0, double h,
                          const RecTab tab, float2 *__restrict__ mom_re, float2 *__restrict__ mom_im)
 {
     extern __shared__ float2 smf[];
@@ -333,9 +333,11 @@ __global__ void k_p2m_df(const uint32_t *__restrict__ key, const int2 *__restric
             for (int t = 0; t < cnt; ++t) {
                 const float2 m2 = mono[t * nc + c];
                 const dfv m = df_make(m2.x, m2.y);
-                const float2 qr = q_re[(size_t)n * nsrc + s0 + t], qi = q_im[(size_t)n * nsrc + s0 + t];
-                df_acc(ar.x, ar.y, df_make(qr.x, qr.y), m);
-                df_acc(ai.x, ai.y, df_make(qi.x, qi.y), m);
+                // amplitudes interleaved by mode pair: (q_2m.hi, q_2m+1.hi, q_2m.lo, q_2m+1.lo)
+                const float4 qr = q_re[(size_t)(n >> 1) * nsrc + s0 + t], qi = q_im[(size_t)(n >> 1) * nsrc + s0 + t];
+                const bool odd = n & 1;
+                df_acc(ar.x, ar.y, df_make(odd ? qr.y : qr.x, odd ? qr.w : qr.z), m);
+                df_acc(ai.x, ai.y, df_make(odd ? qi.y : qi.x, odd ? qi.w : qi.z), m);
             }
             acc[o] = ar;
             acc[nm * nc + o] = ai;
@@ -1260,7 +1262,7 @@ static afmm_status far_field_df(afmm_plan p, int dir)
     const bool fw = dir == 0;
     const double *sr = fw ? p->s_r : p->t_r, *sz = fw ? p->s_z : p->t_z;
     const int64_t nsrc = fw ? p->ns : p->nf;
-    const float2 *q_re = p->qsdf, *q_im = p->qsdf + (size_t)nm * p->n_max;
+    const float4 *q_re = p->qsdf, *q_im = p->qsdf + (size_t)((nm + 1) / 2) * p->n_max;
     {
         Level &v = p->lv[d];
         const double h = p->L / (double)(1 << d);

@@ -3,17 +3,17 @@
 // Algorithm 1 last step, together with the local expansion of Eq. analysis:local), and the
 // all-pairs direct evaluation.
 //
-// Layout: one thread per field point, one warp per work unit (<= 32 field points of one
-// leaf, or of the sorted field array for direct sums); the warp walks the unit's sources
-// in lockstep so each source's coordinates and amplitudes are warp-broadcast loads.  The
-// per-mode accumulators and each lane's Legendre sequence live in shared memory
-// ([mode][lane] planes, conflict-free); on GB300 the FP64 pipe, not shared memory, bounds
-// the kernel (FP64 issues at 1/64 of FP32).
+// AFMM_FP64 and AFMM_MIXED run k_near_ws: warp-specialised blocks (producer warps compute
+// the pairs' Legendre sequences into a ring of shared-memory slots, consumer warps own a
+// range of modes and accumulate), FP32-pair arithmetic on the FP32 pipe, packed f32x2 mode
+// pairs in the accumulation.  AFMM_FP64_NATIVE runs the FP64 kernels k_near / k_near2
+// (one warp per work unit, per-mode accumulators in shared memory).
 #include <cstring>
 #include <mutex>
 #include "common.cuh"
 #include "pair.cuh"
 #include "pair_df.cuh"
+#include "mbar.cuh"
 
 namespace afmm {
 
@@ -33,13 +33,17 @@ struct NearArgs {
     int direct;          // 1: all sources, split into nsplit chunks
     int nsplit;
     int64_t split_len;
-    // FP64 path in FP32 pairs: amplitudes and leaf locals as (hi, lo)
-    const float2 *qdf_re, *qdf_im;
+    // FP64 path in FP32 pairs: amplitudes interleaved by mode pair, [n / 2][nsrc] float4
+    // (q_2m.hi, q_2m+1.hi, q_2m.lo, q_2m+1.lo); leaf locals as (hi, lo)
+    const float4 *qdf_re, *qdf_im;
     const float2 *locdf_re, *locdf_im;
     float df_fwd_switch;
-    // MIXED precision: FP32 amplitudes and local expansions, compensated FP32 sums
-    const float *q32_re, *q32_im;
+    // MIXED precision: FP32 amplitudes interleaved by mode pair, [n / 2][nsrc] float2
+    // (q_2m, q_2m+1), FP32 local expansions, compensated FP32 sums
+    const float2 *q32_re, *q32_im;
     const float *loc32_re, *loc32_im;
+    int mode_lo, mode_hi;  // FP32-pair kernel: the modes [mode_lo, mode_hi) of this launch
+    int *err;              // plan error word (bounded waits that ran out)
     // local expansion at the leaves (near mode, optional)
     const double *loc_re, *loc_im;
     const uint32_t *leaf_key;
@@ -98,6 +102,13 @@ __device__ __forceinline__ void l2p_eval32(const float *__restrict__ F, int M, f
     val = pu;
     du = pdu;
     dv = pdv;
+}
+
+// FP32 amplitude of mode n, source s, in the mode-pair interleaved layout [n / 2][ns] float2
+__device__ __forceinline__ float q32_at(const float2 *__restrict__ q, int n, int64_t s, int64_t ns)
+{
+    const float2 v = q[(size_t)(n >> 1) * ns + s];
+    return (n & 1) ? v.y : v.x;
 }
 
 // Kahan-compensated FP32 accumulation: (sum, running compensation) in a float2
@@ -187,7 +198,7 @@ __global__ void __launch_bounds__(AFMM_NEAR_WARPS * 32) k_near(const NearArgs a,
                 if (!GRAD) {
                     for (int n = 0; n < nm; ++n) {
                         float gn = (float)(sc * ys[n * 32 + lane]);
-                        float qr = a.q32_re[(size_t)n * a.nsrc + s], qi = a.q32_im[(size_t)n * a.nsrc + s];
+                        float qr = q32_at(a.q32_re, n, s, a.nsrc), qi = q32_at(a.q32_im, n, s, a.nsrc);
                         size_t o = (size_t)n * 32 + lane;
                         kadd(acc2[o], qr * gn);
                         kadd(acc2[o + st], qi * gn);
@@ -204,7 +215,7 @@ __global__ void __launch_bounds__(AFMM_NEAR_WARPS * 32) k_near(const NearArgs a,
                         float wt = (float)(sc * fma(yn, A, rho[n] * yprev * B));
                         yprev = yn;
                         float xw = x32 * wt, qw = qfac * wt;
-                        float qr = a.q32_re[(size_t)n * a.nsrc + s], qi = a.q32_im[(size_t)n * a.nsrc + s];
+                        float qr = q32_at(a.q32_re, n, s, a.nsrc), qi = q32_at(a.q32_im, n, s, a.nsrc);
                         size_t o = (size_t)n * 32 + lane;
                         kadd(acc2[o], qr * gn);
                         kadd(acc2[o + st], qi * gn);
@@ -475,7 +486,7 @@ __global__ void __launch_bounds__(NEAR2_WB * 32) k_near2(const NearArgs a, const
                 const double yn = yk[n * 32 + lane];
                 const size_t o = (size_t)(n - n0) * 32 + lane, st = (size_t)mper * 32;
                 if (MIX) {
-                    float qr = a.q32_re[(size_t)n * a.nsrc + s], qi = a.q32_im[(size_t)n * a.nsrc + s];
+                    float qr = q32_at(a.q32_re, n, s, a.nsrc), qi = q32_at(a.q32_im, n, s, a.nsrc);
                     float gn = (float)(sc * yn);
                     kadd(myacc2[o], qr * gn);
                     kadd(myacc2[o + st], qi * gn);
@@ -598,63 +609,157 @@ static size_t near2_smem(int nm, int grad)
 }
 
 // ------------------------------------------------------------------------------------
-// FP64-path near field in FP32-pair arithmetic: the cooperative layout of k_near2 with the
-// pair sequence, the gradient factors, the accumulation and the local-expansion
-// evaluation all in double-float.  Per pair only the three coordinate differences touch
-// the FP64 pipe; the rest runs on the FP32 pipe at ~48-bit precision.
+// Near field in FP32-pair arithmetic (AFMM_FP64 and AFMM_MIXED), warp-specialised.
+//
+// A block takes one work unit: up to 32 field points of one leaf against the sources of
+// its 3 x 3 neighbour leaves (the D list of Sec. 2.2), or one source split of the direct
+// sum.  The unit's (field point, source) pairs are cut into slots of 32 lanes (lane = field
+// point; when the unit has c <= 16 points, T = 2^ceil(log2 c) lanes per source and 32 / T
+// sources per slot).  The warps split into two roles:
+//   producers  take the next slot from a shared counter and compute each lane's pair: the
+//              coordinate differences (FP64, split exactly), the AGM start values, the
+//              forward or Miller sweep of the scaled Legendre recursion (Eq.
+//              gfunc:recursion) and the gradient factors, into a ring of B slots;
+//   consumers  own MPER modes each (register accumulators) and walk the slots in order,
+//              adding q^(n) G^(n) (Eq. analysis:sum) and the gradient terms.
+// A full and an empty mbarrier per ring slot hand the slots over; every wait is bounded
+// (1 s), after which the block records the timeout in the plan's error word and ends.  The
+// sequential, latency-bound recursion of the producers thus runs beside the consumers'
+// independent multiply-adds instead of alternating with them at block barriers.
+//
+// The consumers work on mode pairs (2m, 2m+1) with packed f32x2 instructions: the slot
+// stores y_n interleaved by mode pair (SeqSlot), the amplitudes are stored the same way,
+// and the per-pair factors in broadcast form, so every operand is a ready register pair.
+// The packed operations are the scalar FP32-pair operations lane by lane: the results are
+// those of the same sums in scalar FP32-pair arithmetic.
 // ------------------------------------------------------------------------------------
-template <bool GRAD>
-__device__ __forceinline__ void l2p_eval_df(const float2 *__restrict__ F, int M, dfv u, dfv v, dfv &val, dfv &du,
-                                            dfv &dv)
+constexpr int NWS_THREADS = 512;                             // 16 warps per block
+constexpr int NWS_BMAX = 24;                                 // ring slots (upper bound)
+constexpr int NWS_MODES_PER_LAUNCH = 88;                     // 11 consumer warps x 8 modes
+constexpr unsigned long long NWS_WAIT_NS = 1000000000ull;    // a hand-over wait gives up after 1 s
+
+// Lane 0 waits on the barrier (suspended in hardware between polls; bounded by the timer);
+// the warp learns the outcome and, through __syncwarp, is ordered after lane 0's acquire.
+__device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t parity, int lane, int *err, volatile int *abort_flag)
 {
-    dfv pu = df_make(0.f, 0.f), pdu = pu, pdv = pu;
+    int ok = 1;
+    if (lane == 0 && !mbar_try(bar, parity)) {
+        const unsigned long long t0 = global_ns();
+        for (;;) {
+            if (mbar_try_sleep(bar, parity, 20000u)) break;
+            if (*abort_flag) {
+                ok = 0;
+                break;
+            }
+            if (global_ns() - t0 > NWS_WAIT_NS) {
+                ok = 0;
+                *abort_flag = 1;
+                if (err) *(volatile int *)err = 1;
+                break;
+            }
+        }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    return ok != 0;
+}
+
+__device__ __forceinline__ float4 bcast4(dfv v) { return make_float4(v.hi, v.hi, v.lo, v.lo); }
+
+// Local expansion value and gradient at (u, v) in box units, for the real and imaginary
+// parts at once (packed): the steps of l2p_eval in FP32 pairs
+template <bool GRAD>
+__device__ __forceinline__ void l2p_eval_df2(const float2 *__restrict__ Fr, const float2 *__restrict__ Fi, int M,
+                                             dfv u, dfv v, df2 &val, df2 &du, df2 &dv)
+{
+    const df2 U = df2_bcast(u), V = df2_bcast(v);
+    const df2 Z = df2_make(make_float2(0.f, 0.f), make_float2(0.f, 0.f));
+    df2 pu = Z, pdu = Z, pdv = Z;
     for (int k = M; k >= 0; --k) {
-        int base = k * (M + 1) - k * (k - 1) / 2;
-        dfv pk = df_make(0.f, 0.f), pkd = pk;
+        const int base = k * (M + 1) - k * (k - 1) / 2;
+        df2 pk = Z, pkd = Z;
         for (int l = M - k; l >= 0; --l) {
-            if (GRAD) pkd = df_add(df_mul(pkd, v), pk);
-            float2 f = F[base + l];
-            pk = df_add(df_mul(pk, v), df_make(f.x, f.y));
+            if (GRAD) pkd = df2_add(df2_mul(pkd, V), pk);
+            const float2 fr = Fr[base + l], fi = Fi[base + l];
+            pk = df2_add(df2_mul(pk, V), df2_make(make_float2(fr.x, fi.x), make_float2(fr.y, fi.y)));
         }
         if (GRAD) {
-            pdu = df_add(df_mul(pdu, u), pu);
-            pdv = df_add(df_mul(pdv, u), pkd);
+            pdu = df2_add(df2_mul(pdu, U), pu);
+            pdv = df2_add(df2_mul(pdv, U), pkd);
         }
-        pu = df_add(df_mul(pu, u), pk);
+        pu = df2_add(df2_mul(pu, U), pk);
     }
     val = pu;
     du = pdu;
     dv = pdv;
 }
 
-#define NEARDF_WB 8
-
-// MPER: modes per warp (compile time), accumulators in registers.  MIX: the MIXED precision
-// (same FP32-pair sequence, FP32 products with Kahan-compensated FP32 sums, FP32 locals)
-template <bool GRAD, int MPER, bool MIX>
-__global__ void __launch_bounds__(NEARDF_WB * 32, (MPER <= 5 ? 2 : 1)) k_near_df(const NearArgs a, const RecTab tab)
+// MIXED: FP32 value and gradient of the re and im locals at once
+template <bool GRAD>
+__device__ __forceinline__ void l2p_eval32x2(const float *__restrict__ Fr, const float *__restrict__ Fi, int M, float u,
+                                             float v, float2 &val, float2 &du, float2 &dv)
 {
-    extern __shared__ double smem[];
-    constexpr int WB = NEARDF_WB;
-    constexpr int NPP = GRAD ? 5 : 1;  // per-pair df scalars: scale (, x, qfac, A, B)
-    constexpr int NC = GRAD ? 6 : 2;
+    const float2 U = make_float2(u, u), V = make_float2(v, v), Z = make_float2(0.f, 0.f);
+    float2 pu = Z, pdu = Z, pdv = Z;
+    for (int k = M; k >= 0; --k) {
+        const int base = k * (M + 1) - k * (k - 1) / 2;
+        float2 pk = Z, pkd = Z;
+        for (int l = M - k; l >= 0; --l) {
+            if (GRAD) pkd = ffma2(pkd, V, pk);
+            pk = ffma2(pk, V, make_float2(Fr[base + l], Fi[base + l]));
+        }
+        if (GRAD) {
+            pdu = ffma2(pdu, U, pu);
+            pdv = ffma2(pdv, U, pkd);
+        }
+        pu = ffma2(pu, U, pk);
+    }
+    val = pu;
+    du = pdu;
+    dv = pdv;
+}
+
+// Kahan-compensated FP32 sums of two components at once: S the sums, C the running
+// compensations (true sums ~ S - C)
+__device__ __forceinline__ void kahan2(float2 &S, float2 &C, float2 v)
+{
+    const float2 y = fsub2(v, C);
+    const float2 t = fadd2(S, y);
+    C = fsub2(fsub2(t, S), y);
+    S = t;
+}
+
+// MPER: modes per consumer warp (even); MIX: MIXED precision (same FP32-pair sequence,
+// FP32 products with Kahan-compensated FP32 sums, FP32 locals)
+template <bool GRAD, int MPER, bool MIX>
+__global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, const RecTab tab, int ncons, int nbuf)
+{
+    static_assert(MPER % 2 == 0, "consumers work on mode pairs");
+    extern __shared__ __align__(16) unsigned char smem_ws[];
+    constexpr int NPP = GRAD ? 5 : 1;  // per-pair factors: scale (, x, qfac, A, B)
+    constexpr int NC = GRAD ? 6 : 2;   // accumulated components
+    constexpr int NP = MPER / 2;       // mode pairs per consumer
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nm = a.nmodes, N = a.N;
-    const int Nq = GRAD && N < 1 ? 1 : N;
-    const int nmq = Nq + 1;
-    float2 *gam2 = reinterpret_cast<float2 *>(smem);  // [AFMM_REC_TAB]
-    float2 *rho2 = gam2 + AFMM_REC_TAB;               // [AFMM_MAX_MODES]
-    float2 *ys = rho2 + AFMM_MAX_MODES;               // [WB][nmq][32]
-    float2 *pp = ys + (size_t)WB * nmq * 32;          // [WB][NPP][32]
+    const int Nq = GRAD && N < 1 ? 1 : N;  // the gradient of mode 0 needs y_1
+    const int npair = (Nq + 2) / 2;        // mode pairs of y_0 .. y_Nq
+    float2 *gam2 = reinterpret_cast<float2 *>(smem_ws);                 // [AFMM_REC_TAB]
+    float4 *rho4 = reinterpret_cast<float4 *>(gam2 + AFMM_REC_TAB);     // [pair] rho_n = c_{n-1} / c_n
+    unsigned char *ring = reinterpret_cast<unsigned char *>(rho4 + AFMM_MAX_MODES / 2 + 1);
+    const size_t slot_bytes = (size_t)(npair + NPP) * 32 * sizeof(float4) + 32 * sizeof(int);
+    __shared__ uint64_t s_full[NWS_BMAX], s_empty[NWS_BMAX];
     __shared__ int rb[10], rcum[10];
-    __shared__ int sidx[WB * 32];  // source of each (warp, lane) pair of the chunk
+    __shared__ int s_next;
+    __shared__ volatile int s_abort;
     for (int i = threadIdx.x; i < AFMM_REC_TAB; i += blockDim.x) {
         dfv g = df_from_double(tab.gam[i]);
         gam2[i] = make_float2(g.hi, g.lo);
     }
-    for (int i = threadIdx.x; i < nm; i += blockDim.x) {
-        dfv r = df_from_double(i == 0 ? 1.0 : tab.c[i - 1] / tab.c[i]);
-        rho2[i] = make_float2(r.hi, r.lo);
+    for (int m = threadIdx.x; 2 * m < nm; m += blockDim.x) {
+        const int n = 2 * m;
+        const dfv r0 = df_from_double(n == 0 ? 1.0 : tab.c[n - 1] / tab.c[n]);
+        const dfv r1 = n + 1 < nm ? df_from_double(tab.c[n] / tab.c[n + 1]) : df_make(0.f, 0.f);
+        rho4[m] = make_float4(r0.hi, r1.hi, r0.lo, r1.lo);
     }
     const int64_t unit = blockIdx.x;
     int64_t t0, t1, split = 0;
@@ -692,9 +797,15 @@ __global__ void __launch_bounds__(NEARDF_WB * 32, (MPER <= 5 ? 2 : 1)) k_near_df
             rb[9] = 0;
             rcum[9] = cum;
         }
+        s_next = 0;
+        s_abort = 0;
+        for (int b = 0; b < nbuf; ++b) {
+            mbar_init(&s_full[b], 1);
+            mbar_init(&s_empty[b], (uint32_t)ncons);
+        }
     }
     // lane packing: the unit's c targets take T = 2^ceil(log2 c) lanes, and the 32 / T lane
-    // groups (slices) take interleaved sources; the slices are summed at the end
+    // groups (slices) take consecutive sources of a slot; the slices are summed at the end
     const int cnt = (int)(t1 - t0);
     const int lgT = cnt <= 1 ? 0 : 32 - __clz(cnt - 1);
     const int S = 32 >> lgT;
@@ -703,127 +814,155 @@ __global__ void __launch_bounds__(NEARDF_WB * 32, (MPER <= 5 ? 2 : 1)) k_near_df
     const bool active = t < t1;
     const int64_t tc = active ? t : t0;
     const double rt = a.fr[tc], zt = a.fz[tc];
-    const dfv inv2r = df_from_double(0.5 / rt);
-    float aS[NC][MPER], aE[NC][MPER];
-#pragma unroll
-    for (int c = 0; c < NC; ++c)
-#pragma unroll
-        for (int j = 0; j < MPER; ++j) aS[c][j] = aE[c][j] = 0.f;
-    const int n0 = warp * MPER;
     __syncthreads();
     const int total = rcum[9];
-    const int per_chunk = WB * S;
-    for (int c0 = 0; c0 < total; c0 += per_chunk) {
-        if (c0 + warp * S < total) {  // warp-uniform
-            int k = c0 + warp * S + slice;
-            const bool valid = k < total;
-            if (!valid) k = total - 1;
+    const int nslots = (total + S - 1) / S;
+
+    if (warp >= ncons) {
+        // ---------------- producer ----------------
+        const dfv inv2r = df_from_double(0.5 / rt);
+        for (;;) {
+            int k = 0;
+            if (lane == 0) k = atomicAdd(&s_next, 1);
+            k = __shfl_sync(0xffffffffu, k, 0);
+            if (k >= nslots) break;
+            const int b = k % nbuf;
+            if (!ws_wait(&s_empty[b], ((uint32_t)(k / nbuf) & 1u) ^ 1u, lane, a.err, &s_abort)) break;
+            unsigned char *sl = ring + (size_t)b * slot_bytes;
+            float4 *y4 = reinterpret_cast<float4 *>(sl);
+            float4 *p4 = y4 + (size_t)npair * 32;
+            int *sid = reinterpret_cast<int *>(p4 + NPP * 32);
+            int kk = k * S + slice;
+            const bool valid = kk < total;
+            if (!valid) kk = total - 1;
             int rg = 0;
-            while (rg < 8 && rcum[rg + 1] <= k) ++rg;
-            const int64_t s = rb[rg] + (k - rcum[rg]);
+            while (rg < 8 && rcum[rg + 1] <= kk) ++rg;
+            const int64_t s = rb[rg] + (kk - rcum[rg]);
             const double r1 = a.sr[s], z1 = a.sz[s];
             const dfv inv2w = df_div(inv2r, df_from_double(r1));
             PairDF g;
             pair_geom_df(rt, zt, r1, z1, inv2w, active && valid, g);
-            float2 *yw = ys + (size_t)warp * nmq * 32;
-            dfv sc = pair_sequence_df(g, inv2w, Nq, a.df_fwd_switch, (float)a.pp.miller_extra, gam2, yw + lane, 32);
-            float2 *pw = pp + (size_t)warp * NPP * 32;
-            pw[lane] = make_float2(sc.hi, sc.lo);
-            sidx[warp * 32 + lane] = (int)s;
+            SeqSlot ys;
+            ys.y = reinterpret_cast<float *>(y4 + lane);
+            if ((Nq & 1) == 0) ys.put(Nq + 1, df_make(0.f, 0.f));  // pad of the last mode pair
+            const dfv sc = pair_sequence_df(g, inv2w, Nq, a.df_fwd_switch, (float)a.pp.miller_extra, gam2, ys);
+            sid[lane] = (int)s;
+            p4[lane] = bcast4(sc);
             if (GRAD) {
-                dfv inv = df_div(df_make(1.f, 0.f), df_mul(g.rp2, g.rm2));
-                dfv ip = df_mul(g.rm2, inv), im = df_mul(g.rp2, inv);
-                dfv As = df_mul(sc, df_add(ip, im)), Bs = df_mul(sc, df_sub(ip, im));
-                dfv qf = df_sub(df_mul(g.dr, g.sr), df_mul(g.x, g.x));
-                pw[32 + lane] = make_float2(g.x.hi, g.x.lo);
-                pw[64 + lane] = make_float2(qf.hi, qf.lo);
-                pw[96 + lane] = make_float2(As.hi, As.lo);
-                pw[128 + lane] = make_float2(Bs.hi, Bs.lo);
+                const dfv inv = df_div(df_make(1.f, 0.f), df_mul(g.rp2, g.rm2));
+                const dfv ip = df_mul(g.rm2, inv), im = df_mul(g.rp2, inv);
+                const dfv As = df_mul(sc, df_add(ip, im)), Bs = df_mul(sc, df_sub(ip, im));
+                const dfv qf = df_sub(df_mul(g.dr, g.sr), df_mul(g.x, g.x));
+                p4[32 + lane] = bcast4(g.x);
+                p4[64 + lane] = bcast4(qf);
+                p4[96 + lane] = bcast4(As);
+                p4[128 + lane] = bcast4(Bs);
             }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s_full[b]);
         }
-        __syncthreads();
-        const int kmax = min(WB, (total - c0 + S - 1) / S);
-        for (int kk = 0; kk < kmax; ++kk) {
-            const int64_t s = sidx[kk * 32 + lane];
-            const float2 *yk = ys + (size_t)kk * nmq * 32;
-            const float2 *pk = pp + (size_t)kk * NPP * 32;
-            const dfv sc = df_make(pk[lane].x, pk[lane].y);
-            dfv gx = sc, qf = sc, As = sc, Bs = sc, yprev = sc;
-            if (GRAD) {
-                gx = df_make(pk[32 + lane].x, pk[32 + lane].y);
-                qf = df_make(pk[64 + lane].x, pk[64 + lane].y);
-                As = df_make(pk[96 + lane].x, pk[96 + lane].y);
-                Bs = df_make(pk[128 + lane].x, pk[128 + lane].y);
-                float2 yp = n0 == 0 ? yk[32 + lane] : yk[(n0 - 1) * 32 + lane];  // y_{-1} := y_1
-                yprev = df_make(yp.x, yp.y);
-            }
-            if (MIX) {
-                // FP32 products of the pairs' high words, Kahan-compensated sums (aE: compensation)
-                const float scf = sc.hi, gxf = gx.hi, qff = qf.hi;
-#pragma unroll
-                for (int j = 0; j < MPER; ++j) {
-                    const int n = n0 + j;
-                    if (n < nm) {
-                        const float2 yv = yk[n * 32 + lane];
-                        const float yn = yv.x;
-                        const float qr = a.q32_re[(size_t)n * a.nsrc + s], qi = a.q32_im[(size_t)n * a.nsrc + s];
-                        const float gn = scf * yn;
-                        kahan_add(aS[0][j], aE[0][j], qr * gn);
-                        kahan_add(aS[1][j], aE[1][j], qi * gn);
-                        if (GRAD) {
-                            // y_n A + rho_n y_{n-1} B cancels for near pairs (A ~ -B): FP32 pairs
-                            const dfv ynd = df_make(yv.x, yv.y);
-                            const float2 rr = rho2[n];
-                            const float wt =
-                                df_add(df_mul(ynd, As), df_mul(df_mul(df_make(rr.x, rr.y), yprev), Bs)).hi;
-                            yprev = ynd;
-                            const float xw = gxf * wt, qw = qff * wt;
-                            kahan_add(aS[2 % NC][j], aE[2 % NC][j], qr * qw);
-                            kahan_add(aS[3 % NC][j], aE[3 % NC][j], qi * qw);
-                            kahan_add(aS[4 % NC][j], aE[4 % NC][j], qr * xw);
-                            kahan_add(aS[5 % NC][j], aE[5 % NC][j], qi * xw);
-                        }
-                    }
-                }
-                continue;
-            }
-#pragma unroll
-            for (int j = 0; j < MPER; ++j) {
-                const int n = n0 + j;
-                if (n < nm) {
-                    const float2 yv = yk[n * 32 + lane];
-                    const dfv yn = df_make(yv.x, yv.y);
-                    const float2 q2r = a.qdf_re[(size_t)n * a.nsrc + s], q2i = a.qdf_im[(size_t)n * a.nsrc + s];
-                    const dfv qr = df_make(q2r.x, q2r.y), qi = df_make(q2i.x, q2i.y);
-                    const dfv gn = df_mul(sc, yn);
-                    df_acc(aS[0][j], aE[0][j], qr, gn);
-                    df_acc(aS[1][j], aE[1][j], qi, gn);
-                    if (GRAD) {
-                        float2 rr = rho2[n];
-                        dfv wt = df_add(df_mul(yn, As), df_mul(df_mul(df_make(rr.x, rr.y), yprev), Bs));
-                        yprev = yn;
-                        dfv xw = df_mul(gx, wt), qw = df_mul(qf, wt);
-                        df_acc(aS[2 % NC][j], aE[2 % NC][j], qr, qw);
-                        df_acc(aS[3 % NC][j], aE[3 % NC][j], qi, qw);
-                        df_acc(aS[4 % NC][j], aE[4 % NC][j], qr, xw);
-                        df_acc(aS[5 % NC][j], aE[5 % NC][j], qi, xw);
-                    }
-                }
-            }
-        }
-        __syncthreads();
+        return;
     }
-    // sum the slices in FP64: cs[q][j] on every lane of target tl
+
+    // ---------------- consumer: modes n0 .. n0 + MPER - 1 ----------------
+    const int n0 = a.mode_lo + warp * MPER;  // mode_lo is even
+    const int m0 = n0 / 2;
+    const int nhi = a.mode_hi;
+    float2 aS[NC][NP], aE[NC][NP];  // .x mode 2m, .y mode 2m + 1
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int j = 0; j < NP; ++j) aS[c][j] = aE[c][j] = make_float2(0.f, 0.f);
+    for (int k = 0; k < nslots; ++k) {
+        const int b = k % nbuf;
+        if (!ws_wait(&s_full[b], (uint32_t)(k / nbuf) & 1u, lane, a.err, &s_abort)) return;
+        const unsigned char *sl = ring + (size_t)b * slot_bytes;
+        const float4 *y4 = reinterpret_cast<const float4 *>(sl);
+        const float4 *p4 = y4 + (size_t)npair * 32;
+        const int64_t s = reinterpret_cast<const int *>(p4 + NPP * 32)[lane];
+        const df2 SC = df2_from4(p4[lane]);
+        df2 GX = SC, QF = SC, AS = SC, BS = SC;
+        dfv yprev = df_make(0.f, 0.f);
+        if (GRAD) {
+            GX = df2_from4(p4[32 + lane]);
+            QF = df2_from4(p4[64 + lane]);
+            AS = df2_from4(p4[96 + lane]);
+            BS = df2_from4(p4[128 + lane]);
+            // y_{n0 - 1}: the second mode of the previous pair; y_{-1} := y_1
+            yprev = df2_y(df2_from4(y4[(m0 == 0 ? 0 : m0 - 1) * 32 + lane]));
+        }
+        if (MIX) {
+            // FP32 products of the pairs' high words, Kahan-compensated sums (aE: compensation)
+            const float2 SCf = SC.hi, GXf = GX.hi, QFf = QF.hi;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                const int m = m0 + j;
+                if (2 * m < nhi) {
+                    const df2 Y = df2_from4(y4[m * 32 + lane]);
+                    const float2 QR = a.q32_re[(size_t)m * a.nsrc + s], QI = a.q32_im[(size_t)m * a.nsrc + s];
+                    const float2 G = fmul2(SCf, Y.hi);
+                    kahan2(aS[0][j], aE[0][j], fmul2(QR, G));
+                    kahan2(aS[1][j], aE[1][j], fmul2(QI, G));
+                    if (GRAD) {
+                        // y_n A + rho_n y_{n-1} B cancels for near pairs (A ~ -B): FP32 pairs
+                        const df2 YP = df2_pack(yprev, df2_x(Y));
+                        yprev = df2_y(Y);
+                        const float2 wt = df2_add(df2_mul(Y, AS), df2_mul(df2_mul(df2_from4(rho4[m]), YP), BS)).hi;
+                        const float2 xw = fmul2(GXf, wt), qw = fmul2(QFf, wt);
+                        kahan2(aS[2 % NC][j], aE[2 % NC][j], fmul2(QR, qw));
+                        kahan2(aS[3 % NC][j], aE[3 % NC][j], fmul2(QI, qw));
+                        kahan2(aS[4 % NC][j], aE[4 % NC][j], fmul2(QR, xw));
+                        kahan2(aS[5 % NC][j], aE[5 % NC][j], fmul2(QI, xw));
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                const int m = m0 + j;
+                if (2 * m < nhi) {
+                    const df2 Y = df2_from4(y4[m * 32 + lane]);
+                    const df2 QR = df2_from4(a.qdf_re[(size_t)m * a.nsrc + s]);
+                    const df2 QI = df2_from4(a.qdf_im[(size_t)m * a.nsrc + s]);
+                    const df2 G = df2_mul(SC, Y);
+                    df2_acc(aS[0][j], aE[0][j], QR, G);
+                    df2_acc(aS[1][j], aE[1][j], QI, G);
+                    if (GRAD) {
+                        // w_n = y_n A + rho_n y_{n-1} B, the derivative recursion's weight
+                        const df2 YP = df2_pack(yprev, df2_x(Y));
+                        yprev = df2_y(Y);
+                        const df2 T = df2_mul(df2_from4(rho4[m]), YP);
+                        const df2 WT = df2_add(df2_mul(Y, AS), df2_mul(T, BS));
+                        const df2 XW = df2_mul(GX, WT), QW = df2_mul(QF, WT);
+                        df2_acc(aS[2 % NC][j], aE[2 % NC][j], QR, QW);
+                        df2_acc(aS[3 % NC][j], aE[3 % NC][j], QI, QW);
+                        df2_acc(aS[4 % NC][j], aE[4 % NC][j], QR, XW);
+                        df2_acc(aS[5 % NC][j], aE[5 % NC][j], QI, XW);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s_empty[b]);
+    }
+    // sum the slices in FP64 (every lane of target tl gets the sums); cs is indexed by the
+    // mode at run time below (local memory: once per unit, off the slot loop)
     double cs[NC][MPER];
 #pragma unroll
     for (int q = 0; q < NC; ++q)
 #pragma unroll
-        for (int j = 0; j < MPER; ++j) {
-            double v = MIX ? (double)aS[q][j] - (double)aE[q][j] : (double)aS[q][j] + (double)aE[q][j];
-            for (int o = 1 << lgT; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            cs[q][j] = v;
+        for (int jp = 0; jp < NP; ++jp) {
+            double v0 = MIX ? (double)aS[q][jp].x - (double)aE[q][jp].x : (double)aS[q][jp].x + (double)aE[q][jp].x;
+            double v1 = MIX ? (double)aS[q][jp].y - (double)aE[q][jp].y : (double)aS[q][jp].y + (double)aE[q][jp].y;
+            for (int o = 1 << lgT; o < 32; o <<= 1) {
+                v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+                v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+            }
+            cs[q][2 * jp] = v0;
+            cs[q][2 * jp + 1] = v1;
         }
     if (!active || slice != 0) return;
+    // add the local expansion and write
     dfv u = df_make(0.f, 0.f), v = u;
     double ud = 0.0, vd = 0.0;
     const bool has_loc = MIX ? a.loc32_re != nullptr : a.locdf_re != nullptr;
@@ -836,128 +975,153 @@ __global__ void __launch_bounds__(NEARDF_WB * 32, (MPER <= 5 ? 2 : 1)) k_near_df
         v = df_from_double(vd);
     }
     const int64_t dst = a.out_perm ? a.out_perm[t] : t;
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < MPER; ++j) {
-        const int n = n0 + j;
-        if (n >= nm) continue;
-        double pr = cs[0][j];
-        double pi = cs[1][j];
-        double dr_r = 0, dr_i = 0, dz_r = 0, dz_i = 0;
-        if (GRAD) {
-            double nu = n - 0.5;
-            dr_r = (nu * cs[2 % NC][j] - pr) * (0.5 / rt);
-            dr_i = (nu * cs[3 % NC][j] - pi) * (0.5 / rt);
-            dz_r = nu * cs[4 % NC][j];
-            dz_i = nu * cs[5 % NC][j];
-        }
-        if (has_loc && MIX) {
-            const float *Fr = a.loc32_re + ((size_t)box * nm + n) * a.ncoef;
-            const float *Fi = a.loc32_im + ((size_t)box * nm + n) * a.ncoef;
-            float vr, dur, dvr, vi, dui, dvi;
-            l2p_eval32<GRAD>(Fr, a.M, (float)ud, (float)vd, vr, dur, dvr);
-            l2p_eval32<GRAD>(Fi, a.M, (float)ud, (float)vd, vi, dui, dvi);
-            pr += vr;
-            pi += vi;
+        {
+            const int n = n0 + j;
+            if (n >= nhi) continue;
+            double pr = cs[0][j];
+            double pi = cs[1][j];
+            double dr_r = 0, dr_i = 0, dz_r = 0, dz_i = 0;
             if (GRAD) {
-                const double ih = 1.0 / a.h;
-                dr_r += dur * ih;
-                dr_i += dui * ih;
-                dz_r += dvr * ih;
-                dz_i += dvi * ih;
+                double nu = n - 0.5;
+                dr_r = (nu * cs[2 % NC][j] - pr) * (0.5 / rt);
+                dr_i = (nu * cs[3 % NC][j] - pi) * (0.5 / rt);
+                dz_r = nu * cs[4 % NC][j];
+                dz_i = nu * cs[5 % NC][j];
             }
-        } else if (has_loc) {
-            const float2 *Fr = a.locdf_re + ((size_t)box * nm + n) * a.ncoef;
-            const float2 *Fi = a.locdf_im + ((size_t)box * nm + n) * a.ncoef;
-            dfv vr, dur, dvr, vi, dui, dvi;
-            l2p_eval_df<GRAD>(Fr, a.M, u, v, vr, dur, dvr);
-            l2p_eval_df<GRAD>(Fi, a.M, u, v, vi, dui, dvi);
-            pr += df_to_double(vr);
-            pi += df_to_double(vi);
-            if (GRAD) {
-                double ih = 1.0 / a.h;
-                dr_r += df_to_double(dur) * ih;
-                dr_i += df_to_double(dui) * ih;
-                dz_r += df_to_double(dvr) * ih;
-                dz_i += df_to_double(dvi) * ih;
+            if (has_loc && MIX) {
+                const float *Fr = a.loc32_re + ((size_t)box * nm + n) * a.ncoef;
+                const float *Fi = a.loc32_im + ((size_t)box * nm + n) * a.ncoef;
+                float2 val, du, dv;
+                l2p_eval32x2<GRAD>(Fr, Fi, a.M, (float)ud, (float)vd, val, du, dv);
+                pr += val.x;
+                pi += val.y;
+                if (GRAD) {
+                    const double ih = 1.0 / a.h;
+                    dr_r += du.x * ih;
+                    dr_i += du.y * ih;
+                    dz_r += dv.x * ih;
+                    dz_i += dv.y * ih;
+                }
+            } else if (has_loc) {
+                const float2 *Fr = a.locdf_re + ((size_t)box * nm + n) * a.ncoef;
+                const float2 *Fi = a.locdf_im + ((size_t)box * nm + n) * a.ncoef;
+                df2 val, du, dv;
+                l2p_eval_df2<GRAD>(Fr, Fi, a.M, u, v, val, du, dv);
+                pr += df_to_double(df2_x(val));
+                pi += df_to_double(df2_y(val));
+                if (GRAD) {
+                    double ih = 1.0 / a.h;
+                    dr_r += df_to_double(df2_x(du)) * ih;
+                    dr_i += df_to_double(df2_y(du)) * ih;
+                    dz_r += df_to_double(df2_x(dv)) * ih;
+                    dz_i += df_to_double(df2_y(dv)) * ih;
+                }
             }
-        }
-        if (a.part) {
-            size_t base = (size_t)split * NC;
-            size_t nfm = (size_t)a.nfield;
-            a.part[((base + 0) * nm + n) * nfm + t] = pr;
-            a.part[((base + 1) * nm + n) * nfm + t] = pi;
-            if (GRAD) {
-                a.part[((base + 2) * nm + n) * nfm + t] = dr_r;
-                a.part[((base + 3) * nm + n) * nfm + t] = dr_i;
-                a.part[((base + 4) * nm + n) * nfm + t] = dz_r;
-                a.part[((base + 5) * nm + n) * nfm + t] = dz_i;
-            }
-        } else {
-            size_t od = (size_t)n * a.nfield + dst;
-            if (a.o_re) a.o_re[od] = pr;
-            if (a.o_im) a.o_im[od] = pi;
-            if (GRAD) {
-                a.o_dr_re[od] = dr_r;
-                a.o_dr_im[od] = dr_i;
-                a.o_dz_re[od] = dz_r;
-                a.o_dz_im[od] = dz_i;
+            if (a.part) {
+                size_t base = (size_t)split * NC;
+                size_t nfm = (size_t)a.nfield;
+                a.part[((base + 0) * nm + n) * nfm + t] = pr;
+                a.part[((base + 1) * nm + n) * nfm + t] = pi;
+                if (GRAD) {
+                    a.part[((base + 2) * nm + n) * nfm + t] = dr_r;
+                    a.part[((base + 3) * nm + n) * nfm + t] = dr_i;
+                    a.part[((base + 4) * nm + n) * nfm + t] = dz_r;
+                    a.part[((base + 5) * nm + n) * nfm + t] = dz_i;
+                }
+            } else {
+                size_t od = (size_t)n * a.nfield + dst;
+                if (a.o_re) a.o_re[od] = pr;
+                if (a.o_im) a.o_im[od] = pi;
+                if (GRAD) {
+                    a.o_dr_re[od] = dr_r;
+                    a.o_dr_im[od] = dr_i;
+                    a.o_dz_re[od] = dz_r;
+                    a.o_dz_im[od] = dz_i;
+                }
             }
         }
     }
 }
 
-static size_t neardf_smem(int nm, int grad)
+// shared memory of k_near_ws: tables + ring of nbuf slots
+static size_t nws_slot_bytes(int nm, int grad)
 {
-    int Nq = (grad && nm < 2) ? 1 : nm - 1;
-    int npp = grad ? 5 : 1;
-    return sizeof(double) * ((size_t)AFMM_REC_TAB + AFMM_MAX_MODES + (size_t)NEARDF_WB * (Nq + 1) * 32 +
-                             (size_t)NEARDF_WB * npp * 32);
+    const int Nq = (grad && nm < 2) ? 1 : nm - 1;
+    const int npair = (Nq + 2) / 2, npp = grad ? 5 : 1;
+    return (size_t)(npair + npp) * 32 * 16 + 32 * sizeof(int);
+}
+static size_t nws_table_bytes() { return sizeof(float2) * AFMM_REC_TAB + sizeof(float4) * (AFMM_MAX_MODES / 2 + 1); }
+
+// Modes per consumer warp: the smallest even MPER with at most 11 consumers (>= 5 producers)
+static int nws_mper(int nm)
+{
+    for (int mp = 2; mp <= 8; mp += 2)
+        if ((nm + mp - 1) / mp <= 11) return mp;
+    return 0;
 }
 
 template <bool GRAD, int MPER, bool MIX>
-static afmm_status launch_near_df_k(const NearArgs &a, const RecTab &tab, cudaStream_t st)
+static afmm_status launch_near_ws_k(const NearArgs &a, const RecTab &tab, cudaStream_t st)
 {
-    size_t sm = neardf_smem(a.nmodes, GRAD);
-    if (sm > 227 * 1024) return AFMM_EUNSUPPORTED;
-    AFMM_CUDA(cudaFuncSetAttribute(k_near_df<GRAD, MPER, MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_near_df<GRAD, MPER, MIX><<<(unsigned)a.nunits, NEARDF_WB * 32, sm, st>>>(a, tab);
+    const int ncons = (a.mode_hi - a.mode_lo + MPER - 1) / MPER;
+    const size_t slot = nws_slot_bytes(a.nmodes, GRAD), tabs = nws_table_bytes();
+    const size_t budget = 200 * 1024;
+    int nbuf = (int)((budget - tabs) / slot);
+    if (nbuf > NWS_BMAX) nbuf = NWS_BMAX;
+    if (nbuf < 2) return AFMM_EUNSUPPORTED;
+    // at most nbuf producers: a producer then never waits on a ring slot two rounds behind
+    // (nbuf + 1 producers would all have to be stuck on slots of the same consumer backlog),
+    // so the parity of each wait is unambiguous
+    int nprod = NWS_THREADS / 32 - ncons;
+    if (nprod > nbuf) nprod = nbuf;
+    const size_t sm = tabs + (size_t)nbuf * slot;
+    AFMM_CUDA(cudaFuncSetAttribute(k_near_ws<GRAD, MPER, MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_near_ws<GRAD, MPER, MIX><<<(unsigned)a.nunits, 32 * (ncons + nprod), sm, st>>>(a, tab, ncons, nbuf);
     AFMM_LAUNCH_CHECK();
     return AFMM_OK;
 }
 
 template <bool GRAD, bool MIX>
-static afmm_status launch_near_df(const NearArgs &a, const RecTab &tab, cudaStream_t st)
+static afmm_status launch_near_ws(const NearArgs &a, const RecTab &tab, cudaStream_t st)
 {
-    int mper = (a.nmodes + NEARDF_WB - 1) / NEARDF_WB;
-    if (mper <= 1) return launch_near_df_k<GRAD, 1, MIX>(a, tab, st);
-    if (mper <= 2) return launch_near_df_k<GRAD, 2, MIX>(a, tab, st);
-    if (mper <= 3) return launch_near_df_k<GRAD, 3, MIX>(a, tab, st);
-    if (mper <= 4) return launch_near_df_k<GRAD, 4, MIX>(a, tab, st);
-    if (mper <= 5) return launch_near_df_k<GRAD, 5, MIX>(a, tab, st);
-    if (mper <= 9) return launch_near_df_k<GRAD, 9, MIX>(a, tab, st);
-    if (mper <= 17) return launch_near_df_k<GRAD, 17, MIX>(a, tab, st);
-    return AFMM_EUNSUPPORTED;
+    switch (nws_mper(a.mode_hi - a.mode_lo)) {
+    case 2: return launch_near_ws_k<GRAD, 2, MIX>(a, tab, st);
+    case 4: return launch_near_ws_k<GRAD, 4, MIX>(a, tab, st);
+    case 6: return launch_near_ws_k<GRAD, 6, MIX>(a, tab, st);
+    case 8: return launch_near_ws_k<GRAD, 8, MIX>(a, tab, st);
+    default: return AFMM_EUNSUPPORTED;
+    }
 }
 
-// strengths into sorted order, times c_n, as FP32 pairs (FP64 path; the FP64 copy feeds the
-// far field)
+// strengths into sorted order, times c_n: the FP64 copy (far field) and the FP32-pair copy
+// interleaved by mode pair (near field); one thread per (mode pair, point)
 __global__ void k_permute_df(const double *__restrict__ q_re, const double *__restrict__ q_im,
                              const int32_t *__restrict__ perm, int64_t n, int nm, const RecTab tab,
-                             double *__restrict__ qs_re, double *__restrict__ qs_im, float2 *__restrict__ qd_re,
-                             float2 *__restrict__ qd_im)
+                             double *__restrict__ qs_re, double *__restrict__ qs_im, float4 *__restrict__ qd_re,
+                             float4 *__restrict__ qd_im)
 {
+    const int64_t npq = (nm + 1) / 2;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n * nm) return;
-    int m = (int)(i / n);
-    int64_t j = i % n;
-    size_t src = (size_t)m * n + perm[j];
-    double c = tab.c[m];
-    double vr = q_re[src] * c, vi = q_im[src] * c;
-    qs_re[i] = vr;
-    qs_im[i] = vi;
-    dfv a = df_from_double(vr), b = df_from_double(vi);
-    qd_re[i] = make_float2(a.hi, a.lo);
-    qd_im[i] = make_float2(b.hi, b.lo);
+    if (i >= n * npq) return;
+    const int m = (int)(i / n);
+    const int64_t j = i % n;
+    dfv r[2], im[2];
+    for (int h = 0; h < 2; ++h) {
+        const int mode = 2 * m + h;
+        r[h] = im[h] = df_make(0.f, 0.f);
+        if (mode >= nm) continue;
+        const size_t src = (size_t)mode * n + perm[j];
+        const double c = tab.c[mode];
+        const double vr = q_re[src] * c, vi = q_im[src] * c;
+        qs_re[(size_t)mode * n + j] = vr;
+        qs_im[(size_t)mode * n + j] = vi;
+        r[h] = df_from_double(vr);
+        im[h] = df_from_double(vi);
+    }
+    qd_re[i] = make_float4(r[0].hi, r[1].hi, r[0].lo, r[1].lo);
+    qd_im[i] = make_float4(im[0].hi, im[1].hi, im[0].lo, im[1].lo);
 }
 
 // sum of split partials into the caller layout
@@ -1048,31 +1212,41 @@ static int near_warps(int nm, int grad)
 
 static inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b > 0 ? (n + b - 1) / b : 1); }
 
-// strengths into sorted order, times c_n, rounded to FP32 (MIXED precision)
+// strengths into sorted order, times c_n, rounded to FP32 (MIXED precision), interleaved by
+// mode pair; one thread per (mode pair, point)
 __global__ void k_permute32(const double *__restrict__ q_re, const double *__restrict__ q_im,
                             const int32_t *__restrict__ perm, int64_t n, int nm, const RecTab tab,
-                            float *__restrict__ qs_re, float *__restrict__ qs_im)
+                            float2 *__restrict__ qs_re, float2 *__restrict__ qs_im)
 {
+    const int64_t npq = (nm + 1) / 2;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n * nm) return;
-    int m = (int)(i / n);
-    int64_t j = i % n;
-    size_t src = (size_t)m * n + perm[j];
-    double c = tab.c[m];
-    qs_re[i] = (float)(q_re[src] * c);
-    qs_im[i] = (float)(q_im[src] * c);
+    if (i >= n * npq) return;
+    const int m = (int)(i / n);
+    const int64_t j = i % n;
+    float r[2] = {0.f, 0.f}, im[2] = {0.f, 0.f};
+    for (int h = 0; h < 2; ++h) {
+        const int mode = 2 * m + h;
+        if (mode >= nm) continue;
+        const size_t src = (size_t)mode * n + perm[j];
+        const double c = tab.c[mode];
+        r[h] = (float)(q_re[src] * c);
+        im[h] = (float)(q_im[src] * c);
+    }
+    qs_re[i] = make_float2(r[0], r[1]);
+    qs_im[i] = make_float2(im[0], im[1]);
 }
 
 afmm_status launch_permute(afmm_plan p, int dir, const double *q_re, const double *q_im)
 {
     int64_t n = dir == 0 ? p->ns : p->nf;
     const int32_t *perm = dir == 0 ? p->s_perm : p->t_perm;
+    const int64_t npq = (p->nmodes + 1) / 2;
     if (p->precision == AFMM_MIXED)
-        k_permute32<<<nblk(n * p->nmodes), 256, 0, p->stream>>>(q_re, q_im, perm, n, p->nmodes, *p->rec, p->qs32_re,
-                                                                 p->qs32_im);
+        k_permute32<<<nblk(n * npq), 256, 0, p->stream>>>(q_re, q_im, perm, n, p->nmodes, *p->rec, p->qs32_re,
+                                                           p->qs32_im);
     else if (p->precision == AFMM_FP64)
-        k_permute_df<<<nblk(n * p->nmodes), 256, 0, p->stream>>>(q_re, q_im, perm, n, p->nmodes, *p->rec, p->qs_re,
-                                                                  p->qs_im, p->qsdf, p->qsdf + (size_t)p->nmodes * p->n_max);
+        k_permute_df<<<nblk(n * npq), 256, 0, p->stream>>>(q_re, q_im, perm, n, p->nmodes, *p->rec, p->qs_re, p->qs_im,
+                                                            p->qsdf, p->qsdf + (size_t)npq * p->n_max);
     else
         k_permute<<<nblk(n * p->nmodes), 256, 0, p->stream>>>(q_re, q_im, perm, n, p->nmodes, *p->rec, p->qs_re,
                                                                p->qs_im);
@@ -1150,37 +1324,43 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
     unsigned grid = (unsigned)a.nunits;
     const int T = NEAR2_WB * 32;
     if (p->precision == AFMM_FP64_NATIVE && sm > 227 * 1024) return AFMM_EUNSUPPORTED;
-    if (p->precision == AFMM_FP64) {
-        a.qdf_re = p->qsdf;
-        a.qdf_im = p->qsdf + (size_t)p->nmodes * p->n_max;
-        if (with_local && !direct) {  // the leaf locals are kept as FP32 pairs
-            a.locdf_re = p->lv[d].locd_re;
-            a.locdf_im = p->lv[d].locd_im;
-            a.loc_re = nullptr;
-            a.loc_im = nullptr;
+    if (p->precision == AFMM_FP64 || mix) {
+        // FP32-pair sequence (GB300's FP64 issues at 1/64 of FP32, so the pair arithmetic is
+        // the fast way to the FP64-class sequence); FP64: FP32-pair sums, MIXED: compensated
+        // FP32 sums.  Amplitudes are interleaved by mode pair.
+        const size_t npq = (size_t)(p->nmodes + 1) / 2;
+        if (mix) {
+            a.q32_re = p->qs32_re;
+            a.q32_im = p->qs32_im;
+        } else {
+            a.qdf_re = p->qsdf;
+            a.qdf_im = p->qsdf + npq * p->n_max;
+            if (with_local && !direct) {  // the leaf locals are kept as FP32 pairs
+                a.locdf_re = p->lv[d].locd_re;
+                a.locdf_im = p->lv[d].locd_im;
+                a.loc_re = nullptr;
+                a.loc_im = nullptr;
+            }
         }
         a.df_fwd_switch = (float)p->df_fwd_switch;
-        if (grad)
-            AFMM_TRY((launch_near_df<true, false>(a, *p->rec, p->stream)));
-        else
-            AFMM_TRY((launch_near_df<false, false>(a, *p->rec, p->stream)));
-    } else if (mix) {
-        // MIXED: the FP32-pair sequence with compensated FP32 sums (GB300's FP64 issues at
-        // 1/61 of FP32, so the pair arithmetic is the fast way to the FP64-class sequence)
-        a.df_fwd_switch = (float)p->df_fwd_switch;
-        if (grad)
-            AFMM_TRY((launch_near_df<true, true>(a, *p->rec, p->stream)));
-        else
-            AFMM_TRY((launch_near_df<false, true>(a, *p->rec, p->stream)));
-    } else if (grad && mix) {
-        AFMM_CUDA(cudaFuncSetAttribute(k_near2<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_near2<true, true><<<grid, T, sm, p->stream>>>(a, *p->rec);
+        a.err = p->err_dev;
+        // at most 11 consumer warps x 8 modes per launch; larger mode counts take several
+        // launches over mode ranges (each recomputes the pair sequences)
+        for (int lo = 0; lo < p->nmodes; lo += NWS_MODES_PER_LAUNCH) {
+            a.mode_lo = lo;
+            a.mode_hi = p->nmodes < lo + NWS_MODES_PER_LAUNCH ? p->nmodes : lo + NWS_MODES_PER_LAUNCH;
+            if (grad && mix)
+                AFMM_TRY((launch_near_ws<true, true>(a, *p->rec, p->stream)));
+            else if (grad)
+                AFMM_TRY((launch_near_ws<true, false>(a, *p->rec, p->stream)));
+            else if (mix)
+                AFMM_TRY((launch_near_ws<false, true>(a, *p->rec, p->stream)));
+            else
+                AFMM_TRY((launch_near_ws<false, false>(a, *p->rec, p->stream)));
+        }
     } else if (grad) {
         AFMM_CUDA(cudaFuncSetAttribute(k_near2<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_near2<true, false><<<grid, T, sm, p->stream>>>(a, *p->rec);
-    } else if (mix) {
-        AFMM_CUDA(cudaFuncSetAttribute(k_near2<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_near2<false, true><<<grid, T, sm, p->stream>>>(a, *p->rec);
     } else {
         AFMM_CUDA(cudaFuncSetAttribute(k_near2<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k_near2<false, false><<<grid, T, sm, p->stream>>>(a, *p->rec);

@@ -4,9 +4,11 @@
 // forward / Miller choice, ~48-bit precision.  Only the cancelling coordinate differences
 // r - r1 and z - z1 (and r + r1) are formed in FP64 and split exactly.
 //
-// Precision budget: the forward sweep amplifies rounding by about exp(2 N acosh chi); with
-// df rounding ~2^-47 the forward switch is lowered (df_fwd_switch) so that this stays
-// below ~5e-12, and pairs beyond it use Miller's sweep, which is cheap in FP32 pairs.
+// Precision budget: the forward sweep's rounding grows like exp(n acosh chi) while Q_{n-1/2}
+// decays like exp(-n acosh chi); measured against the pair's G^(0) (the scale of the
+// max-normalised per-mode error) the error is ~2^-47 N exp(s/2) / s with s = 2 N acosh chi,
+// which the forward switch df_fwd_switch (s <= 8) keeps near 1e-12; pairs beyond it use
+// Miller's sweep.
 #pragma once
 #include "common.cuh"
 #include "df.cuh"
@@ -43,10 +45,29 @@ __device__ __forceinline__ void pair_geom_df(double rt, double zt, double r1, do
     g.chi = df_add(df_make(1.f, 0.f), t);
 }
 
-// Writes y_n (n = 0..N) as FP32 pairs to ys[n * stride] and returns the df factor s with
-// G_n = s * c_n * y_n.  gam2: recursion constants gam_n as FP32 pairs (shared memory).
+// The sequence of one lane in a slot of the near-field ring: y_n at mode pair n / 2 of a
+// [pair][32 lanes] float4 array (y_2m.hi, y_2m+1.hi, y_2m.lo, y_2m+1.lo), so that a
+// consumer loads two modes of one pair as one packed operand.  y points at the lane's
+// float4 of pair 0.
+struct SeqSlot {
+    float *y;
+    __device__ __forceinline__ void put(int n, dfv v) const
+    {
+        float *e = y + (n >> 1) * 128 + (n & 1);
+        e[0] = v.hi;
+        e[2] = v.lo;
+    }
+    __device__ __forceinline__ dfv get(int n) const
+    {
+        const float *e = y + (n >> 1) * 128 + (n & 1);
+        return df_make(e[0], e[2]);
+    }
+};
+
+// Writes y_n (n = 0..N) into the slot and returns the df factor s with G_n = s * c_n * y_n.
+// gam2: recursion constants gam_n as FP32 pairs (shared memory).
 __device__ __forceinline__ dfv pair_sequence_df(const PairDF &g, dfv inv2w, int N, float fwd_switch, float extra,
-                                                const float2 *__restrict__ gam2, float2 *ys, int stride)
+                                                const float2 *__restrict__ gam2, const SeqSlot ys)
 {
     float tf = g.t;
     float af = log1pf(tf + sqrtf(tf * (tf + 2.0f)));  // acosh(chi)
@@ -77,8 +98,8 @@ __device__ __forceinline__ dfv pair_sequence_df(const PairDF &g, dfv inv2w, int 
     if (fwd) {
         y0 = G0;
         y1 = df_mul(df_mul(G0, csum), inv2w);
-        ys[0] = make_float2(y0.hi, y0.lo);
-        if (N >= 1) ys[stride] = make_float2(y1.hi, y1.lo);
+        ys.put(0, y0);
+        if (N >= 1) ys.put(1, y1);
     } else {
         y0 = df_make(0.f, 0.f);           // y_L
         y1 = df_make(7.8886091e-31f, 0.f); // y_{L-1} = 2^-100
@@ -94,22 +115,18 @@ __device__ __forceinline__ dfv pair_sequence_df(const PairDF &g, dfv inv2w, int 
             y0 = y1;
             y1 = yn;
             int idx = fwd ? n : n - 2;
-            if (idx <= N) ys[idx * stride] = make_float2(yn.hi, yn.lo);
+            if (idx <= N) ys.put(idx, yn);
             if (!fwd && fabsf(yn.hi) > 1.2676506e30f) {  // > 2^100: rescale by 2^-100 (exact)
                 const float s100 = 7.8886091e-31f;
                 y0 = df_scale2(y0, s100);
                 y1 = df_scale2(y1, s100);
                 for (int m = idx; m <= N; ++m)
-                    if (m >= 0) {
-                        float2 v = ys[m * stride];
-                        ys[m * stride] = make_float2(v.x * s100, v.y * s100);
-                    }
+                    if (m >= 0) ys.put(m, df_scale2(ys.get(m), s100));
             }
         }
     }
     if (fwd) return df_make(g.zero, 0.f);
-    float2 y0s = ys[0];
-    dfv sc = df_div(G0, df_make(y0s.x, y0s.y));
+    dfv sc = df_div(G0, ys.get(0));
     return df_make(sc.hi * g.zero, sc.lo * g.zero);
 }
 

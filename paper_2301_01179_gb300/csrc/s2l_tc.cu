@@ -33,6 +33,7 @@
 
 #include "common.cuh"
 #include "df.cuh"
+#include "mbar.cuh"
 
 namespace afmm {
 
@@ -41,8 +42,6 @@ namespace {
 constexpr int TC_SLICES = 6;
 constexpr int TC_THREADS = 512;
 constexpr unsigned long long TC_WAIT_NS = 1000000000ull;  // a completion wait gives up after 1 s
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // shared-memory matrix descriptor: start address, leading (K) and stride (M/N) byte offsets
 // between core matrices, descriptor version 1, no swizzle
@@ -70,24 +69,6 @@ __device__ __forceinline__ void umma_commit(uint64_t *mbar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
                  : "memory");
-}
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t *mbar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(mbar)), "r"(parity)
-        : "memory");
-    return ok != 0;
 }
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src, int bytes)
