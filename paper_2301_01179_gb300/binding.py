@@ -186,7 +186,7 @@ class Plan:
 
     def timing(self):
         out = {}
-        for name in ("perm", "p2m", "m2m", "gexp", "s2l", "l2l", "near", "total"):
+        for name in ("perm", "p2m", "m2m", "gexp", "s2l", "l2l", "l2p", "near", "total"):
             v = ctypes.c_double()
             _check(self._lib.afmm_get_timing(self._h, name.encode(), ctypes.byref(v)), "afmm_get_timing")
             out[name] = v.value

@@ -332,8 +332,8 @@ afmm_status afmm_set_timing(afmm_plan p, int enable)
 afmm_status afmm_get_timing(afmm_plan p, const char *name, double *ms)
 {
     if (!p || !name || !ms) return AFMM_EINVAL;
-    static const char *names[] = {"perm", "p2m", "m2m", "gexp", "s2l", "l2l", "near", "total"};
-    for (int i = 0; i < 8; ++i)
+    static const char *names[] = {"perm", "p2m", "m2m", "gexp", "s2l", "l2l", "near", "total", "l2p"};
+    for (int i = 0; i < 9; ++i)
         if (!strcmp(name, names[i])) {
             *ms = p->t_ms[i];
             return AFMM_OK;
@@ -367,7 +367,9 @@ static afmm_status run_fmm(afmm_plan p, int dir, const double *q_re, const doubl
         p->t_ms[0] = tdiff(p, 0, 1);
         p->t_ms[1] = tdiff(p, 1, 2);
         p->t_ms[2] = tdiff(p, 2, 3);
-        p->t_ms[6] = tdiff(p, 8, 9);
+        // near: the near-field kernel after the L2P (event AFMM_EV_L2P between them)
+        p->t_ms[8] = tdiff(p, 8, AFMM_EV_L2P);
+        p->t_ms[6] = tdiff(p, AFMM_EV_L2P, 9);
         p->t_ms[7] = tdiff(p, 0, 9);
         double g = 0, s2 = 0, l2 = 0;
         for (int l = 2; l <= p->d; ++l) {  // per level: L2L, expansions, S2L (far_field)

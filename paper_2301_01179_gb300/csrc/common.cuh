@@ -168,6 +168,8 @@ struct NearUnit {       // one warp of near-field work: up to 32 field points of
 
 }  // namespace afmm
 
+#define AFMM_EV_L2P 10  // timing event recorded between the L2P and the near-field kernel
+
 struct afmm_plan_s {
     cudaStream_t stream = nullptr;
     int64_t ns = 0, nf = 0;
@@ -212,8 +214,8 @@ struct afmm_plan_s {
     int64_t near_pairs = 0, s2l_pairs = 0, expansions = 0;
     // timing (events on the plan's stream; read back after the evaluation's last event)
     int timing = 0;
-    cudaEvent_t ev[80];
-    double t_ms[8] = {0};
+    cudaEvent_t ev[80];                         // phase timing events (AFMM_EV_L2P: after the L2P)
+    double t_ms[9] = {0};
     // device allocations to free (from the library's stream-ordered pool when pool != null)
     cudaMemPool_t pool = nullptr;
     void *allocs[512];

@@ -44,6 +44,7 @@ struct NearArgs {
     const float *loc32_re, *loc32_im;
     int mode_lo, mode_hi;  // FP32-pair kernel: the modes [mode_lo, mode_hi) of this launch
     int *err;              // plan error word (bounded waits that ran out)
+    int accumulate;        // FP32-pair kernel: add to the outputs (k_l2p wrote the local expansion)
     // local expansion at the leaves (near mode, optional)
     const double *loc_re, *loc_im;
     const uint32_t *leaf_key;
@@ -666,59 +667,6 @@ __device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t parity, int lane
 
 __device__ __forceinline__ float4 bcast4(dfv v) { return make_float4(v.hi, v.hi, v.lo, v.lo); }
 
-// Local expansion value and gradient at (u, v) in box units, for the real and imaginary
-// parts at once (packed): the steps of l2p_eval in FP32 pairs
-template <bool GRAD>
-__device__ __forceinline__ void l2p_eval_df2(const float2 *__restrict__ Fr, const float2 *__restrict__ Fi, int M,
-                                             dfv u, dfv v, df2 &val, df2 &du, df2 &dv)
-{
-    const df2 U = df2_bcast(u), V = df2_bcast(v);
-    const df2 Z = df2_make(make_float2(0.f, 0.f), make_float2(0.f, 0.f));
-    df2 pu = Z, pdu = Z, pdv = Z;
-    for (int k = M; k >= 0; --k) {
-        const int base = k * (M + 1) - k * (k - 1) / 2;
-        df2 pk = Z, pkd = Z;
-        for (int l = M - k; l >= 0; --l) {
-            if (GRAD) pkd = df2_add(df2_mul(pkd, V), pk);
-            const float2 fr = Fr[base + l], fi = Fi[base + l];
-            pk = df2_add(df2_mul(pk, V), df2_make(make_float2(fr.x, fi.x), make_float2(fr.y, fi.y)));
-        }
-        if (GRAD) {
-            pdu = df2_add(df2_mul(pdu, U), pu);
-            pdv = df2_add(df2_mul(pdv, U), pkd);
-        }
-        pu = df2_add(df2_mul(pu, U), pk);
-    }
-    val = pu;
-    du = pdu;
-    dv = pdv;
-}
-
-// MIXED: FP32 value and gradient of the re and im locals at once
-template <bool GRAD>
-__device__ __forceinline__ void l2p_eval32x2(const float *__restrict__ Fr, const float *__restrict__ Fi, int M, float u,
-                                             float v, float2 &val, float2 &du, float2 &dv)
-{
-    const float2 U = make_float2(u, u), V = make_float2(v, v), Z = make_float2(0.f, 0.f);
-    float2 pu = Z, pdu = Z, pdv = Z;
-    for (int k = M; k >= 0; --k) {
-        const int base = k * (M + 1) - k * (k - 1) / 2;
-        float2 pk = Z, pkd = Z;
-        for (int l = M - k; l >= 0; --l) {
-            if (GRAD) pkd = ffma2(pkd, V, pk);
-            pk = ffma2(pk, V, make_float2(Fr[base + l], Fi[base + l]));
-        }
-        if (GRAD) {
-            pdu = ffma2(pdu, U, pu);
-            pdv = ffma2(pdv, U, pkd);
-        }
-        pu = ffma2(pu, U, pk);
-    }
-    val = pu;
-    du = pdu;
-    dv = pdv;
-}
-
 // Kahan-compensated FP32 sums of two components at once: S the sums, C the running
 // compensations (true sums ~ S - C)
 __device__ __forceinline__ void kahan2(float2 &S, float2 &C, float2 v)
@@ -744,7 +692,8 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
     const int Nq = GRAD && N < 1 ? 1 : N;  // the gradient of mode 0 needs y_1
     const int npair = (Nq + 2) / 2;        // mode pairs of y_0 .. y_Nq
     float2 *gam2 = reinterpret_cast<float2 *>(smem_ws);                 // [AFMM_REC_TAB]
-    float4 *rho4 = reinterpret_cast<float4 *>(gam2 + AFMM_REC_TAB);     // [pair] rho_n = c_{n-1} / c_n
+    float4 *gam4 = reinterpret_cast<float4 *>(gam2 + AFMM_REC_TAB);     // [pair] gam_2m, gam_2m+1
+    float4 *rho4 = gam4 + (AFMM_MAX_MODES / 2 + 1);                     // [pair] rho_n = c_{n-1} / c_n
     unsigned char *ring = reinterpret_cast<unsigned char *>(rho4 + AFMM_MAX_MODES / 2 + 1);
     const size_t slot_bytes = (size_t)(npair + NPP) * 32 * sizeof(float4) + 32 * sizeof(int);
     __shared__ uint64_t s_full[NWS_BMAX], s_empty[NWS_BMAX];
@@ -754,6 +703,10 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
     for (int i = threadIdx.x; i < AFMM_REC_TAB; i += blockDim.x) {
         dfv g = df_from_double(tab.gam[i]);
         gam2[i] = make_float2(g.hi, g.lo);
+    }
+    for (int m = threadIdx.x; m < AFMM_MAX_MODES / 2 + 1; m += blockDim.x) {
+        const dfv g0 = df_from_double(tab.gam[2 * m]), g1 = df_from_double(tab.gam[2 * m + 1]);
+        gam4[m] = make_float4(g0.hi, g1.hi, g0.lo, g1.lo);
     }
     for (int m = threadIdx.x; 2 * m < nm; m += blockDim.x) {
         const int n = 2 * m;
@@ -821,6 +774,7 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
     if (warp >= ncons) {
         // ---------------- producer ----------------
         const dfv inv2r = df_from_double(0.5 / rt);
+        const float extra = (float)a.pp.miller_extra;
         for (;;) {
             int k = 0;
             if (lane == 0) k = atomicAdd(&s_next, 1);
@@ -828,10 +782,8 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
             if (k >= nslots) break;
             const int b = k % nbuf;
             if (!ws_wait(&s_empty[b], ((uint32_t)(k / nbuf) & 1u) ^ 1u, lane, a.err, &s_abort)) break;
-            unsigned char *sl = ring + (size_t)b * slot_bytes;
-            float4 *y4 = reinterpret_cast<float4 *>(sl);
+            float4 *y4 = reinterpret_cast<float4 *>(ring + (size_t)b * slot_bytes);
             float4 *p4 = y4 + (size_t)npair * 32;
-            int *sid = reinterpret_cast<int *>(p4 + NPP * 32);
             int kk = k * S + slice;
             const bool valid = kk < total;
             if (!valid) kk = total - 1;
@@ -845,8 +797,12 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
             SeqSlot ys;
             ys.y = reinterpret_cast<float *>(y4 + lane);
             if ((Nq & 1) == 0) ys.put(Nq + 1, df_make(0.f, 0.f));  // pad of the last mode pair
-            const dfv sc = pair_sequence_df(g, inv2w, Nq, a.df_fwd_switch, (float)a.pp.miller_extra, gam2, ys);
-            sid[lane] = (int)s;
+            float af;
+            const bool fwd = pair_regime(g.t, Nq, a.df_fwd_switch, af);
+            dfv csum;
+            const dfv G0 = df_div(df_make(0.5f, 0.f), pair_agm_df(g, csum));
+            const dfv sc = pair_sweep_df(g.chi, g.zero, inv2w, Nq, fwd, af, extra, G0, csum, gam2, gam4, ys);
+            reinterpret_cast<int *>(p4 + NPP * 32)[lane] = (int)s;
             p4[lane] = bcast4(sc);
             if (GRAD) {
                 const dfv inv = df_div(df_make(1.f, 0.f), df_mul(g.rp2, g.rm2));
@@ -962,86 +918,149 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
             cs[q][2 * jp + 1] = v1;
         }
     if (!active || slice != 0) return;
-    // add the local expansion and write
-    dfv u = df_make(0.f, 0.f), v = u;
-    double ud = 0.0, vd = 0.0;
-    const bool has_loc = MIX ? a.loc32_re != nullptr : a.locdf_re != nullptr;
-    if (has_loc) {
-        uint32_t kk = a.leaf_key[box];
-        double cr = a.r0 + ((double)morton_ir(kk) + 0.5) * a.h, cz = a.z0 + ((double)morton_iz(kk) + 0.5) * a.h;
-        ud = (rt - cr) / a.h;
-        vd = (zt - cz) / a.h;
-        u = df_from_double(ud);
-        v = df_from_double(vd);
-    }
+    // write, or add to the local-expansion values that k_l2p wrote (FMM near field)
+    const bool add = a.accumulate != 0;
     const int64_t dst = a.out_perm ? a.out_perm[t] : t;
 #pragma unroll 1
     for (int j = 0; j < MPER; ++j) {
-        {
-            const int n = n0 + j;
-            if (n >= nhi) continue;
-            double pr = cs[0][j];
-            double pi = cs[1][j];
-            double dr_r = 0, dr_i = 0, dz_r = 0, dz_i = 0;
+        const int n = n0 + j;
+        if (n >= nhi) continue;
+        const double pr = cs[0][j];
+        const double pi = cs[1][j];
+        double dr_r = 0, dr_i = 0, dz_r = 0, dz_i = 0;
+        if (GRAD) {
+            double nu = n - 0.5;
+            dr_r = (nu * cs[2 % NC][j] - pr) * (0.5 / rt);
+            dr_i = (nu * cs[3 % NC][j] - pi) * (0.5 / rt);
+            dz_r = nu * cs[4 % NC][j];
+            dz_i = nu * cs[5 % NC][j];
+        }
+        if (a.part) {
+            size_t base = (size_t)split * NC;
+            size_t nfm = (size_t)a.nfield;
+            a.part[((base + 0) * nm + n) * nfm + t] = pr;
+            a.part[((base + 1) * nm + n) * nfm + t] = pi;
             if (GRAD) {
-                double nu = n - 0.5;
-                dr_r = (nu * cs[2 % NC][j] - pr) * (0.5 / rt);
-                dr_i = (nu * cs[3 % NC][j] - pi) * (0.5 / rt);
-                dz_r = nu * cs[4 % NC][j];
-                dz_i = nu * cs[5 % NC][j];
+                a.part[((base + 2) * nm + n) * nfm + t] = dr_r;
+                a.part[((base + 3) * nm + n) * nfm + t] = dr_i;
+                a.part[((base + 4) * nm + n) * nfm + t] = dz_r;
+                a.part[((base + 5) * nm + n) * nfm + t] = dz_i;
             }
-            if (has_loc && MIX) {
-                const float *Fr = a.loc32_re + ((size_t)box * nm + n) * a.ncoef;
-                const float *Fi = a.loc32_im + ((size_t)box * nm + n) * a.ncoef;
-                float2 val, du, dv;
-                l2p_eval32x2<GRAD>(Fr, Fi, a.M, (float)ud, (float)vd, val, du, dv);
-                pr += val.x;
-                pi += val.y;
-                if (GRAD) {
-                    const double ih = 1.0 / a.h;
-                    dr_r += du.x * ih;
-                    dr_i += du.y * ih;
-                    dz_r += dv.x * ih;
-                    dz_i += dv.y * ih;
-                }
-            } else if (has_loc) {
-                const float2 *Fr = a.locdf_re + ((size_t)box * nm + n) * a.ncoef;
-                const float2 *Fi = a.locdf_im + ((size_t)box * nm + n) * a.ncoef;
-                df2 val, du, dv;
-                l2p_eval_df2<GRAD>(Fr, Fi, a.M, u, v, val, du, dv);
-                pr += df_to_double(df2_x(val));
-                pi += df_to_double(df2_y(val));
-                if (GRAD) {
-                    double ih = 1.0 / a.h;
-                    dr_r += df_to_double(df2_x(du)) * ih;
-                    dr_i += df_to_double(df2_y(du)) * ih;
-                    dz_r += df_to_double(df2_x(dv)) * ih;
-                    dz_i += df_to_double(df2_y(dv)) * ih;
-                }
-            }
-            if (a.part) {
-                size_t base = (size_t)split * NC;
-                size_t nfm = (size_t)a.nfield;
-                a.part[((base + 0) * nm + n) * nfm + t] = pr;
-                a.part[((base + 1) * nm + n) * nfm + t] = pi;
-                if (GRAD) {
-                    a.part[((base + 2) * nm + n) * nfm + t] = dr_r;
-                    a.part[((base + 3) * nm + n) * nfm + t] = dr_i;
-                    a.part[((base + 4) * nm + n) * nfm + t] = dz_r;
-                    a.part[((base + 5) * nm + n) * nfm + t] = dz_i;
-                }
-            } else {
-                size_t od = (size_t)n * a.nfield + dst;
-                if (a.o_re) a.o_re[od] = pr;
-                if (a.o_im) a.o_im[od] = pi;
-                if (GRAD) {
-                    a.o_dr_re[od] = dr_r;
-                    a.o_dr_im[od] = dr_i;
-                    a.o_dz_re[od] = dz_r;
-                    a.o_dz_im[od] = dz_i;
-                }
+        } else {
+            const size_t od = (size_t)n * a.nfield + dst;
+            if (a.o_re) a.o_re[od] = add ? a.o_re[od] + pr : pr;
+            if (a.o_im) a.o_im[od] = add ? a.o_im[od] + pi : pi;
+            if (GRAD) {
+                a.o_dr_re[od] = add ? a.o_dr_re[od] + dr_r : dr_r;
+                a.o_dr_im[od] = add ? a.o_dr_im[od] + dr_i : dr_i;
+                a.o_dz_re[od] = add ? a.o_dz_re[od] + dz_r : dz_r;
+                a.o_dz_im[od] = add ? a.o_dz_im[od] + dz_i : dz_i;
             }
         }
+    }
+}
+
+// Local expansion (Eq. analysis:local) at the field points of the near-field units, the
+// L2P of Algorithm 1: value and gradient, written to the outputs before k_near_ws adds the
+// near sums.  One block of 4 warps per unit (<= 32 field points of one leaf): warp w takes
+// modes w, w + 4, ...; the leaf's coefficients of a mode (re and im) are staged in shared
+// memory by coalesced loads, and each lane runs the packed (re, im) Horner scheme at its
+// point.  AFMM_FP64: FP32-pair locals and arithmetic; MIXED: FP32.
+constexpr int L2P_WARPS = 4;
+constexpr int L2P_MAXC = (AFMM_MAX_ORDER + 1) * (AFMM_MAX_ORDER + 2) / 2;
+
+template <bool GRAD, bool MIX>
+__global__ void __launch_bounds__(L2P_WARPS * 32) k_l2p(const NearArgs a)
+{
+    __shared__ float4 sF[L2P_WARPS][L2P_MAXC];  // (re.hi, im.hi, re.lo, im.lo), or (re, im, -, -)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const NearUnit un = a.units[blockIdx.x];
+    const int box = un.box, nm = a.nmodes, M = a.M, nc = a.ncoef;
+    const int64_t t = un.begin + lane;
+    const bool active = t < un.end;
+    const int64_t tc = active ? t : un.begin;
+    const double rt = a.fr[tc], zt = a.fz[tc];
+    const uint32_t kk = a.leaf_key[box];
+    const double cr = a.r0 + ((double)morton_ir(kk) + 0.5) * a.h, cz = a.z0 + ((double)morton_iz(kk) + 0.5) * a.h;
+    const double ud = (rt - cr) / a.h, vd = (zt - cz) / a.h, ih = 1.0 / a.h;
+    const int64_t dst = a.out_perm ? a.out_perm[tc] : tc;
+    float4 *F = sF[warp];
+    for (int n = warp; n < nm; n += L2P_WARPS) {
+        const size_t off = ((size_t)box * nm + n) * nc;
+        for (int c = lane; c < nc; c += 32) {
+            if (MIX)
+                F[c] = make_float4(a.loc32_re[off + c], a.loc32_im[off + c], 0.f, 0.f);
+            else {
+                const float2 r = a.locdf_re[off + c], i = a.locdf_im[off + c];
+                F[c] = make_float4(r.x, i.x, r.y, i.y);
+            }
+        }
+        __syncwarp();
+        double pr, pi, dr_r = 0, dr_i = 0, dz_r = 0, dz_i = 0;
+        if (MIX) {
+            const float2 U = make_float2((float)ud, (float)ud), V = make_float2((float)vd, (float)vd);
+            const float2 Z = make_float2(0.f, 0.f);
+            float2 pu = Z, pdu = Z, pdv = Z;
+            for (int k = M; k >= 0; --k) {
+                const int base = k * (M + 1) - k * (k - 1) / 2;
+                float2 pk = Z, pkd = Z;
+                for (int l = M - k; l >= 0; --l) {
+                    if (GRAD) pkd = ffma2(pkd, V, pk);
+                    const float4 f = F[base + l];
+                    pk = ffma2(pk, V, make_float2(f.x, f.y));
+                }
+                if (GRAD) {
+                    pdu = ffma2(pdu, U, pu);
+                    pdv = ffma2(pdv, U, pkd);
+                }
+                pu = ffma2(pu, U, pk);
+            }
+            pr = pu.x;
+            pi = pu.y;
+            if (GRAD) {
+                dr_r = pdu.x * ih;
+                dr_i = pdu.y * ih;
+                dz_r = pdv.x * ih;
+                dz_i = pdv.y * ih;
+            }
+        } else {
+            const df2 U = df2_bcast(df_from_double(ud)), V = df2_bcast(df_from_double(vd));
+            const df2 Z = df2_make(make_float2(0.f, 0.f), make_float2(0.f, 0.f));
+            df2 pu = Z, pdu = Z, pdv = Z;
+            for (int k = M; k >= 0; --k) {
+                const int base = k * (M + 1) - k * (k - 1) / 2;
+                df2 pk = Z, pkd = Z;
+                for (int l = M - k; l >= 0; --l) {
+                    if (GRAD) pkd = df2_add(df2_mul(pkd, V), pk);
+                    pk = df2_add(df2_mul(pk, V), df2_from4(F[base + l]));
+                }
+                if (GRAD) {
+                    pdu = df2_add(df2_mul(pdu, U), pu);
+                    pdv = df2_add(df2_mul(pdv, U), pkd);
+                }
+                pu = df2_add(df2_mul(pu, U), pk);
+            }
+            pr = df_to_double(df2_x(pu));
+            pi = df_to_double(df2_y(pu));
+            if (GRAD) {
+                dr_r = df_to_double(df2_x(pdu)) * ih;
+                dr_i = df_to_double(df2_y(pdu)) * ih;
+                dz_r = df_to_double(df2_x(pdv)) * ih;
+                dz_i = df_to_double(df2_y(pdv)) * ih;
+            }
+        }
+        if (active) {
+            const size_t od = (size_t)n * a.nfield + dst;
+            if (a.o_re) a.o_re[od] = pr;
+            if (a.o_im) a.o_im[od] = pi;
+            if (GRAD) {
+                a.o_dr_re[od] = dr_r;
+                a.o_dr_im[od] = dr_i;
+                a.o_dz_re[od] = dz_r;
+                a.o_dz_im[od] = dz_i;
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -1052,7 +1071,10 @@ static size_t nws_slot_bytes(int nm, int grad)
     const int npair = (Nq + 2) / 2, npp = grad ? 5 : 1;
     return (size_t)(npair + npp) * 32 * 16 + 32 * sizeof(int);
 }
-static size_t nws_table_bytes() { return sizeof(float2) * AFMM_REC_TAB + sizeof(float4) * (AFMM_MAX_MODES / 2 + 1); }
+static size_t nws_table_bytes()
+{
+    return sizeof(float2) * AFMM_REC_TAB + sizeof(float4) * 2 * (AFMM_MAX_MODES / 2 + 1);
+}
 
 // Modes per consumer warp: the smallest even MPER with at most 11 consumers (>= 5 producers)
 static int nws_mper(int nm)
@@ -1344,6 +1366,20 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
         }
         a.df_fwd_switch = (float)p->df_fwd_switch;
         a.err = p->err_dev;
+        const bool loc = mix ? a.loc32_re != nullptr : a.locdf_re != nullptr;
+        if (loc) {  // the leaf's local expansion first; the near kernel adds its sums
+            if (grad && mix)
+                k_l2p<true, true><<<(unsigned)a.nunits, L2P_WARPS * 32, 0, p->stream>>>(a);
+            else if (grad)
+                k_l2p<true, false><<<(unsigned)a.nunits, L2P_WARPS * 32, 0, p->stream>>>(a);
+            else if (mix)
+                k_l2p<false, true><<<(unsigned)a.nunits, L2P_WARPS * 32, 0, p->stream>>>(a);
+            else
+                k_l2p<false, false><<<(unsigned)a.nunits, L2P_WARPS * 32, 0, p->stream>>>(a);
+            AFMM_LAUNCH_CHECK();
+            a.accumulate = 1;
+        }
+        if (p->timing) cudaEventRecord(p->ev[AFMM_EV_L2P], p->stream);
         // at most 11 consumer warps x 8 modes per launch; larger mode counts take several
         // launches over mode ranges (each recomputes the pair sequences)
         for (int lo = 0; lo < p->nmodes; lo += NWS_MODES_PER_LAUNCH) {

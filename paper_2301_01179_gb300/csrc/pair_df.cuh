@@ -64,18 +64,21 @@ struct SeqSlot {
     }
 };
 
-// Writes y_n (n = 0..N) into the slot and returns the df factor s with G_n = s * c_n * y_n.
-// gam2: recursion constants gam_n as FP32 pairs (shared memory).
-__device__ __forceinline__ dfv pair_sequence_df(const PairDF &g, dfv inv2w, int N, float fwd_switch, float extra,
-                                                const float2 *__restrict__ gam2, const SeqSlot ys)
+// Regime of the sweep (Appendix A): forward iff 2 N acosh(chi) <= fwd_switch (and
+// acosh(chi) <= 0.96), else Miller's backward sweep.
+__device__ __forceinline__ bool pair_regime(float t, int N, float fwd_switch, float &af)
 {
-    float tf = g.t;
-    float af = log1pf(tf + sqrtf(tf * (tf + 2.0f)));  // acosh(chi)
-    int Nr = N < 1 ? 1 : N;
-    bool fwd = (2.0f * (float)Nr * af <= fwd_switch) && (af <= 0.96f);
-    // AGM of (rho_+, rho_-) with the half-difference sum for G^(1)
+    af = log1pf(t + sqrtf(t * (t + 2.0f)));  // acosh(chi)
+    const int Nr = N < 1 ? 1 : N;
+    return (2.0f * (float)Nr * af <= fwd_switch) && (af <= 0.96f);
+}
+
+// AGM of (rho_+, rho_-) with the half-difference sum csum for G^(1) (Eq. gfunc:Q0 and the
+// start values of Appendix A); returns the mean a: G^(0) = 1 / (2 a)
+__device__ __forceinline__ dfv pair_agm_df(const PairDF &g, dfv &csum)
+{
     dfv a = df_sqrt(g.rp2), b = df_sqrt(g.rm2);
-    dfv csum = df_make(0.f, 0.f);
+    csum = df_make(0.f, 0.f);
     float w = 1.f;
     for (int it = 0; it < 40; ++it) {
         dfv c = df_scale2(df_sub(a, b), 0.5f);
@@ -86,7 +89,41 @@ __device__ __forceinline__ dfv pair_sequence_df(const PairDF &g, dfv inv2w, int 
         a = an;
         if (c.hi <= 1e-7f * a.hi) break;
     }
-    dfv G0 = df_div(df_make(0.5f, 0.f), a);
+    return a;
+}
+
+// The sweep of the scaled recursion (Eq. gfunc:recursion) from the start values G0 and
+// csum: writes y_n (n = 0..N) into the slot and returns the df factor s with
+// G_n = s * c_n * y_n.  gam2: recursion constants gam_n as FP32 pairs, gam4 the same by
+// mode pair (shared memory).
+__device__ __forceinline__ dfv pair_sweep_df(dfv chi, float zero, dfv inv2w, int N, bool fwd, float af, float extra,
+                                             dfv G0, dfv csum, const float2 *__restrict__ gam2,
+                                             const float4 *__restrict__ gam4, const SeqSlot ys)
+{
+    if (__all_sync(0xffffffffu, fwd)) {
+        // the whole warp sweeps forward: two steps per iteration, gam_n chi and gam_{n+1} chi
+        // as one packed product, one 16-byte store per mode pair (the operations and their
+        // order are those of the general sweep below)
+        float4 *yp = reinterpret_cast<float4 *>(ys.y);
+        dfv ym2 = G0, ym1 = df_mul(df_mul(G0, csum), inv2w);
+        if (N == 0) ym1 = df_make(0.f, 0.f);  // pad of pair 0
+        yp[0] = make_float4(ym2.hi, ym1.hi, ym2.lo, ym1.lo);
+        const df2 CHI = df2_bcast(chi);
+        int n = 2;
+        for (; n + 1 <= N; n += 2) {
+            const df2 GC = df2_mul(df2_from4(gam4[n >> 1]), CHI);
+            const dfv ya = df_sub(df_mul(df2_x(GC), ym1), ym2);
+            const dfv yb = df_sub(df_mul(df2_y(GC), ya), ym1);
+            yp[(n >> 1) * 32] = make_float4(ya.hi, yb.hi, ya.lo, yb.lo);
+            ym2 = ya;
+            ym1 = yb;
+        }
+        if (n == N) {  // N even: the last mode alone, with the pad
+            const dfv ya = df_sub(df_mul(df_mul(df_make(gam2[n].x, gam2[n].y), chi), ym1), ym2);
+            yp[(n >> 1) * 32] = make_float4(ya.hi, 0.f, ya.lo, 0.f);
+        }
+        return df_make(zero, 0.f);
+    }
     int L = N + 2;
     if (!fwd) {
         float lf = ceilf(extra / fmaxf(af, 1e-6f));
@@ -111,7 +148,7 @@ __device__ __forceinline__ dfv pair_sequence_df(const PairDF &g, dfv inv2w, int 
         if (s < steps) {
             int n = fwd ? s + 2 : L - s;
             float2 gm = gam2[n];
-            dfv yn = df_sub(df_mul(df_mul(df_make(gm.x, gm.y), g.chi), y1), y0);
+            dfv yn = df_sub(df_mul(df_mul(df_make(gm.x, gm.y), chi), y1), y0);
             y0 = y1;
             y1 = yn;
             int idx = fwd ? n : n - 2;
@@ -125,9 +162,9 @@ __device__ __forceinline__ dfv pair_sequence_df(const PairDF &g, dfv inv2w, int 
             }
         }
     }
-    if (fwd) return df_make(g.zero, 0.f);
+    if (fwd) return df_make(zero, 0.f);
     dfv sc = df_div(G0, ys.get(0));
-    return df_make(sc.hi * g.zero, sc.lo * g.zero);
+    return df_make(sc.hi * zero, sc.lo * zero);
 }
 
 }  // namespace afmm
