@@ -133,12 +133,13 @@ __device__ __forceinline__ float f64_to_f32_bits(double v, double &back)
 
 __device__ __forceinline__ dfv df_from_double(double v)
 {
-    if (v == 0.0) return df_make(0.f, 0.f);
+    // zero tests on the bit patterns (integer pipe, not the FP64 pipe)
+    if ((__double_as_longlong(v) << 1) == 0) return df_make(0.f, 0.f);
     double hb;
     float h = f64_to_f32_bits(v, hb);
     double r = v - hb;  // exact
     double lb;
-    float l = r == 0.0 ? 0.f : f64_to_f32_bits(r, lb);
+    float l = (__double_as_longlong(r) << 1) == 0 ? 0.f : f64_to_f32_bits(r, lb);
     return df_make(h, l);
 }
 
@@ -231,6 +232,36 @@ __device__ __forceinline__ void df2_acc(float2 &S, float2 &E, df2 a, df2 b)
     const float2 s = fadd2(S, p);
     const float2 v = fsub2(s, S);
     const float2 err = fadd2(fsub2(S, fsub2(s, v)), fsub2(p, v));
+    E = fadd2(E, fadd2(err, pe));
+    S = s;
+}
+
+// Negation-free forms.  np = -(a.hi * b.hi), formed by the caller from a negated operand
+// (-a.hi * b.hi or a.hi * -b.hi, exact sign change under round-to-nearest).  df2_mul_np
+// returns a * b as df2_mul does (p + e and its error, with s - p computed as s + np) and
+// also -hi of the result, for products that feed df2_acc_np.
+__device__ __forceinline__ df2 df2_mul_np(df2 a, df2 b, float2 np, float2 &nhi)
+{
+    float2 e = ffma2(a.hi, b.hi, np);  // a.hi b.hi - p, exact
+    e = ffma2(a.hi, b.lo, e);
+    e = ffma2(a.lo, b.hi, e);
+    df2 r;
+    r.hi = fsub2(e, np);               // p + e
+    r.lo = fsub2(e, fadd2(r.hi, np));  // e - (s - p)
+    nhi = fsub2(np, e);                // -(p + e)
+    return r;
+}
+
+// df2_acc(S, E, a, b) given nbh = -b.hi: the same roundings, no negation
+__device__ __forceinline__ void df2_acc_n(float2 &S, float2 &E, df2 a, df2 b, float2 nbh)
+{
+    const float2 np = fmul2(a.hi, nbh);  // -p
+    float2 pe = ffma2(a.hi, b.hi, np);
+    pe = ffma2(a.hi, b.lo, pe);
+    pe = ffma2(a.lo, b.hi, pe);
+    const float2 s = fsub2(S, np);  // S + p
+    const float2 v = fsub2(s, S);
+    const float2 err = fsub2(fsub2(S, fsub2(s, v)), fadd2(np, v));  // (S - (s - v)) + (p - v)
     E = fadd2(E, fadd2(err, pe));
     S = s;
 }

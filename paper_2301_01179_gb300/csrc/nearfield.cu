@@ -23,6 +23,7 @@ struct NearArgs {
     int64_t nfield;
     // source role (sorted), amplitudes [nmodes][nsrc] pre-multiplied by c_n
     const double *sr, *sz, *q_re, *q_im;
+    const float2 *sr_df;  // sources' r as FP32 pairs (FP32-pair kernel)
     int64_t nsrc;
     int nmodes, N;
     // work
@@ -791,7 +792,8 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
             while (rg < 8 && rcum[rg + 1] <= kk) ++rg;
             const int64_t s = rb[rg] + (kk - rcum[rg]);
             const double r1 = a.sr[s], z1 = a.sz[s];
-            const dfv inv2w = df_div(inv2r, df_from_double(r1));
+            const float2 r1d = a.sr_df[s];
+            const dfv inv2w = df_div(inv2r, df_make(r1d.x, r1d.y));
             PairDF g;
             pair_geom_df(rt, zt, r1, z1, inv2w, active && valid, g);
             SeqSlot ys;
@@ -824,6 +826,7 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
     const int n0 = a.mode_lo + warp * MPER;  // mode_lo is even
     const int m0 = n0 / 2;
     const int nhi = a.mode_hi;
+    const int mlast = (nm - 1) / 2;  // last mode pair
     float2 aS[NC][NP], aE[NC][NP];  // .x mode 2m, .y mode 2m + 1
 #pragma unroll
     for (int c = 0; c < NC; ++c)
@@ -852,8 +855,10 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
             const float2 SCf = SC.hi, GXf = GX.hi, QFf = QF.hi;
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
-                const int m = m0 + j;
-                if (2 * m < nhi) {
+                // no branch per mode pair (the compiler interleaves the pairs' chains): a pair
+                // past the last mode reads the last pair and its sums are not written
+                const int m = 2 * (m0 + j) < nm ? m0 + j : mlast;
+                {
                     const df2 Y = df2_from4(y4[m * 32 + lane]);
                     const float2 QR = a.q32_re[(size_t)m * a.nsrc + s], QI = a.q32_im[(size_t)m * a.nsrc + s];
                     const float2 G = fmul2(SCf, Y.hi);
@@ -873,27 +878,38 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
                 }
             }
         } else {
+            // negated high words of the per-slot factors (the products below need no
+            // negation instructions: see df2_mul_np, df2_acc_n)
+            const float2 NEG = make_float2(-1.f, -1.f);
+            const float2 nSC = fmul2(SC.hi, NEG);
+            const float2 nAS = fmul2(AS.hi, NEG), nGX = fmul2(GX.hi, NEG), nQF = fmul2(QF.hi, NEG);
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
-                const int m = m0 + j;
-                if (2 * m < nhi) {
+                const int m = 2 * (m0 + j) < nm ? m0 + j : mlast;  // as above
+                {
                     const df2 Y = df2_from4(y4[m * 32 + lane]);
                     const df2 QR = df2_from4(a.qdf_re[(size_t)m * a.nsrc + s]);
                     const df2 QI = df2_from4(a.qdf_im[(size_t)m * a.nsrc + s]);
-                    const df2 G = df2_mul(SC, Y);
-                    df2_acc(aS[0][j], aE[0][j], QR, G);
-                    df2_acc(aS[1][j], aE[1][j], QI, G);
+                    float2 nG;
+                    const df2 G = df2_mul_np(SC, Y, fmul2(nSC, Y.hi), nG);
+                    df2_acc_n(aS[0][j], aE[0][j], QR, G, nG);
+                    df2_acc_n(aS[1][j], aE[1][j], QI, G, nG);
                     if (GRAD) {
                         // w_n = y_n A + rho_n y_{n-1} B, the derivative recursion's weight
                         const df2 YP = df2_pack(yprev, df2_x(Y));
                         yprev = df2_y(Y);
-                        const df2 T = df2_mul(df2_from4(rho4[m]), YP);
-                        const df2 WT = df2_add(df2_mul(Y, AS), df2_mul(T, BS));
-                        const df2 XW = df2_mul(GX, WT), QW = df2_mul(QF, WT);
-                        df2_acc(aS[2 % NC][j], aE[2 % NC][j], QR, QW);
-                        df2_acc(aS[3 % NC][j], aE[3 % NC][j], QI, QW);
-                        df2_acc(aS[4 % NC][j], aE[4 % NC][j], QR, XW);
-                        df2_acc(aS[5 % NC][j], aE[5 % NC][j], QI, XW);
+                        float2 nT, nU, nV, nXW, nQW;
+                        const df2 R = df2_from4(rho4[m]);
+                        const df2 T = df2_mul_np(R, YP, fmul2(fmul2(R.hi, NEG), YP.hi), nT);
+                        const df2 U = df2_mul_np(Y, AS, fmul2(Y.hi, nAS), nU);
+                        const df2 V = df2_mul_np(T, BS, fmul2(nT, BS.hi), nV);
+                        const df2 WT = df2_add(U, V);
+                        const df2 XW = df2_mul_np(GX, WT, fmul2(nGX, WT.hi), nXW);
+                        const df2 QW = df2_mul_np(QF, WT, fmul2(nQF, WT.hi), nQW);
+                        df2_acc_n(aS[2 % NC][j], aE[2 % NC][j], QR, QW, nQW);
+                        df2_acc_n(aS[3 % NC][j], aE[3 % NC][j], QI, QW, nQW);
+                        df2_acc_n(aS[4 % NC][j], aE[4 % NC][j], QR, XW, nXW);
+                        df2_acc_n(aS[5 % NC][j], aE[5 % NC][j], QI, XW, nXW);
                     }
                 }
             }
@@ -1289,6 +1305,7 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
     a.nfield = fw ? p->nf : p->ns;
     a.sr = fw ? p->s_r : p->t_r;
     a.sz = fw ? p->s_z : p->t_z;
+    a.sr_df = fw ? p->s_rdf : p->t_rdf;
     a.nsrc = fw ? p->ns : p->nf;
     const bool mix = p->precision == AFMM_MIXED;
     a.q_re = p->qs_re;
