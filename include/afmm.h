@@ -70,7 +70,11 @@ typedef struct {
                            (0: default 9 for N <= 16, 9 - 1.5 log2(N/16) above, which keeps
                            the forward sweep's error growth below ~2e-12).  The paper's
                            fixed switch is chi < 1.008 (Appendix A). */
-    int miller_extra;   /* Miller start L = N + ceil(miller_extra / acosh(chi)) + 2 (0: 15) */
+    int miller_extra;   /* Miller start (0: 15).  AFMM_FP64_NATIVE: L = N + ceil(miller_extra /
+                           acosh(chi)) + 2.  FP32-pair kernels (AFMM_FP64, AFMM_MIXED):
+                           L = N + 2 + max(0, ceil(miller_extra / acosh(chi) - N / 2)), which
+                           keeps the error of every mode below e^(-2 miller_extra) times the
+                           pair's G^(0) */
     int s2l_engine;     /* AFMM_FP64 and AFMM_MIXED. 0: S2L (Eq. analysis:s2l) on the tcgen05
                            tensor cores when order <= 12, else on CUDA cores; 1: always on
                            CUDA cores (FP32 pairs for AFMM_FP64, FP32 for AFMM_MIXED) */

@@ -96,14 +96,21 @@ __device__ __forceinline__ dfv pair_agm_df(const PairDF &g, dfv &csum)
 // csum: writes y_n (n = 0..N) into the slot and returns the df factor s with
 // G_n = s * c_n * y_n.  gam2: recursion constants gam_n as FP32 pairs, gam4 the same by
 // mode pair (shared memory).
+//
+// Forward lanes: two steps per iteration, gam_n chi and gam_{n+1} chi as one packed
+// product, one 16-byte store per mode pair; every lane of a warp that has a forward lane
+// runs it (a backward lane's values, possibly overflowing, are overwritten by its own
+// sweep).  Backward lanes (Miller): from y_L = 0, y_{L-1} = 2^-100 down to y_0, rescaled
+// exactly by 2^-100 whenever |y| passes 2^100, normalised by G0 / y_0.  The start is
+// L = max(N + 2, N / 2 + ceil(extra / acosh chi) + 2): the relative error of y_n,
+// e^{-2 a (L - n)} (a = acosh chi), is then below e^{-2 extra} measured against the
+// pair's G^(0), since |G^(n) / G^(0)| ~ e^{-n a}.
 __device__ __forceinline__ dfv pair_sweep_df(dfv chi, float zero, dfv inv2w, int N, bool fwd, float af, float extra,
                                              dfv G0, dfv csum, const float2 *__restrict__ gam2,
                                              const float4 *__restrict__ gam4, const SeqSlot ys)
 {
-    if (__all_sync(0xffffffffu, fwd)) {
-        // the whole warp sweeps forward: two steps per iteration, gam_n chi and gam_{n+1} chi
-        // as one packed product, one 16-byte store per mode pair (the operations and their
-        // order are those of the general sweep below)
+    const bool allf = __all_sync(0xffffffffu, fwd);
+    if (allf || __any_sync(0xffffffffu, fwd)) {
         float4 *yp = reinterpret_cast<float4 *>(ys.y);
         dfv ym2 = G0, ym1 = df_mul(df_mul(G0, csum), inv2w);
         if (N == 0) ym1 = df_make(0.f, 0.f);  // pad of pair 0
@@ -122,47 +129,30 @@ __device__ __forceinline__ dfv pair_sweep_df(dfv chi, float zero, dfv inv2w, int
             const dfv ya = df_sub(df_mul(df_mul(df_make(gam2[n].x, gam2[n].y), chi), ym1), ym2);
             yp[(n >> 1) * 32] = make_float4(ya.hi, 0.f, ya.lo, 0.f);
         }
-        return df_make(zero, 0.f);
-    }
-    int L = N + 2;
-    if (!fwd) {
-        float lf = ceilf(extra / fmaxf(af, 1e-6f));
-        int ext = lf > (float)AFMM_REC_TAB ? AFMM_REC_TAB : (int)lf;
-        L = N + ext + 2;
-        if (L > AFMM_REC_TAB - 1) L = AFMM_REC_TAB - 1;
-    }
-    dfv y0, y1;
-    if (fwd) {
-        y0 = G0;
-        y1 = df_mul(df_mul(G0, csum), inv2w);
-        ys.put(0, y0);
-        if (N >= 1) ys.put(1, y1);
-    } else {
-        y0 = df_make(0.f, 0.f);           // y_L
-        y1 = df_make(7.8886091e-31f, 0.f); // y_{L-1} = 2^-100
-    }
-    int steps = fwd ? N - 1 : L - 1;
-    int smax = steps;
-    for (int o = 16; o > 0; o >>= 1) smax = max(smax, __shfl_xor_sync(0xffffffffu, smax, o));
-    for (int s = 0; s < smax; ++s) {
-        if (s < steps) {
-            int n = fwd ? s + 2 : L - s;
-            float2 gm = gam2[n];
-            dfv yn = df_sub(df_mul(df_mul(df_make(gm.x, gm.y), chi), y1), y0);
-            y0 = y1;
-            y1 = yn;
-            int idx = fwd ? n : n - 2;
-            if (idx <= N) ys.put(idx, yn);
-            if (!fwd && fabsf(yn.hi) > 1.2676506e30f) {  // > 2^100: rescale by 2^-100 (exact)
-                const float s100 = 7.8886091e-31f;
-                y0 = df_scale2(y0, s100);
-                y1 = df_scale2(y1, s100);
-                for (int m = idx; m <= N; ++m)
-                    if (m >= 0) ys.put(m, df_scale2(ys.get(m), s100));
-            }
-        }
+        if (allf) return df_make(zero, 0.f);
     }
     if (fwd) return df_make(zero, 0.f);
+    // backward lane
+    const float lf = ceilf(extra / fmaxf(af, 1e-6f) - 0.5f * (float)N);  // L - N - 2 >= extra / a - N / 2
+    const int ext = lf < 0.f ? 0 : (lf > (float)AFMM_REC_TAB ? AFMM_REC_TAB : (int)lf);
+    int L = N + ext + 2;
+    if (L > AFMM_REC_TAB - 1) L = AFMM_REC_TAB - 1;
+    dfv y0 = df_make(0.f, 0.f);            // y_L
+    dfv y1 = df_make(7.8886091e-31f, 0.f); // y_{L-1} = 2^-100
+    for (int n = L; n >= 2; --n) {
+        const float2 gm = gam2[n];
+        const dfv yn = df_sub(df_mul(df_mul(df_make(gm.x, gm.y), chi), y1), y0);  // y_{n-2}
+        y0 = y1;
+        y1 = yn;
+        const int idx = n - 2;
+        if (idx <= N) ys.put(idx, yn);
+        if (fabsf(yn.hi) > 1.2676506e30f) {  // > 2^100: rescale by 2^-100 (exact)
+            const float s100 = 7.8886091e-31f;
+            y0 = df_scale2(y0, s100);
+            y1 = df_scale2(y1, s100);
+            for (int m = idx; m <= N; ++m) ys.put(m, df_scale2(ys.get(m), s100));
+        }
+    }
     dfv sc = df_div(G0, ys.get(0));
     return df_make(sc.hi * zero, sc.lo * zero);
 }
