@@ -39,6 +39,7 @@ struct NearArgs {
     const float4 *qdf_re, *qdf_im;
     const float2 *locdf_re, *locdf_im;
     float df_fwd_switch;
+    float df_tlim;  // forward iff chi - 1 <= df_tlim (the switch on t = chi - 1)
     // MIXED precision: FP32 amplitudes interleaved by mode pair, [n / 2][nsrc] float2
     // (q_2m, q_2m+1), FP32 local expansions, compensated FP32 sums
     const float2 *q32_re, *q32_im;
@@ -638,6 +639,7 @@ static size_t near2_smem(int nm, int grad)
 constexpr int NWS_THREADS = 512;                             // 16 warps per block
 constexpr int NWS_BMAX = 24;                                 // ring slots (upper bound)
 constexpr int NWS_MODES_PER_LAUNCH = 88;                     // 11 consumer warps x 8 modes
+constexpr int NWS_SRC_STAGE = 1024;                          // unit source lists staged in shared memory
 constexpr unsigned long long NWS_WAIT_NS = 1000000000ull;    // a hand-over wait gives up after 1 s
 
 // Lane 0 waits on the barrier (suspended in hardware between polls; bounded by the timer);
@@ -700,6 +702,7 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
     __shared__ uint64_t s_full[NWS_BMAX], s_empty[NWS_BMAX];
     __shared__ int rb[10], rcum[10];
     __shared__ int s_next;
+    __shared__ int s_src[NWS_SRC_STAGE];
     __shared__ volatile int s_abort;
     for (int i = threadIdx.x; i < AFMM_REC_TAB; i += blockDim.x) {
         dfv g = df_from_double(tab.gam[i]);
@@ -771,6 +774,14 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
     __syncthreads();
     const int total = rcum[9];
     const int nslots = (total + S - 1) / S;
+    if (total <= NWS_SRC_STAGE) {  // the unit's source list, in slot order
+        for (int i = threadIdx.x; i < total; i += blockDim.x) {
+            int rg = 0;
+            while (rg < 8 && rcum[rg + 1] <= i) ++rg;
+            s_src[i] = rb[rg] + (i - rcum[rg]);
+        }
+        __syncthreads();
+    }
 
     if (warp >= ncons) {
         // ---------------- producer ----------------
@@ -788,9 +799,14 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
             int kk = k * S + slice;
             const bool valid = kk < total;
             if (!valid) kk = total - 1;
-            int rg = 0;
-            while (rg < 8 && rcum[rg + 1] <= kk) ++rg;
-            const int64_t s = rb[rg] + (kk - rcum[rg]);
+            int64_t s;
+            if (total <= NWS_SRC_STAGE) {
+                s = s_src[kk];
+            } else {
+                int rg = 0;
+                while (rg < 8 && rcum[rg + 1] <= kk) ++rg;
+                s = rb[rg] + (kk - rcum[rg]);
+            }
             const double r1 = a.sr[s], z1 = a.sz[s];
             const float2 r1d = a.sr_df[s];
             const dfv inv2w = df_div(inv2r, df_make(r1d.x, r1d.y));
@@ -799,11 +815,10 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
             SeqSlot ys;
             ys.y = reinterpret_cast<float *>(y4 + lane);
             if ((Nq & 1) == 0) ys.put(Nq + 1, df_make(0.f, 0.f));  // pad of the last mode pair
-            float af;
-            const bool fwd = pair_regime(g.t, Nq, a.df_fwd_switch, af);
+            const bool fwd = pair_forward(g.t, a.df_tlim);
             dfv csum;
             const dfv G0 = df_div(df_make(0.5f, 0.f), pair_agm_df(g, csum));
-            const dfv sc = pair_sweep_df(g.chi, g.zero, inv2w, Nq, fwd, af, extra, G0, csum, gam2, gam4, ys);
+            const dfv sc = pair_sweep_df(g.chi, g.t, g.zero, inv2w, Nq, fwd, extra, G0, csum, gam2, gam4, ys);
             reinterpret_cast<int *>(p4 + NPP * 32)[lane] = (int)s;
             p4[lane] = bcast4(sc);
             if (GRAD) {
@@ -1382,6 +1397,7 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
             }
         }
         a.df_fwd_switch = (float)p->df_fwd_switch;
+        a.df_tlim = (float)fmin(cosh(p->df_fwd_switch / (2.0 * (p->N < 1 ? 1 : p->N))), cosh(0.96)) - 1.0f;
         a.err = p->err_dev;
         const bool loc = mix ? a.loc32_re != nullptr : a.locdf_re != nullptr;
         if (loc) {  // the leaf's local expansion first; the near kernel adds its sums

@@ -66,12 +66,11 @@ struct SeqSlot {
 
 // Regime of the sweep (Appendix A): forward iff 2 N acosh(chi) <= fwd_switch (and
 // acosh(chi) <= 0.96), else Miller's backward sweep.
-__device__ __forceinline__ bool pair_regime(float t, int N, float fwd_switch, float &af)
-{
-    af = log1pf(t + sqrtf(t * (t + 2.0f)));  // acosh(chi)
-    const int Nr = N < 1 ? 1 : N;
-    return (2.0f * (float)Nr * af <= fwd_switch) && (af <= 0.96f);
-}
+__device__ __forceinline__ float acosh_chi(float t) { return log1pf(t + sqrtf(t * (t + 2.0f))); }  // t = chi - 1
+
+// the same test on t = chi - 1 against tlim = min(cosh(fwd_switch / (2 max(N, 1))), cosh(0.96)) - 1
+// (host-side), without the logarithm
+__device__ __forceinline__ bool pair_forward(float t, float tlim) { return t <= tlim; }
 
 // AGM of (rho_+, rho_-) with the half-difference sum csum for G^(1) (Eq. gfunc:Q0 and the
 // start values of Appendix A); returns the mean a: G^(0) = 1 / (2 a)
@@ -105,7 +104,7 @@ __device__ __forceinline__ dfv pair_agm_df(const PairDF &g, dfv &csum)
 // L = max(N + 2, N / 2 + ceil(extra / acosh chi) + 2): the relative error of y_n,
 // e^{-2 a (L - n)} (a = acosh chi), is then below e^{-2 extra} measured against the
 // pair's G^(0), since |G^(n) / G^(0)| ~ e^{-n a}.
-__device__ __forceinline__ dfv pair_sweep_df(dfv chi, float zero, dfv inv2w, int N, bool fwd, float af, float extra,
+__device__ __forceinline__ dfv pair_sweep_df(dfv chi, float t, float zero, dfv inv2w, int N, bool fwd, float extra,
                                              dfv G0, dfv csum, const float2 *__restrict__ gam2,
                                              const float4 *__restrict__ gam4, const SeqSlot ys)
 {
@@ -133,6 +132,7 @@ __device__ __forceinline__ dfv pair_sweep_df(dfv chi, float zero, dfv inv2w, int
     }
     if (fwd) return df_make(zero, 0.f);
     // backward lane
+    const float af = acosh_chi(t);
     const float lf = ceilf(extra / fmaxf(af, 1e-6f) - 0.5f * (float)N);  // L - N - 2 >= extra / a - N / 2
     const int ext = lf < 0.f ? 0 : (lf > (float)AFMM_REC_TAB ? AFMM_REC_TAB : (int)lf);
     int L = N + ext + 2;
