@@ -101,3 +101,34 @@ def test_direct_is_deterministic():
     b = to_np(*pl.direct(q_re, q_im))
     np.testing.assert_array_equal(a[0], b[0])
     np.testing.assert_array_equal(a[1], b[1])
+
+
+@pytest.mark.parametrize("n_modes", [89, 129])
+def test_direct_mode_ranges_match_oracle(n_modes):
+    """More modes than one launch of the FP32-pair near-field kernel holds (11 consumer warps
+    x 8 modes): the kernel runs over mode ranges, each recomputing the pair sequences; the
+    last range is short (89) or the highest order the plans accept (129).  Both sweeps
+    (forward and Miller) occur at these orders."""
+    w = W.make("cfg1", ns=400, nf=300, n_modes=n_modes)
+    pl = _plan(w)
+    q_re, q_im = to_dev(w["q_re"], w["q_im"])
+    g = to_np(*pl.direct_grad(q_re, q_im))
+    D = oracle.direct(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], w["q_re"], w["q_im"], grad=True)
+    for c in range(0, 6, 2):
+        e = eps_modes(g[c], g[c + 1], D[c], D[c + 1])
+        assert e.max() < TOL, (c, e.max())
+
+
+@pytest.mark.parametrize("nf", [1, 5, 16, 17, 33])
+def test_fmm_near_lane_packing_matches_oracle_fmm(nf):
+    """Near-field units of 1..33 field points: the kernel packs 32 / 2^ceil(log2 c) sources
+    into each slot for small units and sums the lane groups at the end."""
+    w = W.make("cfg1", ns=2000, nf=nf, n_modes=6)
+    pl = _plan(w, order=4, depth=3)
+    q_re, q_im = to_dev(w["q_re"], w["q_im"])
+    g = to_np(*pl.grad(q_re, q_im))
+    _, geom = oracle.tree_setup(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], 1, depth_override=3)
+    F = oracle.fmm(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], w["q_re"], w["q_im"], 4, 3, geom, grad=True)
+    for c in range(0, 6, 2):
+        e = eps_modes(g[c], g[c + 1], F[c], F[c + 1])
+        assert e.max() < TOL, (c, e.max())
