@@ -1108,8 +1108,14 @@ static size_t nws_table_bytes()
 }
 
 // Modes per consumer warp: the smallest even MPER with at most 11 consumers (>= 5 producers)
-static int nws_mper(int nm)
+static int nws_mper(int nm, bool grad)
 {
+    if (!grad) {
+        // potential only: two accumulations per mode, light consumers; at most 6 consumer
+        // warps, so that 10 or more warps compute sequences
+        for (int mp = 4; mp <= 16; mp += 4)
+            if ((nm + mp - 1) / mp <= 6) return mp;
+    }
     for (int mp = 2; mp <= 8; mp += 2)
         if ((nm + mp - 1) / mp <= 11) return mp;
     return 0;
@@ -1139,7 +1145,12 @@ static afmm_status launch_near_ws_k(const NearArgs &a, const RecTab &tab, cudaSt
 template <bool GRAD, bool MIX>
 static afmm_status launch_near_ws(const NearArgs &a, const RecTab &tab, cudaStream_t st)
 {
-    switch (nws_mper(a.mode_hi - a.mode_lo)) {
+    const int mp = nws_mper(a.mode_hi - a.mode_lo, GRAD);
+    if constexpr (!GRAD) {
+        if (mp == 12) return launch_near_ws_k<GRAD, 12, MIX>(a, tab, st);
+        if (mp == 16) return launch_near_ws_k<GRAD, 16, MIX>(a, tab, st);
+    }
+    switch (mp) {
     case 2: return launch_near_ws_k<GRAD, 2, MIX>(a, tab, st);
     case 4: return launch_near_ws_k<GRAD, 4, MIX>(a, tab, st);
     case 6: return launch_near_ws_k<GRAD, 6, MIX>(a, tab, st);
