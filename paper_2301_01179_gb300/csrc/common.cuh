@@ -148,8 +148,8 @@ struct Level {
 
 // tensor-core S2L: factor tables and coefficient-index maps (host-built, passed by value)
 struct TcTables {
-    float2 rjl[14 * 14];      // 1 / (j! l!) as FP32 pairs, j, l <= 13
-    float jfact[14];          // j! (exact in FP32 up to 13!)
+    float2 rjl[16 * 16];      // 1 / (j! l!) as FP32 pairs, j, l <= 15
+    float2 jfact[16];         // j! as FP32 pairs (a single float up to 13!)
     int8_t ci[128], cj[128];  // coefficient index -> (first, second) exponent
 };
 

@@ -638,7 +638,6 @@ static size_t near2_smem(int nm, int grad)
 // ------------------------------------------------------------------------------------
 constexpr int NWS_THREADS = 512;                             // 16 warps per block
 constexpr int NWS_BMAX = 24;                                 // ring slots (upper bound)
-constexpr int NWS_MODES_PER_LAUNCH = 88;                     // 11 consumer warps x 8 modes
 constexpr int NWS_SRC_STAGE = 1024;                          // unit source lists staged in shared memory
 constexpr unsigned long long NWS_WAIT_NS = 1000000000ull;    // a hand-over wait gives up after 1 s
 
@@ -1115,11 +1114,17 @@ static int nws_mper(int nm, bool grad)
         // warps, so that 10 or more warps compute sequences
         for (int mp = 4; mp <= 16; mp += 4)
             if ((nm + mp - 1) / mp <= 6) return mp;
+        return 0;
     }
+    // with the gradient: at most 9 consumer warps, at least 7 producers (measured best on
+    // 33 modes: 9 x 4 against 11 x 3 or 6 x 6; on 65 modes 9 x 8 against 11 x 6)
     for (int mp = 2; mp <= 8; mp += 2)
-        if ((nm + mp - 1) / mp <= 11) return mp;
+        if ((nm + mp - 1) / mp <= 9) return mp;
     return 0;
 }
+
+// modes per launch: 9 x 8 with the gradient, 6 x 16 without
+static int nws_modes_per_launch(bool grad) { return grad ? 72 : 96; }
 
 template <bool GRAD, int MPER, bool MIX>
 static afmm_status launch_near_ws_k(const NearArgs &a, const RecTab &tab, cudaStream_t st)
@@ -1424,11 +1429,12 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
             a.accumulate = 1;
         }
         if (p->timing) cudaEventRecord(p->ev[AFMM_EV_L2P], p->stream);
-        // at most 11 consumer warps x 8 modes per launch; larger mode counts take several
-        // launches over mode ranges (each recomputes the pair sequences)
-        for (int lo = 0; lo < p->nmodes; lo += NWS_MODES_PER_LAUNCH) {
+        // larger mode counts than one launch's consumer warps hold take several launches
+        // over mode ranges (each recomputes the pair sequences)
+        const int per = nws_modes_per_launch(grad != 0);
+        for (int lo = 0; lo < p->nmodes; lo += per) {
             a.mode_lo = lo;
-            a.mode_hi = p->nmodes < lo + NWS_MODES_PER_LAUNCH ? p->nmodes : lo + NWS_MODES_PER_LAUNCH;
+            a.mode_hi = p->nmodes < lo + per ? p->nmodes : lo + per;
             if (grad && mix)
                 AFMM_TRY((launch_near_ws<true, true>(a, *p->rec, p->stream)));
             else if (grad)

@@ -200,7 +200,8 @@ __global__ void __launch_bounds__(256) k_slice_moments(const MT *__restrict__ mr
         const int ij = lane + 32 * t;
         v[t] = df_make(0.f, 0.f);
         if (ij < nc) {
-            v[t] = df_mulf(to_df(src[ij]), tt.jfact[tt.cj[ij]]);
+            const float2 jf = tt.jfact[tt.cj[ij]];
+            v[t] = df_mul(to_df(src[ij]), df_make(jf.x, jf.y));
             m = fmaxf(m, fabsf(v[t].hi));
         }
     }
@@ -250,14 +251,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
     extern __shared__ __align__(128) uint8_t smem[];
     uint8_t *sB = smem;                                       // [NS][KP rows][KP] bf16
     uint8_t *sA = smem + NS * BT;                             // [2][128 rows][KP] bf16
-    float2 *sE = reinterpret_cast<float2 *>(sA + 2 * AT);     // the slot's cube [(M+1)^2 (2M+1)]
+    // the slot's cube [(M+1)^2 (2M+1)]: FP32 pairs, or (128-wide tiles, 4 slices) the high
+    // words only, which keeps the block within shared memory
+    constexpr bool C32 = KP > 112;
+    static_assert(!C32 || NS == 4, "128-wide tiles with 4 digit slices only");
+    float2 *sE = reinterpret_cast<float2 *>(sA + 2 * AT);
+    float *sE32 = reinterpret_cast<float *>(sA + 2 * AT);
+    auto cube = [&](int i) -> float2 {
+        if constexpr (C32)
+            return make_float2(sE32[i], 0.f);
+        else
+            return sE[i];
+    };
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tbase;
     __shared__ int bx[64];
     __shared__ long long rbase[128];        // element offset of each A row's slices, or -1
     __shared__ int colE[KP];
     __shared__ int offK[2][KP], offI[2][KP];  // cube offsets (outward, inward) of kl and ij
-    __shared__ float2 rj[14];               // 1 / j! as FP32 pairs
+    __shared__ float2 rj[16];               // 1 / j! as FP32 pairs
     __shared__ int wait_ok;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -282,7 +294,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
         offI[0][t] = po << 4 | (t < nc ? tp.cj[t] : 0);
         offI[1][t] = pi << 4 | (t < nc ? tp.cj[t] : 0);
     }
-    if (tid < 14) rj[tid] = tp.rjl[tid * 14];
+    if (tid < 16) rj[tid] = tp.rjl[tid * 16];
     const int ucol = a.unit_col[u];
     const int col = ucol & 0xffff, pz = (ucol >> 30) & 1, pr = col & 1;
     const int nl = 1 << a.level;
@@ -373,7 +385,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
         if (abort_) break;
         // the cube (8-byte copies: its offset is a multiple of 8 bytes only), then A slice 0
         for (int t = tid; t < slab; t += TC_THREADS)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(sE + t)), "l"(Eg + t) : "memory");
+            if constexpr (C32)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(sE32 + t)), "l"(&Eg[t].x) : "memory");
+            else
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(sE + t)), "l"(Eg + t) : "memory");
         cp_async_commit();
         load_A(0, 0);
         cp_async_wait<1>();
@@ -386,7 +401,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
                 const int ok = offK[inward][kl] >> 4;
                 for (int ij = lane; ij < nc; ij += 32) {
                     const int oi = offI[inward][ij];
-                    m = fmaxf(m, fabsf(sE[ok + (oi >> 4)].x) * rj[oi & 15].x);
+                    m = fmaxf(m, fabsf(cube(ok + (oi >> 4)).x) * rj[oi & 15].x);
                 }
             }
 #pragma unroll
@@ -413,7 +428,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
                         if (ij < nc) {
                             const int oi = offI[inward][ij];
                             const int j = oi & 15;
-                            float2 ev = sE[ok + (oi >> 4)];
+                            float2 ev = cube(ok + (oi >> 4));
                             if (backward && ((j + l) & 1)) ev = make_float2(-ev.x, -ev.y);
                             const float2 rf = rj[j];
                             const dfv v = df_mul(df_make(ev.x, ev.y), df_make(rf.x, rf.y));
@@ -524,7 +539,13 @@ static int tc_kp(int nc) { return (nc + 15) / 16 * 16; }
 
 bool s2l_tc_enabled(afmm_plan p)
 {
-    return (p->precision == AFMM_FP64 || p->precision == AFMM_MIXED) && p->opt.s2l_engine == 0 && p->ncoef <= 96;
+    // FP64 path: 6 digit slices, five accumulators of KP columns in the 512 TMEM columns
+    // and exact FP32 levels (4 KP products of <= 2^15 units below 2^24): KP <= 96 (order
+    // <= 12).  MIXED: 4 slices, three accumulators, level 1 below 2^22 units: KP <= 128
+    // (order <= 14)
+    if (p->opt.s2l_engine != 0) return false;
+    if (p->precision == AFMM_FP64) return p->ncoef <= 96;
+    return p->precision == AFMM_MIXED && p->ncoef <= 128;
 }
 
 // digit slices per operand: six (48 bits) for the FP64 path, four (32 bits) for MIXED (three
@@ -540,15 +561,16 @@ afmm_status make_tc_tables(afmm_plan p)
 {
     TcTables *t = new (std::nothrow) TcTables();
     if (!t) return AFMM_ENOMEM;
-    double f[14];
+    double f[16];  // j! (exact in FP64)
     f[0] = 1.0;
-    for (int i = 1; i < 14; ++i) f[i] = f[i - 1] * i;
-    for (int j = 0; j < 14; ++j) {
-        t->jfact[j] = (float)f[j];
-        for (int l = 0; l < 14; ++l) {
+    for (int i = 1; i < 16; ++i) f[i] = f[i - 1] * i;
+    for (int j = 0; j < 16; ++j) {
+        const float fh = (float)f[j];
+        t->jfact[j] = make_float2(fh, (float)(f[j] - (double)fh));
+        for (int l = 0; l < 16; ++l) {
             double x = 1.0 / (f[j] * f[l]);
             float hi = (float)x;
-            t->rjl[j * 14 + l] = make_float2(hi, (float)(x - (double)hi));
+            t->rjl[j * 16 + l] = make_float2(hi, (float)(x - (double)hi));
         }
     }
     for (int i = 0; i < 128; ++i) t->ci[i] = t->cj[i] = -1;
@@ -589,7 +611,8 @@ static afmm_status launch_tc_k(afmm_plan p, int l, const R *mre, const R *mim, R
     a.err = p->err_dev;
     a.inject_timeout = p->inject_tc_timeout;
     const int W = p->M + 1;
-    const size_t sm = (size_t)NS * KP * KP * 2 + (size_t)2 * 128 * KP * 2 + (size_t)W * W * (2 * p->M + 1) * 8;
+    const size_t sm = (size_t)NS * KP * KP * 2 + (size_t)2 * 128 * KP * 2 + (size_t)W * W * (2 * p->M + 1) * (KP > 112 ? 4 : 8);
+    if (sm > 227 * 1024) return AFMM_EUNSUPPORTED;
     AFMM_CUDA(cudaFuncSetAttribute(k_s2l_tc<KP, NS, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_s2l_tc<KP, NS, R><<<dim3((unsigned)v.nunit64, (unsigned)nm), TC_THREADS, sm, st>>>(a, *p->tct);
     AFMM_LAUNCH_CHECK();
@@ -606,6 +629,10 @@ static afmm_status launch_tc_ns(afmm_plan p, int l, const R *mre, const R *mim, 
     case 64: return launch_tc_k<64, NS, R>(p, l, mre, mim, lre, lim);
     case 80: return launch_tc_k<80, NS, R>(p, l, mre, mim, lre, lim);
     case 96: return launch_tc_k<96, NS, R>(p, l, mre, mim, lre, lim);
+    }
+    if constexpr (NS == 4) {
+        if (tc_kp(p->ncoef) == 112) return launch_tc_k<112, NS, R>(p, l, mre, mim, lre, lim);
+        if (tc_kp(p->ncoef) == 128) return launch_tc_k<128, NS, R>(p, l, mre, mim, lre, lim);
     }
     return AFMM_EUNSUPPORTED;
 }

@@ -105,10 +105,10 @@ def test_direct_is_deterministic():
 
 @pytest.mark.parametrize("n_modes", [89, 129])
 def test_direct_mode_ranges_match_oracle(n_modes):
-    """More modes than one launch of the FP32-pair near-field kernel holds (11 consumer warps
-    x 8 modes): the kernel runs over mode ranges, each recomputing the pair sequences; the
-    last range is short (89) or the highest order the plans accept (129).  Both sweeps
-    (forward and Miller) occur at these orders."""
+    """More modes than one launch of the FP32-pair near-field kernel holds (72 with the
+    gradient): the kernel runs over mode ranges, each recomputing the pair sequences (89:
+    72 + 17; 129, the highest order the plans accept: 72 + 57).  Both sweeps (forward and
+    Miller) occur at these orders."""
     w = W.make("cfg1", ns=400, nf=300, n_modes=n_modes)
     pl = _plan(w)
     q_re, q_im = to_dev(w["q_re"], w["q_im"])

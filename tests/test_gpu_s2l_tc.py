@@ -68,3 +68,25 @@ def test_tensor_core_s2l_adjoint_direction():
         pl.close()
     for a, b in zip(res[0], res[1]):
         assert np.max(np.abs(a - b)) <= 1e-11 * np.max(np.abs(b)), np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("M", [12, 13, 14])
+def test_mixed_tensor_core_s2l_wide_tiles(M):
+    """MIXED: the tensor-core S2L runs 4 digit slices, so its tiles reach 112 (order 13) and
+    128 columns (order 14; the 128-wide tile keeps the expansion cube in FP32).  Against the
+    MIXED CUDA-core engine and against the oracle's FP64 FMM, at the MIXED FMM bar (2e-5)."""
+    from paper_2301_01179_gb300 import binding
+    w = W.make("cfg1", ns=4000, nf=3000, n_modes=5)
+    sr, sz, tr, tz, qr, qi = to_dev(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], w["q_re"], w["q_im"])
+    out = []
+    for eng in ("auto", "cuda_cores"):
+        pl = binding.Plan(sr, sz, tr, tz, w["n_modes"], order=M, depth=4, precision="mixed", s2l_engine=eng)
+        out.append(to_np(*pl.grad(qr, qi)))
+        pl.close()
+    _, geom = oracle.tree_setup(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], 1, depth_override=4)
+    F = oracle.fmm(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], w["q_re"], w["q_im"], M, 4, geom, grad=True)
+    for c in range(0, 6, 2):
+        e_eng = eps_modes(out[0][c], out[0][c + 1], out[1][c], out[1][c + 1]).max()
+        e_orc = eps_modes(out[0][c], out[0][c + 1], F[c], F[c + 1]).max()
+        print("mixed M=%d comp %d: tc vs cuda cores %.2e, vs oracle %.2e" % (M, c, e_eng, e_orc))
+        assert e_eng < 2e-5 and e_orc < 2e-5, (M, c, e_eng, e_orc)
