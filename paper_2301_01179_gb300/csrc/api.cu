@@ -200,6 +200,10 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
     {
         const char *e = getenv("AFMM_INJECT_TC_TIMEOUT");
         p->inject_tc_timeout = (e && e[0] == '1') ? 1 : 0;
+        // AFMM_INJECT_NEAR_TIMEOUT=1: the near-field producers never hand over slot 0, so
+        // the consumers' bounded wait on it runs out
+        const char *f = getenv("AFMM_INJECT_NEAR_TIMEOUT");
+        p->inject_near_timeout = (f && f[0] == '1') ? 1 : 0;
     }
     p->pp.fwd_switch = opt.fwd_switch > 0.0 ? opt.fwd_switch : default_fwd_switch(p->N);
     p->pp.miller_extra = opt.miller_extra > 0 ? (double)opt.miller_extra : 15.0;

@@ -203,6 +203,7 @@ struct afmm_plan_s {
     afmm::TcTables *tct = nullptr;              // tensor-core S2L tables (host)
     int *err_host = nullptr, *err_dev = nullptr;  // device-side error word (mapped host memory)
     int inject_tc_timeout = 0;                  // test hook (environment): make the S2L wait run out
+    int inject_near_timeout = 0;                // test hook (environment): make a near-field hand-over run out
     int64_t gexp_cap = 0;                       // doubles
     double *m2m_tab = nullptr;                  // [4][2][(M+1)^2] shift tables (see farfield.cu)
     double *l2l_tab = nullptr;

@@ -1329,6 +1329,7 @@ static afmm_status far_field_df(afmm_plan p, int dir)
             else if (kpt <= 16) r = launch_s2l_df_k<16>(a, st, sm);
             else if (kpt <= 24) r = launch_s2l_df_k<24>(a, st, sm);
             else if (kpt <= 32) r = launch_s2l_df_k<32>(a, st, sm);
+            else if (kpt <= 40) r = launch_s2l_df_k<40>(a, st, sm);
             AFMM_TRY(r);
         }
         tmark(p, e + 3);

@@ -47,6 +47,7 @@ struct NearArgs {
     int mode_lo, mode_hi;  // FP32-pair kernel: the modes [mode_lo, mode_hi) of this launch
     int *err;              // plan error word (bounded waits that ran out)
     int accumulate;        // FP32-pair kernel: add to the outputs (k_l2p wrote the local expansion)
+    int inject_timeout;    // test hook: slot 0 is never handed over
     // local expansion at the leaves (near mode, optional)
     const double *loc_re, *loc_im;
     const uint32_t *leaf_key;
@@ -831,7 +832,7 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
                 p4[128 + lane] = bcast4(Bs);
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&s_full[b]);
+            if (lane == 0 && !(a.inject_timeout && k == 0)) mbar_arrive(&s_full[b]);
         }
         return;
     }
@@ -1415,6 +1416,7 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
         a.df_fwd_switch = (float)p->df_fwd_switch;
         a.df_tlim = (float)fmin(cosh(p->df_fwd_switch / (2.0 * (p->N < 1 ? 1 : p->N))), cosh(0.96)) - 1.0f;
         a.err = p->err_dev;
+        a.inject_timeout = p->inject_near_timeout;
         const bool loc = mix ? a.loc32_re != nullptr : a.locdf_re != nullptr;
         if (loc) {  // the leaf's local expansion first; the near kernel adds its sums
             if (grad && mix)

@@ -99,8 +99,9 @@ __device__ __forceinline__ dfv pair_agm_df(const PairDF &g, dfv &csum)
 // Forward lanes: two steps per iteration, gam_n chi and gam_{n+1} chi as one packed
 // product, one 16-byte store per mode pair; every lane of a warp that has a forward lane
 // runs it (a backward lane's values, possibly overflowing, are overwritten by its own
-// sweep).  Backward lanes (Miller): from y_L = 0, y_{L-1} = 2^-100 down to y_0, rescaled
-// exactly by 2^-100 whenever |y| passes 2^100, normalised by G0 / y_0.  The start is
+// sweep).  Backward lanes (Miller): from y_L = 0, y_{L-1} = 2^-e (e ~ the sweep's growth in
+// bits, at most 100) down to y_0, rescaled exactly by 2^-100 whenever |y| passes 2^60,
+// normalised by G0 / y_0.  The start is
 // L = max(N + 2, N / 2 + ceil(extra / acosh chi) + 2): the relative error of y_n,
 // e^{-2 a (L - n)} (a = acosh chi), is then below e^{-2 extra} measured against the
 // pair's G^(0), since |G^(n) / G^(0)| ~ e^{-n a}.
@@ -137,8 +138,12 @@ __device__ __forceinline__ dfv pair_sweep_df(dfv chi, float t, float zero, dfv i
     const int ext = lf < 0.f ? 0 : (lf > (float)AFMM_REC_TAB ? AFMM_REC_TAB : (int)lf);
     int L = N + ext + 2;
     if (L > AFMM_REC_TAB - 1) L = AFMM_REC_TAB - 1;
-    dfv y0 = df_make(0.f, 0.f);            // y_L
-    dfv y1 = df_make(7.8886091e-31f, 0.f); // y_{L-1} = 2^-100
+    // y_L = 0, y_{L-1} = 2^-e with e ~ log2 of the sweep's growth e^{a (L - 1)} (at most 100),
+    // so that y_0 ends near 1 and the normalisation G0 / y_0 (which multiplies the gradient
+    // factors) stays far inside the FP32 range; a power of two scales the whole sweep exactly
+    const int e2 = (int)fminf(100.f, rintf(af * (float)(L - 1) * 1.44269504f));
+    dfv y0 = df_make(0.f, 0.f);
+    dfv y1 = df_make(__int_as_float((127 - e2) << 23), 0.f);
     for (int n = L; n >= 2; --n) {
         const float2 gm = gam2[n];
         const dfv yn = df_sub(df_mul(df_mul(df_make(gm.x, gm.y), chi), y1), y0);  // y_{n-2}
@@ -146,7 +151,9 @@ __device__ __forceinline__ dfv pair_sweep_df(dfv chi, float t, float zero, dfv i
         y1 = yn;
         const int idx = n - 2;
         if (idx <= N) ys.put(idx, yn);
-        if (fabsf(yn.hi) > 1.2676506e30f) {  // > 2^100: rescale by 2^-100 (exact)
+        // above 2^60: rescale by 2^-100 (exact); the margin 2^68 to the FP32 range covers the
+        // growth of one step, ~2 chi, up to chi ~ 1e20 (points near the axis)
+        if (fabsf(yn.hi) > 1.1529215e18f) {
             const float s100 = 7.8886091e-31f;
             y0 = df_scale2(y0, s100);
             y1 = df_scale2(y1, s100);

@@ -132,3 +132,22 @@ def test_fmm_near_lane_packing_matches_oracle_fmm(nf):
     for c in range(0, 6, 2):
         e = eps_modes(g[c], g[c + 1], F[c], F[c + 1])
         assert e.max() < TOL, (c, e.max())
+
+
+def test_direct_near_the_axis_matches_oracle():
+    """Rings within 1e-6..1e-4 of the axis against rings at distance ~0.1-1: chi - 1 reaches
+    ~1e9, so the backward sweep's values grow by ~1e9 per step and must be rescaled before
+    they leave the FP32 range; nearly coincident pairs near the axis as well."""
+    rng = np.random.default_rng(5)
+    w = W.make("paper", ns=300, nf=200, n_modes=18)
+    w["src_r"][:60] = 10.0 ** rng.uniform(-6, -4, 60)
+    w["tgt_r"][:40] = 10.0 ** rng.uniform(-6, -4, 40)
+    w["tgt_z"][:10] = w["src_z"][:10] + 1e-7
+    pl = _plan(w, order=6, leaf=32)
+    q_re, q_im = to_dev(w["q_re"], w["q_im"])
+    g = to_np(*pl.direct_grad(q_re, q_im))
+    D = oracle.direct(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], w["q_re"], w["q_im"], grad=True)
+    assert all(np.all(np.isfinite(x)) for x in g)
+    for c in range(0, 6, 2):
+        e = eps_modes(g[c], g[c + 1], D[c], D[c + 1])
+        assert e.max() < TOL, (c, e.max())

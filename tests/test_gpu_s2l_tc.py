@@ -44,15 +44,18 @@ def test_tensor_core_s2l_deep_tree_many_modes():
     assert e.max() < 1e-11, e.max()
 
 
-def test_tensor_core_s2l_matches_oracle_fmm_order13():
+@pytest.mark.parametrize("M", [13, 14, 15])
+def test_high_orders_match_oracle_fmm(M):
+    """Orders above the FP64 tensor-core width run the S2L on CUDA cores; 15 is the highest
+    order the plans accept."""
     w = W.make("cfg3", ns=3000, nf=2500, n_modes=5)
     from paper_2301_01179_gb300 import binding
     sr, sz, tr, tz, qr, qi = to_dev(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], w["q_re"], w["q_im"])
-    pl = binding.Plan(sr, sz, tr, tz, w["n_modes"], order=13, depth=4)
+    pl = binding.Plan(sr, sz, tr, tz, w["n_modes"], order=M, depth=4)
     g = to_np(*pl.eval(qr, qi))
     pl.close()
     _, geom = oracle.tree_setup(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], 1, depth_override=4)
-    F = oracle.fmm(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], w["q_re"], w["q_im"], 13, 4, geom)
+    F = oracle.fmm(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], w["q_re"], w["q_im"], M, 4, geom)
     assert eps_modes(g[0], g[1], F[0], F[1]).max() < 1e-10
 
 
