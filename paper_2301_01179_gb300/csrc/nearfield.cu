@@ -86,54 +86,6 @@ __device__ __forceinline__ void l2p_eval(const double *__restrict__ F, int M, do
 }
 
 template <bool GRAD>
-__device__ __forceinline__ void l2p_eval32(const float *__restrict__ F, int M, float u, float v, float &val, float &du,
-                                           float &dv)
-{
-    float pu = 0.f, pdu = 0.f, pdv = 0.f;
-    for (int k = M; k >= 0; --k) {
-        int base = k * (M + 1) - k * (k - 1) / 2;
-        float pk = 0.f, pkd = 0.f;
-        for (int l = M - k; l >= 0; --l) {
-            if (GRAD) pkd = fmaf(pkd, v, pk);
-            pk = fmaf(pk, v, F[base + l]);
-        }
-        if (GRAD) {
-            pdu = fmaf(pdu, u, pu);
-            pdv = fmaf(pdv, u, pkd);
-        }
-        pu = fmaf(pu, u, pk);
-    }
-    val = pu;
-    du = pdu;
-    dv = pdv;
-}
-
-// FP32 amplitude of mode n, source s, in the mode-pair interleaved layout [n / 2][ns] float2
-__device__ __forceinline__ float q32_at(const float2 *__restrict__ q, int n, int64_t s, int64_t ns)
-{
-    const float2 v = q[(size_t)(n >> 1) * ns + s];
-    return (n & 1) ? v.y : v.x;
-}
-
-// Kahan-compensated FP32 accumulation: (sum, running compensation) in a float2
-// Kahan-compensated FP32 sum: s holds the sum, c the compensation (true sum ~ s - c)
-__device__ __forceinline__ void kahan_add(float &s, float &c, float v)
-{
-    const float y = __fsub_rn(v, c);
-    const float t = __fadd_rn(s, y);
-    c = __fsub_rn(__fsub_rn(t, s), y);
-    s = t;
-}
-
-__device__ __forceinline__ void kadd(float2 &a, float v)
-{
-    float y = v - a.y;
-    float t = a.x + y;
-    a.y = (t - a.x) - y;
-    a.x = t;
-}
-
-template <bool GRAD, bool MIX>
 __global__ void __launch_bounds__(AFMM_NEAR_WARPS * 32) k_near(const NearArgs a, const RecTab tab)
 {
     extern __shared__ double smem[];
@@ -173,8 +125,7 @@ __global__ void __launch_bounds__(AFMM_NEAR_WARPS * 32) k_near(const NearArgs a,
     const double inv2r = 0.5 / rt;
 
     for (int c = 0; c < ncomp; ++c)
-        for (int n = 0; n < nm; ++n) acc[((size_t)c * nm + n) * 32 + lane] = 0.0;  // also (0.f, 0.f) pairs
-    float2 *acc2 = reinterpret_cast<float2 *>(acc);
+        for (int n = 0; n < nm; ++n) acc[((size_t)c * nm + n) * 32 + lane] = 0.0;
 
     // source ranges: 9 neighbour leaves, or one split of all sources
     int nrange = a.direct ? 1 : 9;
@@ -196,40 +147,7 @@ __global__ void __launch_bounds__(AFMM_NEAR_WARPS * 32) k_near(const NearArgs a,
             PairGeom g;
             pair_geom(rt, zt, r1, z1, inv2w, active, g);
             double sc = pair_sequence(g, inv2w, Nq, a.pp, gam, ys + lane, 32);
-            if (MIX) {
-                // FP64 sequence, FP32 products, Kahan-compensated FP32 sums
-                const size_t st = (size_t)nm * 32;
-                if (!GRAD) {
-                    for (int n = 0; n < nm; ++n) {
-                        float gn = (float)(sc * ys[n * 32 + lane]);
-                        float qr = q32_at(a.q32_re, n, s, a.nsrc), qi = q32_at(a.q32_im, n, s, a.nsrc);
-                        size_t o = (size_t)n * 32 + lane;
-                        kadd(acc2[o], qr * gn);
-                        kadd(acc2[o + st], qi * gn);
-                    }
-                } else {
-                    double inv = 1.0 / (g.rp2 * g.rm2);
-                    double ip = g.rm2 * inv, im = g.rp2 * inv;
-                    double A = ip + im, B = ip - im;
-                    float qfac = (float)fma(rt - r1, rt + r1, -g.x * g.x), x32 = (float)g.x;
-                    double yprev = ys[32 + lane];
-                    for (int n = 0; n < nm; ++n) {
-                        double yn = ys[n * 32 + lane];
-                        float gn = (float)(sc * yn);
-                        float wt = (float)(sc * fma(yn, A, rho[n] * yprev * B));
-                        yprev = yn;
-                        float xw = x32 * wt, qw = qfac * wt;
-                        float qr = q32_at(a.q32_re, n, s, a.nsrc), qi = q32_at(a.q32_im, n, s, a.nsrc);
-                        size_t o = (size_t)n * 32 + lane;
-                        kadd(acc2[o], qr * gn);
-                        kadd(acc2[o + st], qi * gn);
-                        kadd(acc2[o + 2 * st], qr * qw);
-                        kadd(acc2[o + 3 * st], qi * qw);
-                        kadd(acc2[o + 4 * st], qr * xw);
-                        kadd(acc2[o + 5 * st], qi * xw);
-                    }
-                }
-            } else if (!GRAD) {
+            if (!GRAD) {
                 for (int n = 0; n < nm; ++n) {
                     double gn = sc * ys[n * 32 + lane];
                     double qr = a.q_re[(size_t)n * a.nsrc + s], qi = a.q_im[(size_t)n * a.nsrc + s];
@@ -266,7 +184,7 @@ __global__ void __launch_bounds__(AFMM_NEAR_WARPS * 32) k_near(const NearArgs a,
     if (!active) return;
     // local expansion at the field point (far field)
     double u = 0.0, v = 0.0;
-    if (a.loc_re || a.loc32_re) {
+    if (a.loc_re) {
         uint32_t k = a.leaf_key[box];
         double cr = a.r0 + ((double)morton_ir(k) + 0.5) * a.h, cz = a.z0 + ((double)morton_iz(k) + 0.5) * a.h;
         u = (rt - cr) / a.h;
@@ -277,25 +195,12 @@ __global__ void __launch_bounds__(AFMM_NEAR_WARPS * 32) k_near(const NearArgs a,
     for (int n = 0; n < nm; ++n) {
         // (amplitudes carry c_n and the sequence is G_n / c_n, so the sums are plain)
         size_t o = (size_t)n * 32 + lane;
-        double c0, c1, c2 = 0, c3 = 0, c4 = 0, c5 = 0;
-        if (MIX) {
-            c0 = (double)acc2[o].x - (double)acc2[o].y;
-            c1 = (double)acc2[o + st].x - (double)acc2[o + st].y;
-            if (GRAD) {
-                c2 = (double)acc2[o + 2 * st].x - (double)acc2[o + 2 * st].y;
-                c3 = (double)acc2[o + 3 * st].x - (double)acc2[o + 3 * st].y;
-                c4 = (double)acc2[o + 4 * st].x - (double)acc2[o + 4 * st].y;
-                c5 = (double)acc2[o + 5 * st].x - (double)acc2[o + 5 * st].y;
-            }
-        } else {
-            c0 = acc[o];
-            c1 = acc[o + st];
-            if (GRAD) {
-                c2 = acc[o + 2 * st];
-                c3 = acc[o + 3 * st];
-                c4 = acc[o + 4 * st];
-                c5 = acc[o + 5 * st];
-            }
+        double c0 = acc[o], c1 = acc[o + st], c2 = 0, c3 = 0, c4 = 0, c5 = 0;
+        if (GRAD) {
+            c2 = acc[o + 2 * st];
+            c3 = acc[o + 3 * st];
+            c4 = acc[o + 4 * st];
+            c5 = acc[o + 5 * st];
         }
         double pr = c0, pi = c1;
         double dr_r = 0, dr_i = 0, dz_r = 0, dz_i = 0;
@@ -306,23 +211,7 @@ __global__ void __launch_bounds__(AFMM_NEAR_WARPS * 32) k_near(const NearArgs a,
             dz_r = nu * c4;
             dz_i = nu * c5;
         }
-        if (MIX && a.loc32_re) {
-            const float *Fr = a.loc32_re + ((size_t)box * nm + n) * a.ncoef;
-            const float *Fi = a.loc32_im + ((size_t)box * nm + n) * a.ncoef;
-            float vr, dur, dvr, vi, dui, dvi;
-            l2p_eval32<GRAD>(Fr, a.M, (float)u, (float)v, vr, dur, dvr);
-            l2p_eval32<GRAD>(Fi, a.M, (float)u, (float)v, vi, dui, dvi);
-            pr += vr;
-            pi += vi;
-            if (GRAD) {
-                double ih = 1.0 / a.h;
-                dr_r += dur * ih;
-                dr_i += dui * ih;
-                dz_r += dvr * ih;
-                dz_i += dvi * ih;
-            }
-        }
-        if (!MIX && a.loc_re) {
+        if (a.loc_re) {
             const double *Fr = a.loc_re + ((size_t)box * nm + n) * a.ncoef;
             const double *Fi = a.loc_im + ((size_t)box * nm + n) * a.ncoef;
             double vr, dur, dvr, vi, dui, dvi;
@@ -373,7 +262,7 @@ __global__ void __launch_bounds__(AFMM_NEAR_WARPS * 32) k_near(const NearArgs a,
 // ------------------------------------------------------------------------------------
 #define NEAR2_WB 4
 
-template <bool GRAD, bool MIX>
+template <bool GRAD>
 __global__ void __launch_bounds__(NEAR2_WB * 32) k_near2(const NearArgs a, const RecTab tab)
 {
     extern __shared__ double smem[];
@@ -439,7 +328,6 @@ __global__ void __launch_bounds__(NEAR2_WB * 32) k_near2(const NearArgs a, const
     const double inv2r = 0.5 / rt;
     double *myacc = acc + (size_t)warp * ncomp * mper * 32;
     for (int i = lane; i < ncomp * mper * 32; i += 32) myacc[i] = 0.0;
-    float2 *myacc2 = reinterpret_cast<float2 *>(myacc);
     const int n0 = warp * mper, n1 = min(nm, n0 + mper);
     __syncthreads();
     const int total = rcum[9];
@@ -489,34 +377,18 @@ __global__ void __launch_bounds__(NEAR2_WB * 32) k_near2(const NearArgs a, const
             for (int n = n0; n < n1; ++n) {
                 const double yn = yk[n * 32 + lane];
                 const size_t o = (size_t)(n - n0) * 32 + lane, st = (size_t)mper * 32;
-                if (MIX) {
-                    float qr = q32_at(a.q32_re, n, s, a.nsrc), qi = q32_at(a.q32_im, n, s, a.nsrc);
-                    float gn = (float)(sc * yn);
-                    kadd(myacc2[o], qr * gn);
-                    kadd(myacc2[o + st], qi * gn);
-                    if (GRAD) {
-                        float wt = (float)fma(yn, As, rho[n] * yprev * Bs);
-                        yprev = yn;
-                        float xw = (float)gx * wt, qw = (float)qf * wt;
-                        kadd(myacc2[o + 2 * st], qr * qw);
-                        kadd(myacc2[o + 3 * st], qi * qw);
-                        kadd(myacc2[o + 4 * st], qr * xw);
-                        kadd(myacc2[o + 5 * st], qi * xw);
-                    }
-                } else {
-                    double qr = a.q_re[(size_t)n * a.nsrc + s], qi = a.q_im[(size_t)n * a.nsrc + s];
-                    double gn = sc * yn;
-                    myacc[o] = fma(qr, gn, myacc[o]);
-                    myacc[o + st] = fma(qi, gn, myacc[o + st]);
-                    if (GRAD) {
-                        double wt = fma(yn, As, rho[n] * yprev * Bs);
-                        yprev = yn;
-                        double xw = gx * wt, qw = qf * wt;
-                        myacc[o + 2 * st] = fma(qr, qw, myacc[o + 2 * st]);
-                        myacc[o + 3 * st] = fma(qi, qw, myacc[o + 3 * st]);
-                        myacc[o + 4 * st] = fma(qr, xw, myacc[o + 4 * st]);
-                        myacc[o + 5 * st] = fma(qi, xw, myacc[o + 5 * st]);
-                    }
+                double qr = a.q_re[(size_t)n * a.nsrc + s], qi = a.q_im[(size_t)n * a.nsrc + s];
+                double gn = sc * yn;
+                myacc[o] = fma(qr, gn, myacc[o]);
+                myacc[o + st] = fma(qi, gn, myacc[o + st]);
+                if (GRAD) {
+                    double wt = fma(yn, As, rho[n] * yprev * Bs);
+                    yprev = yn;
+                    double xw = gx * wt, qw = qf * wt;
+                    myacc[o + 2 * st] = fma(qr, qw, myacc[o + 2 * st]);
+                    myacc[o + 3 * st] = fma(qi, qw, myacc[o + 3 * st]);
+                    myacc[o + 4 * st] = fma(qr, xw, myacc[o + 4 * st]);
+                    myacc[o + 5 * st] = fma(qi, xw, myacc[o + 5 * st]);
                 }
             }
         }
@@ -524,7 +396,7 @@ __global__ void __launch_bounds__(NEAR2_WB * 32) k_near2(const NearArgs a, const
     }
     if (!active) return;
     double u = 0.0, v = 0.0;
-    if (a.loc_re || a.loc32_re) {
+    if (a.loc_re) {
         uint32_t kk = a.leaf_key[box];
         double cr = a.r0 + ((double)morton_ir(kk) + 0.5) * a.h, cz = a.z0 + ((double)morton_iz(kk) + 0.5) * a.h;
         u = (rt - cr) / a.h;
@@ -536,7 +408,7 @@ __global__ void __launch_bounds__(NEAR2_WB * 32) k_near2(const NearArgs a, const
         size_t o = (size_t)(n - n0) * 32 + lane;
         double c[6] = {0, 0, 0, 0, 0, 0};
         for (int q = 0; q < ncomp; ++q)
-            c[q] = MIX ? (double)myacc2[o + q * st].x - (double)myacc2[o + q * st].y : myacc[o + q * st];
+            c[q] = myacc[o + q * st];
         double pr = c[0], pi = c[1];
         double dr_r = 0, dr_i = 0, dz_r = 0, dz_i = 0;
         if (GRAD) {
@@ -546,23 +418,7 @@ __global__ void __launch_bounds__(NEAR2_WB * 32) k_near2(const NearArgs a, const
             dz_r = nu * c[4];
             dz_i = nu * c[5];
         }
-        if (MIX && a.loc32_re) {
-            const float *Fr = a.loc32_re + ((size_t)box * nm + n) * a.ncoef;
-            const float *Fi = a.loc32_im + ((size_t)box * nm + n) * a.ncoef;
-            float vr, dur, dvr, vi, dui, dvi;
-            l2p_eval32<GRAD>(Fr, a.M, (float)u, (float)v, vr, dur, dvr);
-            l2p_eval32<GRAD>(Fi, a.M, (float)u, (float)v, vi, dui, dvi);
-            pr += vr;
-            pi += vi;
-            if (GRAD) {
-                double ih = 1.0 / a.h;
-                dr_r += dur * ih;
-                dr_i += dui * ih;
-                dz_r += dvr * ih;
-                dz_i += dvi * ih;
-            }
-        }
-        if (!MIX && a.loc_re) {
+        if (a.loc_re) {
             const double *Fr = a.loc_re + ((size_t)box * nm + n) * a.ncoef;
             const double *Fi = a.loc_im + ((size_t)box * nm + n) * a.ncoef;
             double vr, dur, dvr, vi, dui, dvi;
@@ -1447,11 +1303,11 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
                 AFMM_TRY((launch_near_ws<false, false>(a, *p->rec, p->stream)));
         }
     } else if (grad) {
-        AFMM_CUDA(cudaFuncSetAttribute(k_near2<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_near2<true, false><<<grid, T, sm, p->stream>>>(a, *p->rec);
+        AFMM_CUDA(cudaFuncSetAttribute(k_near2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_near2<true><<<grid, T, sm, p->stream>>>(a, *p->rec);
     } else {
-        AFMM_CUDA(cudaFuncSetAttribute(k_near2<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_near2<false, false><<<grid, T, sm, p->stream>>>(a, *p->rec);
+        AFMM_CUDA(cudaFuncSetAttribute(k_near2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_near2<false><<<grid, T, sm, p->stream>>>(a, *p->rec);
     }
     if (p->precision == AFMM_FP64_NATIVE) AFMM_LAUNCH_CHECK();
     if (a.part) {
@@ -1589,8 +1445,8 @@ extern "C" afmm_status afmm_direct_static(int64_t ns, const double *src_r, const
     int w = near_warps(n_modes, 0);
     if (w == 0) return AFMM_EUNSUPPORTED;
     size_t sm = near_smem(n_modes, 0, w);
-    AFMM_CUDA(cudaFuncSetAttribute(k_near<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_near<false, false><<<(unsigned)((a.nunits + w - 1) / w), w * 32, sm, st>>>(a, tab);
+    AFMM_CUDA(cudaFuncSetAttribute(k_near<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_near<false><<<(unsigned)((a.nunits + w - 1) / w), w * 32, sm, st>>>(a, tab);
     AFMM_LAUNCH_CHECK();
     if (a.part) {
         int64_t tot = (int64_t)2 * n_modes * nf;
