@@ -92,10 +92,15 @@ static void tmark(afmm_plan p, int idx)
     if (p->timing && idx < 80) cudaEventRecord(p->ev[idx], p->stream);
 }
 
+// elapsed time between two recorded events; an event a path did not record reads as 0 and
+// its error is cleared so that it cannot surface at a later launch check
 static float tdiff(afmm_plan p, int a, int b)
 {
     float ms = 0.0f;
-    cudaEventElapsedTime(&ms, p->ev[a], p->ev[b]);
+    if (cudaEventElapsedTime(&ms, p->ev[a], p->ev[b]) != cudaSuccess) {
+        (void)cudaGetLastError();
+        ms = 0.0f;
+    }
     return ms;
 }
 

@@ -180,7 +180,7 @@ struct afmm_plan_s {
     double r0 = 0, z0 = 0, L = 1;
     // sorted points
     double *s_r = nullptr, *s_z = nullptr, *t_r = nullptr, *t_z = nullptr;
-    float2 *s_rdf = nullptr, *t_rdf = nullptr;  // sorted r as FP32 pairs (FP32-pair near field)
+    float2 *s_rinv = nullptr, *t_rinv = nullptr;  // sorted 1 / r as FP32 pairs (FP32-pair near field)
     int32_t *s_perm = nullptr, *t_perm = nullptr;
     uint32_t *s_key = nullptr, *t_key = nullptr;
     afmm::Level lv[AFMM_MAX_LEVEL + 1];

@@ -90,6 +90,18 @@ __device__ __forceinline__ dfv df_div(dfv a, dfv b)
     return df_add(q, df_make(__fmul_rn(r2.hi, rb), 0.f));
 }
 
+// 1 / b: the FP32 reciprocal r0 of b.hi (MUFU, ~1 ulp) refined by one Newton step carrying
+// the quadratic term, r = r0 + r0 (e + e^2) with e = 1 - b r0 (FMA-exact to 2^-47 of e), so
+// the relative error is O(e^3 + 2^-47): the accuracy of df_div at a fifth of its operations
+__device__ __forceinline__ dfv df_rcp(dfv b)
+{
+    const float r0 = rcp_approx(b.hi);
+    float e = __fmaf_rn(-b.hi, r0, 1.0f);
+    e = __fmaf_rn(-b.lo, r0, e);
+    const float t = __fmul_rn(r0, __fmaf_rn(e, e, e));
+    return quick_two_sum(r0, t);
+}
+
 // sqrt by one correction of an FP32 seed from the hardware reciprocal square root (Karp):
 // x = rsqrt(a_hi), y = a_hi x, sqrt(a) ~ y + (a - y^2) x / 2
 __device__ __forceinline__ dfv df_sqrt(dfv a)

@@ -23,7 +23,7 @@ struct NearArgs {
     int64_t nfield;
     // source role (sorted), amplitudes [nmodes][nsrc] pre-multiplied by c_n
     const double *sr, *sz, *q_re, *q_im;
-    const float2 *sr_df;  // sources' r as FP32 pairs (FP32-pair kernel)
+    const float2 *rinv_df;  // sources' 1 / r as FP32 pairs (FP32-pair kernel)
     int64_t nsrc;
     int nmodes, N;
     // work
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(AFMM_NEAR_WARPS * 32) k_near(const NearArgs a,
             const double r1 = a.sr[s], z1 = a.sz[s];
             const double inv2w = inv2r / r1;
             PairGeom g;
-            pair_geom(rt, zt, r1, z1, inv2w, active, g);
+            pair_geom(rt, zt, r1, z1, inv2w, true, g);  // a lane past the last target: never written
             double sc = pair_sequence(g, inv2w, Nq, a.pp, gam, ys + lane, 32);
             if (!GRAD) {
                 for (int n = 0; n < nm; ++n) {
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(NEAR2_WB * 32) k_near2(const NearArgs a, const
             const double r1 = a.sr[s], z1 = a.sz[s];
             const double inv2w = inv2r / r1;
             PairGeom g;
-            pair_geom(rt, zt, r1, z1, inv2w, active, g);
+            pair_geom(rt, zt, r1, z1, inv2w, true, g);  // a lane past the last target: never written
             double *yw = ys + (size_t)warp * nmq * 32;
             double sc = pair_sequence(g, inv2w, Nq, a.pp, gam, yw + lane, 32);
             double *pw = pp + (size_t)warp * NPP * 32;
@@ -664,21 +664,24 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
                 s = rb[rg] + (kk - rcum[rg]);
             }
             const double r1 = a.sr[s], z1 = a.sz[s];
-            const float2 r1d = a.sr_df[s];
-            const dfv inv2w = df_div(inv2r, df_make(r1d.x, r1d.y));
+            const float2 ri = a.rinv_df[s];
+            const dfv inv2w = df_mul(inv2r, df_make(ri.x, ri.y));  // 1 / (2 r r1)
             PairDF g;
-            pair_geom_df(rt, zt, r1, z1, inv2w, active && valid, g);
+            // a lane past the unit's last target repeats the first target's pair (tc): its sums
+            // are never written, and its sequence takes the same regime as a real pair's
+            // instead of a full backward sweep
+            pair_geom_df(rt, zt, r1, z1, inv2w, valid, g);
             SeqSlot ys;
             ys.y = reinterpret_cast<float *>(y4 + lane);
             if ((Nq & 1) == 0) ys.put(Nq + 1, df_make(0.f, 0.f));  // pad of the last mode pair
             const bool fwd = pair_forward(g.t, a.df_tlim);
             dfv csum;
-            const dfv G0 = df_div(df_make(0.5f, 0.f), pair_agm_df(g, csum));
+            const dfv G0 = df_scale2(df_rcp(pair_agm_df(g, csum)), 0.5f);  // 1 / (2 AGM)
             const dfv sc = pair_sweep_df(g.chi, g.t, g.zero, inv2w, Nq, fwd, extra, G0, csum, gam2, gam4, ys);
             reinterpret_cast<int *>(p4 + NPP * 32)[lane] = (int)s;
             p4[lane] = bcast4(sc);
             if (GRAD) {
-                const dfv inv = df_div(df_make(1.f, 0.f), df_mul(g.rp2, g.rm2));
+                const dfv inv = df_rcp(df_mul(g.rp2, g.rm2));
                 const dfv ip = df_mul(g.rm2, inv), im = df_mul(g.rp2, inv);
                 const dfv As = df_mul(sc, df_add(ip, im)), Bs = df_mul(sc, df_sub(ip, im));
                 const dfv qf = df_sub(df_mul(g.dr, g.sr), df_mul(g.x, g.x));
@@ -1193,7 +1196,7 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
     a.nfield = fw ? p->nf : p->ns;
     a.sr = fw ? p->s_r : p->t_r;
     a.sz = fw ? p->s_z : p->t_z;
-    a.sr_df = fw ? p->s_rdf : p->t_rdf;
+    a.rinv_df = fw ? p->s_rinv : p->t_rinv;
     a.nsrc = fw ? p->ns : p->nf;
     const bool mix = p->precision == AFMM_MIXED;
     a.q_re = p->qs_re;
@@ -1302,12 +1305,16 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
             else
                 AFMM_TRY((launch_near_ws<false, false>(a, *p->rec, p->stream)));
         }
-    } else if (grad) {
-        AFMM_CUDA(cudaFuncSetAttribute(k_near2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_near2<true><<<grid, T, sm, p->stream>>>(a, *p->rec);
     } else {
-        AFMM_CUDA(cudaFuncSetAttribute(k_near2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_near2<false><<<grid, T, sm, p->stream>>>(a, *p->rec);
+        // the FP64 kernels evaluate the local expansions themselves (no separate L2P phase)
+        if (p->timing) cudaEventRecord(p->ev[AFMM_EV_L2P], p->stream);
+        if (grad) {
+            AFMM_CUDA(cudaFuncSetAttribute(k_near2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            k_near2<true><<<grid, T, sm, p->stream>>>(a, *p->rec);
+        } else {
+            AFMM_CUDA(cudaFuncSetAttribute(k_near2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            k_near2<false><<<grid, T, sm, p->stream>>>(a, *p->rec);
+        }
     }
     if (p->precision == AFMM_FP64_NATIVE) AFMM_LAUNCH_CHECK();
     if (a.part) {

@@ -232,7 +232,7 @@ static afmm_status scan_excl(const int64_t *in, int64_t *out, int64_t n, int64_t
 // ------------------------------------------------------------------------------------
 __global__ void k_gather_sorted(const unsigned long long *__restrict__ srt, int64_t n, const double *__restrict__ r,
                                 const double *__restrict__ z, double *__restrict__ rs, double *__restrict__ zs,
-                                float2 *__restrict__ rdf, int32_t *__restrict__ perm, uint32_t *__restrict__ key)
+                                float2 *__restrict__ rinv, int32_t *__restrict__ perm, uint32_t *__restrict__ key)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -242,8 +242,8 @@ __global__ void k_gather_sorted(const unsigned long long *__restrict__ srt, int6
     key[i] = (uint32_t)(v >> 32);
     rs[i] = r[idx];
     zs[i] = z[idx];
-    const dfv d = df_from_double(r[idx]);  // r as an FP32 pair, for the FP32-pair near field
-    rdf[i] = make_float2(d.hi, d.lo);
+    const dfv d = df_from_double(1.0 / r[idx]);  // 1 / r as an FP32 pair, for the FP32-pair near field
+    rinv[i] = make_float2(d.hi, d.lo);
 }
 
 // number of distinct level-l prefixes among sorted level-16 keys, l = 2..16
@@ -574,8 +574,8 @@ afmm_status build_tree(afmm_plan p, const double *src_r, const double *src_z, co
     AFMM_TRY(dalloc_t(p, &p->t_z, nf));
     AFMM_TRY(dalloc_t(p, &p->t_perm, nf));
     AFMM_TRY(dalloc_t(p, &p->t_key, nf));
-    AFMM_TRY(dalloc_t(p, &p->s_rdf, ns));
-    AFMM_TRY(dalloc_t(p, &p->t_rdf, nf));
+    AFMM_TRY(dalloc_t(p, &p->s_rinv, ns));
+    AFMM_TRY(dalloc_t(p, &p->t_rinv, nf));
     for (int set = 0; set < 2; ++set) {
         int64_t n = set == 0 ? ns : nf;
         int64_t npad = pow2_at_least(n);
@@ -584,9 +584,9 @@ afmm_status build_tree(afmm_plan p, const double *src_r, const double *src_z, co
         AFMM_LAUNCH_CHECK();
         AFMM_TRY(bitonic_sort(srt, npad, st));
         if (set == 0)
-            k_gather_sorted<<<nblk(n), 256, 0, st>>>(srt, n, r, z, p->s_r, p->s_z, p->s_rdf, p->s_perm, p->s_key);
+            k_gather_sorted<<<nblk(n), 256, 0, st>>>(srt, n, r, z, p->s_r, p->s_z, p->s_rinv, p->s_perm, p->s_key);
         else
-            k_gather_sorted<<<nblk(n), 256, 0, st>>>(srt, n, r, z, p->t_r, p->t_z, p->t_rdf, p->t_perm, p->t_key);
+            k_gather_sorted<<<nblk(n), 256, 0, st>>>(srt, n, r, z, p->t_r, p->t_z, p->t_rinv, p->t_perm, p->t_key);
         AFMM_LAUNCH_CHECK();
     }
     // ---- depth

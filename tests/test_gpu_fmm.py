@@ -107,3 +107,24 @@ def test_fmm_is_deterministic():
     a = to_np(*pl.eval(q_re, q_im))
     b = to_np(*pl.eval(q_re, q_im))
     np.testing.assert_array_equal(a[0], b[0])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "fp64_native"])
+def test_phase_timing_every_precision(precision):
+    """Phase timing (CUDA events around each phase) in every precision, twice in a row, with
+    and without the gradient: the FP64-native kernels fold the local expansions into the
+    near-field kernel, so their L2P phase is empty and must not leave an error behind."""
+    from paper_2301_01179_gb300 import binding
+    w = W.make("cfg1", ns=1500, nf=1200, n_modes=5)
+    sr, sz, tr, tz = to_dev(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"])
+    pl = binding.Plan(sr, sz, tr, tz, 5, order=6, leaf_size=32, precision=precision)
+    pl.set_timing(True)
+    q_re, q_im = to_dev(w["q_re"], w["q_im"])
+    for f in (pl.eval, pl.grad, pl.eval):
+        f(q_re, q_im)
+        t = pl.timing()
+        assert all(v >= 0.0 for v in t.values()), t
+        assert t["near"] > 0.0 and t["total"] >= t["near"], t
+    if precision == "fp64_native":  # two events back to back: microseconds apart
+        assert t["l2p"] < 0.1 * t["near"], t
+    pl.close()
