@@ -278,4 +278,29 @@ __device__ __forceinline__ void df2_acc_n(float2 &S, float2 &E, df2 a, df2 b, fl
     S = s;
 }
 
+// a * b + c * d componentwise, given na = -a.hi and nc = -c.hi: both products with their
+// exact errors (FMA), one two-sum of the high parts (in negated form, exact under
+// round-to-nearest), the low parts added, one renormalisation; returns the sum and sets
+// nhi = -(its high part)
+__device__ __forceinline__ df2 df2_dot2_np(df2 a, float2 na, df2 b, df2 c, float2 nc, df2 d, float2 &nhi)
+{
+    const float2 np1 = fmul2(na, b.hi);  // -p1
+    float2 e1 = ffma2(a.hi, b.hi, np1);  // a.hi b.hi - p1, exact
+    e1 = ffma2(a.hi, b.lo, e1);
+    e1 = ffma2(a.lo, b.hi, e1);
+    const float2 np2 = fmul2(nc, d.hi);  // -p2
+    float2 e2 = ffma2(c.hi, d.hi, np2);
+    e2 = ffma2(c.hi, d.lo, e2);
+    e2 = ffma2(c.lo, d.hi, e2);
+    const float2 ns = fadd2(np1, np2);  // -(p1 + p2), rounded
+    const float2 v = fsub2(ns, np1);
+    const float2 nerr = fadd2(fsub2(np1, fsub2(ns, v)), fsub2(np2, v));  // -(p1 + p2 - s)
+    const float2 lo = fsub2(fadd2(e1, e2), nerr);
+    df2 r;
+    r.hi = fsub2(lo, ns);                  // s + lo
+    r.lo = fsub2(lo, fadd2(r.hi, ns));     // lo - (hi - s)
+    nhi = fsub2(ns, lo);
+    return r;
+}
+
 }  // namespace afmm

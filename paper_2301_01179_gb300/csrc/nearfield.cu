@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
 {
     static_assert(MPER % 2 == 0, "consumers work on mode pairs");
     extern __shared__ __align__(16) unsigned char smem_ws[];
-    constexpr int NPP = GRAD ? 5 : 1;  // per-pair factors: scale (, x, qfac, A, B)
+    constexpr int NPP = GRAD ? 4 : 0;  // per-pair factors of the gradient: x, qfac, A, B
     constexpr int NC = GRAD ? 6 : 2;   // accumulated components
     constexpr int NP = MPER / 2;       // mode pairs per consumer
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -677,18 +677,17 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
             const bool fwd = pair_forward(g.t, a.df_tlim);
             dfv csum;
             const dfv G0 = df_scale2(df_rcp(pair_agm_df(g, csum)), 0.5f);  // 1 / (2 AGM)
-            const dfv sc = pair_sweep_df(g.chi, g.t, g.zero, inv2w, Nq, fwd, extra, G0, csum, gam2, gam4, ys);
+            pair_sweep_df(g.chi, g.t, g.zero, inv2w, Nq, fwd, extra, G0, csum, gam2, gam4, ys);
             reinterpret_cast<int *>(p4 + NPP * 32)[lane] = (int)s;
-            p4[lane] = bcast4(sc);
             if (GRAD) {
                 const dfv inv = df_rcp(df_mul(g.rp2, g.rm2));
                 const dfv ip = df_mul(g.rm2, inv), im = df_mul(g.rp2, inv);
-                const dfv As = df_mul(sc, df_add(ip, im)), Bs = df_mul(sc, df_sub(ip, im));
+                const dfv As = df_add(ip, im), Bs = df_sub(ip, im);
                 const dfv qf = df_sub(df_mul(g.dr, g.sr), df_mul(g.x, g.x));
-                p4[32 + lane] = bcast4(g.x);
-                p4[64 + lane] = bcast4(qf);
-                p4[96 + lane] = bcast4(As);
-                p4[128 + lane] = bcast4(Bs);
+                p4[lane] = bcast4(g.x);
+                p4[32 + lane] = bcast4(qf);
+                p4[64 + lane] = bcast4(As);
+                p4[96 + lane] = bcast4(Bs);
             }
             __syncwarp();
             if (lane == 0 && !(a.inject_timeout && k == 0)) mbar_arrive(&s_full[b]);
@@ -713,20 +712,22 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
         const float4 *y4 = reinterpret_cast<const float4 *>(sl);
         const float4 *p4 = y4 + (size_t)npair * 32;
         const int64_t s = reinterpret_cast<const int *>(p4 + NPP * 32)[lane];
-        const df2 SC = df2_from4(p4[lane]);
-        df2 GX = SC, QF = SC, AS = SC, BS = SC;
+        // the slot holds y_n = G_n / c_n (the amplitudes carry c_n), so the potential's
+        // products need no per-pair factor
+        const df2 Z2 = df2_bcast(df_make(0.f, 0.f));
+        df2 GX = Z2, QF = Z2, AS = Z2, BS = Z2;
         dfv yprev = df_make(0.f, 0.f);
         if (GRAD) {
-            GX = df2_from4(p4[32 + lane]);
-            QF = df2_from4(p4[64 + lane]);
-            AS = df2_from4(p4[96 + lane]);
-            BS = df2_from4(p4[128 + lane]);
+            GX = df2_from4(p4[lane]);
+            QF = df2_from4(p4[32 + lane]);
+            AS = df2_from4(p4[64 + lane]);
+            BS = df2_from4(p4[96 + lane]);
             // y_{n0 - 1}: the second mode of the previous pair; y_{-1} := y_1
             yprev = df2_y(df2_from4(y4[(m0 == 0 ? 0 : m0 - 1) * 32 + lane]));
         }
         if (MIX) {
             // FP32 products of the pairs' high words, Kahan-compensated sums (aE: compensation)
-            const float2 SCf = SC.hi, GXf = GX.hi, QFf = QF.hi;
+            const float2 GXf = GX.hi, QFf = QF.hi;
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
                 // no branch per mode pair (the compiler interleaves the pairs' chains): a pair
@@ -735,7 +736,7 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
                 {
                     const df2 Y = df2_from4(y4[m * 32 + lane]);
                     const float2 QR = a.q32_re[(size_t)m * a.nsrc + s], QI = a.q32_im[(size_t)m * a.nsrc + s];
-                    const float2 G = fmul2(SCf, Y.hi);
+                    const float2 G = Y.hi;
                     kahan2(aS[0][j], aE[0][j], fmul2(QR, G));
                     kahan2(aS[1][j], aE[1][j], fmul2(QI, G));
                     if (GRAD) {
@@ -755,8 +756,7 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
             // negated high words of the per-slot factors (the products below need no
             // negation instructions: see df2_mul_np, df2_acc_n)
             const float2 NEG = make_float2(-1.f, -1.f);
-            const float2 nSC = fmul2(SC.hi, NEG);
-            const float2 nAS = fmul2(AS.hi, NEG), nGX = fmul2(GX.hi, NEG), nQF = fmul2(QF.hi, NEG);
+            float2 nyprev = make_float2(0.f, 0.f);  // -(high word of yprev)
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
                 const int m = 2 * (m0 + j) < nm ? m0 + j : mlast;  // as above
@@ -764,22 +764,22 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
                     const df2 Y = df2_from4(y4[m * 32 + lane]);
                     const df2 QR = df2_from4(a.qdf_re[(size_t)m * a.nsrc + s]);
                     const df2 QI = df2_from4(a.qdf_im[(size_t)m * a.nsrc + s]);
-                    float2 nG;
-                    const df2 G = df2_mul_np(SC, Y, fmul2(nSC, Y.hi), nG);
-                    df2_acc_n(aS[0][j], aE[0][j], QR, G, nG);
-                    df2_acc_n(aS[1][j], aE[1][j], QI, G, nG);
+                    const float2 nY = fmul2(Y.hi, NEG);
+                    df2_acc_n(aS[0][j], aE[0][j], QR, Y, nY);
+                    df2_acc_n(aS[1][j], aE[1][j], QI, Y, nY);
                     if (GRAD) {
                         // w_n = y_n A + rho_n y_{n-1} B, the derivative recursion's weight
+                        if (j == 0) nyprev = make_float2(-yprev.hi, 0.f);
                         const df2 YP = df2_pack(yprev, df2_x(Y));
+                        const float2 nYP = make_float2(nyprev.x, nY.x);
                         yprev = df2_y(Y);
-                        float2 nT, nU, nV, nXW, nQW;
+                        nyprev.x = nY.y;
+                        float2 nT, nWT, nXW, nQW;
                         const df2 R = df2_from4(rho4[m]);
-                        const df2 T = df2_mul_np(R, YP, fmul2(fmul2(R.hi, NEG), YP.hi), nT);
-                        const df2 U = df2_mul_np(Y, AS, fmul2(Y.hi, nAS), nU);
-                        const df2 V = df2_mul_np(T, BS, fmul2(nT, BS.hi), nV);
-                        const df2 WT = df2_add(U, V);
-                        const df2 XW = df2_mul_np(GX, WT, fmul2(nGX, WT.hi), nXW);
-                        const df2 QW = df2_mul_np(QF, WT, fmul2(nQF, WT.hi), nQW);
+                        const df2 T = df2_mul_np(R, YP, fmul2(R.hi, nYP), nT);
+                        const df2 WT = df2_dot2_np(Y, nY, AS, T, nT, BS, nWT);
+                        const df2 XW = df2_mul_np(WT, GX, fmul2(nWT, GX.hi), nXW);
+                        const df2 QW = df2_mul_np(WT, QF, fmul2(nWT, QF.hi), nQW);
                         df2_acc_n(aS[2 % NC][j], aE[2 % NC][j], QR, QW, nQW);
                         df2_acc_n(aS[3 % NC][j], aE[3 % NC][j], QI, QW, nQW);
                         df2_acc_n(aS[4 % NC][j], aE[4 % NC][j], QR, XW, nXW);
@@ -958,7 +958,7 @@ __global__ void __launch_bounds__(L2P_WARPS * 32) k_l2p(const NearArgs a)
 static size_t nws_slot_bytes(int nm, int grad)
 {
     const int Nq = (grad && nm < 2) ? 1 : nm - 1;
-    const int npair = (Nq + 2) / 2, npp = grad ? 5 : 1;
+    const int npair = (Nq + 2) / 2, npp = grad ? 4 : 0;
     return (size_t)(npair + npp) * 32 * 16 + 32 * sizeof(int);
 }
 static size_t nws_table_bytes()

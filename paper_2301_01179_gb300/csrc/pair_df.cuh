@@ -92,22 +92,22 @@ __device__ __forceinline__ dfv pair_agm_df(const PairDF &g, dfv &csum)
 }
 
 // The sweep of the scaled recursion (Eq. gfunc:recursion) from the start values G0 and
-// csum: writes y_n (n = 0..N) into the slot and returns the df factor s with
-// G_n = s * c_n * y_n.  gam2: recursion constants gam_n as FP32 pairs, gam4 the same by
-// mode pair (shared memory).
+// csum: writes y_n = G_n / c_n (n = 0..N) into the slot, times zero (0 for a pair that must
+// not contribute).  gam2: recursion constants gam_n as FP32 pairs, gam4 the same by mode
+// pair (shared memory).
 //
 // Forward lanes: two steps per iteration, gam_n chi and gam_{n+1} chi as one packed
 // product, one 16-byte store per mode pair; every lane of a warp that has a forward lane
 // runs it (a backward lane's values, possibly overflowing, are overwritten by its own
 // sweep).  Backward lanes (Miller): from y_L = 0, y_{L-1} = 2^-e (e ~ the sweep's growth in
 // bits, at most 100) down to y_0, rescaled exactly by 2^-100 whenever |y| passes 2^60,
-// normalised by G0 / y_0.  The start is
+// then normalised in place by G0 / y_0.  The start is
 // L = max(N + 2, N / 2 + ceil(extra / acosh chi) + 2): the relative error of y_n,
 // e^{-2 a (L - n)} (a = acosh chi), is then below e^{-2 extra} measured against the
 // pair's G^(0), since |G^(n) / G^(0)| ~ e^{-n a}.
-__device__ __forceinline__ dfv pair_sweep_df(dfv chi, float t, float zero, dfv inv2w, int N, bool fwd, float extra,
-                                             dfv G0, dfv csum, const float2 *__restrict__ gam2,
-                                             const float4 *__restrict__ gam4, const SeqSlot ys)
+__device__ __forceinline__ void pair_sweep_df(dfv chi, float t, float zero, dfv inv2w, int N, bool fwd, float extra,
+                                              dfv G0, dfv csum, const float2 *__restrict__ gam2,
+                                              const float4 *__restrict__ gam4, const SeqSlot ys)
 {
     const bool allf = __all_sync(0xffffffffu, fwd);
     if (allf || __any_sync(0xffffffffu, fwd)) {
@@ -129,9 +129,11 @@ __device__ __forceinline__ dfv pair_sweep_df(dfv chi, float t, float zero, dfv i
             const dfv ya = df_sub(df_mul(df_mul(df_make(gam2[n].x, gam2[n].y), chi), ym1), ym2);
             yp[(n >> 1) * 32] = make_float4(ya.hi, 0.f, ya.lo, 0.f);
         }
-        if (allf) return df_make(zero, 0.f);
+        if (allf) return;
     }
-    if (fwd) return df_make(zero, 0.f);
+    // a forward lane's zero is 1: a pair that must not contribute (coincident, or a padding
+    // source) has chi - 1 >= 2 and takes the backward branch
+    if (fwd) return;
     // backward lane
     const float af = acosh_chi(t);
     const float lf = ceilf(extra / fmaxf(af, 1e-6f) - 0.5f * (float)N);  // L - N - 2 >= extra / a - N / 2
@@ -160,8 +162,10 @@ __device__ __forceinline__ dfv pair_sweep_df(dfv chi, float t, float zero, dfv i
             for (int m = idx; m <= N; ++m) ys.put(m, df_scale2(ys.get(m), s100));
         }
     }
-    dfv sc = df_div(G0, ys.get(0));
-    return df_make(sc.hi * zero, sc.lo * zero);
+    const dfv y0n = ys.get(0);
+    dfv sc = df_div(G0, y0n);
+    sc = df_make(sc.hi * zero, sc.lo * zero);
+    for (int m = 0; m <= N; ++m) ys.put(m, df_mul(ys.get(m), sc));
 }
 
 }  // namespace afmm
