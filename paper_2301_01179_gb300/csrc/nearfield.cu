@@ -699,7 +699,6 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
     const int n0 = a.mode_lo + warp * MPER;  // mode_lo is even
     const int m0 = n0 / 2;
     const int nhi = a.mode_hi;
-    const int mlast = (nm - 1) / 2;  // last mode pair
     float2 aS[NC][NP], aE[NC][NP];  // .x mode 2m, .y mode 2m + 1
 #pragma unroll
     for (int c = 0; c < NC; ++c)
@@ -725,67 +724,80 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
             // y_{n0 - 1}: the second mode of the previous pair; y_{-1} := y_1
             yprev = df2_y(df2_from4(y4[(m0 == 0 ? 0 : m0 - 1) * 32 + lane]));
         }
+        // The last consumer of an odd number of mode pairs has one pair fewer and takes a
+        // warp-uniform branch that skips it: that warp shares its SM sub-partition with two
+        // other consumers (9 consumer warps over 4 sub-partitions), so halving its work
+        // evens the sub-partitions' FMA-pipe load.  Full warps run the pairs unrolled, so
+        // the compiler interleaves their chains.
+        const bool fullp = 2 * (m0 + NP - 1) < nhi;
         if (MIX) {
             // FP32 products of the pairs' high words, Kahan-compensated sums (aE: compensation)
             const float2 GXf = GX.hi, QFf = QF.hi;
-#pragma unroll
-            for (int j = 0; j < NP; ++j) {
-                // no branch per mode pair (the compiler interleaves the pairs' chains): a pair
-                // past the last mode reads the last pair and its sums are not written
-                const int m = 2 * (m0 + j) < nm ? m0 + j : mlast;
-                {
-                    const df2 Y = df2_from4(y4[m * 32 + lane]);
-                    const float2 QR = a.q32_re[(size_t)m * a.nsrc + s], QI = a.q32_im[(size_t)m * a.nsrc + s];
-                    const float2 G = Y.hi;
-                    kahan2(aS[0][j], aE[0][j], fmul2(QR, G));
-                    kahan2(aS[1][j], aE[1][j], fmul2(QI, G));
-                    if (GRAD) {
-                        // y_n A + rho_n y_{n-1} B cancels for near pairs (A ~ -B): FP32 pairs
-                        const df2 YP = df2_pack(yprev, df2_x(Y));
-                        yprev = df2_y(Y);
-                        const float2 wt = df2_add(df2_mul(Y, AS), df2_mul(df2_mul(df2_from4(rho4[m]), YP), BS)).hi;
-                        const float2 xw = fmul2(GXf, wt), qw = fmul2(QFf, wt);
-                        kahan2(aS[2 % NC][j], aE[2 % NC][j], fmul2(QR, qw));
-                        kahan2(aS[3 % NC][j], aE[3 % NC][j], fmul2(QI, qw));
-                        kahan2(aS[4 % NC][j], aE[4 % NC][j], fmul2(QR, xw));
-                        kahan2(aS[5 % NC][j], aE[5 % NC][j], fmul2(QI, xw));
-                    }
+            auto step = [&](const int j) {
+                const int m = m0 + j;
+                const df2 Y = df2_from4(y4[m * 32 + lane]);
+                const float2 QR = a.q32_re[(size_t)m * a.nsrc + s], QI = a.q32_im[(size_t)m * a.nsrc + s];
+                const float2 G = Y.hi;
+                kahan2(aS[0][j], aE[0][j], fmul2(QR, G));
+                kahan2(aS[1][j], aE[1][j], fmul2(QI, G));
+                if (GRAD) {
+                    // y_n A + rho_n y_{n-1} B cancels for near pairs (A ~ -B): FP32 pairs
+                    const df2 YP = df2_pack(yprev, df2_x(Y));
+                    yprev = df2_y(Y);
+                    const float2 wt = df2_add(df2_mul(Y, AS), df2_mul(df2_mul(df2_from4(rho4[m]), YP), BS)).hi;
+                    const float2 xw = fmul2(GXf, wt), qw = fmul2(QFf, wt);
+                    kahan2(aS[2 % NC][j], aE[2 % NC][j], fmul2(QR, qw));
+                    kahan2(aS[3 % NC][j], aE[3 % NC][j], fmul2(QI, qw));
+                    kahan2(aS[4 % NC][j], aE[4 % NC][j], fmul2(QR, xw));
+                    kahan2(aS[5 % NC][j], aE[5 % NC][j], fmul2(QI, xw));
                 }
+            };
+            if (fullp) {
+#pragma unroll
+                for (int j = 0; j < NP; ++j) step(j);
+            } else {
+#pragma unroll
+                for (int j = 0; j < NP; ++j)
+                    if (2 * (m0 + j) < nhi) step(j);
             }
         } else {
             // negated high words of the per-slot factors (the products below need no
             // negation instructions: see df2_mul_np, df2_acc_n)
             const float2 NEG = make_float2(-1.f, -1.f);
-            float2 nyprev = make_float2(0.f, 0.f);  // -(high word of yprev)
-#pragma unroll
-            for (int j = 0; j < NP; ++j) {
-                const int m = 2 * (m0 + j) < nm ? m0 + j : mlast;  // as above
-                {
-                    const df2 Y = df2_from4(y4[m * 32 + lane]);
-                    const df2 QR = df2_from4(a.qdf_re[(size_t)m * a.nsrc + s]);
-                    const df2 QI = df2_from4(a.qdf_im[(size_t)m * a.nsrc + s]);
-                    const float2 nY = fmul2(Y.hi, NEG);
-                    df2_acc_n(aS[0][j], aE[0][j], QR, Y, nY);
-                    df2_acc_n(aS[1][j], aE[1][j], QI, Y, nY);
-                    if (GRAD) {
-                        // w_n = y_n A + rho_n y_{n-1} B, the derivative recursion's weight
-                        if (j == 0) nyprev = make_float2(-yprev.hi, 0.f);
-                        const df2 YP = df2_pack(yprev, df2_x(Y));
-                        const float2 nYP = make_float2(nyprev.x, nY.x);
-                        yprev = df2_y(Y);
-                        nyprev.x = nY.y;
-                        float2 nT, nWT, nXW, nQW;
-                        const df2 R = df2_from4(rho4[m]);
-                        const df2 T = df2_mul_np(R, YP, fmul2(R.hi, nYP), nT);
-                        const df2 WT = df2_dot2_np(Y, nY, AS, T, nT, BS, nWT);
-                        const df2 XW = df2_mul_np(WT, GX, fmul2(nWT, GX.hi), nXW);
-                        const df2 QW = df2_mul_np(WT, QF, fmul2(nWT, QF.hi), nQW);
-                        df2_acc_n(aS[2 % NC][j], aE[2 % NC][j], QR, QW, nQW);
-                        df2_acc_n(aS[3 % NC][j], aE[3 % NC][j], QI, QW, nQW);
-                        df2_acc_n(aS[4 % NC][j], aE[4 % NC][j], QR, XW, nXW);
-                        df2_acc_n(aS[5 % NC][j], aE[5 % NC][j], QI, XW, nXW);
-                    }
+            float2 nyprev = make_float2(-yprev.hi, 0.f);  // -(high word of yprev)
+            auto step = [&](const int j) {
+                const int m = m0 + j;
+                const df2 Y = df2_from4(y4[m * 32 + lane]);
+                const df2 QR = df2_from4(a.qdf_re[(size_t)m * a.nsrc + s]);
+                const df2 QI = df2_from4(a.qdf_im[(size_t)m * a.nsrc + s]);
+                const float2 nY = fmul2(Y.hi, NEG);
+                df2_acc_n(aS[0][j], aE[0][j], QR, Y, nY);
+                df2_acc_n(aS[1][j], aE[1][j], QI, Y, nY);
+                if (GRAD) {
+                    // w_n = y_n A + rho_n y_{n-1} B, the derivative recursion's weight
+                    const df2 YP = df2_pack(yprev, df2_x(Y));
+                    const float2 nYP = make_float2(nyprev.x, nY.x);
+                    yprev = df2_y(Y);
+                    nyprev.x = nY.y;
+                    float2 nT, nWT, nXW, nQW;
+                    const df2 R = df2_from4(rho4[m]);
+                    const df2 T = df2_mul_np(R, YP, fmul2(R.hi, nYP), nT);
+                    const df2 WT = df2_dot2_np(Y, nY, AS, T, nT, BS, nWT);
+                    const df2 XW = df2_mul_np(WT, GX, fmul2(nWT, GX.hi), nXW);
+                    const df2 QW = df2_mul_np(WT, QF, fmul2(nWT, QF.hi), nQW);
+                    df2_acc_n(aS[2 % NC][j], aE[2 % NC][j], QR, QW, nQW);
+                    df2_acc_n(aS[3 % NC][j], aE[3 % NC][j], QI, QW, nQW);
+                    df2_acc_n(aS[4 % NC][j], aE[4 % NC][j], QR, XW, nXW);
+                    df2_acc_n(aS[5 % NC][j], aE[5 % NC][j], QI, XW, nXW);
                 }
+            };
+            if (fullp) {
+#pragma unroll
+                for (int j = 0; j < NP; ++j) step(j);
+            } else {
+#pragma unroll
+                for (int j = 0; j < NP; ++j)
+                    if (2 * (m0 + j) < nhi) step(j);
             }
         }
         __syncwarp();
