@@ -268,6 +268,53 @@ def fwd_bwd(kind, precision, steps, warmup, dev):
             "modal_ring_interactions_per_s": 2.0 * ns * nf * nm / (t_step / 1e3)}
 
 
+def mixed_vs_fp64(kind, steps, dev):
+    """The MIXED path against the FP64 path on a configuration (the near-singular curve
+    workload cfg3 by default): the FMM potential and field gradient step of each (plan
+    creation included) timed on the device, and the MIXED error per mode and component,
+    eps^(n) = max |mixed - fp64| / max |fp64| over the field points.  The FP64 path matches
+    the oracle to 1e-10 per mode (parity tests), so this is the error against the oracle up
+    to that."""
+    import numpy as np
+    import torch
+    from paper_2301_01179_gb300 import binding, workloads as W
+    w = W.make(kind)
+    ns, nf, nm = w["src_r"].size, w["tgt_r"].size, w["n_modes"]
+
+    def d(a):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+
+    sr, sz, tr, tz, qr, qi = map(d, (w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], w["q_re"], w["q_im"]))
+    res, ms = {}, {}
+    for prec in ("fp64", "mixed"):
+        def step():
+            pl = binding.Plan(sr, sz, tr, tz, nm, order=w["order"], leaf_size=w["leaf"], precision=prec)
+            out = pl.grad(qr, qi)
+            pl.close()
+            return out
+        step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            out = step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms[prec] = e0.elapsed_time(e1) / steps
+        res[prec] = [o.cpu().numpy() for o in out]
+        del out
+    eps = {}
+    for name, c in (("potential", 0), ("d_dr", 2), ("d_dz", 4)):
+        a = res["mixed"][c] + 1j * res["mixed"][c + 1]
+        b = res["fp64"][c] + 1j * res["fp64"][c + 1]
+        den = np.max(np.abs(b), axis=1)
+        eps[name] = [float(x) for x in np.max(np.abs(a - b), axis=1) / np.where(den > 0, den, 1.0)]
+    return {"workload": "%s: %d x %d, modes 0..%d, order %d, leaf %d" % (kind, ns, nf, nm - 1, w["order"], w["leaf"]),
+            "step": "plan + FMM potential and field gradient", "fp64_ms": ms["fp64"], "mixed_ms": ms["mixed"],
+            "speedup": ms["fp64"] / ms["mixed"], "steps": steps,
+            "eps_max": {k: max(v) for k, v in eps.items()}, "eps_per_mode": eps}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -438,6 +485,11 @@ def run_ours(args):
             except Exception as exc:  # an extra must not cost the headline line
                 fb[kind] = {"error": str(exc)[:200]}
         extra["fwd_bwd"] = fb
+        # the mixed-precision path on the near-singular curve workload (not the headline)
+        try:
+            extra["mixed_vs_fp64"] = mixed_vs_fp64("cfg3", 2, dev)
+        except Exception as exc:
+            extra["mixed_vs_fp64"] = {"error": str(exc)[:200]}
 
     line = None
     if rank == 0:
