@@ -543,7 +543,13 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
 {
     static_assert(MPER % 2 == 0, "consumers work on mode pairs");
     extern __shared__ __align__(16) unsigned char smem_ws[];
-    constexpr int NPP = GRAD ? 4 : 0;  // per-pair factors of the gradient: x, qfac, A, B
+    // The FP64 path folds the backward sweeps' scale into the sequence (one product less
+    // per mode pair for the consumers); MIXED keeps it as a per-pair factor: its consumers'
+    // FP32 products gain little from the fold, while the in-place scaling costs its
+    // producers N + 1 pair products per backward lane (measured on 65 modes near the axis).
+    constexpr bool FOLD = !MIX;
+    constexpr int PB = FOLD ? 0 : 1;                 // row of the gradient factors
+    constexpr int NPP = PB + (GRAD ? 4 : 0);         // per-pair factors: (scale,) x, qfac, A, B
     constexpr int NC = GRAD ? 6 : 2;   // accumulated components
     constexpr int NP = MPER / 2;       // mode pairs per consumer
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -677,17 +683,22 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
             const bool fwd = pair_forward(g.t, a.df_tlim);
             dfv csum;
             const dfv G0 = df_scale2(df_rcp(pair_agm_df(g, csum)), 0.5f);  // 1 / (2 AGM)
-            pair_sweep_df(g.chi, g.t, g.zero, inv2w, Nq, fwd, extra, G0, csum, gam2, gam4, ys);
+            const dfv sc = pair_sweep_df<FOLD>(g.chi, g.t, g.zero, inv2w, Nq, fwd, extra, G0, csum, gam2, gam4, ys);
             reinterpret_cast<int *>(p4 + NPP * 32)[lane] = (int)s;
+            if (!FOLD) p4[lane] = bcast4(sc);
             if (GRAD) {
                 const dfv inv = df_rcp(df_mul(g.rp2, g.rm2));
                 const dfv ip = df_mul(g.rm2, inv), im = df_mul(g.rp2, inv);
-                const dfv As = df_add(ip, im), Bs = df_sub(ip, im);
+                dfv As = df_add(ip, im), Bs = df_sub(ip, im);
+                if (!FOLD) {
+                    As = df_mul(sc, As);
+                    Bs = df_mul(sc, Bs);
+                }
                 const dfv qf = df_sub(df_mul(g.dr, g.sr), df_mul(g.x, g.x));
-                p4[lane] = bcast4(g.x);
-                p4[32 + lane] = bcast4(qf);
-                p4[64 + lane] = bcast4(As);
-                p4[96 + lane] = bcast4(Bs);
+                p4[32 * PB + lane] = bcast4(g.x);
+                p4[32 * (PB + 1) + lane] = bcast4(qf);
+                p4[32 * (PB + 2) + lane] = bcast4(As);
+                p4[32 * (PB + 3) + lane] = bcast4(Bs);
             }
             __syncwarp();
             if (lane == 0 && !(a.inject_timeout && k == 0)) mbar_arrive(&s_full[b]);
@@ -716,11 +727,12 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
         const df2 Z2 = df2_bcast(df_make(0.f, 0.f));
         df2 GX = Z2, QF = Z2, AS = Z2, BS = Z2;
         dfv yprev = df_make(0.f, 0.f);
+        const float2 SCf = FOLD ? Z2.hi : make_float2(p4[lane].x, p4[lane].y);  // MIXED: the scale
         if (GRAD) {
-            GX = df2_from4(p4[lane]);
-            QF = df2_from4(p4[32 + lane]);
-            AS = df2_from4(p4[64 + lane]);
-            BS = df2_from4(p4[96 + lane]);
+            GX = df2_from4(p4[32 * PB + lane]);
+            QF = df2_from4(p4[32 * (PB + 1) + lane]);
+            AS = df2_from4(p4[32 * (PB + 2) + lane]);
+            BS = df2_from4(p4[32 * (PB + 3) + lane]);
             // y_{n0 - 1}: the second mode of the previous pair; y_{-1} := y_1
             yprev = df2_y(df2_from4(y4[(m0 == 0 ? 0 : m0 - 1) * 32 + lane]));
         }
@@ -737,7 +749,7 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
                 const int m = m0 + j;
                 const df2 Y = df2_from4(y4[m * 32 + lane]);
                 const float2 QR = a.q32_re[(size_t)m * a.nsrc + s], QI = a.q32_im[(size_t)m * a.nsrc + s];
-                const float2 G = Y.hi;
+                const float2 G = fmul2(SCf, Y.hi);
                 kahan2(aS[0][j], aE[0][j], fmul2(QR, G));
                 kahan2(aS[1][j], aE[1][j], fmul2(QI, G));
                 if (GRAD) {
@@ -967,10 +979,10 @@ __global__ void __launch_bounds__(L2P_WARPS * 32) k_l2p(const NearArgs a)
 }
 
 // shared memory of k_near_ws: tables + ring of nbuf slots
-static size_t nws_slot_bytes(int nm, int grad)
+static size_t nws_slot_bytes(int nm, int grad, int mix)
 {
     const int Nq = (grad && nm < 2) ? 1 : nm - 1;
-    const int npair = (Nq + 2) / 2, npp = grad ? 4 : 0;
+    const int npair = (Nq + 2) / 2, npp = (mix ? 1 : 0) + (grad ? 4 : 0);  // as NPP in k_near_ws
     return (size_t)(npair + npp) * 32 * 16 + 32 * sizeof(int);
 }
 static size_t nws_table_bytes()
@@ -1002,7 +1014,7 @@ template <bool GRAD, int MPER, bool MIX>
 static afmm_status launch_near_ws_k(const NearArgs &a, const RecTab &tab, cudaStream_t st)
 {
     const int ncons = (a.mode_hi - a.mode_lo + MPER - 1) / MPER;
-    const size_t slot = nws_slot_bytes(a.nmodes, GRAD), tabs = nws_table_bytes();
+    const size_t slot = nws_slot_bytes(a.nmodes, GRAD, MIX), tabs = nws_table_bytes();
     const size_t budget = 200 * 1024;
     int nbuf = (int)((budget - tabs) / slot);
     if (nbuf > NWS_BMAX) nbuf = NWS_BMAX;

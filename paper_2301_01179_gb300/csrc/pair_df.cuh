@@ -92,9 +92,11 @@ __device__ __forceinline__ dfv pair_agm_df(const PairDF &g, dfv &csum)
 }
 
 // The sweep of the scaled recursion (Eq. gfunc:recursion) from the start values G0 and
-// csum: writes y_n = G_n / c_n (n = 0..N) into the slot, times zero (0 for a pair that must
-// not contribute).  gam2: recursion constants gam_n as FP32 pairs, gam4 the same by mode
-// pair (shared memory).
+// csum: writes y_n (n = 0..N) into the slot and returns the factor s with G_n = s c_n y_n
+// times zero (0 for a pair that must not contribute).  With FOLD the backward lanes apply
+// s in place, so that the slot holds y_n = G_n / c_n on every lane (a forward lane's s is
+// 1) and the return value is not needed.  gam2: recursion constants gam_n as FP32 pairs,
+// gam4 the same by mode pair (shared memory).
 //
 // Forward lanes: two steps per iteration, gam_n chi and gam_{n+1} chi as one packed
 // product, one 16-byte store per mode pair; every lane of a warp that has a forward lane
@@ -105,9 +107,10 @@ __device__ __forceinline__ dfv pair_agm_df(const PairDF &g, dfv &csum)
 // L = max(N + 2, N / 2 + ceil(extra / acosh chi) + 2): the relative error of y_n,
 // e^{-2 a (L - n)} (a = acosh chi), is then below e^{-2 extra} measured against the
 // pair's G^(0), since |G^(n) / G^(0)| ~ e^{-n a}.
-__device__ __forceinline__ void pair_sweep_df(dfv chi, float t, float zero, dfv inv2w, int N, bool fwd, float extra,
-                                              dfv G0, dfv csum, const float2 *__restrict__ gam2,
-                                              const float4 *__restrict__ gam4, const SeqSlot ys)
+template <bool FOLD>
+__device__ __forceinline__ dfv pair_sweep_df(dfv chi, float t, float zero, dfv inv2w, int N, bool fwd, float extra,
+                                             dfv G0, dfv csum, const float2 *__restrict__ gam2,
+                                             const float4 *__restrict__ gam4, const SeqSlot ys)
 {
     const bool allf = __all_sync(0xffffffffu, fwd);
     if (allf || __any_sync(0xffffffffu, fwd)) {
@@ -129,11 +132,11 @@ __device__ __forceinline__ void pair_sweep_df(dfv chi, float t, float zero, dfv 
             const dfv ya = df_sub(df_mul(df_mul(df_make(gam2[n].x, gam2[n].y), chi), ym1), ym2);
             yp[(n >> 1) * 32] = make_float4(ya.hi, 0.f, ya.lo, 0.f);
         }
-        if (allf) return;
+        if (allf) return df_make(zero, 0.f);
     }
     // a forward lane's zero is 1: a pair that must not contribute (coincident, or a padding
     // source) has chi - 1 >= 2 and takes the backward branch
-    if (fwd) return;
+    if (fwd) return df_make(zero, 0.f);
     // backward lane
     const float af = acosh_chi(t);
     const float lf = ceilf(extra / fmaxf(af, 1e-6f) - 0.5f * (float)N);  // L - N - 2 >= extra / a - N / 2
@@ -165,7 +168,9 @@ __device__ __forceinline__ void pair_sweep_df(dfv chi, float t, float zero, dfv 
     const dfv y0n = ys.get(0);
     dfv sc = df_div(G0, y0n);
     sc = df_make(sc.hi * zero, sc.lo * zero);
-    for (int m = 0; m <= N; ++m) ys.put(m, df_mul(ys.get(m), sc));
+    if (FOLD)
+        for (int m = 0; m <= N; ++m) ys.put(m, df_mul(ys.get(m), sc));
+    return sc;
 }
 
 }  // namespace afmm
