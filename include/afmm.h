@@ -66,9 +66,11 @@ typedef struct {
                            leaf_size sources on average; >= 1 */
     int depth_override; /* 0: use the leaf_size rule; 2..16: use this depth */
     int precision;      /* afmm_precision */
-    double fwd_switch;  /* Legendre recursion: forward iff 2 N acosh(chi) <= fwd_switch
-                           (0: default 9 for N <= 16, 9 - 1.5 log2(N/16) above, which keeps
-                           the forward sweep's error growth below ~2e-12).  The paper's
+    double fwd_switch;  /* Legendre recursion: forward iff 2 N acosh(chi) <= fwd_switch.
+                           AFMM_FP64_NATIVE (0: default 9 for N <= 16, 9 - 1.5 log2(N/16)
+                           above, which keeps the forward sweep's error growth below
+                           ~2e-12); FP32-pair kernels (AFMM_FP64, AFMM_MIXED): at most 8
+                           (0: 8), and forward only while acosh(chi) <= 0.96.  The paper's
                            fixed switch is chi < 1.008 (Appendix A). */
     int miller_extra;   /* Miller start (0: 15).  AFMM_FP64_NATIVE: L = N + ceil(miller_extra /
                            acosh(chi)) + 2.  FP32-pair kernels (AFMM_FP64, AFMM_MIXED):
@@ -76,8 +78,9 @@ typedef struct {
                            keeps the error of every mode below e^(-2 miller_extra) times the
                            pair's G^(0) */
     int s2l_engine;     /* AFMM_FP64 and AFMM_MIXED. 0: S2L (Eq. analysis:s2l) on the tcgen05
-                           tensor cores when order <= 12, else on CUDA cores; 1: always on
-                           CUDA cores (FP32 pairs for AFMM_FP64, FP32 for AFMM_MIXED) */
+                           tensor cores when the order allows (AFMM_FP64: order <= 12,
+                           AFMM_MIXED: order <= 14), else on CUDA cores; 1: always on CUDA
+                           cores (FP32 pairs for AFMM_FP64, FP32 for AFMM_MIXED) */
 } afmm_options;
 
 typedef struct afmm_plan_s *afmm_plan;
@@ -224,10 +227,13 @@ afmm_status afmm_direct_static(int64_t ns, const double *src_r, const double *sr
 const char *afmm_status_string(afmm_status s);
 const char *afmm_last_cuda_error(void);
 
-/* Per-kernel timing of the last afmm_eval / afmm_grad / afmm_adjoint on this plan, in
+/* Per-phase timing of the last afmm_eval / afmm_grad / afmm_adjoint on this plan, in
  * milliseconds, measured with CUDA events on the plan's stream when timing is enabled:
- * names are "tree", "p2m", "m2m", "gexp", "s2l", "l2l", "near" (L2P + P2P), "perm".
- * afmm_set_timing(p, 1) enables event recording (adds event records, no sync). */
+ * names are "perm" (strengths into sorted order), "p2m", "m2m", "gexp" (expansion
+ * coefficients), "s2l", "l2l", "l2p" (local expansions at the field points), "near" (the
+ * near-field sums; with AFMM_FP64_NATIVE the local expansions too, and "l2p" is empty)
+ * and "total".  afmm_set_timing(p, 1) enables event recording (adds event records; the
+ * evaluation waits for its last event before returning). */
 afmm_status afmm_set_timing(afmm_plan p, int enable);
 /* Number of CUDA kernel launches this library has made in this process (all plans and
  * unit evaluators), for accounting in benchmarks. */
