@@ -1,0 +1,74 @@
+"""The adaptive-quadtree FMM of the oracle (oracle.adaptive), pinned on the CPU:
+
+- on a tree refined uniformly to depth d its lists reduce to the uniform method's (U: the
+  3 x 3 neighbour leaves, V: the S2L list, W = X = {}), so it must reproduce the uniform
+  oracle FMM (Algorithm 1) to rounding;
+- the four lists must account for every (field leaf, source leaf) pair exactly once (a
+  combinatorial check, independent of the expansions);
+- on clustered points (leaves on several levels, W and X lists in use) it must converge
+  to the direct sum as the order M grows, potential and field gradient."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import adaptive as A
+from paper_2301_01179_gb300 import workloads as W
+
+
+def _eps(F, D, c):
+    a = F[c] + 1j * F[c + 1]
+    b = D[c] + 1j * D[c + 1]
+    return float((np.max(np.abs(a - b), axis=1) / np.max(np.abs(b), axis=1)).max())
+
+
+def test_uniform_refinement_reproduces_uniform_fmm():
+    w = W.make("cfg1", ns=900, nf=700, n_modes=4)
+    sr, sz, tr, tz = w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"]
+    d, geom = oracle.tree_setup(sr, sz, tr, tz, 32, depth_override=4)
+    tree = A.AdaptiveTree(sr, sz, tr, tz, 10 ** 9, refine_to=d, geom=geom)
+    assert {b[0] for b in tree.leaves} == {d}
+    assert not any(tree.W.values()) and not any(tree.X.values())
+    F = A.adaptive_fmm(tree, w["q_re"], w["q_im"], 6, grad=True)
+    U = oracle.fmm(sr, sz, tr, tz, w["q_re"], w["q_im"], 6, d, geom, grad=True)
+    for c in (0, 2, 4):
+        assert _eps(F, U, c) < 1e-12
+
+
+def _ancestors(tree, b):
+    out = []
+    while b is not None:
+        out.append(b)
+        b = tree.parent[b]
+    return out
+
+
+def test_lists_cover_every_leaf_pair_once():
+    w = W.make("cfg5", ns=1500, nf=1100, n_modes=1)
+    tree = A.AdaptiveTree(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], 20)
+    assert len({b[0] for b in tree.leaves}) >= 3
+    assert sum(len(v) for v in tree.W.values()) > 0
+    for B in tree.leaves:
+        upB = _ancestors(tree, B)
+        for C in tree.leaves:
+            upC = set(_ancestors(tree, C))
+            n = int(C in tree.U[B])
+            n += sum(1 for Wc in tree.W[B] if Wc in upC)
+            n += sum(1 for D in upB for Vc in tree.V[D] if Vc in upC)
+            n += sum(1 for D in upB if C in tree.X[D])
+            assert n == 1, (B, C, n)
+
+
+def test_converges_to_direct_on_clustered_points():
+    w = W.make("cfg5", ns=1200, nf=900, n_modes=4)
+    sr, sz, tr, tz = w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"]
+    tree = A.AdaptiveTree(sr, sz, tr, tz, 24)
+    assert len({b[0] for b in tree.leaves}) >= 3
+    assert sum(len(v) for v in tree.W.values()) > 0 and sum(len(v) for v in tree.X.values()) > 0
+    D = oracle.direct(sr, sz, tr, tz, w["q_re"], w["q_im"], grad=True)
+    errs = []
+    for M in (4, 7, 10):
+        F = A.adaptive_fmm(tree, w["q_re"], w["q_im"], M, grad=True)
+        errs.append([_eps(F, D, c) for c in (0, 2, 4)])
+    errs = np.array(errs)
+    assert np.all(errs[1:] < 0.2 * errs[:-1]), errs  # geometric in M
+    assert errs[-1].max() < 1e-5, errs
