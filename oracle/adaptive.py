@@ -117,24 +117,64 @@ class AdaptiveTree:
         return a0i <= b1i and b0i <= a1i and a0j <= b1j and b0j <= a1j
 
     def _lists(self):
-        adj = self.adjacent
-        by_level = {}
-        for b in self.boxes:
-            by_level.setdefault(b[0], []).append(b)
-        self.V = {b: [] for b in self.boxes}
-        for lvl, bs in by_level.items():
-            if lvl < 2:
-                continue
-            for b in bs:
-                pb = self.parent[b]
-                self.V[b] = [c for c in bs if c != b and not adj(c, b) and adj(self.parent[c], pb)]
-        self.U = {b: [c for c in self.leaves if adj(c, b)] for b in self.leaves}
-        self.W = {b: [c for c in self.boxes if c[0] > b[0] and not adj(c, b) and adj(self.parent[c], b)]
-                  for b in self.leaves}
+        """U, V, W, X from each box's colleagues (same-level adjacent boxes), O(boxes)."""
+        adj, box = self.adjacent, self.src
+        self.V, self.U, self.W = {}, {}, {}
         self.X = {b: [] for b in self.boxes}
+
+        def colleagues(b):
+            out = []
+            for di in (-1, 0, 1):
+                for dj in (-1, 0, 1):
+                    c = (b[0], b[1] + di, b[2] + dj)
+                    if c in box:
+                        out.append(c)
+            return out
+
+        for b in self.boxes:
+            pb = self.parent[b]
+            if b[0] < 2 or pb is None:
+                self.V[b] = []
+                continue
+            self.V[b] = [d for c in colleagues(pb) for d in self.children[c] if not adj(d, b)]
         for b in self.leaves:
+            U, W = set(), []
+            stack = list(colleagues(b))
+            while stack:  # same level and finer: descend while adjacent
+                c = stack.pop()
+                if not self.children[c]:
+                    U.add(c)
+                    continue
+                for d in self.children[c]:
+                    if adj(d, b):
+                        stack.append(d)
+                    else:
+                        W.append(d)
+            for lc in range(b[0] - 1, -1, -1):  # coarser adjacent leaves
+                sh = b[0] - lc
+                for di in (-1, 0, 1):
+                    for dj in (-1, 0, 1):
+                        c = (lc, (b[1] + di) >> sh, (b[2] + dj) >> sh)
+                        if c in box and not self.children[c] and adj(c, b):
+                            U.add(c)
+            self.U[b] = sorted(U)
+            self.W[b] = sorted(W)
             for c in self.W[b]:
                 self.X[c].append(b)
+
+    def lists_brute(self):
+        """The same lists from their definitions by exhaustive search (for checking)."""
+        adj = self.adjacent
+        V = {b: ([c for c in self.boxes if c[0] == b[0] and c != b and not adj(c, b)
+                  and adj(self.parent[c], self.parent[b])] if b[0] >= 2 else []) for b in self.boxes}
+        U = {b: sorted(c for c in self.leaves if adj(c, b)) for b in self.leaves}
+        W = {b: sorted(c for c in self.boxes if c[0] > b[0] and not adj(c, b) and adj(self.parent[c], b))
+             for b in self.leaves}
+        X = {b: [] for b in self.boxes}
+        for b in self.leaves:
+            for c in W[b]:
+                X[c].append(b)
+        return U, V, W, X
 
 
 _S2L_TABLES = {}

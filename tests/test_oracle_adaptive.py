@@ -72,3 +72,13 @@ def test_converges_to_direct_on_clustered_points():
     errs = np.array(errs)
     assert np.all(errs[1:] < 0.2 * errs[:-1]), errs  # geometric in M
     assert errs[-1].max() < 1e-5, errs
+
+
+def test_fast_lists_match_their_definitions():
+    w = W.make("cfg5", ns=2000, nf=1500, n_modes=1)
+    tree = A.AdaptiveTree(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], 16)
+    U, V, Wl, X = tree.lists_brute()
+    assert {b: sorted(v) for b, v in tree.U.items()} == U
+    assert {b: sorted(v) for b, v in tree.V.items()} == {b: sorted(v) for b, v in V.items()}
+    assert {b: sorted(v) for b, v in tree.W.items()} == Wl
+    assert {b: sorted(v) for b, v in tree.X.items()} == {b: sorted(v) for b, v in X.items()}
