@@ -7,6 +7,9 @@ the paper each routine follows.
 
 Layouts: amplitudes and results are mode-major planes, ``q[n, i]`` for mode ``n`` of
 source ``i`` and ``phi[n, j]`` for field point ``j`` (numpy float64, C order).
+
+``oracle.adaptive`` holds the FMM on an adaptive quadtree, built on this module's Taylor
+coefficients and direct sum.
 """
 import ctypes
 import os
