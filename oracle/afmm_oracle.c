@@ -657,20 +657,21 @@ int orc_fmm(int64_t ns, const double *sr, const double *sz, int64_t nf, const do
 #define BOXOFF(l, b, n) ((((size_t)(b)) * nmodes + (n)) * nc)
     int nside = 1 << d;
     double hd = L / nside;
-    /* leaf moments, Eq. analysis:moments */
-    double *pw_r = (double *)malloc(sizeof(double) * (M + 1) * 2);
-    double *pw_z = pw_r + (M + 1);
-    for (int64_t q = 0; q < ns; ++q) {
-        int ir = orc_box_coord(sr[q], r0, L, d), iz = orc_box_coord(sz[q], z0, L, d);
-        int b = ir * nside + iz;
-        double cr = r0 + (ir + 0.5) * hd, cz = z0 + (iz + 0.5) * hd;
-        double dr = sr[q] - cr, dz = sz[q] - cz;
-        pw_r[0] = pw_z[0] = 1.0;
-        for (int i = 1; i <= M; ++i) {
-            pw_r[i] = pw_r[i - 1] * dr;
-            pw_z[i] = pw_z[i - 1] * dz;
-        }
-        for (int n = 0; n < nmodes; ++n) {
+    /* leaf moments, Eq. analysis:moments.  Modes are independent, so they run on
+     * separate threads; each moment still sums its sources in source order. */
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int n = 0; n < nmodes; ++n) {
+        double pw_r[61], pw_z[61];
+        for (int64_t q = 0; q < ns; ++q) {
+            int ir = orc_box_coord(sr[q], r0, L, d), iz = orc_box_coord(sz[q], z0, L, d);
+            int b = ir * nside + iz;
+            double cr = r0 + (ir + 0.5) * hd, cz = z0 + (iz + 0.5) * hd;
+            double dr = sr[q] - cr, dz = sz[q] - cz;
+            pw_r[0] = pw_z[0] = 1.0;
+            for (int i = 1; i <= M; ++i) {
+                pw_r[i] = pw_r[i - 1] * dr;
+                pw_z[i] = pw_z[i - 1] * dz;
+            }
             double a = q_re[(size_t)n * ns + q], bb = q_im[(size_t)n * ns + q];
             for (int i = 0; i <= M; ++i)
                 for (int j = 0; i + j <= M; ++j) {
@@ -680,17 +681,20 @@ int orc_fmm(int64_t ns, const double *sr, const double *sz, int64_t nf, const do
                 }
         }
     }
-    /* upward pass, Eq. analysis:shift, Delta = parent centre - child centre */
+    /* upward pass, Eq. analysis:shift, Delta = parent centre - child centre (one thread
+     * per mode; each parent sums its children in the same order for every mode) */
     for (int l = d - 1; l >= 2; --l) {
         int ns_c = 1 << (l + 1);
         double hc = L / ns_c;
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int n = 0; n < nmodes; ++n)
         for (int ci = 0; ci < ns_c; ++ci)
             for (int cj = 0; cj < ns_c; ++cj) {
                 int pi = ci >> 1, pj = cj >> 1;
                 int cb = ci * ns_c + cj, pb = pi * (ns_c >> 1) + pj;
                 double Dr = (pi + 0.5) * 2.0 * hc - (ci + 0.5) * hc;
                 double Dz = (pj + 0.5) * 2.0 * hc - (cj + 0.5) * hc;
-                for (int n = 0; n < nmodes; ++n) {
+                {
                     const double *cre = &mom_re[l + 1][BOXOFF(l + 1, cb, n)];
                     const double *cim = &mom_im[l + 1][BOXOFF(l + 1, cb, n)];
                     double *pre = &mom_re[l][BOXOFF(l, pb, n)];
@@ -719,6 +723,8 @@ int orc_fmm(int64_t ns, const double *sr, const double *sz, int64_t nf, const do
         double h = L / nl;
         /* local shift from the parent, Eq. analysis:l2l (level-1 locals are zero) */
         if (l > 2) {
+            /* each child box is written by one thread */
+#pragma omp parallel for schedule(dynamic, 1)
             for (int ci = 0; ci < nl; ++ci)
                 for (int cj = 0; cj < nl; ++cj) {
                     int pi = ci >> 1, pj = cj >> 1;
@@ -751,16 +757,24 @@ int orc_fmm(int64_t ns, const double *sr, const double *sz, int64_t nf, const do
         for (int si = 0; si < nl; ++si) {
             double rs = r0 + (si + 0.5) * h;
             int have[4][4];
-            for (int a = 0; a < 4; ++a)
-                for (int b = 0; b < 4; ++b) {
-                    have[a][b] = 0;
-                    if (a <= 1 && b <= 1) continue;
-                    if (si + a >= nl) continue;
-                    double rb = r0 + (si + a + 0.5) * h;
-                    double *Eab = E + (size_t)(a * 4 + b) * cube * nmodes;
-                    if (orc_gbar(rb, rs, b * h, N, P, Eab) != 0) return -2;
-                    have[a][b] = 1;
-                }
+            int gfail = 0;
+            /* the twelve expansions of the station are independent: one thread each */
+#pragma omp parallel for schedule(dynamic, 1) reduction(|: gfail)
+            for (int ab = 0; ab < 16; ++ab) {
+                int a = ab / 4, b = ab % 4;
+                have[a][b] = 0;
+                if (a <= 1 && b <= 1) continue;
+                if (si + a >= nl) continue;
+                double rb = r0 + (si + a + 0.5) * h;
+                double *Eab = E + (size_t)(a * 4 + b) * cube * nmodes;
+                if (orc_gbar(rb, rs, b * h, N, P, Eab) != 0) gfail = 1;
+                have[a][b] = 1;
+            }
+            if (gfail) return -2;
+            /* the S2L applications of one mode touch only that mode's moments and locals:
+             * one thread per mode, the same application order within each mode */
+#pragma omp parallel for schedule(dynamic, 1)
+            for (int n = 0; n < nmodes; ++n)
             for (int sj = 0; sj < nl; ++sj) {
                 for (int a = 0; a < 4; ++a)
                     for (int b = 0; b < 4; ++b) {
@@ -773,10 +787,9 @@ int orc_fmm(int64_t ns, const double *sr, const double *sz, int64_t nf, const do
                             if (tj < 0 || tj >= nl) continue;
                             if (!in_s2l_list(ti, tj, si, sj)) continue;
                             int tb = ti * nl + tj, sb = si * nl + sj;
-                            for (int n = 0; n < nmodes; ++n)
-                                orc_s2l(Eab + (size_t)n * cube, P, M, 0, dir, &mom_re[l][BOXOFF(l, sb, n)],
-                                        &mom_im[l][BOXOFF(l, sb, n)], &loc_re[l][BOXOFF(l, tb, n)],
-                                        &loc_im[l][BOXOFF(l, tb, n)]);
+                            orc_s2l(Eab + (size_t)n * cube, P, M, 0, dir, &mom_re[l][BOXOFF(l, sb, n)],
+                                    &mom_im[l][BOXOFF(l, sb, n)], &loc_re[l][BOXOFF(l, tb, n)],
+                                    &loc_im[l][BOXOFF(l, tb, n)]);
                         }
                         /* FI / BI: source box (si + a, sj -+ b) -> field box (si, sj), a >= 1 */
                         if (a == 0) continue;
@@ -787,10 +800,9 @@ int orc_fmm(int64_t ns, const double *sr, const double *sz, int64_t nf, const do
                             if (uj < 0 || uj >= nl) continue;
                             if (!in_s2l_list(ti, tj, ui, uj)) continue;
                             int tb = ti * nl + tj, sb = ui * nl + uj;
-                            for (int n = 0; n < nmodes; ++n)
-                                orc_s2l(Eab + (size_t)n * cube, P, M, 1, dir, &mom_re[l][BOXOFF(l, sb, n)],
-                                        &mom_im[l][BOXOFF(l, sb, n)], &loc_re[l][BOXOFF(l, tb, n)],
-                                        &loc_im[l][BOXOFF(l, tb, n)]);
+                            orc_s2l(Eab + (size_t)n * cube, P, M, 1, dir, &mom_re[l][BOXOFF(l, sb, n)],
+                                    &mom_im[l][BOXOFF(l, sb, n)], &loc_re[l][BOXOFF(l, tb, n)],
+                                    &loc_im[l][BOXOFF(l, tb, n)]);
                         }
                     }
             }
@@ -800,8 +812,6 @@ int orc_fmm(int64_t ns, const double *sr, const double *sz, int64_t nf, const do
     /* leaf evaluation: local expansion (Eq. analysis:local) + direct sums over the 3x3
      * neighbour leaves (the D list) */
     int Nw = N < 1 ? 1 : N;
-    double *G = (double *)malloc(sizeof(double) * (Nw + 1) * 4);
-    double *Gr = G + (Nw + 1), *Gx = Gr + (Nw + 1), *Gw = Gx + (Nw + 1);
     /* bucket sources by leaf (stable, original order inside a leaf) */
     int64_t nleaf = (int64_t)nside * nside;
     int64_t *cnt = (int64_t *)calloc(nleaf + 1, sizeof(int64_t));
@@ -819,7 +829,14 @@ int orc_fmm(int64_t ns, const double *sr, const double *sz, int64_t nf, const do
         for (int64_t q = 0; q < ns; ++q) ord[fill[sleaf[q]]++] = q;
         free(fill);
     }
+    /* field points are independent: one thread per point, private buffers */
+#pragma omp parallel
+    {
+    double pw_r[61], pw_z[61];
+    double *G = (double *)malloc(sizeof(double) * (Nw + 1) * 4);
+    double *Gr = G + (Nw + 1), *Gx = Gr + (Nw + 1), *Gw = Gx + (Nw + 1);
     double *acc = (double *)malloc(sizeof(double) * nmodes * 6);
+#pragma omp for schedule(dynamic, 16)
     for (int64_t j = 0; j < nf; ++j) {
         int ir = orc_box_coord(tr[j], r0, L, d), iz = orc_box_coord(tz[j], z0, L, d);
         int b = ir * nside + iz;
@@ -891,10 +908,10 @@ int orc_fmm(int64_t ns, const double *sr, const double *sz, int64_t nf, const do
     }
     free(acc);
     free(G);
+    }
     free(cnt);
     free(ord);
     free(sleaf);
-    free(pw_r);
     for (int l = 1; l <= d; ++l) {
         free(mom_re[l]);
         free(mom_im[l]);
