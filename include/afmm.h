@@ -37,8 +37,9 @@ typedef enum {
     AFMM_EINVAL = 1,       /* bad size, option, NULL pointer, r <= 0 or non-finite coordinate */
     AFMM_ENOMEM = 2,       /* device allocation failed */
     AFMM_ECUDA = 3,        /* a CUDA call or kernel launch failed (see afmm_last_cuda_error) */
-    AFMM_ETIMEOUT = 4,     /* a bounded device-side wait (the completion barrier of the
-                              tensor-core S2L) ran out during an earlier evaluation on this
+    AFMM_ETIMEOUT = 4,     /* a bounded device-side wait (the MMA completion barrier of the
+                              tensor-core S2L, or a producer/consumer hand-over of the
+                              near-field kernel) ran out during an earlier evaluation on this
                               plan; that evaluation's results are invalid.  Reported once, by
                               the next call on the plan. */
     AFMM_EUNSUPPORTED = 5  /* valid request the library does not implement (e.g. depth > 16) */
@@ -97,6 +98,11 @@ typedef struct {
     int64_t near_pairs;         /* (field point, source) pairs summed directly by the FMM */
     int64_t s2l_pairs;          /* (field box, source box) S2L applications, all levels */
     int64_t expansions;         /* Green's-function expansions generated per evaluation */
+    int64_t s2l_point_pairs;    /* (field point, source) pairs covered by those S2L box pairs;
+                                   every pair of points is covered once, by the near field or
+                                   by one level's interaction list (Sec. 2.2), so
+                                   near_pairs + s2l_point_pairs = ns * nf */
+    int s2l_tensor_cores;       /* 1 if the S2L runs on the tcgen05 tensor cores, else 0 */
 } afmm_plan_info_t;
 
 void afmm_options_default(afmm_options *opt);

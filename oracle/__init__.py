@@ -75,6 +75,13 @@ def _load():
     lib.orc_fmm.restype = I
     lib.orc_adjoint_fmm.argtypes = [I64, P, P, I64, P, P, I, P, P, P, P, I, I, P, P, P, P, P]
     lib.orc_adjoint_fmm.restype = I
+    PI64 = ctypes.POINTER(ctypes.c_int64)
+    lib.orc_fmm_sampled.argtypes = [I64, P, P, I64, P, P, I, P, P, I, I, P, I64, PI64, P, P, P, P, P, P]
+    lib.orc_fmm_sampled.restype = I
+    lib.orc_adjoint_fmm_sampled.argtypes = [I64, P, P, I64, P, P, I, P, P, P, P, I, I, P, I64, PI64, P, P, P, P]
+    lib.orc_adjoint_fmm_sampled.restype = I
+    lib.orc_tree_counts.argtypes = [I64, P, P, I64, P, P, I, P, PI64]
+    lib.orc_tree_counts.restype = I
     lib.orc_num_threads.argtypes = []
     lib.orc_num_threads.restype = I
     lib.orc_fourier_analysis.argtypes = [I64, I, P, I, P, P]
@@ -237,6 +244,66 @@ def adjoint_fmm(src_r, src_z, tgt_r, tgt_z, q_re, q_im, gphi_re, gphi_im, M, d, 
     if rc != 0:
         raise RuntimeError("orc_adjoint_fmm failed: %d" % rc)
     return gq_re, gq_im, g_r, g_z
+
+
+def _idx(a):
+    a = np.ascontiguousarray(a, dtype=np.int64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def fmm_sampled(src_r, src_z, tgt_r, tgt_z, q_re, q_im, M, d, geom, samples, grad=False):
+    """Algorithm 1 (FP64) evaluated only at the field points ``samples`` (indices), for
+    checks at full size: each level's S2L into the sample's ancestor box is evaluated at
+    the point directly (the shifts are exact re-expansions).  Returns arrays
+    [nmodes, len(samples)] as ``fmm``."""
+    sr, sz, tr, tz = map(_f64, (src_r, src_z, tgt_r, tgt_z))
+    q_re = _f64(q_re)
+    q_im = _f64(q_im)
+    geom = _f64(geom)
+    idx, pidx = _idx(samples)
+    nmodes, ns = q_re.shape
+    k = idx.shape[0]
+    outs = [np.zeros((nmodes, k)) for _ in range(6 if grad else 2)]
+    g = outs[2:] if grad else [None] * 4
+    rc = _load().orc_fmm_sampled(ns, _p(sr), _p(sz), tr.shape[0], _p(tr), _p(tz), nmodes, _p(q_re), _p(q_im),
+                                 int(M), int(d), _p(geom), k, pidx, _p(outs[0]), _p(outs[1]), _p(g[0]),
+                                 _p(g[1]), _p(g[2]), _p(g[3]))
+    if rc != 0:
+        raise RuntimeError("orc_fmm_sampled failed: %d" % rc)
+    return tuple(outs)
+
+
+def adjoint_fmm_sampled(src_r, src_z, tgt_r, tgt_z, q_re, q_im, gphi_re, gphi_im, M, d, geom, samples):
+    """The FMM adjoint at the sources ``samples`` only: (gq_re, gq_im) [nmodes, k] and
+    (g_r, g_z) [k]."""
+    sr, sz, tr, tz = map(_f64, (src_r, src_z, tgt_r, tgt_z))
+    q_re, q_im, gphi_re, gphi_im = map(_f64, (q_re, q_im, gphi_re, gphi_im))
+    geom = _f64(geom)
+    idx, pidx = _idx(samples)
+    nmodes, ns = q_re.shape
+    k = idx.shape[0]
+    gq_re = np.zeros((nmodes, k))
+    gq_im = np.zeros((nmodes, k))
+    g_r = np.zeros(k)
+    g_z = np.zeros(k)
+    rc = _load().orc_adjoint_fmm_sampled(ns, _p(sr), _p(sz), tr.shape[0], _p(tr), _p(tz), nmodes, _p(q_re),
+                                         _p(q_im), _p(gphi_re), _p(gphi_im), int(M), int(d), _p(geom), k, pidx,
+                                         _p(gq_re), _p(gq_im), _p(g_r), _p(g_z))
+    if rc != 0:
+        raise RuntimeError("orc_adjoint_fmm_sampled failed: %d" % rc)
+    return gq_re, gq_im, g_r, g_z
+
+
+def tree_counts(src_r, src_z, tgt_r, tgt_z, d, geom):
+    """(near pairs, S2L box pairs, point pairs under those box pairs) of the uniform tree
+    of depth d on the square ``geom``, from the list definitions of Sec. 2.2."""
+    sr, sz, tr, tz = map(_f64, (src_r, src_z, tgt_r, tgt_z))
+    geom = _f64(geom)
+    out, pout = _idx(np.zeros(3, dtype=np.int64))
+    rc = _load().orc_tree_counts(sr.shape[0], _p(sr), _p(sz), tr.shape[0], _p(tr), _p(tz), int(d), _p(geom), pout)
+    if rc != 0:
+        raise RuntimeError("orc_tree_counts failed: %d" % rc)
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def fourier_analysis(samples, n_modes):

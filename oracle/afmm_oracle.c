@@ -951,6 +951,338 @@ int orc_adjoint_fmm(int64_t ns, const double *sr, const double *sz, int64_t nf, 
     return rc;
 }
 
+/* ------------------------------------------------------------------------------------ */
+/* The uniform FMM at selected field points only, for checks at sizes where the full     */
+/* oracle FMM does not fit in memory or time.                                            */
+/* Reading: both truncations are by total degree (i + j <= M, k + l <= M), so the upward  */
+/* and downward shifts (Eqs. analysis:shift, analysis:l2l) re-expand polynomials exactly. */
+/* The FMM field at a point of leaf b therefore equals, up to rounding, the sum over the  */
+/* levels l = 2..d of the level-l ancestor's local expansion built from that level's S2L  */
+/* alone (Eq. analysis:s2l over the interaction list, from the source boxes' moments      */
+/* about their level-l centres, Eq. analysis:moments) and evaluated at the point          */
+/* (Eq. analysis:local), plus the direct sum over the 3x3 neighbour leaves.  The tests    */
+/* check that this equals orc_fmm at every point where both run.                          */
+/* samples[s] indexes the field points; outputs are [nmodes][nsamp].                      */
+/* ------------------------------------------------------------------------------------ */
+
+static int cmp_i64(const void *a, const void *b)
+{
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return x < y ? -1 : (x > y);
+}
+
+int orc_fmm_sampled(int64_t ns, const double *sr, const double *sz, int64_t nf, const double *tr,
+                    const double *tz, int nmodes, const double *q_re, const double *q_im, int M, int d,
+                    const double *geom, int64_t nsamp, const int64_t *samples, double *phi_re,
+                    double *phi_im, double *dr_re, double *dr_im, double *dz_re, double *dz_im)
+{
+    if (d < 2 || M > 60 || nsamp < 0) return -1;
+    for (int64_t s = 0; s < nsamp; ++s)
+        if (samples[s] < 0 || samples[s] >= nf) return -1;
+    binom_init();
+    int N = nmodes - 1;
+    int P = 2 * M;
+    int nc = (M + 1) * (M + 2) / 2;
+    int grad = dr_re != NULL;
+    double r0 = geom[0], z0 = geom[1], L = geom[2];
+    int nside = 1 << d;
+    size_t cube = (size_t)(P + 1) * (P + 1) * (P + 1);
+    /* bucket sources by leaf (stable, original order inside a leaf) */
+    int64_t nleaf = (int64_t)nside * nside;
+    int64_t *cnt = (int64_t *)calloc(nleaf + 1, sizeof(int64_t));
+    int64_t *ord = (int64_t *)malloc(sizeof(int64_t) * (ns > 0 ? ns : 1));
+    int *sleaf = (int *)malloc(sizeof(int) * (ns > 0 ? ns : 1));
+    if (!cnt || !ord || !sleaf) return -2;
+    for (int64_t q = 0; q < ns; ++q) {
+        int ir = orc_box_coord(sr[q], r0, L, d), iz = orc_box_coord(sz[q], z0, L, d);
+        sleaf[q] = ir * nside + iz;
+        cnt[sleaf[q] + 1]++;
+    }
+    for (int64_t b = 0; b < nleaf; ++b) cnt[b + 1] += cnt[b];
+    {
+        int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (nleaf + 1));
+        memcpy(fill, cnt, sizeof(int64_t) * (nleaf + 1));
+        for (int64_t q = 0; q < ns; ++q) ord[fill[sleaf[q]]++] = q;
+        free(fill);
+    }
+    /* per level: the source boxes of the samples' interaction lists and their moments */
+    int64_t *nbx = (int64_t *)calloc(d + 1, sizeof(int64_t));
+    int64_t **bx = (int64_t **)calloc(d + 1, sizeof(int64_t *));
+    double **bm_re = (double **)calloc(d + 1, sizeof(double *));
+    double **bm_im = (double **)calloc(d + 1, sizeof(double *));
+    for (int l = 2; l <= d; ++l) {
+        int nl = 1 << l, sh = d - l;
+        int64_t *lst = (int64_t *)malloc(sizeof(int64_t) * (nsamp * 36 + 1));
+        int64_t m = 0;
+        for (int64_t s = 0; s < nsamp; ++s) {
+            int64_t j = samples[s];
+            int ti = orc_box_coord(tr[j], r0, L, d) >> sh, tj = orc_box_coord(tz[j], z0, L, d) >> sh;
+            for (int ui = 2 * (ti / 2) - 2; ui <= 2 * (ti / 2) + 3; ++ui)
+                for (int uj = 2 * (tj / 2) - 2; uj <= 2 * (tj / 2) + 3; ++uj) {
+                    if (ui < 0 || uj < 0 || ui >= nl || uj >= nl) continue;
+                    if (!in_s2l_list(ti, tj, ui, uj)) continue;
+                    lst[m++] = (int64_t)ui * nl + uj;
+                }
+        }
+        qsort(lst, (size_t)m, sizeof(int64_t), cmp_i64);
+        int64_t u = 0;
+        for (int64_t t = 0; t < m; ++t)
+            if (t == 0 || lst[t] != lst[t - 1]) lst[u++] = lst[t];
+        nbx[l] = u;
+        bx[l] = lst;
+        bm_re[l] = (double *)calloc((size_t)(u > 0 ? u : 1) * nmodes * nc, sizeof(double));
+        bm_im[l] = (double *)calloc((size_t)(u > 0 ? u : 1) * nmodes * nc, sizeof(double));
+        if (!bm_re[l] || !bm_im[l]) return -2;
+        double h = L / nl;
+        /* moments of each listed box about its level-l centre, one thread per (box, mode) */
+#pragma omp parallel for schedule(dynamic, 1) collapse(2)
+        for (int64_t t = 0; t < u; ++t)
+            for (int n = 0; n < nmodes; ++n) {
+                int bi = (int)(bx[l][t] / nl), bj = (int)(bx[l][t] % nl);
+                double cr = r0 + (bi + 0.5) * h, cz = z0 + (bj + 0.5) * h;
+                double *mre = bm_re[l] + ((size_t)t * nmodes + n) * nc;
+                double *mim = bm_im[l] + ((size_t)t * nmodes + n) * nc;
+                double pw_r[61], pw_z[61];
+                for (int ir = bi << sh; ir < (bi + 1) << sh; ++ir) {
+                    int64_t lo = cnt[(int64_t)ir * nside + ((int64_t)bj << sh)];
+                    int64_t hi = cnt[(int64_t)ir * nside + ((int64_t)(bj + 1) << sh)];
+                    for (int64_t k = lo; k < hi; ++k) {
+                        int64_t q = ord[k];
+                        double dr = sr[q] - cr, dz = sz[q] - cz;
+                        pw_r[0] = pw_z[0] = 1.0;
+                        for (int i = 1; i <= M; ++i) {
+                            pw_r[i] = pw_r[i - 1] * dr;
+                            pw_z[i] = pw_z[i - 1] * dz;
+                        }
+                        double a = q_re[(size_t)n * ns + q], bb = q_im[(size_t)n * ns + q];
+                        for (int i = 0; i <= M; ++i)
+                            for (int jj = 0; i + jj <= M; ++jj) {
+                                double w = pw_r[i] * pw_z[jj];
+                                mre[cidx(i, jj, M)] += a * w;
+                                mim[cidx(i, jj, M)] += bb * w;
+                            }
+                    }
+                }
+            }
+    }
+    /* per (sample, level): S2L of that level into the ancestor's local expansion, evaluated
+     * at the sample; level d + 1 stands for the near-field sum over the 3x3 leaves */
+    int nlev = d + 2;
+    double *res = (double *)calloc((size_t)(nsamp > 0 ? nsamp : 1) * nlev * nmodes * 6, sizeof(double));
+    if (!res) return -2;
+    int fail = 0;
+#pragma omp parallel reduction(|: fail)
+    {
+        double *E = (double *)malloc(sizeof(double) * cube * nmodes);
+        double *F = (double *)malloc(sizeof(double) * 2 * (size_t)nmodes * nc);
+        int Nw = N < 1 ? 1 : N;
+        double *G = (double *)malloc(sizeof(double) * (Nw + 1) * 4);
+        double *Gr = G + (Nw + 1), *Gx = Gr + (Nw + 1), *Gw = Gx + (Nw + 1);
+        if (!E || !F || !G) fail = 1;
+#pragma omp for schedule(dynamic, 1) collapse(2)
+        for (int64_t s = 0; s < nsamp; ++s)
+            for (int l = 2; l <= d + 1; ++l) {
+                if (fail) continue;
+                int64_t j = samples[s];
+                double *acc = res + ((size_t)s * nlev + l) * nmodes * 6;
+                int ir = orc_box_coord(tr[j], r0, L, d), iz = orc_box_coord(tz[j], z0, L, d);
+                if (l == d + 1) {
+                    for (int a = -1; a <= 1; ++a)
+                        for (int c = -1; c <= 1; ++c) {
+                            int ni = ir + a, nj = iz + c;
+                            if (ni < 0 || nj < 0 || ni >= nside || nj >= nside) continue;
+                            int64_t nb = (int64_t)ni * nside + nj;
+                            for (int64_t t = cnt[nb]; t < cnt[nb + 1]; ++t) {
+                                int64_t q = ord[t];
+                                double x = tz[j] - sz[q];
+                                if (grad)
+                                    orc_green_grad(tr[j], sr[q], x, N, G, Gr, Gx, Gw);
+                                else
+                                    orc_green(tr[j], sr[q], x, N, G);
+                                for (int n = 0; n < nmodes; ++n) {
+                                    double qa = q_re[(size_t)n * ns + q], qb = q_im[(size_t)n * ns + q];
+                                    acc[6 * n + 0] += qa * G[n];
+                                    acc[6 * n + 1] += qb * G[n];
+                                    if (grad) {
+                                        acc[6 * n + 2] += qa * Gr[n];
+                                        acc[6 * n + 3] += qb * Gr[n];
+                                        acc[6 * n + 4] += qa * Gx[n];
+                                        acc[6 * n + 5] += qb * Gx[n];
+                                    }
+                                }
+                            }
+                        }
+                    continue;
+                }
+                int nl = 1 << l, sh = d - l;
+                double h = L / nl;
+                int ti = ir >> sh, tj = iz >> sh;
+                memset(F, 0, sizeof(double) * 2 * (size_t)nmodes * nc);
+                for (int ui = 2 * (ti / 2) - 2; ui <= 2 * (ti / 2) + 3; ++ui)
+                    for (int uj = 2 * (tj / 2) - 2; uj <= 2 * (tj / 2) + 3; ++uj) {
+                        if (ui < 0 || uj < 0 || ui >= nl || uj >= nl) continue;
+                        if (!in_s2l_list(ti, tj, ui, uj)) continue;
+                        int64_t key = (int64_t)ui * nl + uj;
+                        int64_t *hit = (int64_t *)bsearch(&key, bx[l], (size_t)nbx[l], sizeof(int64_t), cmp_i64);
+                        int64_t t = hit - bx[l];
+                        /* the field box at the larger radius: FO/BO with E_{k,i,j+l}; at the
+                         * smaller radius: FI/BI with E_{i,k,j+l}; field box below: backward */
+                        int inward = ti < ui, backward = tj < uj;
+                        int lo = ti < ui ? ti : ui, hi = ti < ui ? ui : ti;
+                        int b = abs(tj - uj);
+                        double rb = r0 + (hi + 0.5) * h, rs = r0 + (lo + 0.5) * h;
+                        if (orc_gbar(rb, rs, b * h, N, P, E) != 0) {
+                            fail = 1;
+                            continue;
+                        }
+                        for (int n = 0; n < nmodes; ++n)
+                            orc_s2l(E + (size_t)n * cube, P, M, inward, backward,
+                                    bm_re[l] + ((size_t)t * nmodes + n) * nc, bm_im[l] + ((size_t)t * nmodes + n) * nc,
+                                    F + (size_t)n * nc, F + (size_t)(nmodes + n) * nc);
+                    }
+                double dr = tr[j] - (r0 + (ti + 0.5) * h), dz = tz[j] - (z0 + (tj + 0.5) * h);
+                double pw_r[61], pw_z[61];
+                pw_r[0] = pw_z[0] = 1.0;
+                for (int i = 1; i <= M; ++i) {
+                    pw_r[i] = pw_r[i - 1] * dr;
+                    pw_z[i] = pw_z[i - 1] * dz;
+                }
+                for (int n = 0; n < nmodes; ++n) {
+                    const double *Fr = F + (size_t)n * nc, *Fi = F + (size_t)(nmodes + n) * nc;
+                    for (int k = 0; k <= M; ++k)
+                        for (int ll = 0; k + ll <= M; ++ll) {
+                            double w = pw_r[k] * pw_z[ll];
+                            acc[6 * n + 0] += Fr[cidx(k, ll, M)] * w;
+                            acc[6 * n + 1] += Fi[cidx(k, ll, M)] * w;
+                            if (grad) {
+                                if (k >= 1) {
+                                    double wr = k * pw_r[k - 1] * pw_z[ll];
+                                    acc[6 * n + 2] += Fr[cidx(k, ll, M)] * wr;
+                                    acc[6 * n + 3] += Fi[cidx(k, ll, M)] * wr;
+                                }
+                                if (ll >= 1) {
+                                    double wz = ll * pw_r[k] * pw_z[ll - 1];
+                                    acc[6 * n + 4] += Fr[cidx(k, ll, M)] * wz;
+                                    acc[6 * n + 5] += Fi[cidx(k, ll, M)] * wz;
+                                }
+                            }
+                        }
+                }
+            }
+        free(E);
+        free(F);
+        free(G);
+    }
+    /* the levels' contributions in level order, then the near field */
+    for (int64_t s = 0; s < nsamp; ++s)
+        for (int n = 0; n < nmodes; ++n) {
+            double v[6] = {0, 0, 0, 0, 0, 0};
+            for (int l = 2; l <= d + 1; ++l)
+                for (int c = 0; c < 6; ++c) v[c] += res[((size_t)s * nlev + l) * nmodes * 6 + 6 * n + c];
+            size_t o = (size_t)n * nsamp + s;
+            if (phi_re) phi_re[o] = v[0];
+            if (phi_im) phi_im[o] = v[1];
+            if (grad) {
+                dr_re[o] = v[2];
+                dr_im[o] = v[3];
+                dz_re[o] = v[4];
+                dz_im[o] = v[5];
+            }
+        }
+    free(res);
+    for (int l = 2; l <= d; ++l) {
+        free(bx[l]);
+        free(bm_re[l]);
+        free(bm_im[l]);
+    }
+    free(nbx);
+    free(bx);
+    free(bm_re);
+    free(bm_im);
+    free(cnt);
+    free(ord);
+    free(sleaf);
+    return fail ? -2 : 0;
+}
+
+/* Adjoint of the FMM at selected sources: the sampled FMM of the transposed problem
+ * (field points as sources with strengths gphi, evaluated at the sources samples[s]),
+ * then gq = A, dL/dr = sum_n Re(q conj B), dL/dz = sum_n Re(q conj C) there.
+ * Outputs gq [nmodes][nsamp], g_r, g_z [nsamp]. */
+int orc_adjoint_fmm_sampled(int64_t ns, const double *sr, const double *sz, int64_t nf, const double *tr,
+                            const double *tz, int nmodes, const double *q_re, const double *q_im,
+                            const double *gphi_re, const double *gphi_im, int M, int d, const double *geom,
+                            int64_t nsamp, const int64_t *samples, double *gq_re, double *gq_im, double *g_r,
+                            double *g_z)
+{
+    size_t m = (size_t)nmodes * (nsamp > 0 ? nsamp : 1);
+    double *B = (double *)malloc(sizeof(double) * m * 4);
+    if (!B) return -2;
+    int rc = orc_fmm_sampled(nf, tr, tz, ns, sr, sz, nmodes, gphi_re, gphi_im, M, d, geom, nsamp, samples, gq_re,
+                             gq_im, B, B + m, B + 2 * m, B + 3 * m);
+    for (int64_t s = 0; s < nsamp; ++s) {
+        int64_t i = samples[s];
+        double ar = 0.0, az = 0.0;
+        for (int n = 0; n < nmodes; ++n) {
+            size_t o = (size_t)n * ns + i, u = (size_t)n * nsamp + s;
+            ar += q_re[o] * B[u] + q_im[o] * B[m + u];
+            az += q_re[o] * B[2 * m + u] + q_im[o] * B[3 * m + u];
+        }
+        g_r[s] = ar;
+        g_z[s] = az;
+    }
+    free(B);
+    return rc;
+}
+
+/* Counts of the uniform tree's work, from the definitions of Sec. 2.2: a box of level l
+ * is present when it holds a source or a field point; out[0] = (field point, source)
+ * pairs of the near field (3x3 neighbour leaves), out[1] = (field box, source box) pairs
+ * of the interaction lists of levels 2..d with both boxes present, out[2] = the
+ * (field point, source) pairs those box pairs stand for.  Every pair of points is then
+ * counted exactly once: out[0] + out[2] = ns nf. */
+int orc_tree_counts(int64_t ns, const double *sr, const double *sz, int64_t nf, const double *tr,
+                    const double *tz, int d, const double *geom, int64_t *out)
+{
+    if (d < 2 || d > 14) return -1;
+    double r0 = geom[0], z0 = geom[1], L = geom[2];
+    out[0] = out[1] = out[2] = 0;
+    for (int l = 2; l <= d; ++l) {
+        int nl = 1 << l;
+        int64_t nb = (int64_t)nl * nl;
+        int64_t *cs = (int64_t *)calloc(nb, sizeof(int64_t));
+        int64_t *ct = (int64_t *)calloc(nb, sizeof(int64_t));
+        if (!cs || !ct) return -2;
+        for (int64_t q = 0; q < ns; ++q)
+            cs[(int64_t)orc_box_coord(sr[q], r0, L, l) * nl + orc_box_coord(sz[q], z0, L, l)]++;
+        for (int64_t j = 0; j < nf; ++j)
+            ct[(int64_t)orc_box_coord(tr[j], r0, L, l) * nl + orc_box_coord(tz[j], z0, L, l)]++;
+        for (int ti = 0; ti < nl; ++ti)
+            for (int tj = 0; tj < nl; ++tj) {
+                int64_t tb = (int64_t)ti * nl + tj;
+                if (cs[tb] + ct[tb] == 0) continue;
+                for (int ui = 2 * (ti / 2) - 2; ui <= 2 * (ti / 2) + 3; ++ui)
+                    for (int uj = 2 * (tj / 2) - 2; uj <= 2 * (tj / 2) + 3; ++uj) {
+                        if (ui < 0 || uj < 0 || ui >= nl || uj >= nl) continue;
+                        int64_t ub = (int64_t)ui * nl + uj;
+                        if (cs[ub] + ct[ub] == 0 || !in_s2l_list(ti, tj, ui, uj)) continue;
+                        out[1] += 1;
+                        out[2] += ct[tb] * cs[ub];
+                    }
+                if (l == d)
+                    for (int a = -1; a <= 1; ++a)
+                        for (int c = -1; c <= 1; ++c) {
+                            int ni = ti + a, nj = tj + c;
+                            if (ni < 0 || nj < 0 || ni >= nl || nj >= nl) continue;
+                            out[0] += ct[tb] * cs[(int64_t)ni * nl + nj];
+                        }
+            }
+        free(cs);
+        free(ct);
+    }
+    return 0;
+}
+
 /* ---- Fourier analysis and synthesis in the azimuth (Sec. 2, Eqs. analysis:source and
  * analysis:phi).  s(theta) = sum_{n=-N..N} S^(n) e^{i n theta} with S^(-n) = conj(S^(n)) for a
  * real density, and phi(theta) = sum_n Phi^(n) e^{i n theta}.  Reading: the paper's

@@ -43,7 +43,8 @@ class PlanInfo(ctypes.Structure):
                 ("precision", ctypes.c_int), ("r0", ctypes.c_double), ("z0", ctypes.c_double),
                 ("side", ctypes.c_double), ("ns", ctypes.c_int64), ("nf", ctypes.c_int64),
                 ("n_boxes", ctypes.c_int64 * 17), ("near_pairs", ctypes.c_int64),
-                ("s2l_pairs", ctypes.c_int64), ("expansions", ctypes.c_int64)]
+                ("s2l_pairs", ctypes.c_int64), ("expansions", ctypes.c_int64),
+                ("s2l_point_pairs", ctypes.c_int64), ("s2l_tensor_cores", ctypes.c_int)]
 
 
 _lib = None
@@ -179,7 +180,8 @@ class Plan:
         _check(self._lib.afmm_plan_info(self._h, ctypes.byref(inf)), "afmm_plan_info")
         return dict(depth=inf.depth, n_modes=inf.n_modes, order=inf.order, precision=inf.precision, r0=inf.r0,
                     z0=inf.z0, side=inf.side, ns=inf.ns, nf=inf.nf, n_boxes=list(inf.n_boxes),
-                    near_pairs=inf.near_pairs, s2l_pairs=inf.s2l_pairs, expansions=inf.expansions)
+                    near_pairs=inf.near_pairs, s2l_pairs=inf.s2l_pairs, expansions=inf.expansions,
+                    s2l_point_pairs=inf.s2l_point_pairs, s2l_tensor_cores=bool(inf.s2l_tensor_cores))
 
     def set_timing(self, enable=True):
         _check(self._lib.afmm_set_timing(self._h, 1 if enable else 0), "afmm_set_timing")

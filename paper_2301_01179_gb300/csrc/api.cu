@@ -323,6 +323,8 @@ afmm_status afmm_plan_info(afmm_plan p, afmm_plan_info_t *info)
     info->near_pairs = p->near_pairs;
     info->s2l_pairs = p->s2l_pairs;
     info->expansions = p->expansions;
+    info->s2l_point_pairs = p->s2l_point_pairs;
+    info->s2l_tensor_cores = s2l_tc_enabled(p) ? 1 : 0;
     return AFMM_OK;
 }
 

@@ -213,7 +213,7 @@ struct afmm_plan_s {
     int64_t part_cap = 0;                       // doubles in part_buf
     int64_t n_max = 0;
     // statistics
-    int64_t near_pairs = 0, s2l_pairs = 0, expansions = 0;
+    int64_t near_pairs = 0, s2l_pairs = 0, expansions = 0, s2l_point_pairs = 0;
     // timing (events on the plan's stream; read back after the evaluation's last event)
     int timing = 0;
     cudaEvent_t ev[80];                         // phase timing events (AFMM_EV_L2P: after the L2P)

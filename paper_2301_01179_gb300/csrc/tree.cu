@@ -499,13 +499,23 @@ __global__ void k_near_pairs(const int2 *__restrict__ trng, const int2 *__restri
     atomicAdd(acc, (unsigned long long)(nt * s));
 }
 
-__global__ void k_s2l_count(const int32_t *__restrict__ tab, int64_t nbox, unsigned long long *__restrict__ acc)
+// S2L applications of a level (acc[0]) and the (field point, source) pairs they cover (acc[1])
+__global__ void k_s2l_count(const int32_t *__restrict__ tab, const int2 *__restrict__ trng,
+                            const int2 *__restrict__ srng, int64_t nbox, unsigned long long *__restrict__ acc)
 {
     int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= nbox) return;
-    unsigned long long s = 0;
-    for (int k = 0; k < 27; ++k) s += tab[b * 27 + k] >= 0;
+    unsigned long long s = 0, pp = 0;
+    const unsigned long long nt = (unsigned long long)(trng[b].y - trng[b].x);
+    for (int k = 0; k < 27; ++k) {
+        int32_t q = tab[b * 27 + k];
+        if (q >= 0) {
+            s += 1;
+            pp += nt * (unsigned long long)(srng[q].y - srng[q].x);
+        }
+    }
     atomicAdd(acc, s);
+    atomicAdd(acc + 1, pp);
 }
 
 static inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b > 0 ? (n + b - 1) / b : 1); }
@@ -706,19 +716,21 @@ afmm_status build_tree(afmm_plan p, const double *src_r, const double *src_z, co
             AFMM_LAUNCH_CHECK();
         }
         unsigned long long *acc = nullptr;
-        AFMM_TRY(dalloc_t(p, &acc, 2));
-        AFMM_CUDA(cudaMemsetAsync(acc, 0, 2 * sizeof(unsigned long long), st));
+        AFMM_TRY(dalloc_t(p, &acc, 3));
+        AFMM_CUDA(cudaMemsetAsync(acc, 0, 3 * sizeof(unsigned long long), st));
         k_near_pairs<<<nblk(nb), 256, 0, st>>>(v.trng, v.srng, v.nbr, nb, acc);
         AFMM_LAUNCH_CHECK();
         for (int l = 2; l <= d; ++l) {
-            k_s2l_count<<<nblk(p->lv[l].nbox), 256, 0, st>>>(p->lv[l].s2l, p->lv[l].nbox, acc + 1);
+            const Level &u = p->lv[l];
+            k_s2l_count<<<nblk(u.nbox), 256, 0, st>>>(u.s2l, u.trng, u.srng, u.nbox, acc + 1);
             AFMM_LAUNCH_CHECK();
         }
-        unsigned long long h[2];
+        unsigned long long h[3];
         AFMM_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
         AFMM_CUDA(cudaStreamSynchronize(st));
         p->near_pairs = (int64_t)h[0];
         p->s2l_pairs = (int64_t)h[1];
+        p->s2l_point_pairs = (int64_t)h[2];
     }
     p->n_max = nmax;
     return AFMM_OK;

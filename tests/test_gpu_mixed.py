@@ -1,10 +1,14 @@
 """GPU parity of the mixed-precision path (AFMM_MIXED) against the FP64 oracle.
 
-MIXED keeps the Legendre recursion, the elliptic (AGM) start values and the pair geometry
-in FP64, and does the bulk accumulation in Kahan-compensated FP32 and the far field
-(moments, shifts, S2L) in FP32 on box-scaled coordinates.  Its stated error, per mode
-(Eq. results:error): near field and direct sums <= 2e-6, FMM <= 2e-5 on top of the FP64
-FMM's own truncation error (both measured on these workloads on GB300)."""
+MIXED forms the pair geometry (r - r1, r + r1, z - z1) in FP64 and splits it exactly into
+FP32 pairs; the elliptic (AGM) start values and the Legendre recursion run in FP32-pair
+arithmetic (48-bit significands, FP32 exponent range with exact power-of-two rescaling),
+not in IEEE FP64; the products with the strengths are FP32 with Kahan-compensated FP32
+sums, and the far field (moments, shifts, S2L) is FP32 on box-scaled coordinates.  Its
+stated error, per mode (Eq. results:error): near field and direct sums <= 2e-6, FMM <= 2e-5
+on top of the FP64 FMM's own truncation error (both measured on these workloads on GB300).
+The FP32-pair sequence itself is checked against the native FP64 sequence pair by pair on
+near-singular and far pairs (test_fp32_pair_sequence_vs_native_fp64)."""
 import numpy as np
 import pytest
 
@@ -62,3 +66,39 @@ def test_mixed_adjoint_matches_oracle():
     assert eps_modes(g[0], g[1], A[0], A[1]).max() < TOL_FMM
     assert np.max(np.abs(g[2] - A[2])) / np.max(np.abs(A[2])) < TOL_FMM
     assert np.max(np.abs(g[3] - A[3])) / np.max(np.abs(A[3])) < TOL_FMM
+
+
+def test_fp32_pair_sequence_vs_native_fp64():
+    """The Legendre sequence of the FP32-pair kernels (shared by MIXED and the FP64 path)
+    against native FP64 (afmm_green) pair by pair: one ring source on the near-singular
+    curve workload's profile and field points at distances 1e-9 .. 3 from it (chi - 1 from
+    ~1e-18, the logarithmic near-singularity, to the Miller regime).  With unit strengths
+    the direct sum of one source is the sequence G^(n) itself.  Per mode, the error of every
+    pair relative to its G^(0) (the scale of the max-normalised per-mode error):
+      - FP64 path (FP32-pair sequence, pair products): <= 1e-11;
+      - MIXED (the same sequence, FP32 products): <= 2e-6, the FP32 rounding of the product."""
+    import torch
+    from paper_2301_01179_gb300 import binding
+    rng = np.random.default_rng(31)
+    r1, z1 = 0.5 + 0.2 * np.cos(1.1), 0.3 * np.sin(1.1)
+    dist = 10.0 ** rng.uniform(-9.0, 0.5, 3000)
+    ang = rng.uniform(0.0, 2.0 * np.pi, 3000)
+    tr = r1 + dist * np.cos(ang)
+    tz = z1 + dist * np.sin(ang)
+    keep = tr > 1e-3
+    tr, tz = tr[keep], tz[keep]
+    nm = 65
+    sr, sz, dtr, dtz = to_dev(np.array([r1]), np.array([z1]), tr, tz)
+    q_re, q_im = to_dev(np.ones((nm, 1)), np.zeros((nm, 1)))
+    G = binding.green(dtr, torch.full_like(dtr, r1), dtz - z1, nm).cpu().numpy()
+    ref0 = np.abs(G[0])
+    worst = {}
+    for prec, tol in (("fp64", 1e-11), ("mixed", 2e-6)):
+        pl = binding.Plan(sr, sz, dtr, dtz, nm, order=4, leaf_size=64, precision=prec)
+        g = to_np(*pl.direct(q_re, q_im))
+        pl.close()
+        err = np.abs(g[0] - G) / ref0[None, :]
+        worst[prec] = err.max(axis=1)
+        print(prec, "per-mode max error / G0:", np.array2string(worst[prec], precision=1))
+        assert err.max() < tol, (prec, err.max(), np.unravel_index(err.argmax(), err.shape))
+        assert np.abs(g[1]).max() == 0.0

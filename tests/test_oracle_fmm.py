@@ -172,3 +172,83 @@ def test_adjoint_fmm_matches_adjoint_direct():
     assert _eps(B[0], B[1], A[0], A[1]).max() < 1e-5
     assert np.max(np.abs(B[2] - A[2])) / np.max(np.abs(A[2])) < 1e-4
     assert np.max(np.abs(B[3] - A[3])) / np.max(np.abs(A[3])) < 1e-4
+
+
+@pytest.mark.parametrize("kind,ns,nf,nm,M,d", [("cfg1", 2000, 1500, 17, 8, 4), ("cfg3", 4000, 3000, 9, 6, 5),
+                                                ("cfg5", 3000, 2500, 9, 6, 6), ("cfg2", 6000, 6000, 5, 12, 5)])
+def test_fmm_sampled_equals_full_fmm(kind, ns, nf, nm, M, d):
+    """The sampled oracle (each level's S2L evaluated at the point, shifts skipped as exact
+    re-expansions) must give the full Algorithm-1 oracle's field and gradient at the
+    sampled points to rounding; a dropped level, a wrong orientation or a list slot
+    missing would show at 1e-3..1e-8, far above this bar."""
+    w = W.make(kind, ns=ns, nf=nf, n_modes=nm)
+    _, geom = oracle.tree_setup(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], 1, depth_override=d)
+    F = oracle.fmm(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], w["q_re"], w["q_im"], M, d, geom, grad=True)
+    idx = W.subset(nf, 37, seed=9)
+    S = oracle.fmm_sampled(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], w["q_re"], w["q_im"], M, d, geom, idx,
+                           grad=True)
+    for c in range(0, 6, 2):
+        assert _eps(S[c], S[c + 1], F[c][:, idx], F[c + 1][:, idx]).max() < 1e-12, c
+    P = oracle.fmm_sampled(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], w["q_re"], w["q_im"], M, d, geom, idx)
+    np.testing.assert_array_equal(P[0], S[0])
+
+
+def test_adjoint_fmm_sampled_equals_full_adjoint():
+    w = W.make("cfg4", ns=1500, nf=1200, n_modes=7, with_targets=True)
+    d = 5
+    _, geom = oracle.tree_setup(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], 1, depth_override=d)
+    A = oracle.adjoint_fmm(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], w["q_re"], w["q_im"], w["T_re"], w["T_im"],
+                           8, d, geom)
+    idx = W.subset(1500, 29, seed=4)
+    S = oracle.adjoint_fmm_sampled(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], w["q_re"], w["q_im"], w["T_re"],
+                                   w["T_im"], 8, d, geom, idx)
+    assert _eps(S[0], S[1], A[0][:, idx], A[1][:, idx]).max() < 1e-12
+    for c in (2, 3):
+        np.testing.assert_allclose(S[c], A[c][idx], rtol=0, atol=1e-12 * np.abs(A[c]).max())
+
+
+def _box(v, v0, L, l):
+    return np.clip(np.floor((v - v0) * (2 ** l) / L), 0, 2 ** l - 1).astype(np.int64)
+
+
+@pytest.mark.parametrize("kind,n,d", [("cfg1", 300, 4), ("cfg5", 400, 5), ("cfg3", 350, 5)])
+def test_tree_counts_by_brute_force(kind, n, d):
+    """Tree counts against a pair-by-pair classification from the definitions of Sec. 2.2:
+    a pair is near when its leaves are 3x3 neighbours, else it belongs to the one level l
+    where its boxes are not neighbours but their parents are; box pairs count each
+    (field box, source box) of a list once when both boxes hold a point."""
+    w = W.make(kind, ns=n, nf=n - 50, n_modes=1)
+    _, geom = oracle.tree_setup(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], 1, depth_override=d)
+    near, box_pairs, far = oracle.tree_counts(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], d, geom)
+    r0, z0, L = geom
+    near_bf = 0
+    levels_hit = np.zeros(d + 1, dtype=np.int64)
+    for j in range(w["tgt_r"].size):
+        for i in range(n):
+            hit = 0
+            for l in range(2, d + 1):
+                a = [_box(w["tgt_r"][j], r0, L, l), _box(w["tgt_z"][j], z0, L, l)]
+                b = [_box(w["src_r"][i], r0, L, l), _box(w["src_z"][i], z0, L, l)]
+                nbr = max(abs(a[0] - b[0]), abs(a[1] - b[1])) <= 1
+                pnbr = max(abs(a[0] // 2 - b[0] // 2), abs(a[1] // 2 - b[1] // 2)) <= 1
+                if not nbr and pnbr:
+                    hit += 1
+                    levels_hit[l] += 1
+                if l == d and nbr:
+                    near_bf += 1
+                    hit += 1
+            assert hit == 1
+    assert near == near_bf
+    assert near + far == n * (n - 50)
+    assert far == int(levels_hit.sum())
+    # box pairs: occupied boxes per level, list membership by the same rule
+    bp = 0
+    for l in range(2, d + 1):
+        occ = set(zip(_box(w["src_r"], r0, L, l), _box(w["src_z"], z0, L, l))) | \
+            set(zip(_box(w["tgt_r"], r0, L, l), _box(w["tgt_z"], z0, L, l)))
+        for (ti, tj) in occ:
+            for (ui, uj) in occ:
+                nbr = max(abs(ti - ui), abs(tj - uj)) <= 1
+                pnbr = max(abs(ti // 2 - ui // 2), abs(tj // 2 - uj // 2)) <= 1
+                bp += (not nbr) and pnbr
+    assert box_pairs == bp
