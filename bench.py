@@ -28,24 +28,70 @@ UNIT = "modal ring interactions/s"
 WORKLOAD = "cfg2"
 WORKLOAD_DESC = ("1,000,000 ring sources x 1,000,000 field points, r~U[0.05,2], z~U[-2,2], modes n=0..32, "
                  "complex N(0,1) amplitudes, FMM order 12, leaf 64, FP64")
-# FP32 issue peak of the GB300, from its unit counts and clock: 152 SMs x 128 FP32 lanes x
-# 2.07 GHz (one FP32 operation per lane and clock; an FMA counts as one operation)
-FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
-# near field, FP32-pair arithmetic, a-priori operation count per (field point, source) pair:
-# ~600 for the pair geometry, the AGM start values and the gradient factors, then per mode 22
-# (forward recursion step: two products and a difference), 30 (scale and two compensated
-# accumulations) and 88 (derivative weight, its two factors, four compensated accumulations).
-# Miller pairs' longer sweeps are not counted.
-NEAR_SETUP_OPS, NEAR_MODE_OPS = 600, 22 + 30 + 88
+# FP32 issue peak of the GB300 from its unit counts and clock (152 SMs x 128 FP32 lanes x
+# 2.07 GHz, an FMA counting as one operation): context only; the rooflines use the peaks
+# measured at run time by the FMA probes of libafmm_peaks.so.
+FP32_NOMINAL_TOPS = 152 * 128 * 2.07e9 / 1e12
+# Method work of the near field per (field point, source) pair, with the field gradient:
+# ~80 FP64 operations of set-up (pair geometry, 2 square roots, 2 divisions, the AGM start
+# values), then per mode 3 for the recursion step and 2 for the (complex) accumulation, and 6
+# more for the gradient (two derivative weights, four accumulations): 80 + 11 (N + 1).
+NEAR_METHOD_SETUP, NEAR_METHOD_MODE = 80, 3 + 2 + 6
+# What the FP32-pair kernel issues per pair (its own arithmetic, for the issue-utilisation
+# figure): ~600 FP32 operations of set-up, then per mode 22 (forward recursion step), 30 (scale
+# and two compensated accumulations) and 88 (derivative weight and four compensated
+# accumulations).  Miller pairs' longer sweeps are not counted.
+NEAR_ISSUE_SETUP, NEAR_ISSUE_MODE = 600, 22 + 30 + 88
+# S2L on the tensor cores: 21 digit-slice products per FP64-equivalent multiply-add
+S2L_SLICE_PAIRS = 21
 
 
-def l2p_ops(M):
-    """FP32 operations of the local-expansion evaluation (value and gradient, FP32 pairs) per
+def l2p_issue_ops(M):
+    """FP32 operations the local-expansion kernel issues (value and gradient, FP32 pairs) per
     field point, mode and real/imaginary part: per coefficient two pair multiply-adds (32), per
     axial degree three (48)."""
     return 32 * (M + 1) * (M + 2) // 2 + 48 * (M + 1)
-# S2L on the tensor cores: 21 digit-slice products per FP64-equivalent multiply-add
-S2L_SLICE_PAIRS = 21
+
+
+def l2p_method_ops(M):
+    """Method work of the local expansion with gradient per (field point, mode), complex:
+    value 2 ncoef FMA plus 2 ncoef for each gradient component."""
+    return 3 * 2 * (M + 1) * (M + 2) // 2
+
+
+def measure_fma_peaks(dev):
+    """Measured FMA throughput of this GPU (T operations/s, one FMA = one operation) from the
+    probes of libafmm_peaks.so: FP32 scalar, FP32 packed f32x2, FP64; CUDA events on the
+    current stream around 3 launches after one warm-up, each launch sized to ~50 ms."""
+    import ctypes
+    import torch
+    from paper_2301_01179_gb300 import build as B
+    lib = ctypes.CDLL(B.PEAKS_OUT)
+    lib.afmm_peak_launch.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    lib.afmm_peak_launch.restype = ctypes.c_int
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = nsm * 8
+    sink = torch.empty(blocks * 256, dtype=torch.float32, device=dev)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    out = {}
+    for kind, name, iters in ((0, "fp32", 400000), (1, "fp32x2", 200000), (2, "fp64", 6000)):
+        ops = ctypes.c_double()
+        rc = lib.afmm_peak_launch(kind, blocks, iters, ctypes.c_void_p(sink.data_ptr()), ctypes.byref(ops), st)
+        if rc != 0:
+            raise RuntimeError("afmm_peak_launch %d failed: %d" % (kind, rc))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            lib.afmm_peak_launch(kind, blocks, iters, ctypes.c_void_p(sink.data_ptr()), ctypes.byref(ops), st)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = 3 * ops.value / (e0.elapsed_time(e1) / 1e3) / 1e12
+    out["fp32_best"] = max(out["fp32"], out["fp32x2"])
+    out["probe"] = ("libafmm_peaks.so: %d blocks x 256 threads x 8 independent FMA chains, CUDA events over 3 launches"
+                    % blocks)
+    return out
 
 
 def measured_bf16_peak():
@@ -315,6 +361,77 @@ def mixed_vs_fp64(kind, steps, dev):
             "eps_max": {k: max(v) for k, v in eps.items()}, "eps_per_mode": eps}
 
 
+def mixed_vs_fp64_sampled(kind, k, dev):
+    """The MIXED path against the FP64 path at k sampled field points of a configuration
+    (the 4e6-ring workload by default) against all its sources: one plan over the sources
+    and the sampled points per precision (the same tree), FMM potential and gradient,
+    eps^(n) = max |mixed - fp64| / max |fp64| per mode and component."""
+    import numpy as np
+    import torch
+    from paper_2301_01179_gb300 import binding, workloads as W
+    w = W.make(kind)
+    nm = w["n_modes"]
+    idx = W.subset(w["tgt_r"].size, k, seed=13)
+
+    def d(a):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+
+    sr, sz, tr, tz, qr, qi = map(d, (w["src_r"], w["src_z"], w["tgt_r"][idx], w["tgt_z"][idx], w["q_re"], w["q_im"]))
+    res, ms = {}, {}
+    for prec in ("fp64", "mixed"):
+        pl = binding.Plan(sr, sz, tr, tz, nm, order=w["order"], leaf_size=w["leaf"], precision=prec)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = pl.grad(qr, qi)
+        e1.record()
+        torch.cuda.synchronize()
+        ms[prec] = e0.elapsed_time(e1)
+        res[prec] = [o.cpu().numpy() for o in out]
+        depth = pl.info()["depth"]
+        pl.close()
+    eps = {}
+    for name, c in (("potential", 0), ("d_dr", 2), ("d_dz", 4)):
+        a = res["mixed"][c] + 1j * res["mixed"][c + 1]
+        b = res["fp64"][c] + 1j * res["fp64"][c + 1]
+        den = np.max(np.abs(b), axis=1)
+        eps[name] = [float(x) for x in np.max(np.abs(a - b), axis=1) / np.where(den > 0, den, 1.0)]
+    return {"workload": "%s: %d sources x %d sampled field points, modes 0..%d, order %d, leaf %d, depth %d"
+                        % (kind, w["src_r"].size, k, nm - 1, w["order"], w["leaf"], depth),
+            "fp64_grad_ms": ms["fp64"], "mixed_grad_ms": ms["mixed"],
+            "eps_max": {k2: max(v) for k2, v in eps.items()}, "eps_per_mode": eps}
+
+
+def native_step(w, dev):
+    """The headline step (plan + FMM potential and gradient) with AFMM_FP64_NATIVE: every
+    floating-point operation in native FP64 (CUDA cores), one warm-up and one timed step."""
+    import numpy as np
+    import torch
+    from paper_2301_01179_gb300 import binding
+
+    def d(a):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+
+    sr, sz, tr, tz, qr, qi = map(d, (w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], w["q_re"], w["q_im"]))
+    nm = w["n_modes"]
+    phases = None
+    for it in range(2):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pl = binding.Plan(sr, sz, tr, tz, nm, order=w["order"], leaf_size=w["leaf"], precision="fp64_native")
+        if it == 1:
+            pl.set_timing(True)
+        pl.grad(qr, qi)
+        if it == 1:
+            phases = {k: round(v, 2) for k, v in pl.timing().items()}
+        pl.close()
+        e1.record()
+        torch.cuda.synchronize()
+    return {"step_ms": e0.elapsed_time(e1), "phase_ms": phases,
+            "step": "plan + FMM potential and field gradient, AFMM_FP64_NATIVE"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -377,38 +494,53 @@ def run_ours(args):
     clocks = clk.stop()
     value, t_ms = aggregate(ws, units_per_step, e0.elapsed_time(e1) / args.steps, dev)
 
-    # ---- roofline of the dominant kernel, from the live phase split of the timed steps (CUDA
-    # events recorded by the library on the plan's stream around each phase)
+    # ---- rooflines, from the live phase split of the timed steps (CUDA events recorded by the
+    # library on the plan's stream around each phase) and the FMA peaks measured on this GPU.
+    # Achieved = the method's work (SURVEY-style per-unit counts, not the FP32-pair emulation's
+    # own instructions) / the kernel's time; the emulation's issue rate is reported beside it.
     nc = (M + 1) * (M + 2) // 2
     s2l_ms = statistics.mean(p["s2l"] for p in phases)
     near_ms = statistics.mean(p["near"] for p in phases)
     traffic_of = read_traffic()
-    near_ops = NEAR_SETUP_OPS + nm * NEAR_MODE_OPS
-    near_ach = float(info["near_pairs"]) * near_ops / (near_ms / 1e3) / 1e12
+    pk = measure_fma_peaks(dev)
+    near_work = NEAR_METHOD_SETUP + nm * NEAR_METHOD_MODE
+    near_ach = float(info["near_pairs"]) * near_work / (near_ms / 1e3) / 1e12
+    near_issue = float(info["near_pairs"]) * (NEAR_ISSUE_SETUP + nm * NEAR_ISSUE_MODE) / (near_ms / 1e3) / 1e12
     near_roof = {"bound": "alu", "kernel": "k_near_ws (near field, potential and gradient, FP32 pairs)",
-                 "achieved": near_ach, "peak": FP32_PEAK_TOPS, "unit": "FP32 Tops/s",
-                 "frac": near_ach / FP32_PEAK_TOPS, "traffic": traffic_of.get("k_near_ws"),
-                 "work_per_unit": "%d FP32 operations per near pair (%d + %d (N+1)) x %d pairs per launch"
-                                  % (near_ops, NEAR_SETUP_OPS, NEAR_MODE_OPS, info["near_pairs"]),
-                 "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (derived from unit counts and clock)"}
+                 "achieved": near_ach, "peak": pk["fp32_best"], "unit": "T operations/s (FMA = 1)",
+                 "frac": near_ach / pk["fp32_best"], "traffic": traffic_of.get("k_near_ws"),
+                 "work_per_unit": "%d method operations per near pair (%d + %d (N+1), FP64-class: set-up, "
+                                  "recursion, accumulation, gradient) x %d pairs per launch"
+                                  % (near_work, NEAR_METHOD_SETUP, NEAR_METHOD_MODE, info["near_pairs"]),
+                 "peak_source": "measured FP32 FMA peak (of measured; libafmm_peaks.so, best of scalar and f32x2)",
+                 "frac_of_fp64_pipe": near_ach / pk["fp64"],
+                 "fp64_peak": pk["fp64"],
+                 "issue_utilisation": near_issue / pk["fp32_best"],
+                 "issue_work_per_unit": "%d FP32 operations per near pair issued by the FP32-pair kernel"
+                                        % (NEAR_ISSUE_SETUP + nm * NEAR_ISSUE_MODE)}
     bf16_peak, bf16_src = measured_bf16_peak()
-    s2l_flop = float(info["s2l_pairs"]) * nm * 4.0 * nc * nc * S2L_SLICE_PAIRS
-    s2l_ach = s2l_flop / (s2l_ms / 1e3) / 1e12
-    s2l_roof = {"bound": "tensor", "kernel": "k_s2l_tc (tcgen05 bf16, exact 6-digit slicing; all levels)",
+    s2l_method = float(info["s2l_pairs"]) * nm * 4.0 * nc * nc  # 2 ncoef^2 FMA per (box pair, mode)
+    s2l_ach = s2l_method / (s2l_ms / 1e3) / 1e12
+    s2l_roof = {"bound": "tensor", "kernel": "k_slice_moments + k_s2l_tc (tcgen05 bf16, exact 6-digit slicing; "
+                                             "all levels)",
                 "achieved": s2l_ach, "peak": bf16_peak, "unit": "TFLOP/s", "frac": s2l_ach / bf16_peak,
                 "traffic": traffic_of.get("k_s2l_tc"),
-                "work_per_unit": "21 digit-slice products x 4 ncoef^2 flop per (box pair, mode); %d box pairs"
-                                 % info["s2l_pairs"],
-                "peak_source": bf16_src}
+                "work_per_unit": "2 ncoef^2 FMA (4 ncoef^2 flop, FP64-equivalent) per (box pair, mode); %d box pairs "
+                                 "x %d modes" % (info["s2l_pairs"], nm),
+                "peak_source": bf16_src,
+                "tensor_issue_utilisation": s2l_ach * S2L_SLICE_PAIRS / bf16_peak,
+                "tensor_work_per_unit": "21 digit-slice products x 4 ncoef^2 bf16 flop per (box pair, mode)"}
     l2p_ms = statistics.mean(p["l2p"] for p in phases)
-    l2p_pt = 2 * nm * l2p_ops(M)
-    l2p_ach = float(nf) * l2p_pt / (l2p_ms / 1e3) / 1e12
+    l2p_work = nm * l2p_method_ops(M)
+    l2p_ach = float(nf) * l2p_work / (l2p_ms / 1e3) / 1e12
+    l2p_issue = float(nf) * 2 * nm * l2p_issue_ops(M) / (l2p_ms / 1e3) / 1e12
     l2p_roof = {"bound": "alu", "kernel": "k_l2p (local expansion at the field points, value and gradient, FP32 pairs)",
-                "achieved": l2p_ach, "peak": FP32_PEAK_TOPS, "unit": "FP32 Tops/s", "frac": l2p_ach / FP32_PEAK_TOPS,
-                "traffic": traffic_of.get("k_l2p"),
-                "work_per_unit": "%d FP32 operations per field point (2 (N+1) x %d) x %d points"
-                                 % (l2p_pt, l2p_ops(M), nf),
-                "peak_source": near_roof["peak_source"]}
+                "achieved": l2p_ach, "peak": pk["fp32_best"], "unit": "T operations/s (FMA = 1)",
+                "frac": l2p_ach / pk["fp32_best"], "traffic": traffic_of.get("k_l2p"),
+                "work_per_unit": "%d method FMA per field point (6 ncoef per mode: value and two gradient "
+                                 "components, complex) x %d points" % (l2p_work, nf),
+                "peak_source": near_roof["peak_source"], "frac_of_fp64_pipe": l2p_ach / pk["fp64"],
+                "issue_utilisation": l2p_issue / pk["fp32_best"]}
     roofline, secondary = (near_roof, s2l_roof) if near_ms >= s2l_ms else (s2l_roof, near_roof)
     phase_ms = {k: round(statistics.mean(p[k] for p in phases), 3) for k in phases[0]}
 
@@ -417,36 +549,65 @@ def run_ours(args):
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": t_ms,
                               "phase_ms": {k: round(statistics.mean(p[k] for p in phases), 3) for k in phases[0]},
                               "roofline": roofline, "roofline_secondary": secondary, "roofline_l2p": l2p_roof,
-                              "profiling_run": True}),
+                              "fma_peaks": pk, "profiling_run": True}),
                   flush=True)
         return 0
-    # ---- e2e: the public API with host buffers (H2D of inputs, D2H of results each step)
+    # ---- e2e: the public API with host buffers (H2D of inputs, D2H of results each step).
+    # Inputs go from pinned host memory into preallocated device buffers: the coordinates first
+    # (the plan needs them), the amplitudes on a second stream while the plan is built; the
+    # six result planes come back into pinned host memory.  CUDA events split each step.
     hp = [torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64).pin_memory()
           for a in (w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], w["q_re"], w["q_im"])]
     hout = [torch.empty(nm, nf, dtype=torch.float64).pin_memory() for _ in range(6)]
+    dbuf = [torch.empty(t.shape, dtype=torch.float64, device=dev) for t in hp]
+    side = torch.cuda.Stream(device=dev)
     h2d = sum(t.numel() * 8 for t in hp)
     d2h = sum(t.numel() * 8 for t in hout)
 
-    def e2e_step():
-        dv = [t.to(dev, non_blocking=True) for t in hp]
-        pl = binding.Plan(dv[0], dv[1], dv[2], dv[3], nm, order=M, leaf_size=leaf)
-        out = pl.grad(dv[4], dv[5])
+    def e2e_step(ev=None):
+        main = torch.cuda.current_stream()
+        if ev:
+            ev[0].record(main)
+        for i in range(4):
+            dbuf[i].copy_(hp[i], non_blocking=True)
+        side.wait_stream(main)
+        with torch.cuda.stream(side):
+            dbuf[4].copy_(hp[4], non_blocking=True)
+            dbuf[5].copy_(hp[5], non_blocking=True)
+        if ev:
+            ev[1].record(main)
+        pl = binding.Plan(dbuf[0], dbuf[1], dbuf[2], dbuf[3], nm, order=M, leaf_size=leaf)
+        if ev:
+            ev[2].record(main)
+        main.wait_stream(side)
+        out = pl.grad(dbuf[4], dbuf[5])
+        if ev:
+            ev[3].record(main)
         for h, o in zip(hout, out):
             h.copy_(o, non_blocking=True)
+        if ev:
+            ev[4].record(main)
         torch.cuda.synchronize()
         pl.close()
 
     e2e_step()
     barrier(ws)
     torch.cuda.synchronize()
+    ke = max(5, args.steps)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(ke)]
     t0 = time.time()
-    ke = max(1, min(args.steps, 3))
-    for _ in range(ke):
-        e2e_step()
+    for k in range(ke):
+        e2e_step(evs[k])
     barrier(ws)
     te = max_over_ranks(ws, (time.time() - t0) / ke, dev)
+    split = {"h2d_coordinates": statistics.mean(e[0].elapsed_time(e[1]) for e in evs),
+             "plan": statistics.mean(e[1].elapsed_time(e[2]) for e in evs),
+             "grad_incl_amplitude_wait": statistics.mean(e[2].elapsed_time(e[3]) for e in evs),
+             "d2h_results": statistics.mean(e[3].elapsed_time(e[4]) for e in evs),
+             "between_steps_host": statistics.mean(evs[k][4].elapsed_time(evs[k + 1][0]) for k in range(ke - 1))}
     e2e = {"value": ws * units_per_step / te, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-           "ms_per_step": 1e3 * te}
+           "ms_per_step": 1e3 * te, "steps": ke, "timer": "host clock over all steps (events split each step)",
+           "split_ms": {k: round(v, 3) for k, v in split.items()}}
 
     extra = {}
     if rank == 0:
@@ -479,17 +640,30 @@ def run_ours(args):
         extra["plan_ms"] = e0.elapsed_time(e1) / 3
         # forward + backward (adjoint) steps of the gradient configurations (not the headline)
         fb = {}
-        for kind, prec in [("cfg4", "fp64")] + [(k, "mixed") for k in args.fwd_bwd if k == "cfg5"]:
+        kinds = [("cfg4", "fp64")] + ([] if args.no_cfg5 else [("cfg5", "mixed")])
+        for kind, prec in kinds:
             try:
                 fb[kind] = fwd_bwd(kind, prec, 2 if kind == "cfg5" else 3, 1, dev)
             except Exception as exc:  # an extra must not cost the headline line
                 fb[kind] = {"error": str(exc)[:200]}
         extra["fwd_bwd"] = fb
-        # the mixed-precision path on the near-singular curve workload (not the headline)
+        # the mixed-precision path on the near-singular curve workload, and on the 4e6-ring
+        # workload at sampled field points (not the headline)
         try:
             extra["mixed_vs_fp64"] = mixed_vs_fp64("cfg3", 2, dev)
         except Exception as exc:
             extra["mixed_vs_fp64"] = {"error": str(exc)[:200]}
+        if not args.no_cfg5:
+            try:
+                extra["mixed_vs_fp64_cfg5"] = mixed_vs_fp64_sampled("cfg5", 1024, dev)
+            except Exception as exc:
+                extra["mixed_vs_fp64_cfg5"] = {"error": str(exc)[:200]}
+        # the same headline step with every operation in native FP64 (what the FP32-pair and
+        # tensor-core design buys on this chip)
+        try:
+            extra["fp64_native_step"] = native_step(w, dev)
+        except Exception as exc:
+            extra["fp64_native_step"] = {"error": str(exc)[:200]}
 
     line = None
     if rank == 0:
@@ -502,7 +676,7 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (amplitudes 528 MB per step)",
                            "parallelism": "replicas" if ws > 1 else "single GPU"},
                 "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "roofline_secondary": secondary,
-                "roofline_l2p": l2p_roof,
+                "roofline_l2p": l2p_roof, "fma_peaks": pk,
                 "cpu_baseline": cb,
                 "clocks": clocks, "phase_ms": phase_ms,
                 "near_pairs": info["near_pairs"], "s2l_pairs": info["s2l_pairs"]}
@@ -521,8 +695,8 @@ def main():
     ap.add_argument("--ns", type=int, default=None, help="profiling captures: fewer sources (same laws)")
     ap.add_argument("--nf", type=int, default=None, help="profiling captures: fewer field points")
     ap.add_argument("--no-extras", action="store_true", help="profiling captures: skip e2e and accuracy legs")
-    ap.add_argument("--fwd-bwd", default="", type=lambda v: [x for x in v.split(",") if x],
-                    help="also time the forward+adjoint step of these configurations (cfg5: 4e6 x 4e6, MIXED)")
+    ap.add_argument("--no-cfg5", action="store_true",
+                    help="skip the 4e6-ring MIXED forward+adjoint step and its sampled error (about 40 s)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -31,6 +31,20 @@ def test_library_builds_and_exports_every_symbol():
     assert not missing, missing
 
 
+def test_peak_probe_library_exports_its_header():
+    from paper_2301_01179_gb300 import build as B
+    B.build()
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "afmm_peaks.h")).read(), flags=re.S)
+    names = sorted(set(re.findall(r"\b(afmm_[a-z_]+)\s*\(", src)))
+    assert names == ["afmm_peak_launch"]
+    lib = ctypes.CDLL(B.PEAKS_OUT)
+    assert all(hasattr(lib, n) for n in names)
+    # bad arguments are rejected on the host, before any launch
+    lib.afmm_peak_launch.restype = ctypes.c_int
+    ops = ctypes.c_double()
+    assert lib.afmm_peak_launch(7, 1, 1, None, ctypes.byref(ops), None) == -1
+
+
 def test_binding_covers_header():
     torch = pytest.importorskip("torch")  # noqa: F841
     from paper_2301_01179_gb300 import binding
