@@ -15,7 +15,8 @@
  *     start values when the forward direction is stable, otherwise Miller's backward
  *     recursion from arbitrary start values, scaled with the known Q_{-1/2};
  *   - derivative (Taylor) coefficients gbar^(n)_{i,j,k} (Eq. gfunc:gnbar) from the
- *     x-recursion (Eq. gfunc:derivatives:x), the closed r-, r1- and mixed forms, and the
+ *     x-recursion (Eq. gfunc:derivatives:x), the closed r-, r1- and mixed forms (these and
+ *     their Legendre start values in binary128, see the reading there), and the
  *     Laplace-equation recursion (Eq. gfunc:laplace:recursion) with the x-derivative term
  *     that the printed formula leaves out (derived from Eq. gfunc:laplace);
  *   - the direct modal sum (Eq. analysis:sum), its field gradient, and the uniform
@@ -229,6 +230,156 @@ void orc_green_grad(double r, double r1, double x, int N, double *G, double *Gr,
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* binary128 copies of the steps that feed the Taylor coefficients (Appendix A).          */
+/* Reading: the paper gives no precision.  The x-recursion (Eq. gfunc:derivatives:x) and  */
+/* the closed first-derivative forms couple G^(n) with G^(n-1) through their difference,  */
+/* which cancels as chi -> 1; the Laplace recursion then carries those errors into the    */
+/* high mixed coefficients.  At the paper's own sizes (modes 0..17) FP64 loses nothing    */
+/* visible, but at modes 0..32 and beyond the FP64 coefficients of axially adjacent boxes */
+/* on fine levels lose up to ten digits (measured against an 80-bit run).  So the oracle  */
+/* forms the Legendre start values, the Taylor vectors of the rational factors and the    */
+/* four base columns gbar_{0,0,k}, gbar_{1,0,k}, gbar_{0,1,k}, gbar_{1,1,k} in binary128  */
+/* (_Float128: + - * / only, from the compiler), rounds them to FP64, and runs the        */
+/* Laplace recursion (which is stable given accurate base columns) in FP64.               */
+/* ------------------------------------------------------------------------------------ */
+typedef _Float128 orc_q;
+
+static orc_q q_abs(orc_q a) { return a < 0 ? -a : a; }
+static orc_q q_max(orc_q a, orc_q b) { return a > b ? a : b; }
+
+/* square root: Newton's iteration from the FP64 root (three steps reach full precision) */
+static orc_q q_sqrt(orc_q a)
+{
+    if (!(a > 0)) return 0;
+    orc_q s = (orc_q)sqrt((double)a);
+    for (int it = 0; it < 3; ++it) s = (s + a / s) / 2;
+    return s;
+}
+
+/* pi as the sum of its two nearest FP64 parts (about 107 bits) */
+static orc_q q_pi(void) { return (orc_q)3.141592653589793 + (orc_q)1.2246467991473532e-16; }
+
+/* Carlson R_F and R_D as above; the series is used once the deviation is below 3e-6, where
+ * its first neglected term (about dev^6) is below the binary128 rounding. */
+static orc_q q_carlson_rf(orc_q x, orc_q y, orc_q z)
+{
+    for (int m = 0; m < 200; ++m) {
+        orc_q A = (x + y + z) / 3;
+        orc_q X = 1 - x / A, Y = 1 - y / A, Z = 1 - z / A;
+        orc_q dev = q_max(q_abs(X), q_max(q_abs(Y), q_abs(Z)));
+        if (dev < (orc_q)3e-6) {
+            orc_q E2 = X * Y - Z * Z, E3 = X * Y * Z;
+            orc_q s = 1 - E2 / 10 + E3 / 14 + E2 * E2 / 24 - 3 * E2 * E3 / 44;
+            return s / q_sqrt(A);
+        }
+        orc_q sx = q_sqrt(x), sy = q_sqrt(y), sz = q_sqrt(z);
+        orc_q lam = sx * sy + sy * sz + sz * sx;
+        x = (x + lam) / 4;
+        y = (y + lam) / 4;
+        z = (z + lam) / 4;
+    }
+    return 0;
+}
+
+static orc_q q_carlson_rd(orc_q x, orc_q y, orc_q z)
+{
+    orc_q sum = 0, fac = 1;
+    for (int m = 0; m < 200; ++m) {
+        orc_q A = (x + y + 3 * z) / 5;
+        orc_q X = 1 - x / A, Y = 1 - y / A, Z = 1 - z / A;
+        orc_q dev = q_max(q_abs(X), q_max(q_abs(Y), q_abs(Z)));
+        if (dev < (orc_q)3e-6) {
+            orc_q XY = X * Y, Z2 = Z * Z;
+            orc_q E2 = XY - 6 * Z2;
+            orc_q E3 = (3 * XY - 8 * Z2) * Z;
+            orc_q E4 = 3 * (XY - Z2) * Z2;
+            orc_q E5 = XY * Z2 * Z;
+            orc_q s = 1 - 3 * E2 / 14 + E3 / 6 + 9 * E2 * E2 / 88 - 3 * E4 / 22 - 9 * E2 * E3 / 52 + 3 * E5 / 26;
+            return 3 * sum + fac * s / (A * q_sqrt(A));
+        }
+        orc_q sx = q_sqrt(x), sy = q_sqrt(y), sz = q_sqrt(z);
+        orc_q lam = sx * sy + sy * sz + sz * sx;
+        sum += fac / (sz * (z + lam));
+        fac /= 4;
+        x = (x + lam) / 4;
+        y = (y + lam) / 4;
+        z = (z + lam) / 4;
+    }
+    return 0;
+}
+
+/* G^(n)(r, r1, x), n = 0..N, in binary128: the same geometry (from rho_-^2), start values
+ * (Eq. gfunc:Q0) and forward or Miller recursion (Eq. gfunc:recursion) as orc_green with
+ * ORC_RULE_SAFE, whose Miller start error (about e^-60) is below what the Taylor
+ * coefficients need.  The forward/backward decision is taken in FP64. */
+static void q_green(double r_, double r1_, double x_, int N, orc_q *G)
+{
+    orc_q r = r_, r1 = r1_, x = x_;
+    orc_q dr = r - r1, sr = r + r1;
+    orc_q rm2 = dr * dr + x * x, rp2 = sr * sr + x * x;
+    if (rm2 == 0) {
+        for (int n = 0; n <= N; ++n) G[n] = 0;
+        return;
+    }
+    orc_q kp2 = rm2 / rp2, k2 = 4 * r * r1 / rp2, t = rm2 / (2 * r * r1);
+    orc_q mu = q_sqrt(k2);
+    double td = (double)t;
+    double a = log1p(td + sqrt(td * (td + 2.0))); /* acosh(chi) */
+    int Nr = N < 2 ? 2 : N;
+    int forward = 2.0 * Nr * a <= 4.0;
+    double extra = ceil(30.0 / a) + 10.0;
+    if (extra > 100000.0) extra = 100000.0;
+    int L = N + (int)extra;
+    orc_q rf = q_carlson_rf(0, kp2, 1);
+    if (forward) {
+        orc_q K = rf, E = rf - k2 / 3 * q_carlson_rd(0, kp2, 1);
+        G[0] = mu * K;
+        if (N >= 1) G[1] = mu * ((K - 2 * E) + t * (K - E));
+        for (int n = 2; n <= N; ++n)
+            G[n] = (4 * (orc_q)(n - 1) * (G[n - 1] + t * G[n - 1]) - (orc_q)(2 * n - 3) * G[n - 2]) / (orc_q)(2 * n - 1);
+    } else {
+        orc_q q_hi = 0, q_lo = 1;
+        if (L - 1 <= N) G[L - 1] = q_lo;
+        for (int n = L; n >= 2; --n) {
+            orc_q q_new = (4 * (orc_q)(n - 1) * (q_lo + t * q_lo) - (orc_q)(2 * n - 1) * q_hi) / (orc_q)(2 * n - 3);
+            q_hi = q_lo;
+            q_lo = q_new;
+            if (n - 2 <= N) G[n - 2] = q_new;
+            if (q_abs(q_new) > (orc_q)1e200) {
+                q_hi /= (orc_q)1e200;
+                q_lo /= (orc_q)1e200;
+                int top = (L - 1 <= N) ? L - 1 : N;
+                for (int m = n - 2; m <= top; ++m)
+                    if (m >= 0) G[m] /= (orc_q)1e200;
+            }
+        }
+        orc_q s = mu * rf / G[0];
+        for (int n = 0; n <= N; ++n) G[n] *= s;
+    }
+    orc_q c = 1 / (2 * q_pi() * q_sqrt(r * r1));
+    for (int n = 0; n <= N; ++n) G[n] *= c;
+}
+
+/* Taylor coefficients (in x about x0) of 1/(a^2 + x^2) and of (c - x^2) w(x), binary128 */
+static void q_taylor_inv(orc_q a, orc_q x0, int P, orc_q *v)
+{
+    orc_q u0 = a * a + x0 * x0;
+    v[0] = 1 / u0;
+    if (P >= 1) v[1] = -2 * x0 * v[0] / u0;
+    for (int q = 2; q <= P; ++q) v[q] = -(2 * x0 * v[q - 1] + v[q - 2]) / u0;
+}
+
+static void q_taylor_cmx2(orc_q c, orc_q x0, int P, const orc_q *w, orc_q *out)
+{
+    for (int q = 0; q <= P; ++q) {
+        orc_q s = (c - x0 * x0) * w[q];
+        if (q >= 1) s -= 2 * x0 * w[q - 1];
+        if (q >= 2) s -= w[q - 2];
+        out[q] = s;
+    }
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* Taylor coefficients gbar^(n)_{i,j,k}(r, r1, x), i+j+k <= P, n = 0..N (Appendix A).      */
 /* Output layout: g[((n*(P+1) + i)*(P+1) + j)*(P+1) + k] (dense cube; entries with          */
 /* i+j+k > P are left at zero).                                                          */
@@ -236,115 +387,114 @@ void orc_green_grad(double r, double r1, double x, int N, double *G, double *Gr,
 
 #define GIDX(n, i, j, k) ((((size_t)(n) * (P + 1) + (i)) * (P + 1) + (j)) * (P + 1) + (k))
 
-/* Taylor coefficients (in x about x0) of 1/(a^2 + x^2): v_q = (1/q!) d^q/dx^q. */
-static void orc_taylor_inv(double a, double x0, int P, double *v)
-{
-    double u0 = a * a + x0 * x0;
-    v[0] = 1.0 / u0;
-    if (P >= 1) v[1] = -2.0 * x0 * v[0] / u0;
-    for (int q = 2; q <= P; ++q) v[q] = -(2.0 * x0 * v[q - 1] + v[q - 2]) / u0;
-}
-
-/* Taylor coefficients of (c - x^2) * w(x) given those of w. */
-static void orc_taylor_cmx2(double c, double x0, int P, const double *w, double *out)
-{
-    for (int q = 0; q <= P; ++q) {
-        double s = (c - x0 * x0) * w[q];
-        if (q >= 1) s -= 2.0 * x0 * w[q - 1];
-        if (q >= 2) s -= w[q - 2];
-        out[q] = s;
-    }
-}
-
 int orc_gbar(double r, double r1, double x, int N, int P, double *g)
 {
     int Nw = N < 1 ? 1 : N; /* mode 1 is needed for n = 0 via G^(-1) = G^(1) */
     size_t cube = (size_t)(P + 1) * (P + 1) * (P + 1);
+    size_t Q = (size_t)P + 1;
     double *gw = (double *)calloc((size_t)(Nw + 1) * cube, sizeof(double));
-    double *vp = (double *)malloc(sizeof(double) * (P + 2) * 12);
-    if (!gw || !vp) {
+    orc_q *vq = (orc_q *)malloc(sizeof(orc_q) * (P + 2) * 12);
+    /* base columns in binary128: [Nw+1][P+1] each */
+    orc_q *b00 = (orc_q *)calloc((size_t)(Nw + 1) * Q * 4, sizeof(orc_q));
+    if (!gw || !vq || !b00) {
         free(gw);
-        free(vp);
+        free(vq);
+        free(b00);
         return -1;
     }
-    double *vm = vp + (P + 2);
-    double *fxp = vm + (P + 2), *fxm = fxp + (P + 2);      /* x / rho_pm^2 */
-    double *hp = fxm + (P + 2), *hm = hp + (P + 2);        /* (r^2-r1^2-x^2)/rho_pm^2 */
-    double *hp1 = hm + (P + 2), *hm1 = hp1 + (P + 2);      /* (r1^2-r^2-x^2)/rho_pm^2 */
-    double *dhp = hm1 + (P + 2), *dhm = dhp + (P + 2);     /* d/dr1 of hp, hm */
-    double *tmp = dhm + (P + 2), *tmp2 = tmp + (P + 2);
+    orc_q *b10 = b00 + (size_t)(Nw + 1) * Q, *b01 = b10 + (size_t)(Nw + 1) * Q, *b11 = b01 + (size_t)(Nw + 1) * Q;
+    orc_q *vp = vq, *vm = vp + (P + 2);
+    orc_q *fxp = vm + (P + 2), *fxm = fxp + (P + 2);      /* x / rho_pm^2 */
+    orc_q *hp = fxm + (P + 2), *hm = hp + (P + 2);        /* (r^2-r1^2-x^2)/rho_pm^2 */
+    orc_q *hp1 = hm + (P + 2), *hm1 = hp1 + (P + 2);      /* (r1^2-r^2-x^2)/rho_pm^2 */
+    orc_q *dhp = hm1 + (P + 2), *dhm = dhp + (P + 2);     /* d/dr1 of hp, hm */
+    orc_q *tmp = dhm + (P + 2), *tmp2 = tmp + (P + 2);
+    const orc_q rq = r, r1q = r1, xq = x;
 
-    orc_taylor_inv(r + r1, x, P, vp);
-    orc_taylor_inv(r - r1, x, P, vm);
+    q_taylor_inv(rq + r1q, xq, P, vp);
+    q_taylor_inv(rq - r1q, xq, P, vm);
     for (int q = 0; q <= P; ++q) {
-        fxp[q] = x * vp[q] + (q >= 1 ? vp[q - 1] : 0.0);
-        fxm[q] = x * vm[q] + (q >= 1 ? vm[q - 1] : 0.0);
+        fxp[q] = xq * vp[q] + (q >= 1 ? vp[q - 1] : 0);
+        fxm[q] = xq * vm[q] + (q >= 1 ? vm[q - 1] : 0);
     }
-    double c = (r - r1) * (r + r1);
-    orc_taylor_cmx2(c, x, P, vp, hp);
-    orc_taylor_cmx2(c, x, P, vm, hm);
-    orc_taylor_cmx2(-c, x, P, vp, hp1);
-    orc_taylor_cmx2(-c, x, P, vm, hm1);
+    orc_q c = (rq - r1q) * (rq + r1q);
+    q_taylor_cmx2(c, xq, P, vp, hp);
+    q_taylor_cmx2(c, xq, P, vm, hm);
+    q_taylor_cmx2(-c, xq, P, vp, hp1);
+    q_taylor_cmx2(-c, xq, P, vm, hm1);
     /* d/dr1 [(c - x^2)/((r+s r1)^2 + x^2)] = -2 r1 v - 2 s (r + s r1) (c - x^2) v^2, s = +-1 */
     for (int sgn = 0; sgn < 2; ++sgn) {
-        const double *v = sgn == 0 ? vp : vm;
-        double s = sgn == 0 ? 1.0 : -1.0;
-        double a = r + s * r1;
+        const orc_q *v = sgn == 0 ? vp : vm;
+        orc_q s = sgn == 0 ? 1 : -1;
+        orc_q a = rq + s * r1q;
         for (int q = 0; q <= P; ++q) {
-            double acc = 0.0;
+            orc_q acc = 0;
             for (int p = 0; p <= q; ++p) acc += v[p] * v[q - p];
             tmp[q] = acc;
         }
-        orc_taylor_cmx2(c, x, P, tmp, tmp2);
-        double *d = sgn == 0 ? dhp : dhm;
-        for (int q = 0; q <= P; ++q) d[q] = -2.0 * r1 * v[q] - 2.0 * s * a * tmp2[q];
+        q_taylor_cmx2(c, xq, P, tmp, tmp2);
+        orc_q *d = sgn == 0 ? dhp : dhm;
+        for (int q = 0; q <= P; ++q) d[q] = -2 * r1q * v[q] - 2 * s * a * tmp2[q];
     }
 
     /* gbar_{0,0,0} = G^(n) */
     {
-        double *G0 = (double *)malloc(sizeof(double) * (Nw + 1));
-        orc_green(r, r1, x, Nw, G0);
-        for (int n = 0; n <= Nw; ++n) gw[GIDX(n, 0, 0, 0)] = G0[n];
+        orc_q *G0 = (orc_q *)malloc(sizeof(orc_q) * (Nw + 1));
+        q_green(r, r1, x, Nw, G0);
+        for (int n = 0; n <= Nw; ++n) b00[(size_t)n * Q] = G0[n];
         free(G0);
     }
-#define GW(n, i, j, k) gw[GIDX(n, i, j, k)]
-#define GM1(n, i, j, k) gw[GIDX((n) == 0 ? 1 : (n) - 1, i, j, k)]
+#define B(arr, n, k) arr[(size_t)(n) * Q + (k)]
+#define BM(arr, n, k) arr[(size_t)((n) == 0 ? 1 : (n) - 1) * Q + (k)]
     /* x-derivatives, Eq. gfunc:derivatives:x (coupled in n; G^(-1) = G^(1)) */
     for (int k = 0; k < P; ++k) {
         for (int n = 0; n <= Nw; ++n) {
-            double nu = n - 0.5, acc = 0.0;
+            orc_q nu = (orc_q)n - (orc_q)0.5, acc = 0;
             for (int q = 0; q <= k; ++q) {
-                double gp = GW(n, 0, 0, k - q), gm = GM1(n, 0, 0, k - q);
+                orc_q gp = B(b00, n, k - q), gm = BM(b00, n, k - q);
                 acc += (gp + gm) * fxp[q] + (gp - gm) * fxm[q];
             }
-            GW(n, 0, 0, k + 1) = nu / (k + 1) * acc;
+            B(b00, n, k + 1) = nu / (k + 1) * acc;
         }
     }
     /* r-derivatives gbar_{1,0,k} and (by exchanging r and r1) gbar_{0,1,k} */
     for (int k = 0; k + 1 <= P; ++k) {
         for (int n = 0; n <= Nw; ++n) {
-            double nu = n - 0.5, a1 = 0.0, a2 = 0.0;
+            orc_q nu = (orc_q)n - (orc_q)0.5, a1 = 0, a2 = 0;
             for (int q = 0; q <= k; ++q) {
-                double gp = GW(n, 0, 0, k - q), gm = GM1(n, 0, 0, k - q);
+                orc_q gp = B(b00, n, k - q), gm = BM(b00, n, k - q);
                 a1 += (gp + gm) * hp[q] + (gp - gm) * hm[q];
                 a2 += (gp + gm) * hp1[q] + (gp - gm) * hm1[q];
             }
-            GW(n, 1, 0, k) = -GW(n, 0, 0, k) / (2.0 * r) + nu / (2.0 * r) * a1;
-            GW(n, 0, 1, k) = -GW(n, 0, 0, k) / (2.0 * r1) + nu / (2.0 * r1) * a2;
+            B(b10, n, k) = -B(b00, n, k) / (2 * rq) + nu / (2 * rq) * a1;
+            B(b01, n, k) = -B(b00, n, k) / (2 * r1q) + nu / (2 * r1q) * a2;
         }
     }
     /* mixed gbar_{1,1,k} */
     for (int k = 0; k + 2 <= P; ++k) {
         for (int n = 0; n <= Nw; ++n) {
-            double nu = n - 0.5, acc = 0.0;
+            orc_q nu = (orc_q)n - (orc_q)0.5, acc = 0;
             for (int q = 0; q <= k; ++q) {
-                double g0p = GW(n, 0, 0, k - q), g0m = GM1(n, 0, 0, k - q);
-                double g1p = GW(n, 0, 1, k - q), g1m = GM1(n, 0, 1, k - q);
+                orc_q g0p = B(b00, n, k - q), g0m = BM(b00, n, k - q);
+                orc_q g1p = B(b01, n, k - q), g1m = BM(b01, n, k - q);
                 acc += (g0p + g0m) * dhp[q] + (g1p + g1m) * hp[q] + (g0p - g0m) * dhm[q] + (g1p - g1m) * hm[q];
             }
-            GW(n, 1, 1, k) = -GW(n, 0, 1, k) / (2.0 * r) + nu / (2.0 * r) * acc;
+            B(b11, n, k) = -B(b01, n, k) / (2 * rq) + nu / (2 * rq) * acc;
         }
     }
+#undef B
+#undef BM
+#define GW(n, i, j, k) gw[GIDX(n, i, j, k)]
+    /* the base columns, rounded to FP64, start the Laplace recursions */
+    for (int n = 0; n <= Nw; ++n)
+        for (int k = 0; k <= P; ++k) {
+            GW(n, 0, 0, k) = (double)b00[(size_t)n * Q + k];
+            if (k + 1 <= P) GW(n, 1, 0, k) = (double)b10[(size_t)n * Q + k];
+            if (k + 1 <= P) GW(n, 0, 1, k) = (double)b01[(size_t)n * Q + k];
+            if (k + 2 <= P) GW(n, 1, 1, k) = (double)b11[(size_t)n * Q + k];
+        }
+    free(b00);
+    free(vq);
     /* Reading of Eq. gfunc:laplace:recursion: the Laplace equation (Eq. gfunc:laplace)
      * expanded in powers of the radial offset gives the printed sum plus the term
      * -(k+1)(k+2)/((i+1)(i+2)) gbar_{i,j,k+2} from d^2G/dx^2, which the printed formula
@@ -383,10 +533,8 @@ int orc_gbar(double r, double r1, double x, int N, int P, double *g)
         }
     }
 #undef GW
-#undef GM1
     memcpy(g, gw, (size_t)(N + 1) * cube * sizeof(double));
     free(gw);
-    free(vp);
     return 0;
 }
 

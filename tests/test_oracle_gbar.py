@@ -55,6 +55,27 @@ def test_gbar_taylor_shift(geom):
         np.testing.assert_allclose(S, G, rtol=1e-12, atol=1e-14 * abs(G[0]))
 
 
+@pytest.mark.parametrize("geom,frac", [((1.05, 1.05, 2 / 64), 0.35), ((0.6, 0.6, 3 / 64), 0.45),
+                                       ((1.05, 1.05 + 2 / 64, 2 / 64), 0.45)])
+def test_gbar_taylor_shift_high_modes_axial_neighbours(geom, frac):
+    """Modes 0..64 at order 24 for boxes of side h = 1/64 one or two boxes apart along the
+    axis (the geometry where G^(n) and G^(n-1) nearly coincide): the Taylor sum at shifts
+    of up to frac * h in all three variables must reproduce G at the shifted point.  FP64
+    base columns fail this by up to 2e-6 (the cancellation of the x-recursion at high n);
+    the binary128 ones pass at 1e-12."""
+    r, r1, x = geom
+    N, P = 64, 24
+    h = 1 / 64
+    g = oracle.gbar(r, r1, x, N, P)
+    rng = np.random.default_rng(5)
+    i, j, k = np.meshgrid(np.arange(P + 1), np.arange(P + 1), np.arange(P + 1), indexing="ij")
+    for _ in range(8):
+        d = rng.uniform(-frac * h, frac * h, 3)
+        G = oracle.green(r + d[0], r1 + d[1], x + d[2], N)
+        S = np.einsum("nijk,ijk->n", g, d[0] ** i * d[1] ** j * d[2] ** k)
+        assert np.max(np.abs(S - G)) < 1e-12 * abs(G[0])
+
+
 def test_gbar_source_laplace_on_field_recursed_terms():
     # Coefficients with i >= 2 come from the field-side (r) Laplace recursion.  They must
     # also satisfy the source-side (r1) Laplace equation, written here in its local form:
