@@ -178,7 +178,11 @@ afmm_status afmm_green(int64_t npairs, const double *r, const double *r1, const 
  * i + j + k <= P, n = 0..n_modes-1, at npts points, from the x-recursion
  * (Eq. gfunc:derivatives:x), the closed first-derivative forms and the Laplace recursion
  * (Eq. gfunc:laplace).  Output dense: out[((p * n_modes + n) * (P+1) + i) * (P+1) + j) *
- * (P+1) + k], zero where i+j+k > P.  P <= 48. Requires r != r1 or x != 0 at every point. */
+ * (P+1) + k], zero where i+j+k > P.  P <= 48 (AFMM_EINVAL above); AFMM_EUNSUPPORTED when the
+ * per-point working set (8 (24 (P+1) + 6 n_modes (P+1) + 2 n_modes + 2 (P+1)) bytes) exceeds
+ * 227 KiB of shared memory.  Requires r != r1 or x != 0 at every point.  The Legendre start
+ * values and the base columns gbar_{0,0,k}, gbar_{1,0,k}, gbar_{0,1,k}, gbar_{1,1,k} are formed
+ * in double-double, the rest in FP64. */
 afmm_status afmm_green_expansion(int64_t npts, const double *r, const double *r1, const double *x,
                                  int n_modes, int P, double *out, void *stream);
 

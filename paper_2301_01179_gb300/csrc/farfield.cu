@@ -21,6 +21,7 @@
 #include "common.cuh"
 #include "pair.cuh"
 #include "df.cuh"
+#include "dd.cuh"
 
 namespace afmm {
 
@@ -483,9 +484,10 @@ __global__ void k_l2l_df(const int32_t *__restrict__ parent, const uint32_t *__r
 // ------------------------------------------------------------------------------------
 // Green's-function Taylor coefficients gbar^(n)_{a,b,c}(r, r1, x), a <= A, b <= B,
 // a + b + c <= P, all modes, one point per block.
-//   1. G^(n) by the pair routine (AGM start values + Legendre recursion);
+//   1. G^(n) from the AGM start values and the Legendre recursion (double-double);
 //   2. x-derivatives gbar_{0,0,k} by the coupled recursion of Eq. gfunc:derivatives:x;
 //   3. gbar_{1,0,k}, gbar_{0,1,k}, gbar_{1,1,k} from the closed forms (Appendix A);
+//      steps 2 and 3 in double-double (see the reading in gbar_block);
 //   4. the Laplace equation (Eq. gfunc:laplace) in the source radius raises b and in the
 //      field radius raises a.  Expanding r^2 G_rr + r G_r - n^2 G + r^2 G_xx = 0 in the
 //      radial offset gives, for each Taylor coefficient,
@@ -622,135 +624,218 @@ __device__ void gbar_fill_warp(double r, double r1, int N, int P, int A, int Bm,
     }
 }
 
+// Legendre start values and sequence G^(n), n = 0..N, in double-double (one thread): the same
+// AGM start values as pair.cuh (G^(0) = 1 / (2 AGM(rho_+, rho_-)), G^(1) from the
+// half-difference sum) and the recursion of Eq. gfunc:recursion, forward where
+// 2 max(N, 2) acosh(chi) <= 16 (error growth e^16 against 2^-104), otherwise Miller's backward
+// recursion from L = N + ceil(30 / acosh chi) + 10 (start error e^-60), normalised by G^(0).
+__device__ void dd_green_sequence(double r, double r1, double x, int N, ddv *G)
+{
+    const ddv dr = dd_two_sum(r, -r1), sr = dd_two_sum(r, r1), x2 = dd_two_prod(x, x);
+    const ddv rm2 = dd_add(dd_mul(dr, dr), x2), rp2 = dd_add(dd_mul(sr, sr), x2);
+    const ddv w2 = dd_mul_d(dd_two_prod(r, r1), 2.0);  // 2 r r1
+    const ddv t = dd_div(rm2, w2);                     // chi - 1
+    ddv a = dd_sqrt(rp2), b = dd_sqrt(rm2), csum = dd_make(0.0);
+    double wgt = 1.0;
+    for (int it = 0; it < 60; ++it) {
+        const ddv c = dd_mul_d(dd_sub(a, b), 0.5);
+        csum = dd_add(csum, dd_mul_d(dd_mul(c, c), wgt));
+        wgt *= 2.0;
+        const ddv an = dd_mul_d(dd_add(a, b), 0.5);
+        b = dd_sqrt(dd_mul(a, b));
+        a = an;
+        if (fabs(c.hi) <= 1e-17 * a.hi) break;
+    }
+    const ddv G0 = dd_div(dd_make(0.5), a);
+    const double td = t.hi;
+    const double af = log1p(td + sqrt(td * (td + 2.0)));  // acosh(chi), decides the regime only
+    const int Nr = N < 2 ? 2 : N;
+    if (2.0 * Nr * af <= 16.0) {
+        G[0] = G0;
+        if (N >= 1) G[1] = dd_div(dd_mul(G0, csum), w2);
+        for (int n = 2; n <= N; ++n) {
+            const ddv up = dd_mul_d(dd_add(G[n - 1], dd_mul(t, G[n - 1])), 4.0 * (n - 1));
+            G[n] = dd_div_d(dd_sub(up, dd_mul_d(G[n - 2], 2.0 * n - 3.0)), 2.0 * n - 1.0);
+        }
+        return;
+    }
+    const int L = N + (int)ceil(30.0 / af) + 10;
+    ddv qh = dd_make(0.0), ql = dd_make(1.0);  // q_n, q_{n-1}
+    if (L - 1 <= N) G[L - 1] = ql;
+    for (int n = L; n >= 2; --n) {
+        const ddv up = dd_mul_d(dd_add(ql, dd_mul(t, ql)), 4.0 * (n - 1));
+        const ddv qn = dd_div_d(dd_sub(up, dd_mul_d(qh, 2.0 * n - 1.0)), 2.0 * n - 3.0);
+        qh = ql;
+        ql = qn;
+        if (n - 2 <= N) G[n - 2] = qn;
+        if (fabs(qn.hi) > 1e200) {
+            qh = dd_mul_d(qh, 1e-200);
+            ql = dd_mul_d(ql, 1e-200);
+            const int top = L - 1 <= N ? L - 1 : N;
+            for (int m = n - 2 < 0 ? 0 : n - 2; m <= top; ++m) G[m] = dd_mul_d(G[m], 1e-200);
+        }
+    }
+    const ddv s = dd_div(G0, G[0]);
+    for (int n = 0; n <= N; ++n) G[n] = dd_mul(G[n], s);
+}
+
+// sum of products a_i * b_i into (H, L): each product exact (FMA two-product), its high part
+// added by two-sum, the low parts summed in FP64; renormalised by the caller
+__device__ __forceinline__ void dd_acc2(double &H, double &L, ddv a, ddv b)
+{
+    const ddv p = dd_two_prod(a.hi, b.hi);
+    const double cross = __fma_rn(a.hi, b.lo, __dmul_rn(a.lo, b.hi));
+    const ddv s = dd_two_sum(H, p.hi);
+    L = __dadd_rn(L, __dadd_rn(__dadd_rn(s.lo, p.lo), cross));
+    H = s.hi;
+}
+
 __device__ void gbar_block(double r, double r1, double x, int N, int P, int A, int Bm, const RecTab &tab,
                            const PairParams &pp, double *sm, double *out, double scale, int fact,
                            float2 *dfout = nullptr)
 {
+    (void)tab;
+    (void)pp;
     const int Nw = N < 1 ? 1 : N;
     const int nmw = Nw + 1;
     const int Q = P + 1;
-    double *gam = sm;                       // [AFMM_REC_TAB]
-    double *ys = gam + AFMM_REC_TAB;        // [nmw][32]
-    double *tv = ys + (size_t)nmw * 32;     // Taylor vectors [10][Q]
-    double *g00 = tv + 10 * Q;              // [nmw][Q]
+    // Reading of Appendix A (no precision given): the x-recursion and the closed first-derivative
+    // forms couple G^(n) and G^(n-1) through their difference, which cancels as chi -> 1, and the
+    // Laplace recursion (step 4) carries the errors of these base columns into the high mixed
+    // coefficients: in FP64 the base columns of axially adjacent boxes on fine levels lose up to
+    // ten digits at modes 0..32 and beyond.  Steps 1-3 therefore run in double-double; the
+    // Laplace recursion, which is stable given accurate base columns, stays in FP64 / FP32 pairs.
+    ddv *tv = reinterpret_cast<ddv *>(sm);       // Taylor vectors [12][Q]
+    double *g00 = sm + 24 * (size_t)Q;           // FP64 (high) parts [nmw][Q]: the fill's inputs
     double *g10 = g00 + (size_t)nmw * Q;
     double *g01 = g10 + (size_t)nmw * Q;
     double *g11 = g01 + (size_t)nmw * Q;
-    double *G = g11 + (size_t)nmw * Q;      // [nmw]
-    for (int i = threadIdx.x; i < AFMM_REC_TAB; i += blockDim.x) gam[i] = tab.gam[i];
-    __syncthreads();
-    // 1. G^(n), n = 0..Nw (warp 0; lanes 1..31 run inactive pairs)
-    if (threadIdx.x < 32) {
-        double inv2w = 0.5 / (r * r1);
-        PairGeom g;
-        pair_geom(r, x, r1, 0.0, inv2w, threadIdx.x == 0, g);
-        double s = pair_sequence(g, inv2w, Nw, pp, gam, ys + threadIdx.x, 32);
-        if (threadIdx.x == 0)
-            for (int n = 0; n <= Nw; ++n) G[n] = s * tab.c[n] * ys[n * 32];
-    }
+    double *l00 = g11 + (size_t)nmw * Q;         // low parts of gbar_{0,0,k} and gbar_{0,1,k}
+    double *l01 = l00 + (size_t)nmw * Q;
+    ddv *G = reinterpret_cast<ddv *>(l01 + (size_t)nmw * Q);  // [nmw]
+    // 1. G^(n), n = 0..Nw
+    if (threadIdx.x == 0) dd_green_sequence(r, r1, x, Nw, G);
     // 2. Taylor coefficients in x of 1/rho_pm^2 and the rational factors of Appendix A
-    //    (the recursion for v on two threads, the q-wise factors on one thread per q)
-    double *vp = tv, *vm = tv + Q, *fxp_ = tv + 2 * Q, *fxm_ = tv + 3 * Q, *hp_ = tv + 4 * Q, *hm_ = tv + 5 * Q;
-    double *hp1_ = tv + 6 * Q, *hm1_ = tv + 7 * Q, *dhp_ = tv + 8 * Q, *dhm_ = tv + 9 * Q;
+    ddv *vp = tv, *vm = tv + Q, *fxp = tv + 2 * Q, *fxm = tv + 3 * Q, *hp = tv + 4 * Q, *hm = tv + 5 * Q;
+    ddv *hp1 = tv + 6 * Q, *hm1 = tv + 7 * Q, *dhp = tv + 8 * Q, *dhm = tv + 9 * Q;
+    ddv *wsp = tv + 10 * Q, *wsm = tv + 11 * Q;  // (c - x^2) v^2 for the r1 derivative of hp, hm
+    const ddv xd = dd_make(x), r1d = dd_make(r1);
+    const ddv cc = dd_mul(dd_two_sum(r, -r1), dd_two_sum(r, r1));  // r^2 - r1^2
+    const ddv cmx = dd_sub(cc, dd_two_prod(x, x)), cpx = dd_neg(dd_add(cc, dd_two_prod(x, x)));
     if (threadIdx.x < 2) {
         const int sgn = threadIdx.x;
-        double aa = sgn == 0 ? r + r1 : r - r1;
-        double *v = sgn == 0 ? vp : vm;
-        double u0 = aa * aa + x * x, iu0 = 1.0 / u0;
+        const ddv aa = dd_two_sum(r, sgn == 0 ? r1 : -r1);
+        ddv *v = sgn == 0 ? vp : vm;
+        const ddv u0 = dd_add(dd_mul(aa, aa), dd_two_prod(x, x));
+        const ddv iu0 = dd_div(dd_make(1.0), u0);
         v[0] = iu0;
-        if (P >= 1) v[1] = -2.0 * x * iu0 * iu0;
-        for (int q = 2; q <= P; ++q) v[q] = -(2.0 * x * v[q - 1] + v[q - 2]) * iu0;
+        if (P >= 1) v[1] = dd_mul_d(dd_mul(xd, dd_mul(iu0, iu0)), -2.0);
+        for (int q = 2; q <= P; ++q) v[q] = dd_neg(dd_mul(dd_add(dd_mul_d(dd_mul(xd, v[q - 1]), 2.0), v[q - 2]), iu0));
     }
     __syncthreads();
+    // (c - x^2) w for a Taylor vector w: coefficient q
+    auto cm = [&](const ddv *w, ddv c0, int q) {
+        ddv s = dd_mul(c0, w[q]);
+        if (q >= 1) s = dd_sub(s, dd_mul_d(dd_mul(xd, w[q - 1]), 2.0));
+        if (q >= 2) s = dd_sub(s, w[q - 2]);
+        return s;
+    };
     for (int q = threadIdx.x; q <= P; q += blockDim.x) {
-        double *fxp = fxp_, *fxm = fxm_, *hp = hp_, *hm = hm_, *hp1 = hp1_, *hm1 = hm1_, *dhp = dhp_, *dhm = dhm_;
-        double cc = r * r - r1 * r1;
-        {
-            fxp[q] = x * vp[q] + (q >= 1 ? vp[q - 1] : 0.0);
-            fxm[q] = x * vm[q] + (q >= 1 ? vm[q - 1] : 0.0);
-            double a1 = q >= 1 ? 2.0 * x : 0.0;
-            hp[q] = (cc - x * x) * vp[q] - (q >= 1 ? a1 * vp[q - 1] : 0.0) - (q >= 2 ? vp[q - 2] : 0.0);
-            hm[q] = (cc - x * x) * vm[q] - (q >= 1 ? a1 * vm[q - 1] : 0.0) - (q >= 2 ? vm[q - 2] : 0.0);
-            hp1[q] = (-cc - x * x) * vp[q] - (q >= 1 ? a1 * vp[q - 1] : 0.0) - (q >= 2 ? vp[q - 2] : 0.0);
-            hm1[q] = (-cc - x * x) * vm[q] - (q >= 1 ? a1 * vm[q - 1] : 0.0) - (q >= 2 ? vm[q - 2] : 0.0);
+        fxp[q] = dd_add(dd_mul(xd, vp[q]), q >= 1 ? vp[q - 1] : dd_make(0.0));
+        fxm[q] = dd_add(dd_mul(xd, vm[q]), q >= 1 ? vm[q - 1] : dd_make(0.0));
+        hp[q] = cm(vp, cmx, q);
+        hm[q] = cm(vm, cmx, q);
+        hp1[q] = cm(vp, cpx, q);
+        hm1[q] = cm(vm, cpx, q);
+        ddv s0 = dd_make(0.0), s1 = dd_make(0.0);
+        for (int t = 0; t <= q; ++t) {
+            s0 = dd_add(s0, dd_mul(vp[t], vp[q - t]));
+            s1 = dd_add(s1, dd_mul(vm[t], vm[q - t]));
         }
-        // d/dr1 of (cc - x^2)/((r + s r1)^2 + x^2) = -2 r1 v - 2 s (r + s r1) (cc - x^2) v^2
-        for (int sgn = 0; sgn < 2; ++sgn) {
-            const double *v = sgn == 0 ? vp : vm;
-            double s = sgn == 0 ? 1.0 : -1.0, aa = r + s * r1;
-            double *d = sgn == 0 ? dhp : dhm;
-            {
-                // (cc - x^2) v^2 Taylor coefficient q, via w = v*v
-                double wq = 0, wq1 = 0, wq2 = 0;
-                for (int t = 0; t <= q; ++t) wq += v[t] * v[q - t];
-                if (q >= 1)
-                    for (int t = 0; t <= q - 1; ++t) wq1 += v[t] * v[q - 1 - t];
-                if (q >= 2)
-                    for (int t = 0; t <= q - 2; ++t) wq2 += v[t] * v[q - 2 - t];
-                double cw = (cc - x * x) * wq - 2.0 * x * wq1 - wq2;
-                d[q] = -2.0 * r1 * v[q] - 2.0 * s * aa * cw;
-            }
-        }
+        wsp[q] = s0;
+        wsm[q] = s1;
     }
     __syncthreads();
-    const double *fxp = tv + 2 * Q, *fxm = tv + 3 * Q, *hp = tv + 4 * Q, *hm = tv + 5 * Q;
-    const double *hp1 = tv + 6 * Q, *hm1 = tv + 7 * Q, *dhp = tv + 8 * Q, *dhm = tv + 9 * Q;
-    for (int n = threadIdx.x; n <= Nw; n += blockDim.x) g00[n * Q] = G[n];
+    // d/dr1 of (c - x^2)/((r + s r1)^2 + x^2) = -2 r1 v - 2 s (r + s r1) (c - x^2) v^2
+    for (int q = threadIdx.x; q <= P; q += blockDim.x) {
+        const ddv ap = dd_two_sum(r, r1), am = dd_two_sum(r, -r1);
+        const ddv tp = cm(wsp, cmx, q), tm = cm(wsm, cmx, q);
+        dhp[q] = dd_sub(dd_mul_d(dd_mul(r1d, vp[q]), -2.0), dd_mul_d(dd_mul(ap, tp), 2.0));
+        dhm[q] = dd_add(dd_mul_d(dd_mul(r1d, vm[q]), -2.0), dd_mul_d(dd_mul(am, tm), 2.0));
+    }
+    __syncthreads();
+    // the convolutions below use the factor pairs f+ + f- (mode n) and f+ - f- (mode n - 1):
+    // sum_q (g^n + g^m) f+_q + (g^n - g^m) f-_q = sum_q g^n (f+ + f-)_q + g^m (f+ - f-)_q
+    for (int q = threadIdx.x; q <= P; q += blockDim.x) {
+        const ddv a0 = fxp[q], a1 = fxm[q], b0 = hp[q], b1 = hm[q], c0 = hp1[q], c1 = hm1[q], e0 = dhp[q], e1 = dhm[q];
+        fxp[q] = dd_add(a0, a1);
+        fxm[q] = dd_sub(a0, a1);
+        hp[q] = dd_add(b0, b1);
+        hm[q] = dd_sub(b0, b1);
+        hp1[q] = dd_add(c0, c1);
+        hm1[q] = dd_sub(c0, c1);
+        dhp[q] = dd_add(e0, e1);
+        dhm[q] = dd_sub(e0, e1);
+    }
+    for (int n = threadIdx.x; n <= Nw; n += blockDim.x) {
+        g00[n * Q] = G[n].hi;
+        l00[n * Q] = G[n].lo;
+    }
     __syncthreads();
     // 3a. x-recursion, coupled in n (G^(-1) = G^(1))
     for (int k = 0; k < P; ++k) {
         for (int n = threadIdx.x; n <= Nw; n += blockDim.x) {
-            int m = n == 0 ? 1 : n - 1;
-            double acc0 = 0.0, acc1 = 0.0;  // two chains: the FP64 FMA latency dominates
+            const int m = n == 0 ? 1 : n - 1;
+            double H = 0.0, Lw = 0.0;
             for (int q = 0; q <= k; ++q) {
-                double gp = g00[n * Q + k - q], gm = g00[m * Q + k - q];
-                acc0 = fma(gp + gm, fxp[q], acc0);
-                acc1 = fma(gp - gm, fxm[q], acc1);
+                dd_acc2(H, Lw, dd_make(g00[n * Q + k - q], l00[n * Q + k - q]), fxp[q]);
+                dd_acc2(H, Lw, dd_make(g00[m * Q + k - q], l00[m * Q + k - q]), fxm[q]);
             }
-            g00[n * Q + k + 1] = (n - 0.5) / (k + 1) * (acc0 + acc1);
+            const ddv v = dd_div_d(dd_mul_d(dd_quick_two_sum(H, Lw), n - 0.5), (double)(k + 1));
+            g00[n * Q + k + 1] = v.hi;
+            l00[n * Q + k + 1] = v.lo;
         }
         __syncthreads();
     }
-    // 3b. first r and r1 derivatives
-    for (int n = threadIdx.x; n <= Nw; n += blockDim.x) {
-        int m = n == 0 ? 1 : n - 1;
-        double nu = n - 0.5;
-        const double i2r = 1.0 / (2.0 * r), i2r1 = 1.0 / (2.0 * r1);
-        for (int k = 0; k + 1 <= P; ++k) {
-            double a1p = 0.0, a1m = 0.0, a2p = 0.0, a2m = 0.0;
-            for (int q = 0; q <= k; ++q) {
-                double gp = g00[n * Q + k - q], gm = g00[m * Q + k - q];
-                a1p = fma(gp + gm, hp[q], a1p);
-                a1m = fma(gp - gm, hm[q], a1m);
-                a2p = fma(gp + gm, hp1[q], a2p);
-                a2m = fma(gp - gm, hm1[q], a2m);
-            }
-            g10[n * Q + k] = (-g00[n * Q + k] + nu * (a1p + a1m)) * i2r;
-            g01[n * Q + k] = (-g00[n * Q + k] + nu * (a2p + a2m)) * i2r1;
+    // 3b. first r and r1 derivatives, one task per (mode, order)
+    for (int task = threadIdx.x; task < nmw * P; task += blockDim.x) {
+        const int n = task / P, k = task % P;
+        const int m = n == 0 ? 1 : n - 1;
+        double H1 = 0.0, L1 = 0.0, H2 = 0.0, L2 = 0.0;
+        for (int q = 0; q <= k; ++q) {
+            const ddv gn = dd_make(g00[n * Q + k - q], l00[n * Q + k - q]);
+            const ddv gm = dd_make(g00[m * Q + k - q], l00[m * Q + k - q]);
+            dd_acc2(H1, L1, gn, hp[q]);
+            dd_acc2(H1, L1, gm, hm[q]);
+            dd_acc2(H2, L2, gn, hp1[q]);
+            dd_acc2(H2, L2, gm, hm1[q]);
         }
+        const ddv g = dd_make(g00[n * Q + k], l00[n * Q + k]);
+        const ddv v10 = dd_div_d(dd_sub(dd_mul_d(dd_quick_two_sum(H1, L1), n - 0.5), g), 2.0 * r);
+        const ddv v01 = dd_div_d(dd_sub(dd_mul_d(dd_quick_two_sum(H2, L2), n - 0.5), g), 2.0 * r1);
+        g10[n * Q + k] = v10.hi;
+        g01[n * Q + k] = v01.hi;
+        l01[n * Q + k] = v01.lo;
     }
     __syncthreads();
-    // 3c. mixed
-    for (int n = threadIdx.x; n <= Nw; n += blockDim.x) {
-        int m = n == 0 ? 1 : n - 1;
-        double nu = n - 0.5;
-        const double i2r = 1.0 / (2.0 * r);
-        for (int k = 0; k + 2 <= P; ++k) {
-            double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
-            for (int q = 0; q <= k; ++q) {
-                double g0p = g00[n * Q + k - q], g0m = g00[m * Q + k - q];
-                double g1p = g01[n * Q + k - q], g1m = g01[m * Q + k - q];
-                c0 = fma(g0p + g0m, dhp[q], c0);
-                c1 = fma(g1p + g1m, hp[q], c1);
-                c2 = fma(g0p - g0m, dhm[q], c2);
-                c3 = fma(g1p - g1m, hm[q], c3);
-            }
-            g11[n * Q + k] = (-g01[n * Q + k] + nu * ((c0 + c1) + (c2 + c3))) * i2r;
+    // 3c. mixed, one task per (mode, order)
+    for (int task = threadIdx.x; task < nmw * (P - 1); task += blockDim.x) {
+        const int n = task / (P - 1), k = task % (P - 1);
+        const int m = n == 0 ? 1 : n - 1;
+        double H = 0.0, Lw = 0.0;
+        for (int q = 0; q <= k; ++q) {
+            dd_acc2(H, Lw, dd_make(g00[n * Q + k - q], l00[n * Q + k - q]), dhp[q]);
+            dd_acc2(H, Lw, dd_make(g00[m * Q + k - q], l00[m * Q + k - q]), dhm[q]);
+            dd_acc2(H, Lw, dd_make(g01[n * Q + k - q], l01[n * Q + k - q]), hp[q]);
+            dd_acc2(H, Lw, dd_make(g01[m * Q + k - q], l01[m * Q + k - q]), hm[q]);
         }
+        const ddv g = dd_make(g01[n * Q + k], l01[n * Q + k]);
+        const ddv v = dd_div_d(dd_sub(dd_mul_d(dd_quick_two_sum(H, Lw), n - 0.5), g), 2.0 * r);
+        g11[n * Q + k] = v.hi;
     }
     __syncthreads();
     if (P <= 31) {  // warp-parallel fill (every order a plan accepts: 2M <= 30)
-        double *dtab = G + nmw;  // [2 Q]
+        double *dtab = reinterpret_cast<double *>(G + nmw);  // [2 Q]
         if (dfout)
             gbar_fill_warp<NumDF>(r, r1, N, P, A, Bm, Q, g00, g10, g01, g11, dfout, scale, fact,
                                   reinterpret_cast<float2 *>(dtab));
@@ -813,9 +898,10 @@ __device__ void gbar_block(double r, double r1, double x, int N, int P, int A, i
 
 static size_t gbar_smem(int N, int P)
 {
-    int nmw = (N < 1 ? 1 : N) + 1;
-    return sizeof(double) * ((size_t)AFMM_REC_TAB + (size_t)nmw * 32 + 10 * (size_t)(P + 1) + 4 * (size_t)nmw * (P + 1) + nmw +
-                             2 * (size_t)(P + 1));
+    // Taylor vectors [12][Q] double-double, base columns [6][nmw][Q], G^(n) [nmw] double-double,
+    // the fill's denominators [2 Q]
+    const size_t nmw = (size_t)(N < 1 ? 1 : N) + 1, Q = (size_t)P + 1;
+    return sizeof(double) * (24 * Q + 6 * nmw * Q + 2 * nmw + 2 * Q);
 }
 
 // unit entry point: one point per block, dense (P+1)^3 per mode
@@ -865,6 +951,7 @@ afmm_status launch_green_expansion(int64_t npts, const double *r, const double *
     size_t per = (size_t)n_modes * (P + 1) * (P + 1) * (P + 1);
     AFMM_CUDA(cudaMemsetAsync(out, 0, per * npts * sizeof(double), st));
     size_t sm = gbar_smem(n_modes - 1, P);
+    if (sm > 227 * 1024) return AFMM_EUNSUPPORTED;  // shared-memory working set of one point
     AFMM_CUDA(cudaFuncSetAttribute(k_gbar_points, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_gbar_points<<<(unsigned)npts, 128, sm, st>>>(npts, r, r1, x, n_modes, P, tab, pp, out);
     AFMM_LAUNCH_CHECK();

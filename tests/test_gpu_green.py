@@ -63,3 +63,42 @@ def test_green_expansion_matches_oracle():
         sc = np.abs(g[:, 0, 0, 0]).max() * dist ** (-(i + j + k)).astype(float)
         err = np.abs(E[p] - g) / sc[None]
         assert err.max() < 1e-11, (p, err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
+def test_green_expansion_high_modes_axial_neighbours():
+    """Modes 0..64 at Taylor order 24 for boxes of side h = 1/64 one to three boxes apart, in
+    plain and in box units (as the S2L expansions are generated): there the x-recursion's
+    G^(n) - G^(n-1) cancels, and FP64 start values and base columns lose up to ten digits.
+    The GPU forms them in double-double.  Checked two ways:
+      - the Taylor sum at shifts of up to 0.35 h in all three variables (the offsets an S2L
+        application meets) reproduces the oracle's G at the shifted point, 1e-12 of G^(0),
+        for every mode;
+      - against the oracle (binary128 base columns) for modes 0..32, normwise per mode and
+        total order i + j + k: max |E - g| / max |g| over the order's coefficients <= 1e-11.
+        (Mixed coefficients of these geometries exceed |G^(0)| dist^-(i+j+k) by up to 2^24,
+        so FP64 rounding alone shows at 1e-8 on that scale.)  Above mode 32 the Laplace
+        recursion magnifies even binary128 rounding in the highest mixed coefficients
+        (about 6e-19 in the base columns at n = 64), which the S2L weights by (h/2)^(i+j+k)."""
+    from paper_2301_01179_gb300 import binding
+    h = 1.0 / 64
+    pts = np.array([[1.05, 1.05, 2 * h], [0.6, 0.6, 3 * h], [1.05, 1.05 + 2 * h, 2 * h], [1.05 + 3 * h, 1.05, h],
+                    [1.05 / h, 1.05 / h, 2.0], [0.3 / h + 2.0, 0.3 / h, 2.0]])
+    box = [h, h, h, h, 1.0, 1.0]
+    N, P = 64, 24
+    r, r1, x = to_dev(pts[:, 0], pts[:, 1], pts[:, 2])
+    E = to_np(binding.green_expansion(r, r1, x, N + 1, P))[0]
+    i, j, k = np.meshgrid(np.arange(P + 1), np.arange(P + 1), np.arange(P + 1), indexing="ij")
+    rng = np.random.default_rng(8)
+    for p, (a, b, c) in enumerate(pts):
+        for _ in range(6):
+            d = rng.uniform(-0.35 * box[p], 0.35 * box[p], 3)
+            G = oracle.green(a + d[0], b + d[1], c + d[2], N)
+            S = np.einsum("nijk,ijk->n", E[p], d[0] ** i * d[1] ** j * d[2] ** k)
+            assert np.max(np.abs(S - G)) < 1e-12 * abs(G[0]), (p, np.max(np.abs(S - G)) / abs(G[0]))
+        g = oracle.gbar(a, b, c, 32, P)
+        o = i + j + k
+        for order in range(P + 1):
+            sel = o == order
+            den = np.abs(g[:, sel]).max(axis=1)
+            err = np.abs(E[p][:33][:, sel] - g[:, sel]).max(axis=1) / np.where(den > 0, den, 1.0)
+            assert err.max() < 1e-11, (p, order, err.max(), int(err.argmax()))
