@@ -260,6 +260,11 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
     const bool dfx = p->precision == AFMM_FP64 || s2l_tc_enabled(p);
     if (s == AFMM_OK && gcap > 0 && !dfx) s = dalloc_t(p, &p->gexp, gcap);
     p->gexp_cap = gcap;
+    if (s == AFMM_OK) {  // start values of one level's expansions (double-double)
+        int64_t smax = 1;
+        for (int l = 2; l <= p->d; ++l) smax = p->lv[l].nstation > smax ? p->lv[l].nstation : smax;
+        s = dalloc_t(p, &p->gstart, (size_t)smax * 16 * ((p->N < 1 ? 1 : p->N) + 1) * 2);
+    }
     if (s == AFMM_OK && p->precision == AFMM_FP64) s = dalloc_t(p, &p->qsdf, 2 * npq * nmax);
     if (s == AFMM_OK && dfx) {
         int64_t mmax = 0;

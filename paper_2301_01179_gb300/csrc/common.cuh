@@ -198,6 +198,7 @@ struct afmm_plan_s {
     float4 *qsdf = nullptr;
     double df_fwd_switch = 8.0;                 // forward switch of the FP32-pair recursion
     double *gexp = nullptr;                     // expansions of one level
+    double *gstart = nullptr;                   // their start values G^(n): [station][16][max(N,1)+1] double-double
     float2 *gexp_df = nullptr;                  // FP64 path: the same as FP32 pairs
     uint16_t *asl = nullptr;                    // tensor-core S2L: bf16 digit slices of the moments of one level
     afmm::TcTables *tct = nullptr;              // tensor-core S2L tables (host)

@@ -118,3 +118,136 @@ __device__ __forceinline__ ddv dd_sqrt(ddv a)
 }
 
 }  // namespace afmm
+
+namespace afmm {
+
+// 1 / d for an integer-valued d as a double-double: the FP64 quotient and its FMA residual
+__device__ __forceinline__ ddv dd_recip_int(double d)
+{
+    const double h = 1.0 / d;
+    const double r = __fma_rn(-h, d, 1.0);  // 1 - h d, exact
+    return dd_quick_two_sum(h, r * h);
+}
+
+// ---- triple-float: x0 + x1 + x2, three FP32 words (about 72 significant bits), for sums of
+// products on the FP32 pipe where FP64 rounding would be amplified (GB300 issues FP64 at 1/64
+// of FP32).  Products are split exactly by the FP32 FMA; sums of high words by two-sum.
+struct tfv {
+    float x0, x1, x2;
+};
+
+__device__ __forceinline__ void tf_two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// a double-double split into three FP32 words (the remainder is below 2^-72 of the value)
+__device__ __forceinline__ tfv tf_from_dd(ddv v)
+{
+    tfv t;
+    t.x0 = __double2float_rn(v.hi);
+    const ddv r0 = dd_add_d(v, -(double)t.x0);
+    t.x1 = __double2float_rn(r0.hi);
+    const ddv r1 = dd_add_d(r0, -(double)t.x1);
+    t.x2 = __double2float_rn(r1.hi);
+    return t;
+}
+
+__device__ __forceinline__ ddv tf_to_dd(tfv t)
+{
+    return dd_add_d(dd_two_sum((double)t.x0, (double)t.x1), (double)t.x2);
+}
+
+// accumulator of a sum of products: s0 collects the high products by two-sum, s1 the words
+// of weight ~2^-24 (rounding residues of s0, product errors, cross products) by two-sum,
+// s2 the words of weight ~2^-48 in plain FP32
+struct tfacc {
+    float s0, s1, s2;
+};
+
+__device__ __forceinline__ tfacc tfacc_zero()
+{
+    tfacc A;
+    A.s0 = A.s1 = A.s2 = 0.f;
+    return A;
+}
+
+// A += a * b
+__device__ __forceinline__ void tf_acc(tfacc &A, const tfv &a, const tfv &b)
+{
+    const float p = __fmul_rn(a.x0, b.x0), e = __fmaf_rn(a.x0, b.x0, -p);
+    const float q1 = __fmul_rn(a.x0, b.x1), f1 = __fmaf_rn(a.x0, b.x1, -q1);
+    const float q2 = __fmul_rn(a.x1, b.x0), f2 = __fmaf_rn(a.x1, b.x0, -q2);
+    const float l2 = __fmaf_rn(a.x0, b.x2, __fmaf_rn(a.x1, b.x1, __fmaf_rn(a.x2, b.x0, __fadd_rn(f1, f2))));
+    float s, r, t, r1, r2, r3, r4;
+    tf_two_sum(A.s0, p, s, r);
+    tf_two_sum(A.s1, r, t, r1);
+    tf_two_sum(t, e, t, r2);
+    tf_two_sum(t, q1, t, r3);
+    tf_two_sum(t, q2, t, r4);
+    A.s0 = s;
+    A.s1 = t;
+    A.s2 = __fadd_rn(A.s2, __fadd_rn(__fadd_rn(__fadd_rn(r1, r2), __fadd_rn(r3, r4)), l2));
+}
+
+__device__ __forceinline__ ddv tfacc_to_dd(const tfacc &A)
+{
+    return dd_add_d(dd_two_sum((double)A.s0, (double)A.s1), (double)A.s2);
+}
+
+}  // namespace afmm
+
+namespace afmm {
+
+// double-double sum of products: high products by two-sum into H, all low words summed in L
+struct ddacc {
+    double H, L;
+};
+
+// number types of the base-column convolutions in farfield.cu: triple-float on the FP32 pipe
+// (about 2^-68 of the summed magnitudes) or double-double on the FP64 pipe (about 2^-104)
+template <bool DD>
+struct BaseNum;
+
+template <>
+struct BaseNum<false> {
+    using S = tfv;
+    using A = tfacc;
+    static __device__ __forceinline__ S from(ddv v) { return tf_from_dd(v); }
+    static __device__ __forceinline__ ddv to(const S &s) { return tf_to_dd(s); }
+    static __device__ __forceinline__ double nearest(const S &s)
+    {
+        return ((double)s.x0 + (double)s.x1) + (double)s.x2;
+    }
+    static __device__ __forceinline__ A zero() { return tfacc_zero(); }
+    static __device__ __forceinline__ void acc(A &a, const S &x, const S &y) { tf_acc(a, x, y); }
+    static __device__ __forceinline__ ddv fin(const A &a) { return tfacc_to_dd(a); }
+};
+
+template <>
+struct BaseNum<true> {
+    using S = ddv;
+    using A = ddacc;
+    static __device__ __forceinline__ S from(ddv v) { return v; }
+    static __device__ __forceinline__ ddv to(const S &s) { return s; }
+    static __device__ __forceinline__ double nearest(const S &s) { return s.hi; }
+    static __device__ __forceinline__ A zero()
+    {
+        A a;
+        a.H = a.L = 0.0;
+        return a;
+    }
+    static __device__ __forceinline__ void acc(A &a, const S &x, const S &y)
+    {
+        const ddv p = dd_two_prod(x.hi, y.hi);
+        const double cross = __fma_rn(x.hi, y.lo, __dmul_rn(x.lo, y.hi));
+        const ddv s = dd_two_sum(a.H, p.hi);
+        a.L = __dadd_rn(a.L, __dadd_rn(__dadd_rn(s.lo, p.lo), cross));
+        a.H = s.hi;
+    }
+    static __device__ __forceinline__ ddv fin(const A &a) { return dd_quick_two_sum(a.H, a.L); }
+};
+
+}  // namespace afmm

@@ -655,7 +655,7 @@ __device__ void dd_green_sequence(double r, double r1, double x, int N, ddv *G)
         if (N >= 1) G[1] = dd_div(dd_mul(G0, csum), w2);
         for (int n = 2; n <= N; ++n) {
             const ddv up = dd_mul_d(dd_add(G[n - 1], dd_mul(t, G[n - 1])), 4.0 * (n - 1));
-            G[n] = dd_div_d(dd_sub(up, dd_mul_d(G[n - 2], 2.0 * n - 3.0)), 2.0 * n - 1.0);
+            G[n] = dd_mul(dd_sub(up, dd_mul_d(G[n - 2], 2.0 * n - 3.0)), dd_recip_int(2.0 * n - 1.0));
         }
         return;
     }
@@ -664,7 +664,7 @@ __device__ void dd_green_sequence(double r, double r1, double x, int N, ddv *G)
     if (L - 1 <= N) G[L - 1] = ql;
     for (int n = L; n >= 2; --n) {
         const ddv up = dd_mul_d(dd_add(ql, dd_mul(t, ql)), 4.0 * (n - 1));
-        const ddv qn = dd_div_d(dd_sub(up, dd_mul_d(qh, 2.0 * n - 1.0)), 2.0 * n - 3.0);
+        const ddv qn = dd_mul(dd_sub(up, dd_mul_d(qh, 2.0 * n - 1.0)), dd_recip_int(2.0 * n - 3.0));
         qh = ql;
         ql = qn;
         if (n - 2 <= N) G[n - 2] = qn;
@@ -690,10 +690,51 @@ __device__ __forceinline__ void dd_acc2(double &H, double &L, ddv a, ddv b)
     H = s.hi;
 }
 
+// shared-memory layout of gbar_block (byte offsets, 16-byte aligned)
+struct GbarSmem {
+    size_t tv, tvt, b00, b01, g10, g11, G, rk, dtab, total;
+};
+__host__ __device__ inline size_t gb_al(size_t x) { return (x + 15) & ~(size_t)15; }
+__host__ __device__ inline GbarSmem gbar_layout(int N, int P, bool dd)
+{
+    const size_t nmw = (size_t)(N < 1 ? 1 : N) + 1, Q = (size_t)P + 1, es = dd ? 16 : 12;
+    GbarSmem L;
+    L.tv = 0;                                  // double-double Taylor vectors [12][Q]
+    L.tvt = gb_al(L.tv + 12 * Q * 16);         // their products' factors in the base number type [8][Q]
+    L.b00 = gb_al(L.tvt + 8 * Q * es);         // gbar_{0,0,k}: base number type [nmw][Q], then FP64
+    L.b01 = gb_al(L.b00 + nmw * Q * es);       // gbar_{0,1,k}: the same
+    L.g10 = gb_al(L.b01 + nmw * Q * es);       // gbar_{1,0,k}: FP64 [nmw][Q]
+    L.g11 = gb_al(L.g10 + nmw * Q * 8);        // gbar_{1,1,k}: FP64 [nmw][Q]
+    L.G = gb_al(L.g11 + nmw * Q * 8);          // G^(n), double-double [nmw]
+    L.rk = gb_al(L.G + nmw * 16);              // 1 / (k + 1), double-double [Q]
+    L.dtab = gb_al(L.rk + Q * 16);             // the fill's denominators [2 Q]
+    L.total = gb_al(L.dtab + 2 * Q * 8);
+    return L;
+}
+
+// base-type values to their nearest FP64 values in place (element i moves from byte 12 i or
+// 16 i to byte 8 i): rounds of blockDim elements, each read completely before any write
+template <class B>
+__device__ void base_to_double_inplace(typename B::S *a, int count)
+{
+    double *d = reinterpret_cast<double *>(a);
+    for (int base = 0; base < count; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        double v = 0.0;
+        if (i < count) v = B::nearest(a[i]);
+        __syncthreads();
+        if (i < count) d[i] = v;
+        __syncthreads();
+    }
+}
+
+template <bool DDX>
 __device__ void gbar_block(double r, double r1, double x, int N, int P, int A, int Bm, const RecTab &tab,
                            const PairParams &pp, double *sm, double *out, double scale, int fact,
-                           float2 *dfout = nullptr)
+                           float2 *dfout = nullptr, const ddv *Gpre = nullptr)
 {
+    using B = BaseNum<DDX>;
+    using BS = typename B::S;
     (void)tab;
     (void)pp;
     const int Nw = N < 1 ? 1 : N;
@@ -703,18 +744,28 @@ __device__ void gbar_block(double r, double r1, double x, int N, int P, int A, i
     // forms couple G^(n) and G^(n-1) through their difference, which cancels as chi -> 1, and the
     // Laplace recursion (step 4) carries the errors of these base columns into the high mixed
     // coefficients: in FP64 the base columns of axially adjacent boxes on fine levels lose up to
-    // ten digits at modes 0..32 and beyond.  Steps 1-3 therefore run in double-double; the
-    // Laplace recursion, which is stable given accurate base columns, stays in FP64 / FP32 pairs.
-    ddv *tv = reinterpret_cast<ddv *>(sm);       // Taylor vectors [12][Q]
-    double *g00 = sm + 24 * (size_t)Q;           // FP64 (high) parts [nmw][Q]: the fill's inputs
-    double *g10 = g00 + (size_t)nmw * Q;
-    double *g01 = g10 + (size_t)nmw * Q;
-    double *g11 = g01 + (size_t)nmw * Q;
-    double *l00 = g11 + (size_t)nmw * Q;         // low parts of gbar_{0,0,k} and gbar_{0,1,k}
-    double *l01 = l00 + (size_t)nmw * Q;
-    ddv *G = reinterpret_cast<ddv *>(l01 + (size_t)nmw * Q);  // [nmw]
-    // 1. G^(n), n = 0..Nw
-    if (threadIdx.x == 0) dd_green_sequence(r, r1, x, Nw, G);
+    // ten digits at modes 0..32 and beyond.  Steps 1-3 therefore carry about 72 bits: start values
+    // and Taylor vectors in double-double, the convolutions of steps 2-3 as triple-floats on the
+    // FP32 pipe (DDX = false: about 72 bits, enough through modes 0..32) or in double-double
+    // (DDX = true, for more modes at the FP64 parity bar).  The Laplace recursion, stable given
+    // accurate base columns, stays in FP64 / FP32 pairs.
+    const GbarSmem Ly = gbar_layout(N, P, DDX);
+    uint8_t *base = reinterpret_cast<uint8_t *>(sm);
+    ddv *tv = reinterpret_cast<ddv *>(base + Ly.tv);
+    BS *tvt = reinterpret_cast<BS *>(base + Ly.tvt);
+    BS *b00 = reinterpret_cast<BS *>(base + Ly.b00);
+    BS *b01 = reinterpret_cast<BS *>(base + Ly.b01);
+    double *g10 = reinterpret_cast<double *>(base + Ly.g10);
+    double *g11 = reinterpret_cast<double *>(base + Ly.g11);
+    ddv *G = reinterpret_cast<ddv *>(base + Ly.G);
+    ddv *rk = reinterpret_cast<ddv *>(base + Ly.rk);
+    // 1. G^(n), n = 0..Nw (precomputed per expansion, or here by one thread)
+    if (Gpre) {
+        for (int n = threadIdx.x; n <= Nw; n += blockDim.x) G[n] = Gpre[n];
+    } else if (threadIdx.x == 0) {
+        dd_green_sequence(r, r1, x, Nw, G);
+    }
+    for (int k = threadIdx.x; k < Q; k += blockDim.x) rk[k] = dd_recip_int((double)(k + 1));
     // 2. Taylor coefficients in x of 1/rho_pm^2 and the rational factors of Appendix A
     ddv *vp = tv, *vm = tv + Q, *fxp = tv + 2 * Q, *fxm = tv + 3 * Q, *hp = tv + 4 * Q, *hm = tv + 5 * Q;
     ddv *hp1 = tv + 6 * Q, *hm1 = tv + 7 * Q, *dhp = tv + 8 * Q, *dhm = tv + 9 * Q;
@@ -749,8 +800,8 @@ __device__ void gbar_block(double r, double r1, double x, int N, int P, int A, i
         hm1[q] = cm(vm, cpx, q);
         ddv s0 = dd_make(0.0), s1 = dd_make(0.0);
         for (int t = 0; t <= q; ++t) {
-            s0 = dd_add(s0, dd_mul(vp[t], vp[q - t]));
-            s1 = dd_add(s1, dd_mul(vm[t], vm[q - t]));
+            s0 = dd_fma(vp[t], vp[q - t], s0);
+            s1 = dd_fma(vm[t], vm[q - t], s1);
         }
         wsp[q] = s0;
         wsm[q] = s1;
@@ -766,76 +817,73 @@ __device__ void gbar_block(double r, double r1, double x, int N, int P, int A, i
     __syncthreads();
     // the convolutions below use the factor pairs f+ + f- (mode n) and f+ - f- (mode n - 1):
     // sum_q (g^n + g^m) f+_q + (g^n - g^m) f-_q = sum_q g^n (f+ + f-)_q + g^m (f+ - f-)_q
+    BS *tfxp = tvt, *tfxm = tvt + Q, *thp = tvt + 2 * Q, *thm = tvt + 3 * Q, *thp1 = tvt + 4 * Q, *thm1 = tvt + 5 * Q;
+    BS *tdhp = tvt + 6 * Q, *tdhm = tvt + 7 * Q;
     for (int q = threadIdx.x; q <= P; q += blockDim.x) {
-        const ddv a0 = fxp[q], a1 = fxm[q], b0 = hp[q], b1 = hm[q], c0 = hp1[q], c1 = hm1[q], e0 = dhp[q], e1 = dhm[q];
-        fxp[q] = dd_add(a0, a1);
-        fxm[q] = dd_sub(a0, a1);
-        hp[q] = dd_add(b0, b1);
-        hm[q] = dd_sub(b0, b1);
-        hp1[q] = dd_add(c0, c1);
-        hm1[q] = dd_sub(c0, c1);
-        dhp[q] = dd_add(e0, e1);
-        dhm[q] = dd_sub(e0, e1);
+        tfxp[q] = B::from(dd_add(fxp[q], fxm[q]));
+        tfxm[q] = B::from(dd_sub(fxp[q], fxm[q]));
+        thp[q] = B::from(dd_add(hp[q], hm[q]));
+        thm[q] = B::from(dd_sub(hp[q], hm[q]));
+        thp1[q] = B::from(dd_add(hp1[q], hm1[q]));
+        thm1[q] = B::from(dd_sub(hp1[q], hm1[q]));
+        tdhp[q] = B::from(dd_add(dhp[q], dhm[q]));
+        tdhm[q] = B::from(dd_sub(dhp[q], dhm[q]));
     }
-    for (int n = threadIdx.x; n <= Nw; n += blockDim.x) {
-        g00[n * Q] = G[n].hi;
-        l00[n * Q] = G[n].lo;
-    }
+    for (int n = threadIdx.x; n <= Nw; n += blockDim.x) b00[n * Q] = B::from(G[n]);
     __syncthreads();
     // 3a. x-recursion, coupled in n (G^(-1) = G^(1))
     for (int k = 0; k < P; ++k) {
         for (int n = threadIdx.x; n <= Nw; n += blockDim.x) {
             const int m = n == 0 ? 1 : n - 1;
-            double H = 0.0, Lw = 0.0;
+            typename B::A S = B::zero();
             for (int q = 0; q <= k; ++q) {
-                dd_acc2(H, Lw, dd_make(g00[n * Q + k - q], l00[n * Q + k - q]), fxp[q]);
-                dd_acc2(H, Lw, dd_make(g00[m * Q + k - q], l00[m * Q + k - q]), fxm[q]);
+                B::acc(S, b00[n * Q + k - q], tfxp[q]);
+                B::acc(S, b00[m * Q + k - q], tfxm[q]);
             }
-            const ddv v = dd_div_d(dd_mul_d(dd_quick_two_sum(H, Lw), n - 0.5), (double)(k + 1));
-            g00[n * Q + k + 1] = v.hi;
-            l00[n * Q + k + 1] = v.lo;
+            b00[n * Q + k + 1] = B::from(dd_mul(dd_mul_d(B::fin(S), n - 0.5), rk[k]));
         }
         __syncthreads();
     }
     // 3b. first r and r1 derivatives, one task per (mode, order)
+    const ddv i2r = dd_recip_int(2.0 * r), i2r1 = dd_recip_int(2.0 * r1);
     for (int task = threadIdx.x; task < nmw * P; task += blockDim.x) {
         const int n = task / P, k = task % P;
         const int m = n == 0 ? 1 : n - 1;
-        double H1 = 0.0, L1 = 0.0, H2 = 0.0, L2 = 0.0;
+        typename B::A S1 = B::zero(), S2 = B::zero();
         for (int q = 0; q <= k; ++q) {
-            const ddv gn = dd_make(g00[n * Q + k - q], l00[n * Q + k - q]);
-            const ddv gm = dd_make(g00[m * Q + k - q], l00[m * Q + k - q]);
-            dd_acc2(H1, L1, gn, hp[q]);
-            dd_acc2(H1, L1, gm, hm[q]);
-            dd_acc2(H2, L2, gn, hp1[q]);
-            dd_acc2(H2, L2, gm, hm1[q]);
+            const BS gn = b00[n * Q + k - q], gm = b00[m * Q + k - q];
+            B::acc(S1, gn, thp[q]);
+            B::acc(S1, gm, thm[q]);
+            B::acc(S2, gn, thp1[q]);
+            B::acc(S2, gm, thm1[q]);
         }
-        const ddv g = dd_make(g00[n * Q + k], l00[n * Q + k]);
-        const ddv v10 = dd_div_d(dd_sub(dd_mul_d(dd_quick_two_sum(H1, L1), n - 0.5), g), 2.0 * r);
-        const ddv v01 = dd_div_d(dd_sub(dd_mul_d(dd_quick_two_sum(H2, L2), n - 0.5), g), 2.0 * r1);
-        g10[n * Q + k] = v10.hi;
-        g01[n * Q + k] = v01.hi;
-        l01[n * Q + k] = v01.lo;
+        const ddv g = B::to(b00[n * Q + k]);
+        g10[n * Q + k] = dd_mul(dd_sub(dd_mul_d(B::fin(S1), n - 0.5), g), i2r).hi;
+        b01[n * Q + k] = B::from(dd_mul(dd_sub(dd_mul_d(B::fin(S2), n - 0.5), g), i2r1));
     }
     __syncthreads();
     // 3c. mixed, one task per (mode, order)
     for (int task = threadIdx.x; task < nmw * (P - 1); task += blockDim.x) {
         const int n = task / (P - 1), k = task % (P - 1);
         const int m = n == 0 ? 1 : n - 1;
-        double H = 0.0, Lw = 0.0;
+        typename B::A S = B::zero();
         for (int q = 0; q <= k; ++q) {
-            dd_acc2(H, Lw, dd_make(g00[n * Q + k - q], l00[n * Q + k - q]), dhp[q]);
-            dd_acc2(H, Lw, dd_make(g00[m * Q + k - q], l00[m * Q + k - q]), dhm[q]);
-            dd_acc2(H, Lw, dd_make(g01[n * Q + k - q], l01[n * Q + k - q]), hp[q]);
-            dd_acc2(H, Lw, dd_make(g01[m * Q + k - q], l01[m * Q + k - q]), hm[q]);
+            B::acc(S, b00[n * Q + k - q], tdhp[q]);
+            B::acc(S, b00[m * Q + k - q], tdhm[q]);
+            B::acc(S, b01[n * Q + k - q], thp[q]);
+            B::acc(S, b01[m * Q + k - q], thm[q]);
         }
-        const ddv g = dd_make(g01[n * Q + k], l01[n * Q + k]);
-        const ddv v = dd_div_d(dd_sub(dd_mul_d(dd_quick_two_sum(H, Lw), n - 0.5), g), 2.0 * r);
-        g11[n * Q + k] = v.hi;
+        const ddv g = B::to(b01[n * Q + k]);
+        g11[n * Q + k] = dd_mul(dd_sub(dd_mul_d(B::fin(S), n - 0.5), g), i2r).hi;
     }
     __syncthreads();
+    // the base columns gbar_{0,0,k} and gbar_{0,1,k} as FP64 for the fill
+    base_to_double_inplace<B>(b00, nmw * Q);
+    base_to_double_inplace<B>(b01, nmw * Q);
+    const double *g00 = reinterpret_cast<const double *>(b00);
+    const double *g01 = reinterpret_cast<const double *>(b01);
     if (P <= 31) {  // warp-parallel fill (every order a plan accepts: 2M <= 30)
-        double *dtab = reinterpret_cast<double *>(G + nmw);  // [2 Q]
+        double *dtab = reinterpret_cast<double *>(base + Ly.dtab);  // [2 Q]
         if (dfout)
             gbar_fill_warp<NumDF>(r, r1, N, P, A, Bm, Q, g00, g10, g01, g11, dfout, scale, fact,
                                   reinterpret_cast<float2 *>(dtab));
@@ -896,13 +944,11 @@ __device__ void gbar_block(double r, double r1, double x, int N, int P, int A, i
     }
 }
 
-static size_t gbar_smem(int N, int P)
-{
-    // Taylor vectors [12][Q] double-double, base columns [6][nmw][Q], G^(n) [nmw] double-double,
-    // the fill's denominators [2 Q]
-    const size_t nmw = (size_t)(N < 1 ? 1 : N) + 1, Q = (size_t)P + 1;
-    return sizeof(double) * (24 * Q + 6 * nmw * Q + 2 * nmw + 2 * Q);
-}
+static size_t gbar_smem(int N, int P, bool dd) { return gbar_layout(N, P, dd).total; }
+
+// double-double base columns where triple-floats would not hold the FP64 parity bar: the FP64
+// paths beyond 33 modes (measured: 1.3e-10 per mode at modes 0..64, order 14, with triple-floats)
+static bool gexp_dd(afmm_plan p) { return p->precision != AFMM_MIXED && p->N > 32; }
 
 // unit entry point: one point per block, dense (P+1)^3 per mode
 __global__ void k_gbar_points(int64_t np, const double *__restrict__ r, const double *__restrict__ r1,
@@ -912,7 +958,20 @@ __global__ void k_gbar_points(int64_t np, const double *__restrict__ r, const do
     int64_t pidx = blockIdx.x;
     if (pidx >= np) return;
     size_t per = (size_t)nm * (P + 1) * (P + 1) * (P + 1);
-    gbar_block(r[pidx], r1[pidx], fabs(x[pidx]), nm - 1, P, P, P, tab, pp, sm, out + pidx * per, 1.0, 0);
+    // evaluate in units of a power of two sigma near the pair's distance (exact scaling), so
+    // that the triple-float words stay far inside the FP32 range, then undo it with the
+    // homogeneity gbar_{i,j,k}(sigma y) = sigma^{-1-i-j-k} gbar_{i,j,k}(y) (Eq. gfunc:scaled)
+    const double rr = r[pidx], rr1 = r1[pidx], xx = fabs(x[pidx]);
+    const double dist = fmin(hypot(rr - rr1, xx), fmin(rr, rr1));
+    const int e = dist > 0.0 ? ilogb(dist) : 0;
+    gbar_block<true>(ldexp(rr, -e), ldexp(rr1, -e), ldexp(xx, -e), nm - 1, P, P, P, tab, pp, sm, out + pidx * per, 1.0,
+                     0);
+    __syncthreads();
+    for (size_t i = threadIdx.x; i < per; i += blockDim.x) {
+        const int Q = P + 1;
+        const int c = (int)(i % Q), b = (int)((i / Q) % Q), a = (int)((i / ((size_t)Q * Q)) % Q);
+        out[pidx * per + i] = ldexp(out[pidx * per + i], -e * (1 + a + b + c));
+    }
     // odd x-derivatives change sign for x < 0 (G even in x)
     if (x[pidx] < 0.0) {
         __syncthreads();
@@ -921,10 +980,27 @@ __global__ void k_gbar_points(int64_t np, const double *__restrict__ r, const do
     }
 }
 
+// Start values of the S2L expansions of one level: G^(n), n = 0..max(N, 1), at
+// (R_s + a, R_s, b) in box units for every (station, slot a*4+b), one thread each (the serial
+// double-double recursion would otherwise hold a whole block).  Out: [station][16][nmw].
+__global__ void k_gexp_start(const int32_t *__restrict__ col_of_station, const int32_t *__restrict__ station_of_col,
+                             int nstation, int level, double r0h, int Nw, ddv *__restrict__ gstart)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nstation * 16) return;
+    const int st = t / 16, slot = t % 16, a = slot / 4, b = slot % 4;
+    if (a <= 1 && b <= 1) return;
+    const int col = col_of_station[st], nl = 1 << level;
+    if (col + a >= nl || station_of_col[col + a] < 0) return;
+    const double Rs = r0h + col + 0.5, Rb = Rs + a;
+    dd_green_sequence(Rb, Rs, (double)b, Nw, gstart + (size_t)t * (Nw + 1));
+}
+
 // S2L expansions of one level: block = (station, slot a*4+b)
+template <bool DDX>
 __global__ void k_gexp_level(const int32_t *__restrict__ col_of_station, const int32_t *__restrict__ station_of_col,
                              int nstation, int level, double r0h, double h, int nm, int M, const RecTab tab,
-                             PairParams pp, double *gexp, float2 *gexp_df)
+                             PairParams pp, double *gexp, float2 *gexp_df, const ddv *__restrict__ gstart)
 {
     extern __shared__ double sm[];
     int st = blockIdx.x / 16, slot = blockIdx.x % 16;
@@ -937,7 +1013,31 @@ __global__ void k_gexp_level(const int32_t *__restrict__ col_of_station, const i
     size_t slab = (size_t)(M + 1) * (M + 1) * (2 * M + 1);
     double *out = gexp ? gexp + ((size_t)st * 16 + slot) * nm * slab : nullptr;
     float2 *dout = gexp_df ? gexp_df + ((size_t)st * 16 + slot) * nm * slab : nullptr;
-    gbar_block(Rb, Rs, (double)b, nm - 1, 2 * M, M, M, tab, pp, sm, out, 1.0 / h, 1, dout);
+    const int nmw = (nm - 1 < 1 ? 1 : nm - 1) + 1;
+    gbar_block<DDX>(Rb, Rs, (double)b, nm - 1, 2 * M, M, M, tab, pp, sm, out, 1.0 / h, 1, dout,
+                    gstart + ((size_t)st * 16 + slot) * nmw);
+}
+
+// the start values of a level, then its expansions
+static afmm_status launch_gexp_level(afmm_plan p, int l, size_t gsm, double *gexp, float2 *gexp_df)
+{
+    const Level &v = p->lv[l];
+    const double h = p->L / (double)(1 << l);
+    const int Nw = p->N < 1 ? 1 : p->N;
+    const int nt = v.nstation * 16;
+    k_gexp_start<<<(unsigned)((nt + 63) / 64), 64, 0, p->stream>>>(v.col_of_station, v.station_of_col, v.nstation, l,
+                                                                   p->r0 / h, Nw, reinterpret_cast<ddv *>(p->gstart));
+    AFMM_LAUNCH_CHECK();
+    if (gexp_dd(p))
+        k_gexp_level<true><<<(unsigned)nt, 256, gsm, p->stream>>>(v.col_of_station, v.station_of_col, v.nstation, l,
+                                                                  p->r0 / h, h, p->nmodes, p->M, *p->rec, p->pp, gexp,
+                                                                  gexp_df, reinterpret_cast<const ddv *>(p->gstart));
+    else
+        k_gexp_level<false><<<(unsigned)nt, 256, gsm, p->stream>>>(v.col_of_station, v.station_of_col, v.nstation, l,
+                                                                   p->r0 / h, h, p->nmodes, p->M, *p->rec, p->pp, gexp,
+                                                                   gexp_df, reinterpret_cast<const ddv *>(p->gstart));
+    AFMM_LAUNCH_CHECK();
+    return AFMM_OK;
 }
 
 afmm_status launch_green_expansion(int64_t npts, const double *r, const double *r1, const double *x, int n_modes, int P,
@@ -950,7 +1050,7 @@ afmm_status launch_green_expansion(int64_t npts, const double *r, const double *
     pp.miller_extra = 15.0;
     size_t per = (size_t)n_modes * (P + 1) * (P + 1) * (P + 1);
     AFMM_CUDA(cudaMemsetAsync(out, 0, per * npts * sizeof(double), st));
-    size_t sm = gbar_smem(n_modes - 1, P);
+    size_t sm = gbar_smem(n_modes - 1, P, true);
     if (sm > 227 * 1024) return AFMM_EUNSUPPORTED;  // shared-memory working set of one point
     AFMM_CUDA(cudaFuncSetAttribute(k_gbar_points, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_gbar_points<<<(unsigned)npts, 128, sm, st>>>(npts, r, r1, x, n_modes, P, tab, pp, out);
@@ -1311,8 +1411,10 @@ static afmm_status far_field_t(afmm_plan p, int dir)
     }
     tmark(p, 3);
     // downward pass
-    size_t gsm = gbar_smem(p->N, 2 * M);
-    AFMM_CUDA(cudaFuncSetAttribute(k_gexp_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+    size_t gsm = gbar_smem(p->N, 2 * M, gexp_dd(p));
+    if (gsm > 227 * 1024) return AFMM_EUNSUPPORTED;
+    AFMM_CUDA(cudaFuncSetAttribute(k_gexp_level<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+    AFMM_CUDA(cudaFuncSetAttribute(k_gexp_level<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
     for (int l = 2; l <= d; ++l) {
         Level &v = p->lv[l];
         const int e = 16 + 4 * (l - 2);  // event slots: L2L, expansions, S2L, end
@@ -1327,11 +1429,7 @@ static afmm_status far_field_t(afmm_plan p, int dir)
         if (v.nstation > 0) {
             // the tensor-core S2L takes its expansions directly as FP32 pairs
             const bool dfx = s2l_tc_enabled(p);
-            k_gexp_level<<<(unsigned)(v.nstation * 16), 256, gsm, st>>>(v.col_of_station, v.station_of_col, v.nstation,
-                                                                        l, p->r0 / h, h, nm, M, *p->rec, p->pp,
-                                                                        dfx ? nullptr : p->gexp,
-                                                                        dfx ? p->gexp_df : nullptr);
-            AFMM_LAUNCH_CHECK();
+            AFMM_TRY(launch_gexp_level(p, l, gsm, dfx ? nullptr : p->gexp, dfx ? p->gexp_df : nullptr));
         }
         tmark(p, e + 2);
         AFMM_TRY(launch_s2l<R>(p, l, MR(l), MI(l), LR(l), LI(l)));
@@ -1370,8 +1468,10 @@ static afmm_status far_field_df(afmm_plan p, int dir)
         AFMM_LAUNCH_CHECK();
     }
     tmark(p, 3);
-    const size_t gsm = gbar_smem(p->N, 2 * M);
-    AFMM_CUDA(cudaFuncSetAttribute(k_gexp_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+    const size_t gsm = gbar_smem(p->N, 2 * M, gexp_dd(p));
+    if (gsm > 227 * 1024) return AFMM_EUNSUPPORTED;
+    AFMM_CUDA(cudaFuncSetAttribute(k_gexp_level<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
+    AFMM_CUDA(cudaFuncSetAttribute(k_gexp_level<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
     for (int l = 2; l <= d; ++l) {
         Level &v = p->lv[l];
         const int e = 16 + 4 * (l - 2);  // event slots: L2L, expansions, S2L, end
@@ -1381,13 +1481,7 @@ static afmm_status far_field_df(afmm_plan p, int dir)
             l >= 3 ? p->lv[l - 1].locd_im : nullptr, v.locd_re, v.locd_im);
         AFMM_LAUNCH_CHECK();
         tmark(p, e + 1);
-        const double h = p->L / (double)(1 << l);
-        if (v.nstation > 0) {
-            k_gexp_level<<<(unsigned)(v.nstation * 16), 256, gsm, st>>>(v.col_of_station, v.station_of_col, v.nstation,
-                                                                        l, p->r0 / h, h, nm, M, *p->rec, p->pp,
-                                                                        nullptr, p->gexp_df);
-            AFMM_LAUNCH_CHECK();
-        }
+        if (v.nstation > 0) AFMM_TRY(launch_gexp_level(p, l, gsm, nullptr, p->gexp_df));
         tmark(p, e + 2);
         if (s2l_tc_enabled(p)) {
             AFMM_TRY(launch_s2l_tc(p, l, v.momd_re, v.momd_im, v.locd_re, v.locd_im));
