@@ -95,6 +95,18 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float v[4])
     for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 lanes x 8 consecutive FP32 columns, the load and its wait
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v)
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
 // e with 2^(e-1) <= m < 2^e for normal m > 0
 __device__ __forceinline__ int grid_exp(float m) { return (int)((__float_as_uint(m) >> 23) & 0xff) - 126; }
 
@@ -477,22 +489,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
 #pragma unroll
         for (int lv = 0; lv < NE; ++lv) {
 #pragma unroll
-            for (int c = 0; c < QC / 4; ++c) {
-                float v[4];
-                tmem_ld4(tmem + (uint32_t)(KP * lv) + ((uint32_t)(32 * q) << 16) + c0 + 4 * c, v);
+            for (int c8 = 0; c8 < QC; c8 += 8) {  // 8 columns per load and wait (4 for a remainder)
+            float v[8];
+            if (c8 + 8 <= QC)
+                tmem_ld8(tmem + (uint32_t)(KP * lv) + ((uint32_t)(32 * q) << 16) + c0 + c8, v);
+            else
+                tmem_ld4(tmem + (uint32_t)(KP * lv) + ((uint32_t)(32 * q) << 16) + c0 + c8, v);
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    float &S = accS[4 * c + t], &Er = accE[4 * c + t];
-                    if (lv == 3) {
-                        Er = __fadd_rn(Er, v[t]);
-                    } else {
-                        const float s = __fadd_rn(S, v[t]);
-                        const float bb = __fsub_rn(s, S);
-                        const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bb)), __fsub_rn(v[t], bb));
-                        Er = __fadd_rn(Er, err);
-                        S = s;
-                    }
+            for (int tt = 0; tt < 8 && c8 + tt < QC; ++tt) {
+                const int t = c8 + tt;
+                float &S = accS[t], &Er = accE[t];
+                if (lv == 3) {
+                    Er = __fadd_rn(Er, v[tt]);
+                } else {
+                    const float s = __fadd_rn(S, v[tt]);
+                    const float bb = __fsub_rn(s, S);
+                    const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bb)), __fsub_rn(v[tt], bb));
+                    Er = __fadd_rn(Er, err);
+                    S = s;
                 }
+            }
             }
         }
         tc_fence_before();
