@@ -10,7 +10,7 @@ produces the same curves for this implementation:
   E1  eps^(n) against n            (Ns = 2^16, d = 6, several M)
   E2  eps against M for n = 0, 8   (Ns = 2^14, 2^16; d = 5, 6, 7) with the fitted slope
       of log10 eps against M (the paper reports eps ~ C^(-0.4 M))
-  E3  time against Ns, direct and FMM (M = 6 and the highest GPU order, 15)
+  E3  time against Ns, direct and FMM (M = 6 and the paper's highest order, 16)
   E4  FMM time per phase (tree and set-up, upward pass, expansion coefficients, S2L,
       downward pass, near field and local evaluation)
   E5  error against FMM time over (M, d) at Ns = 2^16
@@ -97,7 +97,7 @@ def e1(quick):
     n = 2 ** 14 if quick else 2 ** 16
     c = Case(n)
     ref = c.reference()
-    for M in (6, 8, 10, 12, 14, 15):
+    for M in (6, 8, 10, 12, 14, 16):
         res, ms, _ = c.fmm(M, 6)
         yield {"exp": "E1", "Ns": n, "d": 6, "M": M, "eps_per_mode": [float(x) for x in _eps(res, ref)]}
 
@@ -108,7 +108,7 @@ def e2(quick):
         c = Case(n)
         ref = c.reference()
         for d in (5, 6, 7):
-            eps0, eps8, Ms = [], [], list(range(6, 16))
+            eps0, eps8, Ms = [], [], list(range(6, 17))
             for M in Ms:
                 res, ms, _ = c.fmm(M, d)
                 e = _eps(res, ref)
@@ -128,7 +128,7 @@ def e3(quick):
         c = Case(n)
         c.reference() if k <= 18 else None
         row = {"exp": "E3", "Ns": n, "direct_ms": c.direct_ms}
-        for M in (6, 15):
+        for M in (6, 16):
             pl = c.plan(M, leaf=32)
             out, ms = c.timed(lambda: pl.eval(c.qr, c.qi))
             info = pl.info()
@@ -143,7 +143,7 @@ def e3(quick):
 def e4(quick):
     n = 2 ** 14 if quick else 2 ** 16
     c = Case(n)
-    for M in (6, 12, 15):
+    for M in (6, 12, 16):
         res, ms, ph = c.fmm(M, 6)
         yield {"exp": "E4", "Ns": n, "d": 6, "M": M, "total_ms": ms, "phase_ms": {k: round(v, 4) for k, v in ph.items()}}
 
@@ -153,7 +153,7 @@ def e5(quick):
     c = Case(n)
     ref = c.reference()
     for d in (4, 5, 6, 7):
-        for M in (6, 8, 10, 12, 14, 15):
+        for M in (6, 8, 10, 12, 14, 16):
             res, ms, _ = c.fmm(M, d)
             e = _eps(res, ref)
             yield {"exp": "E5", "Ns": n, "d": d, "M": M, "fmm_ms": ms, "direct_ms": c.direct_ms,

@@ -61,7 +61,7 @@ typedef enum {
 /* Options of the FMM (Sec. 3, Algorithm 1).  Zero-initialise and set what you need;
  * afmm_options_default() fills the defaults. */
 typedef struct {
-    int order;          /* expansion order M (moments i+j <= M, locals k+l <= M); 0..15
+    int order;          /* expansion order M (moments i+j <= M, locals k+l <= M); 0..16
                            (larger orders: AFMM_EUNSUPPORTED) */
     int leaf_size;      /* depth rule: smallest d >= 2 whose non-empty leaves hold at most
                            leaf_size sources on average; >= 1 */

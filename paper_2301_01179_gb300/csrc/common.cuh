@@ -17,7 +17,7 @@
 
 #define AFMM_MAX_LEVEL 16
 #define AFMM_MAX_MODES 129     // n_modes <= 129 (N <= 128)
-#define AFMM_MAX_ORDER 15      // expansion order M <= 15 (S2L Taylor order 2M <= 30 fits a warp)
+#define AFMM_MAX_ORDER 16      // expansion order M <= 16 (S2L Taylor order 2M <= 32: two Taylor indices per lane)
 #define AFMM_NEAR_WARPS 4      // warps per near-field block
 
 namespace afmm {

@@ -512,6 +512,7 @@ struct NumF64 {
     static __device__ __forceinline__ T neg(T a) { return -a; }
     static __device__ __forceinline__ T zero() { return 0.0; }
     static __device__ __forceinline__ T down2(T a) { return __shfl_down_sync(0xffffffffu, a, 2); }
+    static __device__ __forceinline__ T idx(int src, T a) { return __shfl_sync(0xffffffffu, a, src); }
     static __device__ __forceinline__ T ld(const S *p) { return *p; }
     static __device__ __forceinline__ void st(S *p, T v) { *p = v; }
 };
@@ -528,6 +529,10 @@ struct NumDF {
     {
         return df_make(__shfl_down_sync(0xffffffffu, a.hi, 2), __shfl_down_sync(0xffffffffu, a.lo, 2));
     }
+    static __device__ __forceinline__ T idx(int src, T a)
+    {
+        return df_make(__shfl_sync(0xffffffffu, a.hi, src), __shfl_sync(0xffffffffu, a.lo, src));
+    }
     static __device__ __forceinline__ T ld(const S *p)
     {
         const float2 v = *p;
@@ -536,20 +541,36 @@ struct NumDF {
     static __device__ __forceinline__ void st(S *p, T v) { *p = make_float2(v.hi, v.lo); }
 };
 
-// Step 4 of gbar_block, warp-parallel (P <= 31): lane c holds the c-th Taylor coefficient of
-// one row (a, b) of one mode.  The Laplace recursion of a row needs rows b+1, b, b-1, b-2
-// (resp. a+1 .. a-2) at c and c+2 only, so a warp walks the rows with a register window and
-// a shuffle for c+2:  phase A raises b for a = 0, 1 (one warp per (mode, a)); phase B raises
-// a for each b (one warp per (mode, b)), reading the phase-A rows and writing every entry
-// scaled by scale * c!.  Same recursions and coefficients as the serial fill below.
-template <class O>
+// Step 4 of gbar_block, warp-parallel (P <= 32 NH - 1): lane l holds the Taylor coefficients
+// c = l + 32 h, h < NH, of one row (a, b) of one mode.  The Laplace recursion of a row needs
+// rows b+1, b, b-1, b-2 (resp. a+1 .. a-2) at c and c+2 only, so a warp walks the rows with a
+// register window and a shuffle for c+2 (across the halves when NH = 2):  phase A raises b for
+// a = 0, 1 (one warp per (mode, a)); phase B raises a for each b (one warp per (mode, b)),
+// reading the phase-A rows and writing every entry scaled by scale * c!.  Same recursions and
+// coefficients as the serial fill below.
+template <class O, int NH>
+__device__ __forceinline__ void fill_down2(const typename O::T (&x)[NH], typename O::T (&d)[NH], int lane)
+{
+    // d[h] = the value at c + 2 (zero beyond the last half)
+    d[0] = O::down2(x[0]);
+    if constexpr (NH == 2) {
+        const typename O::T w = O::idx((lane + 2) & 31, x[1]);
+        if (lane >= 30) d[0] = w;
+        d[1] = O::down2(x[1]);
+        if (lane >= 30) d[1] = O::zero();
+    }
+}
+
+template <class O, int NH>
 __device__ void gbar_fill_warp(double r, double r1, int N, int P, int A, int Bm, int Q, const double *g00,
                                const double *g10, const double *g01, const double *g11, typename O::S *out,
                                double scale, int fact, typename O::S *dtab)
 {
     using T = typename O::T;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int c = lane;
+    int cc[NH];
+#pragma unroll
+    for (int h = 0; h < NH; ++h) cc[h] = lane + 32 * h;
     const int SA = (Bm + 1) * Q;
     // 1 / (r1^2 (b+1)(b+2)) and 1 / (r^2 (a+1)(a+2)), once per block (FP64 division is slow)
     typename O::S *denB = dtab, *denA = dtab + Q;
@@ -560,7 +581,9 @@ __device__ void gbar_fill_warp(double r, double r1, int N, int P, int A, int Bm,
     __syncthreads();
     const T r1d = O::from(r1), r1s = O::from(r1 * r1), r1x2 = O::from(2.0 * r1);
     const T rd = O::from(r), rs = O::from(r * r), rx2 = O::from(2.0 * r);
-    const float cc2 = (float)((c + 1) * (c + 2));
+    float cc2[NH];
+#pragma unroll
+    for (int h = 0; h < NH; ++h) cc2[h] = (float)((cc[h] + 1) * (cc[h] + 2));
     // phase A: rows (a, b), a <= 1, unscaled
     const int na = A >= 1 ? 2 : 1;
     for (int task = warp; task < (N + 1) * na; task += nw) {
@@ -568,58 +591,88 @@ __device__ void gbar_fill_warp(double r, double r1, int N, int P, int A, int Bm,
         typename O::S *E = out + (size_t)n * (A + 1) * SA + (size_t)a * SA;
         const float n2 = (float)(n * n);
         const double *gb0 = a == 0 ? g00 : g10, *gb1 = a == 0 ? g01 : g11;
-        T R0 = c <= P - a ? O::from(gb0[n * Q + c]) : O::zero();                           // b = 0
-        T R1 = (Bm >= 1 && c <= P - a - 1) ? O::from(gb1[n * Q + c]) : O::zero();         // b = 1
-        T Rm1 = O::zero(), Rm2 = O::zero();                                                // b - 1, b - 2
-        if (c <= P - a) O::st(E + c, R0);
-        if (Bm >= 1 && c <= P - a - 1) O::st(E + Q + c, R1);
+        T R0[NH], R1[NH], Rm1[NH], Rm2[NH];
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+            const int c = cc[h];
+            R0[h] = c <= P - a ? O::from(gb0[n * Q + c]) : O::zero();                    // b = 0
+            R1[h] = (Bm >= 1 && c <= P - a - 1) ? O::from(gb1[n * Q + c]) : O::zero();  // b = 1
+            Rm1[h] = Rm2[h] = O::zero();                                                 // b - 1, b - 2
+            if (c <= P - a) O::st(E + c, R0[h]);
+            if (Bm >= 1 && c <= P - a - 1) O::st(E + Q + c, R1[h]);
+        }
         for (int b = 0; b + 2 <= Bm && a + b + 2 <= P; ++b) {
             const T den = O::ld(denB + b);
-            const T d0 = O::down2(R0), dm1 = O::down2(Rm1), dm2 = O::down2(Rm2);
-            T sv = O::add(O::mulf(O::mul(r1d, R1), (float)((b + 1) * (2 * b + 1))), O::mulf(R0, (float)(b * b) - n2));
-            T t = O::mul(r1s, d0);
-            if (b >= 1) t = O::add(t, O::mul(r1x2, dm1));
-            if (b >= 2) t = O::add(t, dm2);
-            sv = O::add(sv, O::mulf(t, cc2));
-            const T R2 = O::neg(O::mul(sv, den));
-            if (a + b + 2 + c <= P) O::st(E + (size_t)(b + 2) * Q + c, R2);
-            Rm2 = Rm1;
-            Rm1 = R0;
-            R0 = R1;
-            R1 = R2;
+            T d0[NH], dm1[NH], dm2[NH];
+            fill_down2<O, NH>(R0, d0, lane);
+            fill_down2<O, NH>(Rm1, dm1, lane);
+            fill_down2<O, NH>(Rm2, dm2, lane);
+#pragma unroll
+            for (int h = 0; h < NH; ++h) {
+                T sv = O::add(O::mulf(O::mul(r1d, R1[h]), (float)((b + 1) * (2 * b + 1))), O::mulf(R0[h], (float)(b * b) - n2));
+                T t = O::mul(r1s, d0[h]);
+                if (b >= 1) t = O::add(t, O::mul(r1x2, dm1[h]));
+                if (b >= 2) t = O::add(t, dm2[h]);
+                sv = O::add(sv, O::mulf(t, cc2[h]));
+                const T R2 = O::neg(O::mul(sv, den));
+                if (a + b + 2 + cc[h] <= P) O::st(E + (size_t)(b + 2) * Q + cc[h], R2);
+                Rm2[h] = Rm1[h];
+                Rm1[h] = R0[h];
+                R0[h] = R1[h];
+                R1[h] = R2;
+            }
         }
     }
     __syncthreads();
     // phase B: raise a for each (mode, b); write every entry scaled
-    double fcd = scale;
-    if (fact)
-        for (int k = 2; k <= c; ++k) fcd *= k;
-    const T fc = O::from(fcd);
+    T fc[NH];
+#pragma unroll
+    for (int h = 0; h < NH; ++h) {
+        double fcd = scale;
+        if (fact)
+            for (int k = 2; k <= cc[h]; ++k) fcd *= k;
+        fc[h] = O::from(fcd);
+    }
     for (int task = warp; task < (N + 1) * (Bm + 1); task += nw) {
         const int n = task / (Bm + 1), b = task % (Bm + 1);
         if (b > P) continue;  // warp-uniform
         typename O::S *E = out + (size_t)n * (A + 1) * SA + (size_t)b * Q;
         const float n2 = (float)(n * n);
-        T R0 = c <= P - b ? O::ld(E + c) : O::zero();                                       // a = 0
-        T R1 = (A >= 1 && c <= P - b - 1) ? O::ld(E + SA + c) : O::zero();                  // a = 1
-        T Rm1 = O::zero(), Rm2 = O::zero();
+        T R0[NH], R1[NH], Rm1[NH], Rm2[NH];
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+            const int c = cc[h];
+            R0[h] = c <= P - b ? O::ld(E + c) : O::zero();                       // a = 0
+            R1[h] = (A >= 1 && c <= P - b - 1) ? O::ld(E + SA + c) : O::zero();  // a = 1
+            Rm1[h] = Rm2[h] = O::zero();
+        }
         __syncwarp();
-        if (c <= P - b) O::st(E + c, O::mul(R0, fc));
-        if (A >= 1 && c <= P - b - 1) O::st(E + SA + c, O::mul(R1, fc));
+#pragma unroll
+        for (int h = 0; h < NH; ++h) {
+            const int c = cc[h];
+            if (c <= P - b) O::st(E + c, O::mul(R0[h], fc[h]));
+            if (A >= 1 && c <= P - b - 1) O::st(E + SA + c, O::mul(R1[h], fc[h]));
+        }
         for (int a = 0; a + 2 <= A && a + 2 + b <= P; ++a) {
             const T den = O::ld(denA + a);
-            const T d0 = O::down2(R0), dm1 = O::down2(Rm1), dm2 = O::down2(Rm2);
-            T sv = O::add(O::mulf(O::mul(rd, R1), (float)((a + 1) * (2 * a + 1))), O::mulf(R0, (float)(a * a) - n2));
-            T t = O::mul(rs, d0);
-            if (a >= 1) t = O::add(t, O::mul(rx2, dm1));
-            if (a >= 2) t = O::add(t, dm2);
-            sv = O::add(sv, O::mulf(t, cc2));
-            const T R2 = O::neg(O::mul(sv, den));
-            if (a + 2 + b + c <= P) O::st(E + (size_t)(a + 2) * SA + c, O::mul(R2, fc));
-            Rm2 = Rm1;
-            Rm1 = R0;
-            R0 = R1;
-            R1 = R2;
+            T d0[NH], dm1[NH], dm2[NH];
+            fill_down2<O, NH>(R0, d0, lane);
+            fill_down2<O, NH>(Rm1, dm1, lane);
+            fill_down2<O, NH>(Rm2, dm2, lane);
+#pragma unroll
+            for (int h = 0; h < NH; ++h) {
+                T sv = O::add(O::mulf(O::mul(rd, R1[h]), (float)((a + 1) * (2 * a + 1))), O::mulf(R0[h], (float)(a * a) - n2));
+                T t = O::mul(rs, d0[h]);
+                if (a >= 1) t = O::add(t, O::mul(rx2, dm1[h]));
+                if (a >= 2) t = O::add(t, dm2[h]);
+                sv = O::add(sv, O::mulf(t, cc2[h]));
+                const T R2 = O::neg(O::mul(sv, den));
+                if (a + 2 + b + cc[h] <= P) O::st(E + (size_t)(a + 2) * SA + cc[h], O::mul(R2, fc[h]));
+                Rm2[h] = Rm1[h];
+                Rm1[h] = R0[h];
+                R0[h] = R1[h];
+                R1[h] = R2;
+            }
         }
     }
 }
@@ -882,16 +935,24 @@ __device__ void gbar_block(double r, double r1, double x, int N, int P, int A, i
     base_to_double_inplace<B>(b01, nmw * Q);
     const double *g00 = reinterpret_cast<const double *>(b00);
     const double *g01 = reinterpret_cast<const double *>(b01);
-    if (P <= 31) {  // warp-parallel fill (every order a plan accepts: 2M <= 30)
+    if (P <= 63) {  // warp-parallel fill (every order a plan accepts: 2M <= 32)
         double *dtab = reinterpret_cast<double *>(base + Ly.dtab);  // [2 Q]
-        if (dfout)
-            gbar_fill_warp<NumDF>(r, r1, N, P, A, Bm, Q, g00, g10, g01, g11, dfout, scale, fact,
-                                  reinterpret_cast<float2 *>(dtab));
-        else
-            gbar_fill_warp<NumF64>(r, r1, N, P, A, Bm, Q, g00, g10, g01, g11, out, scale, fact, dtab);
+        if (P <= 31) {
+            if (dfout)
+                gbar_fill_warp<NumDF, 1>(r, r1, N, P, A, Bm, Q, g00, g10, g01, g11, dfout, scale, fact,
+                                         reinterpret_cast<float2 *>(dtab));
+            else
+                gbar_fill_warp<NumF64, 1>(r, r1, N, P, A, Bm, Q, g00, g10, g01, g11, out, scale, fact, dtab);
+        } else {
+            if (dfout)
+                gbar_fill_warp<NumDF, 2>(r, r1, N, P, A, Bm, Q, g00, g10, g01, g11, dfout, scale, fact,
+                                         reinterpret_cast<float2 *>(dtab));
+            else
+                gbar_fill_warp<NumF64, 2>(r, r1, N, P, A, Bm, Q, g00, g10, g01, g11, out, scale, fact, dtab);
+        }
         return;
     }
-    if (dfout) return;  // not reached: FP32-pair expansions come from plans (P = 2M <= 30)
+    if (dfout) return;  // not reached: FP32-pair expansions come from plans (P = 2M <= 32)
     // 4. Laplace recursions, one mode per thread, into the output slab
     const int SA = (Bm + 1) * Q;  // stride of a
     for (int n = threadIdx.x; n <= N; n += blockDim.x) {
