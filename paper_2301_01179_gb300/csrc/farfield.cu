@@ -1007,9 +1007,11 @@ __device__ void gbar_block(double r, double r1, double x, int N, int P, int A, i
 
 static size_t gbar_smem(int N, int P, bool dd) { return gbar_layout(N, P, dd).total; }
 
-// double-double base columns where triple-floats would not hold the FP64 parity bar: the FP64
-// paths beyond 33 modes (measured: 1.3e-10 per mode at modes 0..64, order 14, with triple-floats)
-static bool gexp_dd(afmm_plan p) { return p->precision != AFMM_MIXED && p->N > 32; }
+// double-double base columns beyond 33 modes, in every precision: there the cancellation of
+// the base columns outruns the triple-float's ~72 bits (measured with triple-floats at modes
+// 0..64, order 14: 1.3e-10 per mode on a depth-5 tree, FP64 path; 4.9e-5 at mode 64 on the
+// depth-10 tree of 4e6 rings, MIXED path, whose other errors are ~1e-7)
+static bool gexp_dd(afmm_plan p) { return p->N > 32; }
 
 // unit entry point: one point per block, dense (P+1)^3 per mode
 __global__ void k_gbar_points(int64_t np, const double *__restrict__ r, const double *__restrict__ r1,

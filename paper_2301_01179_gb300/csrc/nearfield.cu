@@ -9,7 +9,6 @@
 // pairs in the accumulation.  AFMM_FP64_NATIVE runs the FP64 kernels k_near / k_near2
 // (one warp per work unit, per-mode accumulators in shared memory).
 #include <cstring>
-#include <mutex>
 #include "common.cuh"
 #include "pair.cuh"
 #include "pair_df.cuh"
@@ -1384,26 +1383,15 @@ namespace afmm {
 // ------------------------------------------------------------------------------------
 static __device__ __align__(256) double g_static_scratch[AFMM_STATIC_SCRATCH_DOUBLES];
 
-static double *g_static_addr[64];
-static bool g_static_ready[64];
-static std::mutex g_static_mu;
-
 // Host code may not take the address of g_static_scratch directly (it names a host-side
-// stand-in); the device address comes from cudaGetSymbolAddress, once per device, with
-// that device current.
+// stand-in); the device address comes from cudaGetSymbolAddress on every call, in the
+// caller's current context, so that nothing stale survives a cudaDeviceReset or a change
+// of context.  The lookup is a host-side query, cheap next to the kernels.
 static afmm_status static_scratch(double **out)
 {
-    int dev = 0;
-    AFMM_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return AFMM_EUNSUPPORTED;
-    std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_ready[dev]) {
-        void *ptr = nullptr;
-        AFMM_CUDA(cudaGetSymbolAddress(&ptr, g_static_scratch));
-        g_static_addr[dev] = (double *)ptr;
-        g_static_ready[dev] = true;
-    }
-    *out = g_static_addr[dev];
+    void *ptr = nullptr;
+    AFMM_CUDA(cudaGetSymbolAddress(&ptr, g_static_scratch));
+    *out = (double *)ptr;
     return AFMM_OK;
 }
 

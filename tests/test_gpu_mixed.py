@@ -102,3 +102,27 @@ def test_fp32_pair_sequence_vs_native_fp64():
         print(prec, "per-mode max error / G0:", np.array2string(worst[prec], precision=1))
         assert err.max() < tol, (prec, err.max(), np.unravel_index(err.argmax(), err.shape))
         assert np.abs(g[1]).max() == 0.0
+
+
+def test_mixed_fmm_deep_tree_65_modes():
+    """MIXED against the FP64 path (itself oracle-pinned at 1e-10) on the deep tree of the
+    4e6-ring workload: its laws (r ~ Exp(mean 0.5) on [0.01, 3], z ~ N(0, 1), |S^(n)| ~
+    n^-2), modes 0..64, order 14, depth 10 as the full workload's leaf rule gives, on 1e5
+    points.  The Taylor coefficients of the smallest boxes at the highest modes are where
+    the base columns cancel most (Eq. analysis:taylor's x-recursion as chi -> 1); the bound
+    is MIXED's stated FMM bound, 2e-5 per mode."""
+    w = W.make("cfg5", ns=100000, nf=100000)
+    assert w["n_modes"] == 65 and w["order"] == 14
+    q_re, q_im = to_dev(w["q_re"], w["q_im"])
+    out = {}
+    for prec in ("fp64", "mixed"):
+        from paper_2301_01179_gb300 import binding
+        sr, sz, tr, tz = to_dev(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"])
+        pl = binding.Plan(sr, sz, tr, tz, 65, order=14, leaf_size=64, depth=10, precision=prec)
+        assert pl.info()["depth"] == 10
+        out[prec] = to_np(*pl.grad(q_re, q_im))
+        pl.close()
+    for c in range(0, 6, 2):
+        e = eps_modes(out["mixed"][c], out["mixed"][c + 1], out["fp64"][c], out["fp64"][c + 1])
+        print("component", c // 2, "per-mode eps, modes 56..64:", np.array2string(e[56:], precision=1))
+        assert e.max() < TOL_FMM, (c, e.max(), int(e.argmax()))
