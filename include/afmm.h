@@ -219,8 +219,12 @@ afmm_status afmm_fourier_synthesis(int64_t npts, int n_modes, const double *phi_
  *  - Scratch comes from one file-scope device array of AFMM_STATIC_SCRATCH_DOUBLES doubles
  *    (16 MiB) that every GPU loading this library holds until the process exits.  Requests
  *    with 2 * n_modes * ns > AFMM_STATIC_SCRATCH_DOUBLES return AFMM_EINVAL.
- *  - The first call on a device looks the array's device address up (cudaGetSymbolAddress,
- *    with that device current); make that first call before any stream capture.
+ *  - Every call looks the array's device address up (cudaGetSymbolAddress) in the caller's
+ *    current context.  The first call in a process may load the library's device code:
+ *    make it outside stream capture; later calls may be captured into a CUDA graph.
+ *  - It runs the native FP64 pair kernel, not afmm_direct's FP32-pair kernel (whose extra
+ *    per-point inputs do not fit the array): measured 2.8x afmm_direct's time on GB300
+ *    (4096 x 4096 points, 17 modes: 12.8 ms against 4.6 ms).
  *  - Every call shares the array and leaves its contents behind; nothing is read before
  *    this call writes it.  Calls whose work overlaps on the GPU (other streams, other host
  *    threads) race on the array: serialise them.
