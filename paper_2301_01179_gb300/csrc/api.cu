@@ -51,6 +51,78 @@ static cudaMemPool_t plan_pool(int dev)
     return g_pool_state[dev] == 1 ? g_pool[dev] : nullptr;
 }
 
+// Mapped pinned host words of the plans (error word, small readbacks): one block per device,
+// made once, with a 256-byte slot per live plan.  Page-locked allocations and frees
+// synchronise with the work of other streams, so a plan that made its own would wait for,
+// e.g., the download of an earlier result.  A plan that finds no free slot makes its own.
+constexpr int HW_SLOTS = 512, HW_SLOT_BYTES = 256;
+static char *g_hw_host[64], *g_hw_dev[64];
+static unsigned char g_hw_used[64][HW_SLOTS];
+static int g_hw_state[64];
+
+static afmm_status hostwords_take(afmm_plan p)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        dev = -1;
+    }
+    char *h = nullptr, *d = nullptr;
+    if (dev >= 0) {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (g_hw_state[dev] == 0) {
+            char *bh = nullptr, *bd = nullptr;
+            cudaError_t e = cudaHostAlloc((void **)&bh, (size_t)HW_SLOTS * HW_SLOT_BYTES, cudaHostAllocMapped);
+            if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&bd, bh, 0);
+            if (e == cudaSuccess) {
+                g_hw_host[dev] = bh;
+                g_hw_dev[dev] = bd;
+                g_hw_state[dev] = 1;
+            } else {
+                cudaGetLastError();
+                g_hw_state[dev] = -1;
+            }
+        }
+        if (g_hw_state[dev] == 1)
+            for (int i = 0; i < HW_SLOTS; ++i)
+                if (!g_hw_used[dev][i]) {
+                    g_hw_used[dev][i] = 1;
+                    p->hw_dev = dev;
+                    p->hw_slot = i;
+                    h = g_hw_host[dev] + (size_t)i * HW_SLOT_BYTES;
+                    d = g_hw_dev[dev] + (size_t)i * HW_SLOT_BYTES;
+                    break;
+                }
+    }
+    if (!h) {
+        cudaError_t e = cudaHostAlloc((void **)&h, HW_SLOT_BYTES, cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&d, h, 0);
+        if (e != cudaSuccess) {
+            set_cuda_error(e);
+            cudaGetLastError();
+            return AFMM_ECUDA;
+        }
+    }
+    memset(h, 0, HW_SLOT_BYTES);
+    p->err_host = (int *)h;
+    p->err_dev = (int *)d;
+    p->rb_host = (unsigned long long *)(h + 64);
+    p->rb_dev = (unsigned long long *)(d + 64);
+    return AFMM_OK;
+}
+
+static void hostwords_give(afmm_plan p)
+{
+    if (!p->err_host) return;
+    if (p->hw_slot >= 0) {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        g_hw_used[p->hw_dev][p->hw_slot] = 0;
+    } else {
+        cudaFreeHost(p->err_host);
+    }
+    p->err_host = p->err_dev = nullptr;
+}
+
 afmm_status dalloc(afmm_plan p, void **ptr, size_t bytes)
 {
     *ptr = nullptr;
@@ -148,7 +220,7 @@ void afmm_plan_destroy(afmm_plan p)
         cudaStreamSynchronize(p->stream);
         for (int i = 0; i < p->nalloc; ++i) cudaFree(p->allocs[i]);
     }
-    if (p->err_host) cudaFreeHost(p->err_host);
+    hostwords_give(p);
     delete p->tct;
     if (p->timing)
         for (int i = 0; i < 80; ++i) cudaEventDestroy(p->ev[i]);
@@ -219,7 +291,8 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
     // for s = 2 N a <= 8 (N <= 64)
     p->df_fwd_switch = opt.fwd_switch > 0.0 ? fmin(opt.fwd_switch, 8.0) : 8.0;
 
-    afmm_status s = build_tree(p, src_r, src_z, tgt_r, tgt_z);
+    afmm_status s = hostwords_take(p);
+    if (s == AFMM_OK) s = build_tree(p, src_r, src_z, tgt_r, tgt_z);
     if (s == AFMM_OK) s = make_shift_tables(p);
     // evaluation scratch: nothing is allocated by the evaluation calls
     const int nm = p->nmodes, nc = p->ncoef;
@@ -228,8 +301,7 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
     if (s == AFMM_OK && !mix) s = dalloc_t(p, &p->qs_re, (size_t)nm * nmax);
     if (s == AFMM_OK && !mix) s = dalloc_t(p, &p->qs_im, (size_t)nm * nmax);
     const size_t npq = (size_t)(nm + 1) / 2;  // mode pairs of the interleaved amplitude copies
-    if (s == AFMM_OK && mix) s = dalloc_t(p, &p->qs32_re, npq * nmax);
-    if (s == AFMM_OK && mix) s = dalloc_t(p, &p->qs32_im, npq * nmax);
+    if (s == AFMM_OK && mix) s = dalloc_t(p, &p->qs32, npq * nmax);
     if (s == AFMM_OK) s = dalloc_t(p, &p->acc_buf, (size_t)6 * nm * p->ns);
     int64_t gcap = 0, nexp = 0;
     for (int l = 2; s == AFMM_OK && l <= p->d; ++l) {
@@ -266,6 +338,7 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
         s = dalloc_t(p, &p->gstart, (size_t)smax * 16 * ((p->N < 1 ? 1 : p->N) + 1) * 2);
     }
     if (s == AFMM_OK && p->precision == AFMM_FP64) s = dalloc_t(p, &p->qsdf, 2 * npq * nmax);
+    if (s == AFMM_OK && p->precision != AFMM_FP64_NATIVE) s = dalloc_t(p, &p->osort, (size_t)6 * nm * nmax);
     if (s == AFMM_OK && dfx) {
         int64_t mmax = 0;
         for (int l = 2; l <= p->d; ++l) mmax = p->lv[l].nbox > mmax ? p->lv[l].nbox : mmax;
@@ -273,18 +346,6 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
         if (s2l_tc_enabled(p)) {
             if (s == AFMM_OK) s = dalloc_t(p, &p->asl, (size_t)s2l_tc_slice_elems(p, mmax));
             if (s == AFMM_OK) s = make_tc_tables(p);
-        }
-    }
-    // device-side error word in mapped host memory (set by kernels whose bounded waits run out)
-    if (s == AFMM_OK) {
-        cudaError_t e = cudaHostAlloc((void **)&p->err_host, sizeof(int), cudaHostAllocMapped);
-        if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&p->err_dev, p->err_host, 0);
-        if (e != cudaSuccess) {
-            set_cuda_error(e);
-            cudaGetLastError();
-            s = AFMM_ECUDA;
-        } else {
-            *(volatile int *)p->err_host = 0;
         }
     }
     // direct sums over few field points are split over sources: room for the partials

@@ -154,11 +154,15 @@ struct TcTables {
 };
 
 // amplitude of mode n, source s: FP64 copies are planar [n][ns]; FP32 copies (MIXED) are
-// interleaved by mode pair, [n / 2][ns] x (q_2m, q_2m+1)
-__device__ __forceinline__ double amp_at(const double *q, int n, int64_t s, int64_t ns) { return q[(size_t)n * ns + s]; }
-__device__ __forceinline__ float amp_at(const float *q, int n, int64_t s, int64_t ns)
+// per source by mode pair, [ns][npq] x (re_2m, re_2m+1, im_2m, im_2m+1), the re part at
+// q = the copy, the im part at q = the copy + 2 floats
+__device__ __forceinline__ double amp_at(const double *q, int n, int64_t s, int64_t ns, int npq)
 {
-    return q[((size_t)(n >> 1) * ns + s) * 2 + (n & 1)];
+    return q[(size_t)n * ns + s];
+}
+__device__ __forceinline__ float amp_at(const float *q, int n, int64_t s, int64_t ns, int npq)
+{
+    return q[((size_t)s * npq + (n >> 1)) * 4 + (n & 1)];
 }
 
 struct NearUnit {       // one warp of near-field work: up to 32 field points of one leaf
@@ -180,7 +184,9 @@ struct afmm_plan_s {
     double r0 = 0, z0 = 0, L = 1;
     // sorted points
     double *s_r = nullptr, *s_z = nullptr, *t_r = nullptr, *t_z = nullptr;
-    float2 *s_rinv = nullptr, *t_rinv = nullptr;  // sorted 1 / r as FP32 pairs (FP32-pair near field)
+    // sorted coordinates for the FP32-pair near field, [n][2] float4: (r0, r1, z0, z1) and
+    // (r2, z2, 1/r hi, 1/r lo), r = r0 + r1 + r2 and z = z0 + z1 + z2 exactly
+    float4 *s_geo = nullptr, *t_geo = nullptr;
     int32_t *s_perm = nullptr, *t_perm = nullptr;
     uint32_t *s_key = nullptr, *t_key = nullptr;
     afmm::Level lv[AFMM_MAX_LEVEL + 1];
@@ -191,11 +197,16 @@ struct afmm_plan_s {
     afmm::NearUnit *dir_unit[2] = {nullptr, nullptr};
     // eval scratch
     double *qs_re = nullptr, *qs_im = nullptr;  // [nmodes][max(ns,nf)] strengths, sorted, * c_n
-    // MIXED: the same in FP32, interleaved by mode pair: [n / 2][n_max] (q_2m, q_2m+1)
-    float2 *qs32_re = nullptr, *qs32_im = nullptr;
-    // FP64 path: the same as FP32 pairs interleaved by mode pair, re plane then im plane:
-    // [2][n / 2][n_max] (q_2m.hi, q_2m+1.hi, q_2m.lo, q_2m+1.lo)
+    // MIXED: the same in FP32, per point by mode pair: [n_max][n / 2]
+    // (re_2m, re_2m+1, im_2m, im_2m+1)
+    float4 *qs32 = nullptr;
+    // FP64 path: the same as FP32 pairs, per point by mode pair, re then im:
+    // [n_max][n / 2][2] (q_2m.hi, q_2m+1.hi, q_2m.lo, q_2m+1.lo)
     float4 *qsdf = nullptr;
+    // FP64 path and MIXED: the L2P and near-field sums in sorted point order,
+    // [6][nmodes][n_max] (potential re, im, d/dr re, im, d/dz re, im), un-permuted into the
+    // caller's layout by one pass
+    double *osort = nullptr;
     double df_fwd_switch = 8.0;                 // forward switch of the FP32-pair recursion
     double *gexp = nullptr;                     // expansions of one level
     double *gstart = nullptr;                   // their start values G^(n): [station][16][max(N,1)+1] double-double
@@ -203,6 +214,10 @@ struct afmm_plan_s {
     uint16_t *asl = nullptr;                    // tensor-core S2L: bf16 digit slices of the moments of one level
     afmm::TcTables *tct = nullptr;              // tensor-core S2L tables (host)
     int *err_host = nullptr, *err_dev = nullptr;  // device-side error word (mapped host memory)
+    // small device-to-host reads of the tree build: a kernel writes them into mapped host
+    // memory (RB_WORDS words), so they never queue behind bulk copies on the copy engines
+    unsigned long long *rb_host = nullptr, *rb_dev = nullptr;
+    int hw_dev = -1, hw_slot = -1;  // the plan's slot of the per-device mapped block (-1: own)
     int inject_tc_timeout = 0;                  // test hook (environment): make the S2L wait run out
     int inject_near_timeout = 0;                // test hook (environment): make a near-field hand-over run out
     int64_t gexp_cap = 0;                       // doubles
@@ -242,6 +257,10 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
 afmm_status launch_green(int64_t npairs, const double *r, const double *r1, const double *x, int n_modes,
                          double *G, double *Gr, double *Gx, cudaStream_t st);
 afmm_status launch_permute(afmm_plan p, int dir, const double *q_re, const double *q_im);
+constexpr int RB_WORDS = 24;
+// bytes (a multiple of 8, at most 8 RB_WORDS) from device memory to host memory through the
+// plan's mapped words; synchronises the plan's stream
+afmm_status readback(afmm_plan p, void *host, const void *dev, size_t bytes);
 // farfield.cu
 afmm_status far_field(afmm_plan p, int dir);
 afmm_status launch_green_expansion(int64_t npts, const double *r, const double *r1, const double *x,

@@ -96,6 +96,7 @@ __global__ void k_p2m(const uint32_t *__restrict__ key, const int2 *__restrict__
     T *mono = sm;                        // [32][nc]
     T *acc = mono + 32 * nc;             // [2][nm][nc]
     T *invf = acc + 2 * (size_t)nm * nc;  // [M+1] 1/j!
+    const int npq = (nm + 1) / 2;
     int64_t b = blockIdx.x;
     if (b >= nbox) return;
     for (int i = threadIdx.x; i < 2 * nm * nc; i += blockDim.x) acc[i] = (T)0;
@@ -131,8 +132,8 @@ __global__ void k_p2m(const uint32_t *__restrict__ key, const int2 *__restrict__
             T ar = acc[o], ai = acc[nm * nc + o];
             for (int t = 0; t < cnt; ++t) {
                 T m = mono[t * nc + c];
-                ar = fma(amp_at(q_re, n, s0 + t, nsrc), m, ar);
-                ai = fma(amp_at(q_im, n, s0 + t, nsrc), m, ai);
+                ar = fma(amp_at(q_re, n, s0 + t, nsrc, npq), m, ar);
+                ai = fma(amp_at(q_im, n, s0 + t, nsrc, npq), m, ai);
             }
             acc[o] = ar;
             acc[nm * nc + o] = ai;
@@ -284,14 +285,15 @@ __global__ void k_l2l(const int32_t *__restrict__ parent, const uint32_t *__rest
 // of FP32).  Sums are (hi, err) pairs updated by exact two-sums.
 // ------------------------------------------------------------------------------------
 __global__ void k_p2m_df(const uint32_t *__restrict__ key, const int2 *__restrict__ rng, int64_t nbox,
-                         const double *__restrict__ sr, const double *__restrict__ sz, const float4 *__restrict__ q_re,
-                         const float4 *__restrict__ q_im, int64_t nsrc, int nm, int M, double r0, double z0, double h,
-                         const RecTab tab, float2 *__restrict__ mom_re, float2 *__restrict__ mom_im)
+                         const double *__restrict__ sr, const double *__restrict__ sz, const float4 *__restrict__ qri,
+                         int64_t nsrc, int nm, int M, double r0, double z0, double h,
+                         const RecTab tab, float2 *__restrict__ mom_re, float2 *__restrict__ mom_im, int CH)
 {
-    extern __shared__ float2 smf[];
-    const int nc = (M + 1) * (M + 2) / 2;
-    float2 *mono = smf;                    // [32][nc] U^i W^j / j!
-    float2 *acc = mono + 32 * nc;          // [2][nm][nc] (hi, err)
+    extern __shared__ float4 smq[];
+    const int nc = (M + 1) * (M + 2) / 2, npq = (nm + 1) / 2;
+    float4 *qst = smq;                     // [CH][nm] the chunk's amplitudes (re.hi, re.lo, im.hi, im.lo)
+    float2 *mono = reinterpret_cast<float2 *>(qst + (size_t)CH * nm);  // [CH][nc] U^i W^j / j!
+    float2 *acc = mono + CH * nc;          // [2][nm][nc] (hi, err)
     float2 *invf = acc + 2 * (size_t)nm * nc;  // [M+1] 1/j!
     float2 *ic = invf + (M + 1);           // [nm] 1/c_n
     const int64_t b = blockIdx.x;
@@ -312,8 +314,16 @@ __global__ void k_p2m_df(const uint32_t *__restrict__ key, const int2 *__restric
     const double ih = 1.0 / h;
     const int2 R = rng[b];
     __syncthreads();
-    for (int s0 = R.x; s0 < R.y; s0 += 32) {
-        const int cnt = min(32, R.y - s0);
+    for (int s0 = R.x; s0 < R.y; s0 += CH) {
+        const int cnt = min(CH, R.y - s0);
+        // the chunk's amplitudes: one contiguous run of the per-source copy, split by mode
+        const float4 *qc = qri + (size_t)s0 * npq * 2;
+        for (int e = threadIdx.x; e < cnt * npq; e += blockDim.x) {
+            const int t = e / npq, m = e - t * npq;
+            const float4 qr = qc[2 * (size_t)e], qi = qc[2 * (size_t)e + 1];
+            qst[t * nm + 2 * m] = make_float4(qr.x, qr.z, qi.x, qi.z);
+            if (2 * m + 1 < nm) qst[t * nm + 2 * m + 1] = make_float4(qr.y, qr.w, qi.y, qi.w);
+        }
         for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
             const dfv U = df_from_double((sr[s0 + t] - cr) * ih), Wv = df_from_double(-(sz[s0 + t] - cz) * ih);
             dfv ui = df_make(1.f, 0.f);
@@ -334,11 +344,9 @@ __global__ void k_p2m_df(const uint32_t *__restrict__ key, const int2 *__restric
             for (int t = 0; t < cnt; ++t) {
                 const float2 m2 = mono[t * nc + c];
                 const dfv m = df_make(m2.x, m2.y);
-                // amplitudes interleaved by mode pair: (q_2m.hi, q_2m+1.hi, q_2m.lo, q_2m+1.lo)
-                const float4 qr = q_re[(size_t)(n >> 1) * nsrc + s0 + t], qi = q_im[(size_t)(n >> 1) * nsrc + s0 + t];
-                const bool odd = n & 1;
-                df_acc(ar.x, ar.y, df_make(odd ? qr.y : qr.x, odd ? qr.w : qr.z), m);
-                df_acc(ai.x, ai.y, df_make(odd ? qi.y : qi.x, odd ? qi.w : qi.z), m);
+                const float4 q = qst[t * nm + n];
+                df_acc(ar.x, ar.y, df_make(q.x, q.y), m);
+                df_acc(ai.x, ai.y, df_make(q.z, q.w), m);
             }
             acc[o] = ar;
             acc[nm * nc + o] = ai;
@@ -1450,8 +1458,8 @@ static afmm_status far_field_t(afmm_plan p, int dir)
     auto MI = [&](int l) { return mix ? (R *)p->lv[l].mom32_im : (R *)p->lv[l].mom_im; };
     auto LR = [&](int l) { return mix ? (R *)p->lv[l].loc32_re : (R *)p->lv[l].loc_re; };
     auto LI = [&](int l) { return mix ? (R *)p->lv[l].loc32_im : (R *)p->lv[l].loc_im; };
-    const R *q_re = mix ? (const R *)p->qs32_re : (const R *)p->qs_re;
-    const R *q_im = mix ? (const R *)p->qs32_im : (const R *)p->qs_im;
+    const R *q_re = mix ? (const R *)p->qs32 : (const R *)p->qs_re;
+    const R *q_im = mix ? (const R *)p->qs32 + 2 : (const R *)p->qs_im;
     // P2M at the leaves
     {
         Level &v = p->lv[d];
@@ -1510,15 +1518,20 @@ static afmm_status far_field_df(afmm_plan p, int dir)
     const bool fw = dir == 0;
     const double *sr = fw ? p->s_r : p->t_r, *sz = fw ? p->s_z : p->t_z;
     const int64_t nsrc = fw ? p->ns : p->nf;
-    const float4 *q_re = p->qsdf, *q_im = p->qsdf + (size_t)((nm + 1) / 2) * p->n_max;
+    const float4 *qri = p->qsdf;
     {
         Level &v = p->lv[d];
         const double h = p->L / (double)(1 << d);
-        const size_t sm = sizeof(float2) * (32 * (size_t)nc + 2 * (size_t)nm * nc + M + 1 + nm);
+        // chunks of 32 sources, or 16 where the staging of 32 does not fit
+        auto smem = [&](int ch) {
+            return sizeof(float4) * (size_t)ch * nm + sizeof(float2) * ((size_t)ch * nc + 2 * (size_t)nm * nc + M + 1 + nm);
+        };
+        const int CH = smem(32) <= 227 * 1024 ? 32 : 16;
+        const size_t sm = smem(CH);
         if (sm > 227 * 1024) return AFMM_EUNSUPPORTED;
         AFMM_CUDA(cudaFuncSetAttribute(k_p2m_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_p2m_df<<<(unsigned)v.nbox, 128, sm, st>>>(v.key, fw ? v.srng : v.trng, v.nbox, sr, sz, q_re, q_im, nsrc, nm,
-                                                   M, p->r0, p->z0, h, *p->rec, v.momd_re, v.momd_im);
+        k_p2m_df<<<(unsigned)v.nbox, 128, sm, st>>>(v.key, fw ? v.srng : v.trng, v.nbox, sr, sz, qri, nsrc, nm,
+                                                   M, p->r0, p->z0, h, *p->rec, v.momd_re, v.momd_im, CH);
         AFMM_LAUNCH_CHECK();
     }
     tmark(p, 2);

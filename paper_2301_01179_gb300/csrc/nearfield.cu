@@ -22,7 +22,9 @@ struct NearArgs {
     int64_t nfield;
     // source role (sorted), amplitudes [nmodes][nsrc] pre-multiplied by c_n
     const double *sr, *sz, *q_re, *q_im;
-    const float2 *rinv_df;  // sources' 1 / r as FP32 pairs (FP32-pair kernel)
+    // FP32-pair kernel: sorted coordinates as exact FP32 triples with 1 / r as an FP32 pair,
+    // [n][2] float4 (r0, r1, z0, z1), (r2, z2, 1/r hi, 1/r lo); field role and source role
+    const float4 *geo_f, *geo_s;
     int64_t nsrc;
     int nmodes, N;
     // work
@@ -33,15 +35,15 @@ struct NearArgs {
     int direct;          // 1: all sources, split into nsplit chunks
     int nsplit;
     int64_t split_len;
-    // FP64 path in FP32 pairs: amplitudes interleaved by mode pair, [n / 2][nsrc] float4
-    // (q_2m.hi, q_2m+1.hi, q_2m.lo, q_2m+1.lo); leaf locals as (hi, lo)
-    const float4 *qdf_re, *qdf_im;
+    // FP64 path in FP32 pairs: amplitudes per source by mode pair, re then im,
+    // [nsrc][n / 2][2] float4 (q_2m.hi, q_2m+1.hi, q_2m.lo, q_2m+1.lo); leaf locals as (hi, lo)
+    const float4 *qdf;
     const float2 *locdf_re, *locdf_im;
     float df_fwd_switch;
     float df_tlim;  // forward iff chi - 1 <= df_tlim (the switch on t = chi - 1)
-    // MIXED precision: FP32 amplitudes interleaved by mode pair, [n / 2][nsrc] float2
-    // (q_2m, q_2m+1), FP32 local expansions, compensated FP32 sums
-    const float2 *q32_re, *q32_im;
+    // MIXED precision: FP32 amplitudes per source by mode pair, [nsrc][n / 2] float4
+    // (re_2m, re_2m+1, im_2m, im_2m+1), FP32 local expansions, compensated FP32 sums
+    const float4 *q32;
     const float *loc32_re, *loc32_im;
     int mode_lo, mode_hi;  // FP32-pair kernel: the modes [mode_lo, mode_hi) of this launch
     int *err;              // plan error word (bounded waits that ran out)
@@ -555,6 +557,7 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
     const int nm = a.nmodes, N = a.N;
     const int Nq = GRAD && N < 1 ? 1 : N;  // the gradient of mode 0 needs y_1
     const int npair = (Nq + 2) / 2;        // mode pairs of y_0 .. y_Nq
+    const int npq_all = (nm + 1) / 2;      // mode pairs of the amplitude copies
     float2 *gam2 = reinterpret_cast<float2 *>(smem_ws);                 // [AFMM_REC_TAB]
     float4 *gam4 = reinterpret_cast<float4 *>(gam2 + AFMM_REC_TAB);     // [pair] gam_2m, gam_2m+1
     float4 *rho4 = gam4 + (AFMM_MAX_MODES / 2 + 1);                     // [pair] rho_n = c_{n-1} / c_n
@@ -646,7 +649,8 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
 
     if (warp >= ncons) {
         // ---------------- producer ----------------
-        const dfv inv2r = df_from_double(0.5 / rt);
+        const float4 tg0 = a.geo_f[2 * tc], tg1 = a.geo_f[2 * tc + 1];
+        const dfv inv2r = df_scale2(df_make(tg1.z, tg1.w), 0.5f);  // 1 / (2 r)
         const float extra = (float)a.pp.miller_extra;
         for (;;) {
             int k = 0;
@@ -668,14 +672,13 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
                 while (rg < 8 && rcum[rg + 1] <= kk) ++rg;
                 s = rb[rg] + (kk - rcum[rg]);
             }
-            const double r1 = a.sr[s], z1 = a.sz[s];
-            const float2 ri = a.rinv_df[s];
-            const dfv inv2w = df_mul(inv2r, df_make(ri.x, ri.y));  // 1 / (2 r r1)
+            const float4 sg0 = a.geo_s[2 * s], sg1 = a.geo_s[2 * s + 1];
+            const dfv inv2w = df_mul(inv2r, df_make(sg1.z, sg1.w));  // 1 / (2 r r1)
             PairDF g;
             // a lane past the unit's last target repeats the first target's pair (tc): its sums
             // are never written, and its sequence takes the same regime as a real pair's
             // instead of a full backward sweep
-            pair_geom_df(rt, zt, r1, z1, inv2w, valid, g);
+            pair_geom_f32x3(tg0, tg1, sg0, sg1, inv2w, valid, g);
             SeqSlot ys;
             ys.y = reinterpret_cast<float *>(y4 + lane);
             if ((Nq & 1) == 0) ys.put(Nq + 1, df_make(0.f, 0.f));  // pad of the last mode pair
@@ -747,7 +750,8 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
             auto step = [&](const int j) {
                 const int m = m0 + j;
                 const df2 Y = df2_from4(y4[m * 32 + lane]);
-                const float2 QR = a.q32_re[(size_t)m * a.nsrc + s], QI = a.q32_im[(size_t)m * a.nsrc + s];
+                const float4 Q4 = a.q32[(size_t)s * npq_all + m];
+                const float2 QR = make_float2(Q4.x, Q4.y), QI = make_float2(Q4.z, Q4.w);
                 const float2 G = fmul2(SCf, Y.hi);
                 kahan2(aS[0][j], aE[0][j], fmul2(QR, G));
                 kahan2(aS[1][j], aE[1][j], fmul2(QI, G));
@@ -779,8 +783,9 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
             auto step = [&](const int j) {
                 const int m = m0 + j;
                 const df2 Y = df2_from4(y4[m * 32 + lane]);
-                const df2 QR = df2_from4(a.qdf_re[(size_t)m * a.nsrc + s]);
-                const df2 QI = df2_from4(a.qdf_im[(size_t)m * a.nsrc + s]);
+                const float4 *qs = a.qdf + ((size_t)s * npq_all + m) * 2;
+                const df2 QR = df2_from4(qs[0]);
+                const df2 QI = df2_from4(qs[1]);
                 const float2 nY = fmul2(Y.hi, NEG);
                 df2_acc_n(aS[0][j], aE[0][j], QR, Y, nY);
                 df2_acc_n(aS[1][j], aE[1][j], QI, Y, nY);
@@ -1047,12 +1052,12 @@ static afmm_status launch_near_ws(const NearArgs &a, const RecTab &tab, cudaStre
     }
 }
 
-// strengths into sorted order, times c_n: the FP64 copy (far field) and the FP32-pair copy
-// interleaved by mode pair (near field); one thread per (mode pair, point)
+// strengths into sorted order, times c_n: the FP64 copy [mode][point] (far field) and the
+// FP32-pair copy [point][mode pair][re, im] (near field: a source's amplitudes of all modes
+// in one contiguous run); one thread per (mode pair, point)
 __global__ void k_permute_df(const double *__restrict__ q_re, const double *__restrict__ q_im,
                              const int32_t *__restrict__ perm, int64_t n, int nm, const RecTab tab,
-                             double *__restrict__ qs_re, double *__restrict__ qs_im, float4 *__restrict__ qd_re,
-                             float4 *__restrict__ qd_im)
+                             double *__restrict__ qs_re, double *__restrict__ qs_im, float4 *__restrict__ qd_ri)
 {
     const int64_t npq = (nm + 1) / 2;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1072,8 +1077,26 @@ __global__ void k_permute_df(const double *__restrict__ q_re, const double *__re
         r[h] = df_from_double(vr);
         im[h] = df_from_double(vi);
     }
-    qd_re[i] = make_float4(r[0].hi, r[1].hi, r[0].lo, r[1].lo);
-    qd_im[i] = make_float4(im[0].hi, im[1].hi, im[0].lo, im[1].lo);
+    // per source, all mode pairs contiguous: [j][m][re, im] (one 32-byte sector per thread)
+    float4 *qd = qd_ri + ((size_t)j * npq + m) * 2;
+    qd[0] = make_float4(r[0].hi, r[1].hi, r[0].lo, r[1].lo);
+    qd[1] = make_float4(im[0].hi, im[1].hi, im[0].lo, im[1].lo);
+}
+
+// sorted-order sums [comp][mode][t] into the caller's layout: out_c[mode][perm[t]]; one
+// thread per element in plane order, so that each plane's scattered writes meet in L2
+struct UnpermOut {
+    double *o[6];
+};
+__global__ void k_unpermute(const double *__restrict__ S, const int32_t *__restrict__ perm, int nm, int64_t nf,
+                            int ncomp, UnpermOut uo)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)ncomp * nm * nf) return;
+    const int64_t plane = i / nf, t = i - plane * nf;
+    const int c = (int)(plane / nm), n = (int)(plane - (int64_t)c * nm);
+    double *dst = uo.o[c];
+    if (dst) dst[(size_t)n * nf + perm[t]] = S[i];
 }
 
 // sum of split partials into the caller layout
@@ -1164,11 +1187,12 @@ static int near_warps(int nm, int grad)
 
 static inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b > 0 ? (n + b - 1) / b : 1); }
 
-// strengths into sorted order, times c_n, rounded to FP32 (MIXED precision), interleaved by
-// mode pair; one thread per (mode pair, point)
+// strengths into sorted order, times c_n, rounded to FP32 (MIXED precision), per point by
+// mode pair: [point][mode pair] (re_2m, re_2m+1, im_2m, im_2m+1); one thread per (mode
+// pair, point)
 __global__ void k_permute32(const double *__restrict__ q_re, const double *__restrict__ q_im,
                             const int32_t *__restrict__ perm, int64_t n, int nm, const RecTab tab,
-                            float2 *__restrict__ qs_re, float2 *__restrict__ qs_im)
+                            float4 *__restrict__ qs_ri)
 {
     const int64_t npq = (nm + 1) / 2;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1184,8 +1208,7 @@ __global__ void k_permute32(const double *__restrict__ q_re, const double *__res
         r[h] = (float)(q_re[src] * c);
         im[h] = (float)(q_im[src] * c);
     }
-    qs_re[i] = make_float2(r[0], r[1]);
-    qs_im[i] = make_float2(im[0], im[1]);
+    qs_ri[(size_t)j * npq + m] = make_float4(r[0], r[1], im[0], im[1]);
 }
 
 afmm_status launch_permute(afmm_plan p, int dir, const double *q_re, const double *q_im)
@@ -1194,11 +1217,10 @@ afmm_status launch_permute(afmm_plan p, int dir, const double *q_re, const doubl
     const int32_t *perm = dir == 0 ? p->s_perm : p->t_perm;
     const int64_t npq = (p->nmodes + 1) / 2;
     if (p->precision == AFMM_MIXED)
-        k_permute32<<<nblk(n * npq), 256, 0, p->stream>>>(q_re, q_im, perm, n, p->nmodes, *p->rec, p->qs32_re,
-                                                           p->qs32_im);
+        k_permute32<<<nblk(n * npq), 256, 0, p->stream>>>(q_re, q_im, perm, n, p->nmodes, *p->rec, p->qs32);
     else if (p->precision == AFMM_FP64)
         k_permute_df<<<nblk(n * npq), 256, 0, p->stream>>>(q_re, q_im, perm, n, p->nmodes, *p->rec, p->qs_re, p->qs_im,
-                                                            p->qsdf, p->qsdf + (size_t)npq * p->n_max);
+                                                            p->qsdf);
     else
         k_permute<<<nblk(n * p->nmodes), 256, 0, p->stream>>>(q_re, q_im, perm, n, p->nmodes, *p->rec, p->qs_re,
                                                                p->qs_im);
@@ -1219,13 +1241,13 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
     a.nfield = fw ? p->nf : p->ns;
     a.sr = fw ? p->s_r : p->t_r;
     a.sz = fw ? p->s_z : p->t_z;
-    a.rinv_df = fw ? p->s_rinv : p->t_rinv;
+    a.geo_f = fw ? p->t_geo : p->s_geo;
+    a.geo_s = fw ? p->s_geo : p->t_geo;
     a.nsrc = fw ? p->ns : p->nf;
     const bool mix = p->precision == AFMM_MIXED;
     a.q_re = p->qs_re;
     a.q_im = p->qs_im;
-    a.q32_re = p->qs32_re;
-    a.q32_im = p->qs32_im;
+    a.q32 = p->qs32;
     a.nmodes = p->nmodes;
     a.N = p->N;
     a.pp = p->pp;
@@ -1273,6 +1295,20 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
         }
     }
     if (a.nunits == 0) return AFMM_OK;
+    // The FP32-pair kernels write their sums in sorted point order (each unit's points are a
+    // contiguous run, so the writes and the near field's additions to the L2P values are
+    // coalesced); one pass then scatters them into the caller's layout, plane by plane, so
+    // that the scattered writes of a plane meet in L2.  Split direct sums keep their own
+    // reduction into the caller's layout.
+    double *user[6] = {phi_re, phi_im, dr_re, dr_im, dz_re, dz_im};
+    const int ncomp = grad ? 6 : 2;
+    const bool sorted = p->precision != AFMM_FP64_NATIVE && !a.part && p->osort;
+    if (sorted) {
+        const size_t P = (size_t)a.nmodes * a.nfield;
+        double **o[6] = {&a.o_re, &a.o_im, &a.o_dr_re, &a.o_dr_im, &a.o_dz_re, &a.o_dz_im};
+        for (int c = 0; c < 6; ++c) *o[c] = (c < ncomp && user[c]) ? p->osort + c * P : nullptr;
+        a.out_perm = nullptr;
+    }
     size_t sm = near2_smem(p->nmodes, grad);
     unsigned grid = (unsigned)a.nunits;
     const int T = NEAR2_WB * 32;
@@ -1281,13 +1317,10 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
         // FP32-pair sequence (GB300's FP64 issues at 1/64 of FP32, so the pair arithmetic is
         // the fast way to the FP64-class sequence); FP64: FP32-pair sums, MIXED: compensated
         // FP32 sums.  Amplitudes are interleaved by mode pair.
-        const size_t npq = (size_t)(p->nmodes + 1) / 2;
         if (mix) {
-            a.q32_re = p->qs32_re;
-            a.q32_im = p->qs32_im;
+            a.q32 = p->qs32;
         } else {
-            a.qdf_re = p->qsdf;
-            a.qdf_im = p->qsdf + npq * p->n_max;
+            a.qdf = p->qsdf;
             if (with_local && !direct) {  // the leaf locals are kept as FP32 pairs
                 a.locdf_re = p->lv[d].locd_re;
                 a.locdf_im = p->lv[d].locd_im;
@@ -1340,6 +1373,14 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
         }
     }
     if (p->precision == AFMM_FP64_NATIVE) AFMM_LAUNCH_CHECK();
+    if (sorted) {
+        UnpermOut uo;
+        for (int c = 0; c < 6; ++c) uo.o[c] = c < ncomp ? user[c] : nullptr;
+        const int32_t *perm = dir == 0 ? p->t_perm : p->s_perm;
+        const int64_t tot = (int64_t)ncomp * a.nmodes * a.nfield;
+        k_unpermute<<<nblk(tot), 256, 0, p->stream>>>(p->osort, perm, a.nmodes, a.nfield, ncomp, uo);
+        AFMM_LAUNCH_CHECK();
+    }
     if (a.part) {
         int ncomp = grad ? 6 : 2;
         int64_t tot = (int64_t)ncomp * a.nmodes * a.nfield;

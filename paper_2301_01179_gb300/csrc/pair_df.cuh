@@ -1,8 +1,9 @@
 // pair_df.cuh -- the per-pair modal Green's function sequence of pair.cuh, in FP32-pair
 // (double-float) arithmetic: same start values (G^(0) = 1/(2 AGM(rho_+, rho_-)), G^(1) from
 // the AGM half-difference sum), same scaled Legendre recursion (Eq. gfunc:recursion), same
-// forward / Miller choice, ~48-bit precision.  Only the cancelling coordinate differences
-// r - r1 and z - z1 (and r + r1) are formed in FP64 and split exactly.
+// forward / Miller choice, ~48-bit precision.  The cancelling coordinate differences r - r1
+// and z - z1 (and r + r1) come from exact FP32 triples of the coordinates by error-free
+// FP32 sums, so the kernels issue no FP64 arithmetic per pair.
 //
 // Precision budget: the forward sweep's rounding grows like exp(n acosh chi) while Q_{n-1/2}
 // decays like exp(-n acosh chi); measured against the pair's G^(0) (the scale of the
@@ -26,12 +27,27 @@ struct PairDF {
     float zero;
 };
 
-__device__ __forceinline__ void pair_geom_df(double rt, double zt, double r1, double z1, dfv inv2w, bool active,
-                                             PairDF &g)
+// (a0 + a1 + a2) + (b0 + b1 + b2) as an FP32 pair, for exact FP32 triples of coordinates:
+// the high and middle words by exact two-sums, the rest summed in FP32.  When the high words
+// cancel (Sterbenz), the pair holds the difference to ~2^-47 of itself plus ~2^-72 of the
+// coordinates: the accuracy of the FP64 difference split into a pair, without FP64 work.
+__device__ __forceinline__ dfv sum_f32x3(float a0, float a1, float a2, float b0, float b1, float b2)
 {
-    g.x = df_from_double(zt - z1);
-    g.dr = df_from_double(rt - r1);
-    g.sr = df_from_double(rt + r1);
+    const dfv p = two_sum(a0, b0);
+    const dfv q = two_sum(a1, b1);
+    const dfv h = two_sum(p.hi, q.hi);
+    const float l = __fadd_rn(__fadd_rn(p.lo, q.lo), __fadd_rn(h.lo, __fadd_rn(a2, b2)));
+    return quick_two_sum(h.hi, l);
+}
+
+// pair_geom_df from the exact FP32 triples of the sorted points (tg: the field point's two
+// float4, sg: the source's; layout (r0, r1, z0, z1), (r2, z2, 1/r hi, 1/r lo))
+__device__ __forceinline__ void pair_geom_f32x3(const float4 tg0, const float4 tg1, const float4 sg0,
+                                                const float4 sg1, dfv inv2w, bool active, PairDF &g)
+{
+    g.x = sum_f32x3(tg0.z, tg0.w, tg1.y, -sg0.z, -sg0.w, -sg1.y);
+    g.dr = sum_f32x3(tg0.x, tg0.y, tg1.x, -sg0.x, -sg0.y, -sg1.x);
+    g.sr = sum_f32x3(tg0.x, tg0.y, tg1.x, sg0.x, sg0.y, sg1.x);
     dfv x2 = df_mul(g.x, g.x);
     dfv rm2 = df_add(df_mul(g.dr, g.dr), x2);
     dfv rp2 = df_add(df_mul(g.sr, g.sr), x2);

@@ -10,6 +10,7 @@
 // All steps are device kernels; the host reads back a handful of counts.
 #include "common.cuh"
 #include "df.cuh"
+#include <cstring>
 #include <vector>
 #include <algorithm>
 
@@ -230,9 +231,24 @@ static afmm_status scan_excl(const int64_t *in, int64_t *out, int64_t n, int64_t
 // ------------------------------------------------------------------------------------
 // per-point outputs of the sort
 // ------------------------------------------------------------------------------------
+__global__ void k_copy_words(const unsigned long long *__restrict__ src, unsigned long long *__restrict__ dst, int n)
+{
+    if ((int)threadIdx.x < n) dst[threadIdx.x] = src[threadIdx.x];
+}
+
+// v = a0 + a1 + a2 exactly: a0 is v rounded to FP32, a1 the remainder rounded to FP32 (the
+// remainders are exact in FP64), a2 the last few bits
+__device__ __forceinline__ void split_f32x3(double v, float &a0, float &a1, float &a2)
+{
+    a0 = __double2float_rn(v);
+    const double r = v - (double)a0;
+    a1 = __double2float_rn(r);
+    a2 = __double2float_rn(r - (double)a1);
+}
+
 __global__ void k_gather_sorted(const unsigned long long *__restrict__ srt, int64_t n, const double *__restrict__ r,
                                 const double *__restrict__ z, double *__restrict__ rs, double *__restrict__ zs,
-                                float2 *__restrict__ rinv, int32_t *__restrict__ perm, uint32_t *__restrict__ key)
+                                float4 *__restrict__ geo, int32_t *__restrict__ perm, uint32_t *__restrict__ key)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -242,8 +258,14 @@ __global__ void k_gather_sorted(const unsigned long long *__restrict__ srt, int6
     key[i] = (uint32_t)(v >> 32);
     rs[i] = r[idx];
     zs[i] = z[idx];
-    const dfv d = df_from_double(1.0 / r[idx]);  // 1 / r as an FP32 pair, for the FP32-pair near field
-    rinv[i] = make_float2(d.hi, d.lo);
+    // exact FP32 triples of the coordinates and 1 / r as an FP32 pair, for the FP32-pair near
+    // field (its coordinate differences then need no FP64 arithmetic)
+    float r0, r1, r2, z0, z1, z2;
+    split_f32x3(r[idx], r0, r1, r2);
+    split_f32x3(z[idx], z0, z1, z2);
+    const dfv d = df_from_double(1.0 / r[idx]);
+    geo[2 * i] = make_float4(r0, r1, z0, z1);
+    geo[2 * i + 1] = make_float4(r2, z2, d.hi, d.lo);
 }
 
 // number of distinct level-l prefixes among sorted level-16 keys, l = 2..16
@@ -520,6 +542,17 @@ __global__ void k_s2l_count(const int32_t *__restrict__ tab, const int2 *__restr
 
 static inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b > 0 ? (n + b - 1) / b : 1); }
 
+afmm_status readback(afmm_plan p, void *host, const void *dev, size_t bytes)
+{
+    const int n = (int)(bytes / 8);
+    if (bytes % 8 != 0 || n > RB_WORDS || !p->rb_dev) return AFMM_EINVAL;
+    k_copy_words<<<1, 32, 0, p->stream>>>((const unsigned long long *)dev, p->rb_dev, n);
+    AFMM_LAUNCH_CHECK();
+    AFMM_CUDA(cudaStreamSynchronize(p->stream));
+    memcpy(host, (const void *)p->rb_host, bytes);
+    return AFMM_OK;
+}
+
 // compaction helper: distinct keys of a sorted 64-bit array (value >> 32 >> extra) -> keys
 static afmm_status uniq_keys(afmm_plan p, const unsigned long long *a, int64_t n, int extra, int64_t *f,
                              int64_t *pos, int64_t *tmp, uint32_t **keys_out, int64_t *count)
@@ -529,8 +562,7 @@ static afmm_status uniq_keys(afmm_plan p, const unsigned long long *a, int64_t n
     AFMM_LAUNCH_CHECK();
     AFMM_TRY(scan_excl(f, pos, n, tmp, st));
     int64_t c = 0;
-    AFMM_CUDA(cudaMemcpyAsync(&c, pos + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    AFMM_CUDA(cudaStreamSynchronize(st));
+    AFMM_TRY(readback(p, &c, pos + n, sizeof(int64_t)));
     uint32_t *k = nullptr;
     AFMM_TRY(dalloc_t(p, &k, c > 0 ? c : 1));
     k_unique_scatter<<<nblk(n), 256, 0, st>>>(a, n, extra, f, pos, k);
@@ -555,8 +587,7 @@ afmm_status build_tree(afmm_plan p, const double *src_r, const double *src_z, co
     k_minmax_final<<<1, 32, 0, st>>>(part, mmb, mm);
     AFMM_LAUNCH_CHECK();
     double h_mm[5];
-    AFMM_CUDA(cudaMemcpyAsync(h_mm, mm, sizeof(h_mm), cudaMemcpyDeviceToHost, st));
-    AFMM_CUDA(cudaStreamSynchronize(st));
+    AFMM_TRY(readback(p, h_mm, mm, sizeof(h_mm)));
     if (h_mm[4] != 0.0) return AFMM_EINVAL;
     p->r0 = h_mm[0];
     p->z0 = h_mm[2];
@@ -584,8 +615,8 @@ afmm_status build_tree(afmm_plan p, const double *src_r, const double *src_z, co
     AFMM_TRY(dalloc_t(p, &p->t_z, nf));
     AFMM_TRY(dalloc_t(p, &p->t_perm, nf));
     AFMM_TRY(dalloc_t(p, &p->t_key, nf));
-    AFMM_TRY(dalloc_t(p, &p->s_rinv, ns));
-    AFMM_TRY(dalloc_t(p, &p->t_rinv, nf));
+    AFMM_TRY(dalloc_t(p, &p->s_geo, 2 * ns));
+    AFMM_TRY(dalloc_t(p, &p->t_geo, 2 * nf));
     for (int set = 0; set < 2; ++set) {
         int64_t n = set == 0 ? ns : nf;
         int64_t npad = pow2_at_least(n);
@@ -594,9 +625,9 @@ afmm_status build_tree(afmm_plan p, const double *src_r, const double *src_z, co
         AFMM_LAUNCH_CHECK();
         AFMM_TRY(bitonic_sort(srt, npad, st));
         if (set == 0)
-            k_gather_sorted<<<nblk(n), 256, 0, st>>>(srt, n, r, z, p->s_r, p->s_z, p->s_rinv, p->s_perm, p->s_key);
+            k_gather_sorted<<<nblk(n), 256, 0, st>>>(srt, n, r, z, p->s_r, p->s_z, p->s_geo, p->s_perm, p->s_key);
         else
-            k_gather_sorted<<<nblk(n), 256, 0, st>>>(srt, n, r, z, p->t_r, p->t_z, p->t_rinv, p->t_perm, p->t_key);
+            k_gather_sorted<<<nblk(n), 256, 0, st>>>(srt, n, r, z, p->t_r, p->t_z, p->t_geo, p->t_perm, p->t_key);
         AFMM_LAUNCH_CHECK();
     }
     // ---- depth
@@ -608,8 +639,7 @@ afmm_status build_tree(afmm_plan p, const double *src_r, const double *src_z, co
         k_depth_counts<<<nblk(ns), 256, 0, st>>>(p->s_key, ns, cnt);
         AFMM_LAUNCH_CHECK();
         unsigned long long hc[17];
-        AFMM_CUDA(cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, st));
-        AFMM_CUDA(cudaStreamSynchronize(st));
+        AFMM_TRY(readback(p, hc, cnt, sizeof(hc)));
         d = -1;
         for (int l = 2; l <= 16; ++l)
             if (hc[l] > 0 && (double)ns <= (double)p->opt.leaf_size * (double)hc[l]) {
@@ -667,8 +697,7 @@ afmm_status build_tree(afmm_plan p, const double *src_r, const double *src_z, co
         AFMM_LAUNCH_CHECK();
         AFMM_TRY(scan_excl(f, pos, ncol, tmp, st));
         int64_t nst = 0;
-        AFMM_CUDA(cudaMemcpyAsync(&nst, pos + ncol, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        AFMM_CUDA(cudaStreamSynchronize(st));
+        AFMM_TRY(readback(p, &nst, pos + ncol, sizeof(int64_t)));
         v.nstation = (int)nst;
         AFMM_TRY(dalloc_t(p, &v.col_of_station, nst > 0 ? nst : 1));
         k_station_map<<<nblk(ncol), 256, 0, st>>>(flag, ncol, pos, v.station_of_col, v.col_of_station);
@@ -684,8 +713,7 @@ afmm_status build_tree(afmm_plan p, const double *src_r, const double *src_z, co
             AFMM_LAUNCH_CHECK();
             AFMM_TRY(scan_excl(f, pos, nb, tmp, st));
             int64_t nu = 0;
-            AFMM_CUDA(cudaMemcpyAsync(&nu, pos + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-            AFMM_CUDA(cudaStreamSynchronize(st));
+            AFMM_TRY(readback(p, &nu, pos + nb, sizeof(int64_t)));
             int32_t **ub = us == 32 ? &v.unit_box : &v.unit64_box, **uc = us == 32 ? &v.unit_col : &v.unit64_col;
             (us == 32 ? v.nunit : v.nunit64) = nu;
             AFMM_TRY(dalloc_t(p, ub, (nu > 0 ? nu : 1) * us));
@@ -708,8 +736,7 @@ afmm_status build_tree(afmm_plan p, const double *src_r, const double *src_z, co
             AFMM_LAUNCH_CHECK();
             AFMM_TRY(scan_excl(f, pos, nb, tmp, st));
             int64_t nu = 0;
-            AFMM_CUDA(cudaMemcpyAsync(&nu, pos + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-            AFMM_CUDA(cudaStreamSynchronize(st));
+            AFMM_TRY(readback(p, &nu, pos + nb, sizeof(int64_t)));
             p->n_near_unit[dir] = nu;
             AFMM_TRY(dalloc_t(p, &p->near_unit[dir], nu > 0 ? nu : 1));
             k_near_fill<<<nblk(nb), 256, 0, st>>>(rng, nb, pos, p->near_unit[dir]);
@@ -726,8 +753,7 @@ afmm_status build_tree(afmm_plan p, const double *src_r, const double *src_z, co
             AFMM_LAUNCH_CHECK();
         }
         unsigned long long h[3];
-        AFMM_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
-        AFMM_CUDA(cudaStreamSynchronize(st));
+        AFMM_TRY(readback(p, h, acc, sizeof(h)));
         p->near_pairs = (int64_t)h[0];
         p->s2l_pairs = (int64_t)h[1];
         p->s2l_point_pairs = (int64_t)h[2];
