@@ -240,9 +240,33 @@ def _shift_down(F, D, M):
     return F @ A.T
 
 
-def adaptive_fmm(tree, q_re, q_im, M, grad=False):
+def direct_sources(tree, B):
+    """Sources that the W / X-as-direct variant of :func:`adaptive_fmm` sums directly at the
+    field points of leaf B: the sources of U(B), of the subtrees of W(B), and of the leaves
+    in X(b) for every b that contains B (B itself included).  These are exactly the pairs
+    that the expansion variant takes through W and X, so the far field (V lists and the
+    shifts) is the same in both variants."""
+    boxes = list(tree.U[B]) + list(tree.W[B])
+    b = B
+    while b is not None:
+        boxes += tree.X[b]
+        b = tree.parent[b]
+    if not boxes:
+        return np.zeros(0, np.int64)
+    return np.concatenate([tree.src[c] for c in boxes])
+
+
+def adaptive_fmm(tree, q_re, q_im, M, grad=False, wx="expansion"):
     """The FMM on an :class:`AdaptiveTree`.  Returns (phi_re, phi_im[, dr_re, dr_im, dz_re,
-    dz_im]), each [nmodes, nf], in the caller's point order."""
+    dz_im]), each [nmodes, nf], in the caller's point order.
+
+    wx = "expansion": W and X through the generalised source-to-local (the standard
+    adaptive FMM).  wx = "direct": the point pairs of W and X summed directly (Eq.
+    analysis:sum) with the U list, as :func:`direct_sources` lists them; exact for those
+    pairs, and no expansion about a single point is needed."""
+    if wx not in ("expansion", "direct"):
+        raise ValueError("wx must be 'expansion' or 'direct'")
+    wxd = wx == "direct"
     q = _f64(q_re) + 1j * _f64(q_im)
     nm = q.shape[0]
     N = nm - 1
@@ -276,7 +300,7 @@ def adaptive_fmm(tree, q_re, q_im, M, grad=False):
             cr, cz = tree.centre(c)
             T = _s2l_matrix(rc, zc, cr, cz, N, M, M)
             F += np.einsum('nab,nb->na', T, mom[c])
-        for c in tree.X[b]:
+        for c in ([] if wxd else tree.X[b]):
             for s in tree.src[c]:
                 T = _s2l_matrix(rc, zc, tree.sr[s], tree.sz[s], N, M, 0)
                 F += T[:, :, 0] * q[:, s][:, None]
@@ -296,7 +320,7 @@ def adaptive_fmm(tree, q_re, q_im, M, grad=False):
             pz_ = np.where(Lf > 0, Lf, 0)[None, :] * du[:, None] ** K[None, :] * dv[:, None] ** np.maximum(Lf - 1, 0)[None, :]
             out[1][:, t] += loc[b] @ pr_.T
             out[2][:, t] += loc[b] @ pz_.T
-        for c in tree.W[b]:
+        for c in ([] if wxd else tree.W[b]):
             cr, cz = tree.centre(c)
             for jj, j in enumerate(t):
                 T = _s2l_matrix(tree.tr[j], tree.tz[j], cr, cz, N, 1 if grad else 0, M)
@@ -305,7 +329,10 @@ def adaptive_fmm(tree, q_re, q_im, M, grad=False):
                 if grad:
                     out[1][:, j] += v[:, 2]  # (k, l) = (1, 0)
                     out[2][:, j] += v[:, 1]  # (k, l) = (0, 1)
-        s = np.concatenate([tree.src[c] for c in tree.U[b]]) if tree.U[b] else np.zeros(0, np.int64)
+        if wxd:
+            s = direct_sources(tree, b)
+        else:
+            s = np.concatenate([tree.src[c] for c in tree.U[b]]) if tree.U[b] else np.zeros(0, np.int64)
         if len(s):
             d = direct(tree.sr[s], tree.sz[s], tree.tr[t], tree.tz[t], q.real[:, s], q.imag[:, s], grad=grad)
             out[0][:, t] += d[0] + 1j * d[1]

@@ -6,7 +6,11 @@
 - the four lists must account for every (field leaf, source leaf) pair exactly once (a
   combinatorial check, independent of the expansions);
 - on clustered points (leaves on several levels, W and X lists in use) it must converge
-  to the direct sum as the order M grows, potential and field gradient."""
+  to the direct sum as the order M grows, potential and field gradient;
+- the variant that sums the point pairs of W and X directly (wx="direct", the form the GPU
+  plans take) must sum, at every field point, each source exactly once: directly or through
+  the V lists of the boxes that contain the point's leaf; it converges to the direct sum
+  like the expansion variant, and the two agree within their truncation errors."""
 import numpy as np
 import pytest
 
@@ -82,3 +86,50 @@ def test_fast_lists_match_their_definitions():
     assert {b: sorted(v) for b, v in tree.V.items()} == {b: sorted(v) for b, v in V.items()}
     assert {b: sorted(v) for b, v in tree.W.items()} == Wl
     assert {b: sorted(v) for b, v in tree.X.items()} == {b: sorted(v) for b, v in X.items()}
+
+
+def test_wx_direct_sources_and_v_lists_partition_the_sources():
+    w = W.make("cfg5", ns=1800, nf=1300, n_modes=1)
+    tree = A.AdaptiveTree(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], 20, refine_to=2)
+    assert len({b[0] for b in tree.leaves}) >= 3
+    assert sum(len(v) for v in tree.W.values()) > 0 and sum(len(v) for v in tree.X.values()) > 0
+    ns = w["src_r"].size
+    for B in tree.leaves:
+        if len(tree.tgt[B]) == 0:
+            continue
+        cnt = np.bincount(A.direct_sources(tree, B), minlength=ns)
+        for D in _ancestors(tree, B):
+            for c in tree.V[D]:
+                cnt += np.bincount(tree.src[c], minlength=ns)
+        assert cnt.min() == 1 and cnt.max() == 1, (B, cnt.min(), cnt.max())
+
+
+def test_wx_direct_converges_and_agrees_with_expansions():
+    w = W.make("cfg5", ns=1200, nf=900, n_modes=4)
+    sr, sz, tr, tz = w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"]
+    tree = A.AdaptiveTree(sr, sz, tr, tz, 24, refine_to=2)
+    assert sum(len(v) for v in tree.W.values()) > 0 and sum(len(v) for v in tree.X.values()) > 0
+    D = oracle.direct(sr, sz, tr, tz, w["q_re"], w["q_im"], grad=True)
+    errs = []
+    for M in (4, 7, 10):
+        F = A.adaptive_fmm(tree, w["q_re"], w["q_im"], M, grad=True, wx="direct")
+        E = A.adaptive_fmm(tree, w["q_re"], w["q_im"], M, grad=True)
+        e_d = [_eps(F, D, c) for c in (0, 2, 4)]
+        e_e = [_eps(E, D, c) for c in (0, 2, 4)]
+        errs.append(e_d)
+        for c, k in zip((0, 2, 4), range(3)):
+            assert _eps(F, E, c) <= 1.01 * (e_d[k] + e_e[k]) + 1e-14
+    errs = np.array(errs)
+    assert np.all(errs[1:] < 0.2 * errs[:-1]), errs
+    assert errs[-1].max() < 1e-5, errs
+
+
+def test_wx_direct_on_a_uniform_tree_is_the_uniform_fmm():
+    w = W.make("cfg1", ns=700, nf=600, n_modes=3)
+    sr, sz, tr, tz = w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"]
+    d, geom = oracle.tree_setup(sr, sz, tr, tz, 32, depth_override=4)
+    tree = A.AdaptiveTree(sr, sz, tr, tz, 10 ** 9, refine_to=d, geom=geom)
+    F = A.adaptive_fmm(tree, w["q_re"], w["q_im"], 6, grad=True, wx="direct")
+    U = oracle.fmm(sr, sz, tr, tz, w["q_re"], w["q_im"], 6, d, geom, grad=True)
+    for c in (0, 2, 4):
+        assert _eps(F, U, c) < 1e-12
