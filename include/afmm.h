@@ -64,8 +64,10 @@ typedef struct {
     int order;          /* expansion order M (moments i+j <= M, locals k+l <= M); 0..16
                            (larger orders: AFMM_EUNSUPPORTED) */
     int leaf_size;      /* depth rule: smallest d >= 2 whose non-empty leaves hold at most
-                           leaf_size sources on average; >= 1 */
-    int depth_override; /* 0: use the leaf_size rule; 2..16: use this depth */
+                           leaf_size sources on average; >= 1 (adaptive tree: the split
+                           threshold, see tree) */
+    int depth_override; /* 0: use the leaf_size rule; 2..16: use this depth (adaptive tree:
+                           the maximum level, 0: 16) */
     int precision;      /* afmm_precision */
     double fwd_switch;  /* Legendre recursion: forward iff 2 N acosh(chi) <= fwd_switch.
                            AFMM_FP64_NATIVE (0: default 9 for N <= 16, 9 - 1.5 log2(N/16)
@@ -82,13 +84,31 @@ typedef struct {
                            tensor cores when the order allows (AFMM_FP64: order <= 12,
                            AFMM_MIXED: order <= 14), else on CUDA cores; 1: always on CUDA
                            cores (FP32 pairs for AFMM_FP64, FP32 for AFMM_MIXED) */
+    int tree;           /* afmm_tree.  AFMM_TREE_UNIFORM (0): the paper's uniform quadtree of
+                           depth d (Sec. 2.1, Algorithm 1).  AFMM_TREE_ADAPTIVE (1): the same
+                           expansions on a tree refined only where points are dense: every
+                           box of levels 0..1 is split, and a box of level l >= 2 is split
+                           while it holds more than leaf_size sources or more than leaf_size
+                           field points and l < the maximum level (depth_override, 0: 16).
+                           Each box of level >= 2 takes the S2L from the same-level boxes of
+                           its interaction list (the uniform list restricted to the boxes
+                           that exist); a leaf's field points take its local expansion plus
+                           the direct sum over (a) the sources of the existing boxes of the
+                           3 x 3 block around the leaf at its level, whole subtrees included,
+                           and (b) the sources of every coarser leaf adjacent to the leaf's
+                           ancestor at that leaf's level.  (a) and (b) are the U, W and X
+                           lists of the standard adaptive FMM, the W and X pairs summed
+                           directly; every (field point, source) pair is still covered once.
+                           AFMM_FP64 and AFMM_MIXED only (AFMM_FP64_NATIVE: EUNSUPPORTED). */
 } afmm_options;
+
+typedef enum { AFMM_TREE_UNIFORM = 0, AFMM_TREE_ADAPTIVE = 1 } afmm_tree;
 
 typedef struct afmm_plan_s *afmm_plan;
 
 /* Plan metadata (host struct filled by afmm_plan_info). */
 typedef struct {
-    int depth;          /* tree depth d */
+    int depth;          /* tree depth d (adaptive tree: the deepest level that holds a leaf) */
     int n_modes;        /* N + 1 */
     int order;          /* M */
     int precision;
@@ -103,6 +123,8 @@ typedef struct {
                                    by one level's interaction list (Sec. 2.2), so
                                    near_pairs + s2l_point_pairs = ns * nf */
     int s2l_tensor_cores;       /* 1 if the S2L runs on the tcgen05 tensor cores, else 0 */
+    int tree;                   /* afmm_tree of the plan */
+    int64_t n_leaves[17];       /* leaf boxes per level (uniform tree: all boxes of level d) */
 } afmm_plan_info_t;
 
 void afmm_options_default(afmm_options *opt);

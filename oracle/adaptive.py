@@ -287,8 +287,10 @@ def adaptive_fmm(tree, q_re, q_im, M, grad=False, wx="expansion"):
                 cr, cz = tree.centre(c)
                 acc += _shift_up(mom[c], (rc - cr, zc - cz), M)
             mom[b] = acc
-    # downward pass: parent locals, V list (moments), X list (sources)
-    loc = {}
+    # downward pass: parent locals, V list (moments), X list (sources).  A V-list operator
+    # depends only on the level, the two radial stations and the axial box offset (Sec. 2.2:
+    # the operators are shared along z), so it is built once per such key
+    loc, vop = {}, {}
     for b in sorted(tree.boxes, key=lambda k: k[0]):
         rc, zc = tree.centre(b)
         F = np.zeros((nm, nc), complex)
@@ -297,9 +299,11 @@ def adaptive_fmm(tree, q_re, q_im, M, grad=False, wx="expansion"):
             pr, pz = tree.centre(pb)
             F += _shift_down(loc[pb], (pr - rc, pz - zc), M)
         for c in tree.V[b]:
-            cr, cz = tree.centre(c)
-            T = _s2l_matrix(rc, zc, cr, cz, N, M, M)
-            F += np.einsum('nab,nb->na', T, mom[c])
+            key = (b[0], b[1], c[1], b[2] - c[2])
+            if key not in vop:
+                cr, cz = tree.centre(c)
+                vop[key] = _s2l_matrix(rc, zc, cr, cz, N, M, M)
+            F += np.einsum('nab,nb->na', vop[key], mom[c])
         for c in ([] if wxd else tree.X[b]):
             for s in tree.src[c]:
                 T = _s2l_matrix(rc, zc, tree.sr[s], tree.sz[s], N, M, 0)
@@ -343,3 +347,25 @@ def adaptive_fmm(tree, q_re, q_im, M, grad=False, wx="expansion"):
     for c in range(ncomp):
         res += [np.ascontiguousarray(out[c].real), np.ascontiguousarray(out[c].imag)]
     return tuple(res)
+
+
+def transposed(tree):
+    """The same tree with the roles of sources and field points exchanged.  The split rule
+    (more than leaf_size sources or field points) and the square are symmetric in the two
+    roles, so the boxes and the V lists are the same; the lists of each role follow."""
+    return AdaptiveTree(tree.tr, tree.tz, tree.sr, tree.sz, tree.leaf_size, max_level=tree.max_level,
+                        refine_to=tree.refine_to, geom=(tree.r0, tree.z0, tree.L))
+
+
+def adaptive_adjoint(tree, q_re, q_im, gphi_re, gphi_im, M, wx="direct"):
+    """Adjoint of :func:`adaptive_fmm` for a real loss with dL/dPhi = gphi (the FMM with the
+    roles exchanged, evaluated with its gradient at the sources; G is symmetric in r <-> r1
+    and even in x, Sec. 2.2).  Returns (gq_re, gq_im [nmodes, ns], g_r, g_z [ns]) with
+    g_r = sum_n Re(S) dPsi_re/dr + Im(S) dPsi_im/dr (the same for z), Psi the transposed
+    field at the sources."""
+    T = transposed(tree)
+    P = adaptive_fmm(T, gphi_re, gphi_im, M, grad=True, wx=wx)
+    q_re, q_im = _f64(q_re), _f64(q_im)
+    g_r = np.sum(q_re * P[2] + q_im * P[3], axis=0)
+    g_z = np.sum(q_re * P[4] + q_im * P[5], axis=0)
+    return P[0], P[1], g_r, g_z

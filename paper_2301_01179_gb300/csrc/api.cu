@@ -244,11 +244,13 @@ afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, co
     if (!src_r || !src_z || !tgt_r || !tgt_z) return AFMM_EINVAL;
     if (opt.order < 0 || opt.leaf_size < 1 || opt.depth_override < 0 || opt.depth_override == 1 ||
         opt.depth_override > AFMM_MAX_LEVEL || opt.fwd_switch < 0.0 || opt.miller_extra < 0 ||
-        (opt.s2l_engine != 0 && opt.s2l_engine != 1))
+        (opt.s2l_engine != 0 && opt.s2l_engine != 1) ||
+        (opt.tree != AFMM_TREE_UNIFORM && opt.tree != AFMM_TREE_ADAPTIVE))
         return AFMM_EINVAL;
     if (opt.precision != AFMM_FP64 && opt.precision != AFMM_MIXED && opt.precision != AFMM_FP64_NATIVE)
         return AFMM_EINVAL;
     if (opt.order > AFMM_MAX_ORDER) return AFMM_EUNSUPPORTED;
+    if (opt.tree == AFMM_TREE_ADAPTIVE && opt.precision == AFMM_FP64_NATIVE) return AFMM_EUNSUPPORTED;
 
     afmm_plan p = new (std::nothrow) afmm_plan_s();
     if (!p) return AFMM_ENOMEM;
@@ -391,6 +393,8 @@ afmm_status afmm_plan_info(afmm_plan p, afmm_plan_info_t *info)
     info->expansions = p->expansions;
     info->s2l_point_pairs = p->s2l_point_pairs;
     info->s2l_tensor_cores = s2l_tc_enabled(p) ? 1 : 0;
+    info->tree = p->adaptive ? AFMM_TREE_ADAPTIVE : AFMM_TREE_UNIFORM;
+    for (int l = 2; l <= p->d; ++l) info->n_leaves[l] = p->adaptive ? p->lv[l].nleaf : (l == p->d ? p->lv[l].nbox : 0);
     return AFMM_OK;
 }
 

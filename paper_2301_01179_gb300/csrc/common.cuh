@@ -126,7 +126,11 @@ struct Level {
     int2 *srng = nullptr;        // [nbox] [begin, end) into sorted sources
     int2 *trng = nullptr;        // [nbox] [begin, end) into sorted field points
     int32_t *parent = nullptr;   // [nbox] index at level l-1 (level >= 3)
-    int2 *child = nullptr;       // [nbox] child index range at level l+1 (level < d)
+    int2 *child = nullptr;       // [nbox] child index range at level l+1 (level < d; adaptive
+                                 // tree: every level, an empty range marks a leaf)
+    int2 *srng_leaf = nullptr;   // adaptive tree: srng of the leaves, empty for split boxes
+    int2 *trng_leaf = nullptr;   // adaptive tree: trng of the leaves, empty for split boxes
+    int64_t nleaf = 0;           // leaves of this level
     int32_t *s2l = nullptr;      // [nbox][27] interaction-list box index or -1
     int32_t *nbr = nullptr;      // [nbox][9] neighbour box index or -1 (leaf level only)
     int64_t nunit = 0;           // S2L work units: up to 32 boxes of one column and parity
@@ -168,7 +172,12 @@ __device__ __forceinline__ float amp_at(const float *q, int n, int64_t s, int64_
 struct NearUnit {       // one warp of near-field work: up to 32 field points of one leaf
     int32_t box;        // leaf box index
     int32_t begin, end; // field-point range (sorted order)
+    int32_t level;      // the leaf's level (d on the uniform tree)
 };
+
+// adaptive tree: a leaf's near list holds at most 9 boxes of its own level and 8 leaves of
+// each coarser level >= 2 (9 + 8 x 14 for a leaf of level 16)
+#define AFMM_NEAR_MAXRG 128
 
 }  // namespace afmm
 
@@ -193,6 +202,14 @@ struct afmm_plan_s {
     // near-field work units per direction (0: field points <- sources, 1: transposed)
     int64_t n_near_unit[2] = {0, 0};
     afmm::NearUnit *near_unit[2] = {nullptr, nullptr};
+    // adaptive tree: per (level, box) the near list as source-role ranges, CSR over the boxes
+    // of all levels (level l's boxes start at nl_base[l]; split boxes have empty lists);
+    // nl_rng[0]: source ranges (field points <- sources), nl_rng[1]: field-point ranges
+    int adaptive = 0;
+    int64_t nl_base[AFMM_MAX_LEVEL + 2] = {0};
+    int64_t *nl_off = nullptr;
+    int2 *nl_rng[2] = {nullptr, nullptr};
+    int nl_maxrg = 0;
     int64_t n_dir_unit[2] = {0, 0};  // direct (all pairs): units of 32 points
     afmm::NearUnit *dir_unit[2] = {nullptr, nullptr};
     // eval scratch

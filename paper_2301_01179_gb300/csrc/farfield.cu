@@ -168,6 +168,7 @@ __global__ void k_m2m(const int2 *__restrict__ child, const uint32_t *__restrict
     __syncthreads();
     if (P >= npar) return;
     int2 ch = child[P];
+    if (ch.x >= ch.y) return;  // a leaf of the adaptive tree keeps its P2M moments
     {
         R accr[2] = {0, 0}, acci[2] = {0, 0};  // outputs o = tid, tid + blockDim (nc <= 2 * blockDim)
         for (int c = ch.x; c < ch.y; ++c) {
@@ -379,6 +380,7 @@ __global__ void k_m2m_df(const int2 *__restrict__ child, const uint32_t *__restr
     __syncthreads();
     if (P >= npar) return;
     const int2 ch = child[P];
+    if (ch.x >= ch.y) return;  // a leaf of the adaptive tree keeps its P2M moments
     for (int n = blockIdx.y * SHIFT_MB; n < nm && n < (blockIdx.y + 1) * SHIFT_MB; ++n) {
     float2 accr[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, acci[2] = {accr[0], accr[1]};
     for (int c = ch.x; c < ch.y; ++c) {
@@ -1460,21 +1462,25 @@ static afmm_status far_field_t(afmm_plan p, int dir)
     auto LI = [&](int l) { return mix ? (R *)p->lv[l].loc32_im : (R *)p->lv[l].loc_im; };
     const R *q_re = mix ? (const R *)p->qs32 : (const R *)p->qs_re;
     const R *q_im = mix ? (const R *)p->qs32 + 2 : (const R *)p->qs_im;
-    // P2M at the leaves
-    {
-        Level &v = p->lv[d];
-        double h = p->L / (double)(1 << d);
-        size_t sm = sizeof(R) * (32 * (size_t)nc + 2 * (size_t)nm * nc + M + 1);
-        if (sm > 227 * 1024) return AFMM_EUNSUPPORTED;
-        AFMM_CUDA(cudaFuncSetAttribute(k_p2m<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_p2m<R><<<(unsigned)v.nbox, 128, sm, st>>>(v.key, fw ? v.srng : v.trng, v.nbox, sr, sz, q_re, q_im, nsrc,
-                                                    nm, M, p->r0, p->z0, h, *p->rec, MR(d), MI(d));
-        AFMM_LAUNCH_CHECK();
-    }
-    tmark(p, 2);
-    // upward pass
-    for (int l = d - 1; l >= 2; --l) {
+    // P2M at the leaves (adaptive tree: the leaves of every level, deepest first, each level
+    // before its M2M, which keeps the leaves' moments), then the upward pass
+    const size_t psm = sizeof(R) * (32 * (size_t)nc + 2 * (size_t)nm * nc + M + 1);
+    if (psm > 227 * 1024) return AFMM_EUNSUPPORTED;
+    AFMM_CUDA(cudaFuncSetAttribute(k_p2m<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
+    auto p2m = [&](int l, const int2 *rng) -> afmm_status {
         Level &v = p->lv[l];
+        const double h = p->L / (double)(1 << l);
+        k_p2m<R><<<(unsigned)v.nbox, 128, psm, st>>>(v.key, rng, v.nbox, sr, sz, q_re, q_im, nsrc, nm, M, p->r0, p->z0,
+                                                     h, *p->rec, MR(l), MI(l));
+        AFMM_LAUNCH_CHECK();
+        return AFMM_OK;
+    };
+    if (!p->adaptive) AFMM_TRY(p2m(d, fw ? p->lv[d].srng : p->lv[d].trng));
+    tmark(p, 2);
+    for (int l = p->adaptive ? d : d - 1; l >= 2; --l) {
+        Level &v = p->lv[l];
+        if (p->adaptive) AFMM_TRY(p2m(l, fw ? v.srng_leaf : v.trng_leaf));
+        if (l == d) continue;
         size_t sm = sizeof(R) * (2 * (size_t)nc + 4 * (size_t)(M + 1) * (M + 1));
         k_m2m<R><<<dim3((unsigned)v.nbox, (unsigned)nm), 128, sm, st>>>(v.child, p->lv[l + 1].key, v.nbox, nm, M, p->m2m_tab, MR(l + 1),
                                                     MI(l + 1), MR(l), MI(l));
@@ -1519,25 +1525,30 @@ static afmm_status far_field_df(afmm_plan p, int dir)
     const double *sr = fw ? p->s_r : p->t_r, *sz = fw ? p->s_z : p->t_z;
     const int64_t nsrc = fw ? p->ns : p->nf;
     const float4 *qri = p->qsdf;
-    {
-        Level &v = p->lv[d];
-        const double h = p->L / (double)(1 << d);
-        // chunks of 32 sources, or 16 where the staging of 32 does not fit
-        auto smem = [&](int ch) {
-            return sizeof(float4) * (size_t)ch * nm + sizeof(float2) * ((size_t)ch * nc + 2 * (size_t)nm * nc + M + 1 + nm);
-        };
-        const int CH = smem(32) <= 227 * 1024 ? 32 : 16;
-        const size_t sm = smem(CH);
-        if (sm > 227 * 1024) return AFMM_EUNSUPPORTED;
-        AFMM_CUDA(cudaFuncSetAttribute(k_p2m_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_p2m_df<<<(unsigned)v.nbox, 128, sm, st>>>(v.key, fw ? v.srng : v.trng, v.nbox, sr, sz, qri, nsrc, nm,
-                                                   M, p->r0, p->z0, h, *p->rec, v.momd_re, v.momd_im, CH);
+    // chunks of 32 sources, or 16 where the staging of 32 does not fit
+    auto smem = [&](int ch) {
+        return sizeof(float4) * (size_t)ch * nm + sizeof(float2) * ((size_t)ch * nc + 2 * (size_t)nm * nc + M + 1 + nm);
+    };
+    const int CH = smem(32) <= 227 * 1024 ? 32 : 16;
+    const size_t psm = smem(CH);
+    if (psm > 227 * 1024) return AFMM_EUNSUPPORTED;
+    AFMM_CUDA(cudaFuncSetAttribute(k_p2m_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
+    auto p2m = [&](int l, const int2 *rng) -> afmm_status {
+        Level &v = p->lv[l];
+        const double h = p->L / (double)(1 << l);
+        k_p2m_df<<<(unsigned)v.nbox, 128, psm, st>>>(v.key, rng, v.nbox, sr, sz, qri, nsrc, nm, M, p->r0, p->z0, h,
+                                                    *p->rec, v.momd_re, v.momd_im, CH);
         AFMM_LAUNCH_CHECK();
-    }
+        return AFMM_OK;
+    };
+    // P2M at the leaves (adaptive tree: every level's leaves, each level before its M2M)
+    if (!p->adaptive) AFMM_TRY(p2m(d, fw ? p->lv[d].srng : p->lv[d].trng));
     tmark(p, 2);
     const size_t ssm = sizeof(float2) * (2 * (size_t)nc + 4 * (size_t)W * W);
-    for (int l = d - 1; l >= 2; --l) {
+    for (int l = p->adaptive ? d : d - 1; l >= 2; --l) {
         Level &v = p->lv[l];
+        if (p->adaptive) AFMM_TRY(p2m(l, fw ? v.srng_leaf : v.trng_leaf));
+        if (l == d) continue;
         k_m2m_df<<<dim3((unsigned)v.nbox, (unsigned)((nm + SHIFT_MB - 1) / SHIFT_MB)), 128, ssm, st>>>(v.child, p->lv[l + 1].key, v.nbox, nm, M,
                                                                          p->m2m_tab_df, p->lv[l + 1].momd_re,
                                                                          p->lv[l + 1].momd_im, v.momd_re, v.momd_im);

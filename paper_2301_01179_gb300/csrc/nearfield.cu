@@ -32,6 +32,16 @@ struct NearArgs {
     int64_t nunits;
     const int32_t *nbr;  // [nbox][9] (near mode)
     const int2 *srng;    // source-role ranges per leaf (near mode)
+    // adaptive tree (near mode): the unit's source-role ranges are nl_rng[nl_off[g] ..
+    // nl_off[g + 1]) with g = nl_base[level] + box; the L2P takes the leaf's key and locals
+    // from its level's tables
+    const int64_t *nl_off;
+    const int2 *nl_rng;
+    int64_t nl_base[AFMM_MAX_LEVEL + 1];
+    const uint32_t *lv_key[AFMM_MAX_LEVEL + 1];
+    const float2 *lv_locd_re[AFMM_MAX_LEVEL + 1], *lv_locd_im[AFMM_MAX_LEVEL + 1];
+    const float *lv_loc32_re[AFMM_MAX_LEVEL + 1], *lv_loc32_im[AFMM_MAX_LEVEL + 1];
+    double side;         // the domain square's side (box size h = side / 2^level)
     int direct;          // 1: all sources, split into nsplit chunks
     int nsplit;
     int64_t split_len;
@@ -537,6 +547,27 @@ __device__ __forceinline__ void kahan2(float2 &S, float2 &C, float2 v)
     S = t;
 }
 
+// the range k (< nrg) of a flattened source list holding position i: rcum[k] <= i < rcum[k + 1]
+// (empty ranges are skipped); a linear scan for the 9 ranges of the uniform tree, a binary
+// search over the longer lists of the adaptive tree
+__device__ __forceinline__ int ws_range_of(const int *rcum, int nrg, int i)
+{
+    if (nrg <= 9) {
+        int rg = 0;
+        while (rg < nrg - 1 && rcum[rg + 1] <= i) ++rg;
+        return rg;
+    }
+    int lo = 0, hi = nrg - 1;  // the largest k with rcum[k] <= i
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (rcum[mid] <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
 // MPER: modes per consumer warp (even); MIX: MIXED precision (same FP32-pair sequence,
 // FP32 products with Kahan-compensated FP32 sums, FP32 locals)
 template <bool GRAD, int MPER, bool MIX>
@@ -564,7 +595,8 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
     unsigned char *ring = reinterpret_cast<unsigned char *>(rho4 + AFMM_MAX_MODES / 2 + 1);
     const size_t slot_bytes = (size_t)(npair + NPP) * 32 * sizeof(float4) + 32 * sizeof(int);
     __shared__ uint64_t s_full[NWS_BMAX], s_empty[NWS_BMAX];
-    __shared__ int rb[10], rcum[10];
+    __shared__ int rb[AFMM_NEAR_MAXRG + 1], rcum[AFMM_NEAR_MAXRG + 1];
+    __shared__ int s_nrg;
     __shared__ int s_next;
     __shared__ int s_src[NWS_SRC_STAGE];
     __shared__ volatile int s_abort;
@@ -584,7 +616,7 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
     }
     const int64_t unit = blockIdx.x;
     int64_t t0, t1, split = 0;
-    int box = -1;
+    int box = -1, ulevel = 0;
     if (a.direct) {
         int64_t tu = unit / a.nsplit;
         split = unit % a.nsplit;
@@ -595,9 +627,11 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
         box = u.box;
         t0 = u.begin;
         t1 = u.end;
+        ulevel = u.level;
     }
     if (threadIdx.x == 0) {
-        int cum = 0;
+        // the unit's sources as nrg ranges [rb[k], rb[k] + rcum[k + 1] - rcum[k]), flattened
+        int cum = 0, nrg = 9;
         if (a.direct) {
             int64_t s0 = split * a.split_len, s1 = min(s0 + a.split_len, a.nsrc);
             rb[0] = (int)s0;
@@ -607,6 +641,17 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
                 rb[k] = 0;
                 rcum[k] = cum;
             }
+        } else if (a.nl_off) {  // adaptive tree: the leaf's near list (at most AFMM_NEAR_MAXRG)
+            const int64_t g = a.nl_base[ulevel] + box, o0 = a.nl_off[g];
+            nrg = (int)(a.nl_off[g + 1] - o0);
+            for (int k = 0; k < nrg; ++k) {
+                const int2 r = a.nl_rng[o0 + k];
+                rb[k] = r.x;
+                rcum[k] = cum;
+                cum += r.y - r.x;
+            }
+            rb[nrg] = 0;
+            rcum[nrg] = cum;
         } else {
             for (int k = 0; k < 9; ++k) {
                 int32_t nb = a.nbr[(int64_t)box * 9 + k];
@@ -618,6 +663,7 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
             rb[9] = 0;
             rcum[9] = cum;
         }
+        s_nrg = nrg;
         s_next = 0;
         s_abort = 0;
         for (int b = 0; b < nbuf; ++b) {
@@ -636,12 +682,12 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
     const int64_t tc = active ? t : t0;
     const double rt = a.fr[tc], zt = a.fz[tc];
     __syncthreads();
-    const int total = rcum[9];
+    const int nrg = s_nrg;
+    const int total = rcum[nrg];
     const int nslots = (total + S - 1) / S;
     if (total <= NWS_SRC_STAGE) {  // the unit's source list, in slot order
         for (int i = threadIdx.x; i < total; i += blockDim.x) {
-            int rg = 0;
-            while (rg < 8 && rcum[rg + 1] <= i) ++rg;
+            const int rg = ws_range_of(rcum, nrg, i);
             s_src[i] = rb[rg] + (i - rcum[rg]);
         }
         __syncthreads();
@@ -668,8 +714,7 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
             if (total <= NWS_SRC_STAGE) {
                 s = s_src[kk];
             } else {
-                int rg = 0;
-                while (rg < 8 && rcum[rg + 1] <= kk) ++rg;
+                const int rg = ws_range_of(rcum, nrg, kk);
                 s = rb[rg] + (kk - rcum[rg]);
             }
             const float4 sg0 = a.geo_s[2 * s], sg1 = a.geo_s[2 * s + 1];
@@ -898,18 +943,25 @@ __global__ void __launch_bounds__(L2P_WARPS * 32) k_l2p(const NearArgs a)
     const bool active = t < un.end;
     const int64_t tc = active ? t : un.begin;
     const double rt = a.fr[tc], zt = a.fz[tc];
-    const uint32_t kk = a.leaf_key[box];
-    const double cr = a.r0 + ((double)morton_ir(kk) + 0.5) * a.h, cz = a.z0 + ((double)morton_iz(kk) + 0.5) * a.h;
-    const double ud = (rt - cr) / a.h, vd = (zt - cz) / a.h, ih = 1.0 / a.h;
+    // the leaf's level: d on the uniform tree, the unit's own on the adaptive tree
+    const bool ad = a.nl_off != nullptr;
+    const double h = ad ? a.side / (double)(1 << un.level) : a.h;
+    const uint32_t kk = ad ? a.lv_key[un.level][box] : a.leaf_key[box];
+    const float2 *locdf_re = ad ? a.lv_locd_re[un.level] : a.locdf_re;
+    const float2 *locdf_im = ad ? a.lv_locd_im[un.level] : a.locdf_im;
+    const float *loc32_re = ad ? a.lv_loc32_re[un.level] : a.loc32_re;
+    const float *loc32_im = ad ? a.lv_loc32_im[un.level] : a.loc32_im;
+    const double cr = a.r0 + ((double)morton_ir(kk) + 0.5) * h, cz = a.z0 + ((double)morton_iz(kk) + 0.5) * h;
+    const double ud = (rt - cr) / h, vd = (zt - cz) / h, ih = 1.0 / h;
     const int64_t dst = a.out_perm ? a.out_perm[tc] : tc;
     float4 *F = sF[warp];
     for (int n = warp; n < nm; n += L2P_WARPS) {
         const size_t off = ((size_t)box * nm + n) * nc;
         for (int c = lane; c < nc; c += 32) {
             if (MIX)
-                F[c] = make_float4(a.loc32_re[off + c], a.loc32_im[off + c], 0.f, 0.f);
+                F[c] = make_float4(loc32_re[off + c], loc32_im[off + c], 0.f, 0.f);
             else {
-                const float2 r = a.locdf_re[off + c], i = a.locdf_im[off + c];
+                const float2 r = locdf_re[off + c], i = locdf_im[off + c];
                 F[c] = make_float4(r.x, i.x, r.y, i.y);
             }
         }
@@ -1281,6 +1333,20 @@ afmm_status launch_near(afmm_plan p, int dir, int with_local, int grad, double *
         a.nunits = p->n_near_unit[dir];
         a.nbr = p->lv[d].nbr;
         a.srng = fw ? p->lv[d].srng : p->lv[d].trng;
+        if (p->adaptive) {
+            if (p->precision == AFMM_FP64_NATIVE) return AFMM_EUNSUPPORTED;
+            a.nl_off = p->nl_off;
+            a.nl_rng = p->nl_rng[dir];
+            for (int l = 0; l <= AFMM_MAX_LEVEL; ++l) {
+                a.nl_base[l] = p->nl_base[l];
+                a.lv_key[l] = p->lv[l].key;
+                a.lv_locd_re[l] = p->lv[l].locd_re;
+                a.lv_locd_im[l] = p->lv[l].locd_im;
+                a.lv_loc32_re[l] = p->lv[l].loc32_re;
+                a.lv_loc32_im[l] = p->lv[l].loc32_im;
+            }
+            a.side = p->L;
+        }
         if (with_local) {
             a.loc_re = mix ? nullptr : p->lv[d].loc_re;
             a.loc_im = mix ? nullptr : p->lv[d].loc_im;

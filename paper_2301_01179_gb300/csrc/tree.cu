@@ -492,7 +492,7 @@ __global__ void k_near_counts(const int2 *__restrict__ rng, int64_t nbox, int64_
     if (b < nbox) cnt[b] = (rng[b].y - rng[b].x + 31) / 32;
 }
 
-__global__ void k_near_fill(const int2 *__restrict__ rng, int64_t nbox, const int64_t *__restrict__ pos,
+__global__ void k_near_fill(const int2 *__restrict__ rng, int64_t nbox, int level, const int64_t *__restrict__ pos,
                             NearUnit *__restrict__ u)
 {
     int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -503,6 +503,7 @@ __global__ void k_near_fill(const int2 *__restrict__ rng, int64_t nbox, const in
         x.box = (int32_t)b;
         x.begin = s;
         x.end = min(s + 32, rng[b].y);
+        x.level = level;
         u[p++] = x;
     }
 }
@@ -540,6 +541,169 @@ __global__ void k_s2l_count(const int32_t *__restrict__ tab, const int2 *__restr
     atomicAdd(acc + 1, pp);
 }
 
+// ------------------------------------------------------------------------------------
+// adaptive tree: levels built top-down.  Level 2 holds every non-empty box; a box of level
+// l is split while it holds more than leaf_size sources or field points and l < lmax, and
+// its non-empty children form level l + 1 (sorted by key, since the parents are and the
+// child quadrant c = (radial bit << 1) | axial bit is the key's lowest digit).
+// ------------------------------------------------------------------------------------
+__global__ void k_split_flags(const int2 *__restrict__ srng, const int2 *__restrict__ trng, int64_t nbox, int leaf,
+                              int64_t *__restrict__ flag)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    flag[b] = (srng[b].y - srng[b].x > leaf || trng[b].y - trng[b].x > leaf) ? 1 : 0;
+}
+
+// four candidates per split parent (pkey == nullptr: the 4 boxes of level 1, all split);
+// each gets its key, parent and point ranges at level lc, and ne = 1 if it holds a point
+__global__ void k_child_cand(const uint32_t *__restrict__ pkey, const int64_t *__restrict__ flag,
+                             const int64_t *__restrict__ pos, int64_t npar, int lc, const uint32_t *__restrict__ sk,
+                             int64_t ns, const uint32_t *__restrict__ tk, int64_t nf, uint32_t *__restrict__ ckey,
+                             int32_t *__restrict__ cpar, int2 *__restrict__ csr, int2 *__restrict__ ctr,
+                             int64_t *__restrict__ ne)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= 4 * npar) return;
+    const int64_t b = t >> 2;
+    const uint32_t c = (uint32_t)(t & 3);
+    if (pkey && !flag[b]) return;
+    const int64_t i = 4 * (pkey ? pos[b] : b) + c;
+    const uint32_t k = ((pkey ? pkey[b] : (uint32_t)b) << 2) | c;
+    const int sh = 2 * (16 - lc);
+    const unsigned long long lo = (unsigned long long)k << sh, hi = ((unsigned long long)k + 1) << sh;
+    const int2 rs = make_int2((int)lower_bound_u32(sk, ns, lo), (int)lower_bound_u32(sk, ns, hi));
+    const int2 rt = make_int2((int)lower_bound_u32(tk, nf, lo), (int)lower_bound_u32(tk, nf, hi));
+    ckey[i] = k;
+    cpar[i] = (int32_t)b;
+    csr[i] = rs;
+    ctr[i] = rt;
+    ne[i] = (rs.y > rs.x || rt.y > rt.x) ? 1 : 0;
+}
+
+__global__ void k_child_compact(const uint32_t *__restrict__ ckey, const int32_t *__restrict__ cpar,
+                                const int2 *__restrict__ csr, const int2 *__restrict__ ctr,
+                                const int64_t *__restrict__ ne, const int64_t *__restrict__ pos, int64_t ncand,
+                                uint32_t *__restrict__ key, int32_t *__restrict__ par, int2 *__restrict__ srng,
+                                int2 *__restrict__ trng)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ncand || !ne[i]) return;
+    const int64_t o = pos[i];
+    key[o] = ckey[i];
+    if (par) par[o] = cpar[i];
+    srng[o] = csr[i];
+    trng[o] = ctr[i];
+}
+
+// leaf ranges for the P2M (empty for split boxes) and the leaf count of a level
+__global__ void k_leaf_ranges(const int2 *__restrict__ child, const int2 *__restrict__ srng,
+                              const int2 *__restrict__ trng, int64_t nbox, int2 *__restrict__ sl,
+                              int2 *__restrict__ tl, unsigned long long *__restrict__ nleaf)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    const bool leaf = child[b].x >= child[b].y;
+    sl[b] = leaf ? srng[b] : make_int2(0, 0);
+    tl[b] = leaf ? trng[b] : make_int2(0, 0);
+    if (leaf) atomicAdd(nleaf, 1ull);
+}
+
+// per-level tables of the adaptive tree, passed by value
+struct AdTab {
+    const uint32_t *key[AFMM_MAX_LEVEL + 1];
+    const int2 *child[AFMM_MAX_LEVEL + 1];
+    const int2 *srng[AFMM_MAX_LEVEL + 1];
+    const int2 *trng[AFMM_MAX_LEVEL + 1];
+    int64_t nbox[AFMM_MAX_LEVEL + 1];
+};
+
+// The near list of leaf b of level l: (a) the existing boxes of level l in the 3 x 3 block
+// around b (b included; a split box brings its whole subtree), (b) for every coarser level
+// c >= 2, the leaves of level c among the 8 boxes around b's ancestor.  A source leaf C and a
+// field leaf B are summed directly exactly when their ancestors at the coarser of their two
+// levels touch; every other pair meets in the interaction list of the first level at which
+// their ancestors separate.  f(level, box) is called once per listed box.
+template <typename F>
+__device__ void anear_visit(const AdTab &T, int l, int64_t b, F f)
+{
+    const uint32_t k = T.key[l][b];
+    const int ir = (int)morton_ir(k), iz = (int)morton_iz(k);
+    for (int dr = -1; dr <= 1; ++dr)
+        for (int dz = -1; dz <= 1; ++dz) {
+            const int i = ir + dr, j = iz + dz, nl = 1 << l;
+            if (i < 0 || j < 0 || i >= nl || j >= nl) continue;
+            const int64_t q = find_key(T.key[l], T.nbox[l], morton_key(i, j));
+            if (q >= 0) f(l, q);
+        }
+    for (int c = l - 1; c >= 2; --c) {
+        const int ai = ir >> (l - c), aj = iz >> (l - c), nc = 1 << c;
+        for (int dr = -1; dr <= 1; ++dr)
+            for (int dz = -1; dz <= 1; ++dz) {
+                const int i = ai + dr, j = aj + dz;
+                if ((dr == 0 && dz == 0) || i < 0 || j < 0 || i >= nc || j >= nc) continue;
+                const int64_t q = find_key(T.key[c], T.nbox[c], morton_key(i, j));
+                if (q >= 0 && T.child[c][q].x >= T.child[c][q].y) f(c, q);
+            }
+    }
+}
+
+__global__ void k_anear_count(const AdTab T, int l, int64_t *__restrict__ cnt, unsigned long long *__restrict__ mx)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= T.nbox[l]) return;
+    int n = 0;
+    if (T.child[l][b].x >= T.child[l][b].y) anear_visit(T, l, b, [&](int, int64_t) { ++n; });
+    cnt[b] = n;
+    atomicMax(mx, (unsigned long long)n);
+}
+
+// ranges of both roles; acc[0] += (field points) x (listed sources), acc[1] the transposed
+__global__ void k_anear_fill(const AdTab T, int l, const int64_t *__restrict__ off, int2 *__restrict__ rs,
+                             int2 *__restrict__ rt, unsigned long long *__restrict__ acc)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= T.nbox[l] || T.child[l][b].x < T.child[l][b].y) return;
+    int64_t o = off[b];
+    unsigned long long ss = 0, st = 0;
+    anear_visit(T, l, b, [&](int c, int64_t q) {
+        const int2 a = T.srng[c][q], z = T.trng[c][q];
+        rs[o] = a;
+        rt[o] = z;
+        ++o;
+        ss += (unsigned long long)(a.y - a.x);
+        st += (unsigned long long)(z.y - z.x);
+    });
+    const int2 mb = T.trng[l][b], ms = T.srng[l][b];
+    atomicAdd(acc, (unsigned long long)(mb.y - mb.x) * ss);
+    atomicAdd(acc + 1, (unsigned long long)(ms.y - ms.x) * st);
+}
+
+// near-field units of the adaptive tree: ceil(count / 32) per leaf with points of the role
+__global__ void k_anear_units_count(const int2 *__restrict__ rng, const int2 *__restrict__ child, int64_t nbox,
+                                    int64_t *__restrict__ cnt)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    cnt[b] = child[b].x >= child[b].y ? (rng[b].y - rng[b].x + 31) / 32 : 0;
+}
+
+__global__ void k_anear_units_fill(const int2 *__restrict__ rng, const int2 *__restrict__ child, int64_t nbox, int l,
+                                   const int64_t *__restrict__ pos, NearUnit *__restrict__ u)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nbox || child[b].x < child[b].y) return;
+    int64_t p = pos[b];
+    for (int s = rng[b].x; s < rng[b].y; s += 32) {
+        NearUnit x;
+        x.box = (int32_t)b;
+        x.begin = s;
+        x.end = min(s + 32, rng[b].y);
+        x.level = l;
+        u[p++] = x;
+    }
+}
+
 static inline unsigned nblk(int64_t n, int b = 256) { return (unsigned)((n + b - 1) / b > 0 ? (n + b - 1) / b : 1); }
 
 afmm_status readback(afmm_plan p, void *host, const void *dev, size_t bytes)
@@ -569,6 +733,157 @@ static afmm_status uniq_keys(afmm_plan p, const unsigned long long *a, int64_t n
     AFMM_LAUNCH_CHECK();
     *keys_out = k;
     *count = c;
+    return AFMM_OK;
+}
+
+// Levels 2..d of the adaptive tree (keys, point ranges, parents, child ranges, leaf ranges)
+static afmm_status build_levels_adaptive(afmm_plan p)
+{
+    cudaStream_t st = p->stream;
+    const int64_t ns = p->ns, nf = p->nf;
+    const int lmax = p->opt.depth_override > 0 ? p->opt.depth_override : AFMM_MAX_LEVEL;
+    const int leaf = p->opt.leaf_size;
+    // split boxes of one level are disjoint and hold more than leaf_size points each
+    const int64_t ccap = 4 * ((ns + nf) / (leaf + 1)) + 64, bcap = ns + nf + 64;
+    const int64_t ncap = ccap > bcap ? ccap : bcap;
+    uint32_t *ckey = nullptr;
+    int32_t *cpar = nullptr;
+    int2 *csr = nullptr, *ctr = nullptr;
+    int64_t *ne = nullptr, *cpos = nullptr, *ctmp = nullptr, *flag = nullptr, *fpos = nullptr;
+    AFMM_TRY(dalloc_t(p, &ckey, ccap));
+    AFMM_TRY(dalloc_t(p, &cpar, ccap));
+    AFMM_TRY(dalloc_t(p, &csr, ccap));
+    AFMM_TRY(dalloc_t(p, &ctr, ccap));
+    AFMM_TRY(dalloc_t(p, &ne, ccap));
+    AFMM_TRY(dalloc_t(p, &cpos, ccap + 1));
+    AFMM_TRY(dalloc_t(p, &flag, bcap));
+    AFMM_TRY(dalloc_t(p, &fpos, bcap + 1));
+    AFMM_TRY(dalloc_t(p, &ctmp, 2 * (ncap / 1024 + 64) + 256));
+    const uint32_t *pkey = nullptr;  // level 1: the four boxes, all split
+    int64_t npar = 4;
+    int l = 1;
+    for (;;) {
+        int64_t nsplit = 4;
+        if (pkey) {
+            if (l >= lmax) break;
+            k_split_flags<<<nblk(npar), 256, 0, st>>>(p->lv[l].srng, p->lv[l].trng, npar, leaf, flag);
+            AFMM_LAUNCH_CHECK();
+            AFMM_TRY(scan_excl(flag, fpos, npar, ctmp, st));
+            AFMM_TRY(readback(p, &nsplit, fpos + npar, sizeof(int64_t)));
+            if (nsplit == 0) break;
+        }
+        const int lc = l + 1;
+        const int64_t ncand = 4 * nsplit;
+        if (ncand > ccap) return AFMM_ECUDA;  // cannot happen: split boxes hold > leaf_size points
+        k_child_cand<<<nblk(4 * npar), 256, 0, st>>>(pkey, flag, fpos, npar, lc, p->s_key, ns, p->t_key, nf, ckey,
+                                                      cpar, csr, ctr, ne);
+        AFMM_LAUNCH_CHECK();
+        AFMM_TRY(scan_excl(ne, cpos, ncand, ctmp, st));
+        int64_t nb = 0;
+        AFMM_TRY(readback(p, &nb, cpos + ncand, sizeof(int64_t)));
+        Level &v = p->lv[lc];
+        v.nbox = nb;
+        AFMM_TRY(dalloc_t(p, &v.key, nb));
+        AFMM_TRY(dalloc_t(p, &v.srng, nb));
+        AFMM_TRY(dalloc_t(p, &v.trng, nb));
+        if (lc >= 3) AFMM_TRY(dalloc_t(p, &v.parent, nb));
+        AFMM_TRY(dalloc_t(p, &v.child, nb));
+        AFMM_CUDA(cudaMemsetAsync(v.child, 0, nb * sizeof(int2), st));
+        k_child_compact<<<nblk(ncand), 256, 0, st>>>(ckey, cpar, csr, ctr, ne, cpos, ncand, v.key,
+                                                     lc >= 3 ? v.parent : nullptr, v.srng, v.trng);
+        AFMM_LAUNCH_CHECK();
+        if (pkey) {
+            k_child_ranges<<<nblk(nb), 256, 0, st>>>(v.parent, nb, p->lv[l].child);
+            AFMM_LAUNCH_CHECK();
+        }
+        pkey = v.key;
+        npar = nb;
+        l = lc;
+    }
+    p->d = l;
+    unsigned long long *cnt = nullptr;
+    AFMM_TRY(dalloc_t(p, &cnt, AFMM_MAX_LEVEL + 1));
+    AFMM_CUDA(cudaMemsetAsync(cnt, 0, (AFMM_MAX_LEVEL + 1) * sizeof(unsigned long long), st));
+    for (int k = 2; k <= p->d; ++k) {
+        Level &v = p->lv[k];
+        AFMM_TRY(dalloc_t(p, &v.srng_leaf, v.nbox));
+        AFMM_TRY(dalloc_t(p, &v.trng_leaf, v.nbox));
+        k_leaf_ranges<<<nblk(v.nbox), 256, 0, st>>>(v.child, v.srng, v.trng, v.nbox, v.srng_leaf, v.trng_leaf, cnt + k);
+        AFMM_LAUNCH_CHECK();
+    }
+    unsigned long long h[AFMM_MAX_LEVEL + 1];
+    AFMM_TRY(readback(p, h, cnt, sizeof(h)));
+    for (int k = 2; k <= p->d; ++k) p->lv[k].nleaf = (int64_t)h[k];
+    return AFMM_OK;
+}
+
+// Near lists (CSR of point ranges per box of every level) and near-field units of the
+// adaptive tree; near_pairs counts the (field point, source) pairs summed directly
+static afmm_status build_near_adaptive(afmm_plan p)
+{
+    cudaStream_t st = p->stream;
+    const int d = p->d;
+    AdTab T;
+    memset(&T, 0, sizeof(T));
+    int64_t tot = 0;
+    for (int l = 2; l <= d; ++l) {
+        const Level &v = p->lv[l];
+        T.key[l] = v.key;
+        T.child[l] = v.child;
+        T.srng[l] = v.srng;
+        T.trng[l] = v.trng;
+        T.nbox[l] = v.nbox;
+        p->nl_base[l] = tot;
+        tot += v.nbox;
+    }
+    p->nl_base[d + 1] = tot;
+    int64_t *cnt = nullptr, *tmp = nullptr, *upos = nullptr;
+    unsigned long long *acc = nullptr;
+    AFMM_TRY(dalloc_t(p, &cnt, tot + 1));
+    AFMM_TRY(dalloc_t(p, &upos, tot + 1));
+    AFMM_TRY(dalloc_t(p, &p->nl_off, tot + 1));
+    AFMM_TRY(dalloc_t(p, &tmp, 2 * (tot / 1024 + 64) + 256));
+    AFMM_TRY(dalloc_t(p, &acc, 4));
+    AFMM_CUDA(cudaMemsetAsync(acc, 0, 4 * sizeof(unsigned long long), st));
+    for (int l = 2; l <= d; ++l) {
+        k_anear_count<<<nblk(T.nbox[l]), 256, 0, st>>>(T, l, cnt + p->nl_base[l], acc + 2);
+        AFMM_LAUNCH_CHECK();
+    }
+    AFMM_TRY(scan_excl(cnt, p->nl_off, tot, tmp, st));
+    int64_t h2[2] = {0, 0};
+    AFMM_TRY(readback(p, &h2[0], p->nl_off + tot, sizeof(int64_t)));
+    AFMM_TRY(readback(p, &h2[1], acc + 2, sizeof(int64_t)));
+    const int64_t nrg = h2[0];
+    p->nl_maxrg = (int)h2[1];
+    if (p->nl_maxrg > AFMM_NEAR_MAXRG) return AFMM_EUNSUPPORTED;
+    AFMM_TRY(dalloc_t(p, &p->nl_rng[0], nrg > 0 ? nrg : 1));
+    AFMM_TRY(dalloc_t(p, &p->nl_rng[1], nrg > 0 ? nrg : 1));
+    for (int l = 2; l <= d; ++l) {
+        k_anear_fill<<<nblk(T.nbox[l]), 256, 0, st>>>(T, l, p->nl_off + p->nl_base[l], p->nl_rng[0], p->nl_rng[1], acc);
+        AFMM_LAUNCH_CHECK();
+    }
+    for (int dir = 0; dir < 2; ++dir) {
+        for (int l = 2; l <= d; ++l) {
+            const Level &v = p->lv[l];
+            k_anear_units_count<<<nblk(v.nbox), 256, 0, st>>>(dir == 0 ? v.trng : v.srng, v.child, v.nbox,
+                                                              cnt + p->nl_base[l]);
+            AFMM_LAUNCH_CHECK();
+        }
+        AFMM_TRY(scan_excl(cnt, upos, tot, tmp, st));
+        int64_t nu = 0;
+        AFMM_TRY(readback(p, &nu, upos + tot, sizeof(int64_t)));
+        p->n_near_unit[dir] = nu;
+        AFMM_TRY(dalloc_t(p, &p->near_unit[dir], nu > 0 ? nu : 1));
+        for (int l = 2; l <= d; ++l) {
+            const Level &v = p->lv[l];
+            k_anear_units_fill<<<nblk(v.nbox), 256, 0, st>>>(dir == 0 ? v.trng : v.srng, v.child, v.nbox, l,
+                                                             upos + p->nl_base[l], p->near_unit[dir]);
+            AFMM_LAUNCH_CHECK();
+        }
+    }
+    unsigned long long h[2];
+    AFMM_TRY(readback(p, h, acc, sizeof(h)));
+    p->near_pairs = (int64_t)h[0];
     return AFMM_OK;
 }
 
@@ -630,9 +945,11 @@ afmm_status build_tree(afmm_plan p, const double *src_r, const double *src_z, co
             k_gather_sorted<<<nblk(n), 256, 0, st>>>(srt, n, r, z, p->t_r, p->t_z, p->t_geo, p->t_perm, p->t_key);
         AFMM_LAUNCH_CHECK();
     }
-    // ---- depth
-    int d = p->opt.depth_override;
-    if (d <= 0) {
+    // ---- depth (uniform tree), or the levels of the adaptive tree
+    p->adaptive = p->opt.tree == AFMM_TREE_ADAPTIVE ? 1 : 0;
+    if (p->adaptive) AFMM_TRY(build_levels_adaptive(p));
+    int d = p->adaptive ? p->d : p->opt.depth_override;
+    if (!p->adaptive && d <= 0) {
         unsigned long long *cnt = nullptr;
         AFMM_TRY(dalloc_t(p, &cnt, 17));
         AFMM_CUDA(cudaMemsetAsync(cnt, 0, 17 * sizeof(unsigned long long), st));
@@ -652,7 +969,7 @@ afmm_status build_tree(afmm_plan p, const double *src_r, const double *src_z, co
     p->d = d;
 
     // ---- boxes per level: union of leaf keys, then parents
-    {
+    if (!p->adaptive) {
         int64_t npad = pow2_at_least(ns + nf);
         k_leaf_union<<<nblk(npad), 256, 0, st>>>(p->s_key, ns, p->t_key, nf, 2 * (16 - d), npad, srt);
         AFMM_LAUNCH_CHECK();
@@ -670,17 +987,19 @@ afmm_status build_tree(afmm_plan p, const double *src_r, const double *src_z, co
         Level &v = p->lv[l];
         int64_t nb = v.nbox;
         if (nb >= (1 << 24)) return AFMM_EUNSUPPORTED;  // S2L unit keys hold 24-bit box indices
-        AFMM_TRY(dalloc_t(p, &v.srng, nb));
-        AFMM_TRY(dalloc_t(p, &v.trng, nb));
-        k_box_ranges<<<nblk(nb), 256, 0, st>>>(v.key, nb, 2 * (16 - l), p->s_key, ns, p->t_key, nf, v.srng, v.trng);
-        AFMM_LAUNCH_CHECK();
-        if (l >= 3) {
-            AFMM_TRY(dalloc_t(p, &v.parent, nb));
-            k_parents<<<nblk(nb), 256, 0, st>>>(v.key, nb, p->lv[l - 1].key, p->lv[l - 1].nbox, v.parent);
+        if (!p->adaptive) {  // (the adaptive tree builds these with its levels)
+            AFMM_TRY(dalloc_t(p, &v.srng, nb));
+            AFMM_TRY(dalloc_t(p, &v.trng, nb));
+            k_box_ranges<<<nblk(nb), 256, 0, st>>>(v.key, nb, 2 * (16 - l), p->s_key, ns, p->t_key, nf, v.srng, v.trng);
             AFMM_LAUNCH_CHECK();
-            AFMM_TRY(dalloc_t(p, &p->lv[l - 1].child, p->lv[l - 1].nbox));
-            k_child_ranges<<<nblk(nb), 256, 0, st>>>(v.parent, nb, p->lv[l - 1].child);
-            AFMM_LAUNCH_CHECK();
+            if (l >= 3) {
+                AFMM_TRY(dalloc_t(p, &v.parent, nb));
+                k_parents<<<nblk(nb), 256, 0, st>>>(v.key, nb, p->lv[l - 1].key, p->lv[l - 1].nbox, v.parent);
+                AFMM_LAUNCH_CHECK();
+                AFMM_TRY(dalloc_t(p, &p->lv[l - 1].child, p->lv[l - 1].nbox));
+                k_child_ranges<<<nblk(nb), 256, 0, st>>>(v.parent, nb, p->lv[l - 1].child);
+                AFMM_LAUNCH_CHECK();
+            }
         }
         AFMM_TRY(dalloc_t(p, &v.s2l, nb * 27));
         k_s2l_table<<<nblk(nb * 27), 256, 0, st>>>(v.key, nb, l, v.s2l);
@@ -724,7 +1043,21 @@ afmm_status build_tree(afmm_plan p, const double *src_r, const double *src_z, co
         }
     }
     // ---- leaf neighbours and near-field units for both directions
-    {
+    if (p->adaptive) {
+        AFMM_TRY(build_near_adaptive(p));
+        unsigned long long *acc = nullptr;
+        AFMM_TRY(dalloc_t(p, &acc, 3));
+        AFMM_CUDA(cudaMemsetAsync(acc, 0, 3 * sizeof(unsigned long long), st));
+        for (int l = 2; l <= d; ++l) {
+            const Level &u = p->lv[l];
+            k_s2l_count<<<nblk(u.nbox), 256, 0, st>>>(u.s2l, u.trng, u.srng, u.nbox, acc + 1);
+            AFMM_LAUNCH_CHECK();
+        }
+        unsigned long long h[3];
+        AFMM_TRY(readback(p, h, acc, sizeof(h)));
+        p->s2l_pairs = (int64_t)h[1];
+        p->s2l_point_pairs = (int64_t)h[2];
+    } else {
         Level &v = p->lv[d];
         int64_t nb = v.nbox;
         AFMM_TRY(dalloc_t(p, &v.nbr, nb * 9));
@@ -739,7 +1072,7 @@ afmm_status build_tree(afmm_plan p, const double *src_r, const double *src_z, co
             AFMM_TRY(readback(p, &nu, pos + nb, sizeof(int64_t)));
             p->n_near_unit[dir] = nu;
             AFMM_TRY(dalloc_t(p, &p->near_unit[dir], nu > 0 ? nu : 1));
-            k_near_fill<<<nblk(nb), 256, 0, st>>>(rng, nb, pos, p->near_unit[dir]);
+            k_near_fill<<<nblk(nb), 256, 0, st>>>(rng, nb, d, pos, p->near_unit[dir]);
             AFMM_LAUNCH_CHECK();
         }
         unsigned long long *acc = nullptr;

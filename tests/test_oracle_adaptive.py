@@ -133,3 +133,31 @@ def test_wx_direct_on_a_uniform_tree_is_the_uniform_fmm():
     U = oracle.fmm(sr, sz, tr, tz, w["q_re"], w["q_im"], 6, d, geom, grad=True)
     for c in (0, 2, 4):
         assert _eps(F, U, c) < 1e-12
+
+
+def test_adaptive_adjoint_on_a_uniform_tree_is_the_uniform_adjoint():
+    w = W.make("cfg4", ns=600, nf=500, n_modes=3, with_targets=True)
+    sr, sz, tr, tz = w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"]
+    d, geom = oracle.tree_setup(sr, sz, tr, tz, 32, depth_override=4)
+    tree = A.AdaptiveTree(sr, sz, tr, tz, 10 ** 9, refine_to=d, geom=geom)
+    rng = np.random.default_rng(5)
+    g_re, g_im = rng.standard_normal((2, 3, tr.size))
+    a = A.adaptive_adjoint(tree, w["q_re"], w["q_im"], g_re, g_im, 6)
+    u = oracle.adjoint_fmm(sr, sz, tr, tz, w["q_re"], w["q_im"], g_re, g_im, 6, d, geom)
+    assert _eps(a, u, 0) < 1e-12
+    for k in (2, 3):
+        assert np.max(np.abs(a[k] - u[k])) < 1e-12 * np.max(np.abs(u[k]))
+
+
+def test_adaptive_adjoint_matches_the_direct_adjoint():
+    w = W.make("cfg5", ns=900, nf=700, n_modes=3)
+    sr, sz, tr, tz = w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"]
+    tree = A.AdaptiveTree(sr, sz, tr, tz, 20, refine_to=2)
+    assert len({b[0] for b in tree.leaves}) >= 3
+    rng = np.random.default_rng(6)
+    g_re, g_im = rng.standard_normal((2, 3, tr.size))
+    a = A.adaptive_adjoint(tree, w["q_re"], w["q_im"], g_re, g_im, 10)
+    u = oracle.adjoint_direct(sr, sz, tr, tz, w["q_re"], w["q_im"], g_re, g_im)
+    assert _eps(a, u, 0) < 1e-5
+    for k in (2, 3):
+        assert np.max(np.abs(a[k] - u[k])) < 1e-5 * np.max(np.abs(u[k]))
