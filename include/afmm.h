@@ -100,6 +100,12 @@ typedef struct {
                            lists of the standard adaptive FMM, the W and X pairs summed
                            directly; every (field point, source) pair is still covered once.
                            AFMM_FP64 and AFMM_MIXED only (AFMM_FP64_NATIVE: EUNSUPPORTED). */
+    int balance;        /* adaptive tree: also split a box (below the maximum level) when a
+                           same-level neighbour holds more than balance x leaf_size sources
+                           or field points (0: 4; negative: off).  It bounds the direct sums
+                           of every leaf by (9 balance + 8 (level - 2)) x leaf_size points of
+                           the other role; without it a sparse coarse leaf touching a dense
+                           box sums that box's whole subtree directly. */
 } afmm_options;
 
 typedef enum { AFMM_TREE_UNIFORM = 0, AFMM_TREE_ADAPTIVE = 1 } afmm_tree;
@@ -125,6 +131,7 @@ typedef struct {
     int s2l_tensor_cores;       /* 1 if the S2L runs on the tcgen05 tensor cores, else 0 */
     int tree;                   /* afmm_tree of the plan */
     int64_t n_leaves[17];       /* leaf boxes per level (uniform tree: all boxes of level d) */
+    int64_t near_max_sources;   /* the most sources one leaf with field points sums directly */
 } afmm_plan_info_t;
 
 void afmm_options_default(afmm_options *opt);

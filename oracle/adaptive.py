@@ -58,9 +58,16 @@ def _binom(n, k):
 class AdaptiveTree:
     """Boxes keyed by (level, ir, iz); each box holds the indices of its sources and field
     points.  ``refine_to`` forces every non-empty box to split down to that level (with a
-    large ``leaf_size`` this reproduces the uniform tree of that depth)."""
+    large ``leaf_size`` this reproduces the uniform tree of that depth).
 
-    def __init__(self, src_r, src_z, tgt_r, tgt_z, leaf_size, max_level=12, refine_to=0, geom=None):
+    ``balance`` = K > 0 also splits a box (below the maximum level) when one of its
+    same-level neighbours holds more than K leaf_size sources or field points.  A leaf then
+    sums directly at most the points of 9 boxes of its level, each holding at most
+    K leaf_size, plus at most 8 coarser leaves per level: without it a sparse coarse leaf
+    touching a dense box would sum that box's whole subtree directly.  The tree is built
+    level by level, since the rule looks at a box's neighbours."""
+
+    def __init__(self, src_r, src_z, tgt_r, tgt_z, leaf_size, max_level=12, refine_to=0, geom=None, balance=0):
         self.sr, self.sz, self.tr, self.tz = map(_f64, (src_r, src_z, tgt_r, tgt_z))
         if geom is None:
             geom = tree_setup(self.sr, self.sz, self.tr, self.tz, max(1, int(leaf_size)))[1]
@@ -68,37 +75,47 @@ class AdaptiveTree:
         self.leaf_size = int(leaf_size)
         self.max_level = int(max_level)
         self.refine_to = int(refine_to)
+        self.balance = int(balance)
         self.src, self.tgt, self.children, self.parent = {}, {}, {}, {}
         root = (0, 0, 0)
         self.src[root] = np.arange(self.sr.shape[0])
         self.tgt[root] = np.arange(self.tr.shape[0])
         self.parent[root] = None
-        stack = [root]
-        while stack:
-            b = stack.pop()
-            lvl = b[0]
-            s, t = self.src[b], self.tgt[b]
-            split = lvl < self.refine_to or len(s) > self.leaf_size or len(t) > self.leaf_size
-            if not split or lvl >= self.max_level:
-                self.children[b] = []
-                continue
-            kids = []
-            si = _box_coord(self.sr[s], self.r0, self.L, lvl + 1)
-            sj = _box_coord(self.sz[s], self.z0, self.L, lvl + 1)
-            ti = _box_coord(self.tr[t], self.r0, self.L, lvl + 1)
-            tj = _box_coord(self.tz[t], self.z0, self.L, lvl + 1)
-            for a in (0, 1):
-                for c in (0, 1):
-                    ir, iz = 2 * b[1] + a, 2 * b[2] + c
-                    cs = s[(si == ir) & (sj == iz)]
-                    ct = t[(ti == ir) & (tj == iz)]
-                    if len(cs) == 0 and len(ct) == 0:
-                        continue
-                    k = (lvl + 1, ir, iz)
-                    self.src[k], self.tgt[k], self.parent[k] = cs, ct, b
-                    kids.append(k)
-                    stack.append(k)
-            self.children[b] = kids
+        level = [root]
+        while level:
+            nxt = []
+            for b in level:
+                lvl = b[0]
+                s, t = self.src[b], self.tgt[b]
+                split = lvl < self.refine_to or len(s) > self.leaf_size or len(t) > self.leaf_size
+                if not split and self.balance > 0:
+                    lim = self.balance * self.leaf_size
+                    for di in (-1, 0, 1):
+                        for dj in (-1, 0, 1):
+                            c = (lvl, b[1] + di, b[2] + dj)
+                            if c != b and c in self.src and (len(self.src[c]) > lim or len(self.tgt[c]) > lim):
+                                split = True
+                if not split or lvl >= self.max_level:
+                    self.children[b] = []
+                    continue
+                kids = []
+                si = _box_coord(self.sr[s], self.r0, self.L, lvl + 1)
+                sj = _box_coord(self.sz[s], self.z0, self.L, lvl + 1)
+                ti = _box_coord(self.tr[t], self.r0, self.L, lvl + 1)
+                tj = _box_coord(self.tz[t], self.z0, self.L, lvl + 1)
+                for a in (0, 1):
+                    for c in (0, 1):
+                        ir, iz = 2 * b[1] + a, 2 * b[2] + c
+                        cs = s[(si == ir) & (sj == iz)]
+                        ct = t[(ti == ir) & (tj == iz)]
+                        if len(cs) == 0 and len(ct) == 0:
+                            continue
+                        k = (lvl + 1, ir, iz)
+                        self.src[k], self.tgt[k], self.parent[k] = cs, ct, b
+                        kids.append(k)
+                        nxt.append(k)
+                self.children[b] = kids
+            level = nxt
         self.boxes = sorted(self.src)
         self.leaves = [b for b in self.boxes if not self.children[b]]
         self._lists()
@@ -354,7 +371,7 @@ def transposed(tree):
     (more than leaf_size sources or field points) and the square are symmetric in the two
     roles, so the boxes and the V lists are the same; the lists of each role follow."""
     return AdaptiveTree(tree.tr, tree.tz, tree.sr, tree.sz, tree.leaf_size, max_level=tree.max_level,
-                        refine_to=tree.refine_to, geom=(tree.r0, tree.z0, tree.L))
+                        refine_to=tree.refine_to, geom=(tree.r0, tree.z0, tree.L), balance=tree.balance)
 
 
 def adaptive_adjoint(tree, q_re, q_im, gphi_re, gphi_im, M, wx="direct"):

@@ -35,7 +35,7 @@ class AfmmError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int), ("leaf_size", ctypes.c_int), ("depth_override", ctypes.c_int),
                 ("precision", ctypes.c_int), ("fwd_switch", ctypes.c_double), ("miller_extra", ctypes.c_int),
-                ("s2l_engine", ctypes.c_int), ("tree", ctypes.c_int)]
+                ("s2l_engine", ctypes.c_int), ("tree", ctypes.c_int), ("balance", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -45,7 +45,7 @@ class PlanInfo(ctypes.Structure):
                 ("n_boxes", ctypes.c_int64 * 17), ("near_pairs", ctypes.c_int64),
                 ("s2l_pairs", ctypes.c_int64), ("expansions", ctypes.c_int64),
                 ("s2l_point_pairs", ctypes.c_int64), ("s2l_tensor_cores", ctypes.c_int), ("tree", ctypes.c_int),
-                ("n_leaves", ctypes.c_int64 * 17)]
+                ("n_leaves", ctypes.c_int64 * 17), ("near_max_sources", ctypes.c_int64)]
 
 
 _lib = None
@@ -140,12 +140,13 @@ class Plan:
     ``precision`` ("fp64", "mixed" or "fp64_native"), ``fwd_switch``, ``miller_extra``,
     ``s2l_engine`` ("auto": tensor cores where supported, "cuda_cores"), ``tree`` ("uniform":
     the paper's uniform quadtree; "adaptive": boxes split while they hold more than
-    ``leaf_size`` sources or field points, ``depth`` then the maximum level).  The plan is
-    bound to the current torch stream at creation.
+    ``leaf_size`` sources or field points, ``depth`` then the maximum level) and ``balance``
+    (adaptive tree: also split boxes whose neighbour holds more than balance x leaf_size
+    points; 0: 4, negative: off).  The plan is bound to the current torch stream at creation.
     """
 
     def __init__(self, src_r, src_z, tgt_r, tgt_z, n_modes, order=8, leaf_size=32, depth=0, precision="fp64",
-                 fwd_switch=0.0, miller_extra=0, s2l_engine="auto", tree="uniform"):
+                 fwd_switch=0.0, miller_extra=0, s2l_engine="auto", tree="uniform", balance=0):
         lib = load()
         self._lib = lib
         self.ns = int(src_r.numel())
@@ -162,6 +163,7 @@ class Plan:
         opt.miller_extra = int(miller_extra)
         opt.s2l_engine = {"auto": 0, "cuda_cores": 1}[s2l_engine]
         opt.tree = {"uniform": 0, "adaptive": 1}[tree]
+        opt.balance = int(balance)
         h = ctypes.c_void_p()
         st = lib.afmm_plan_create(ctypes.byref(h), self.ns, _ptr(src_r), _ptr(src_z), self.nf, _ptr(tgt_r),
                                   _ptr(tgt_z), self.n_modes, ctypes.byref(opt), _stream())
@@ -186,7 +188,8 @@ class Plan:
                     z0=inf.z0, side=inf.side, ns=inf.ns, nf=inf.nf, n_boxes=list(inf.n_boxes),
                     near_pairs=inf.near_pairs, s2l_pairs=inf.s2l_pairs, expansions=inf.expansions,
                     s2l_point_pairs=inf.s2l_point_pairs, s2l_tensor_cores=bool(inf.s2l_tensor_cores),
-                    tree=("uniform", "adaptive")[inf.tree], n_leaves=list(inf.n_leaves))
+                    tree=("uniform", "adaptive")[inf.tree], n_leaves=list(inf.n_leaves),
+                    near_max_sources=inf.near_max_sources)
 
     def set_timing(self, enable=True):
         _check(self._lib.afmm_set_timing(self._h, 1 if enable else 0), "afmm_set_timing")

@@ -394,6 +394,7 @@ afmm_status afmm_plan_info(afmm_plan p, afmm_plan_info_t *info)
     info->s2l_point_pairs = p->s2l_point_pairs;
     info->s2l_tensor_cores = s2l_tc_enabled(p) ? 1 : 0;
     info->tree = p->adaptive ? AFMM_TREE_ADAPTIVE : AFMM_TREE_UNIFORM;
+    info->near_max_sources = p->near_max_src;
     for (int l = 2; l <= p->d; ++l) info->n_leaves[l] = p->adaptive ? p->lv[l].nleaf : (l == p->d ? p->lv[l].nbox : 0);
     return AFMM_OK;
 }

@@ -247,13 +247,14 @@ struct afmm_plan_s {
     int64_t n_max = 0;
     // statistics
     int64_t near_pairs = 0, s2l_pairs = 0, expansions = 0, s2l_point_pairs = 0;
+    int64_t near_max_src = 0;  // the most sources one leaf sums directly
     // timing (events on the plan's stream; read back after the evaluation's last event)
     int timing = 0;
     cudaEvent_t ev[80];                         // phase timing events (AFMM_EV_L2P: after the L2P)
     double t_ms[9] = {0};
     // device allocations to free (from the library's stream-ordered pool when pool != null)
     cudaMemPool_t pool = nullptr;
-    void *allocs[512];
+    void *allocs[1024];
     int nalloc = 0;
 };
 

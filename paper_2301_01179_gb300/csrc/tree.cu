@@ -520,6 +520,7 @@ __global__ void k_near_pairs(const int2 *__restrict__ trng, const int2 *__restri
         if (q >= 0) s += srng[q].y - srng[q].x;
     }
     atomicAdd(acc, (unsigned long long)(nt * s));
+    if (nt > 0) atomicMax(acc + 3, (unsigned long long)s);
 }
 
 // S2L applications of a level (acc[0]) and the (field point, source) pairs they cover (acc[1])
@@ -547,12 +548,30 @@ __global__ void k_s2l_count(const int32_t *__restrict__ tab, const int2 *__restr
 // its non-empty children form level l + 1 (sorted by key, since the parents are and the
 // child quadrant c = (radial bit << 1) | axial bit is the key's lowest digit).
 // ------------------------------------------------------------------------------------
-__global__ void k_split_flags(const int2 *__restrict__ srng, const int2 *__restrict__ trng, int64_t nbox, int leaf,
+// split flags of level l: more than leaf points of either role, or (balance lim > 0) a
+// same-level neighbour with more than lim points of either role
+__global__ void k_split_flags(const uint32_t *__restrict__ key, const int2 *__restrict__ srng,
+                              const int2 *__restrict__ trng, int64_t nbox, int l, int leaf, int64_t lim,
                               int64_t *__restrict__ flag)
 {
     int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= nbox) return;
-    flag[b] = (srng[b].y - srng[b].x > leaf || trng[b].y - trng[b].x > leaf) ? 1 : 0;
+    bool split = srng[b].y - srng[b].x > leaf || trng[b].y - trng[b].x > leaf;
+    if (!split && lim > 0) {
+        const uint32_t k = key[b];
+        const int ir = (int)morton_ir(k), iz = (int)morton_iz(k), nl = 1 << l;
+        for (int dr = -1; dr <= 1 && !split; ++dr)
+            for (int dz = -1; dz <= 1; ++dz) {
+                const int i = ir + dr, j = iz + dz;
+                if ((dr == 0 && dz == 0) || i < 0 || j < 0 || i >= nl || j >= nl) continue;
+                const int64_t q = find_key(key, nbox, morton_key(i, j));
+                if (q >= 0 && (srng[q].y - srng[q].x > lim || trng[q].y - trng[q].x > lim)) {
+                    split = true;
+                    break;
+                }
+            }
+    }
+    flag[b] = split ? 1 : 0;
 }
 
 // four candidates per split parent (pkey == nullptr: the 4 boxes of level 1, all split);
@@ -677,6 +696,7 @@ __global__ void k_anear_fill(const AdTab T, int l, const int64_t *__restrict__ o
     const int2 mb = T.trng[l][b], ms = T.srng[l][b];
     atomicAdd(acc, (unsigned long long)(mb.y - mb.x) * ss);
     atomicAdd(acc + 1, (unsigned long long)(ms.y - ms.x) * st);
+    if (mb.y > mb.x) atomicMax(acc + 3, ss);  // the largest direct sum of a leaf with field points
 }
 
 // near-field units of the adaptive tree: ceil(count / 32) per leaf with points of the role
@@ -743,22 +763,18 @@ static afmm_status build_levels_adaptive(afmm_plan p)
     const int64_t ns = p->ns, nf = p->nf;
     const int lmax = p->opt.depth_override > 0 ? p->opt.depth_override : AFMM_MAX_LEVEL;
     const int leaf = p->opt.leaf_size;
-    // split boxes of one level are disjoint and hold more than leaf_size points each
-    const int64_t ccap = 4 * ((ns + nf) / (leaf + 1)) + 64, bcap = ns + nf + 64;
-    const int64_t ncap = ccap > bcap ? ccap : bcap;
+    const int64_t lim = p->opt.balance < 0 ? 0 : (int64_t)(p->opt.balance == 0 ? 4 : p->opt.balance) * leaf;
+    // boxes of one level are disjoint and non-empty (at most ns + nf); four candidates per
+    // split box, in buffers that grow (doubling) with the largest level met so far
+    const int64_t bcap = ns + nf + 64;
+    int64_t ccap = 0;
     uint32_t *ckey = nullptr;
     int32_t *cpar = nullptr;
     int2 *csr = nullptr, *ctr = nullptr;
     int64_t *ne = nullptr, *cpos = nullptr, *ctmp = nullptr, *flag = nullptr, *fpos = nullptr;
-    AFMM_TRY(dalloc_t(p, &ckey, ccap));
-    AFMM_TRY(dalloc_t(p, &cpar, ccap));
-    AFMM_TRY(dalloc_t(p, &csr, ccap));
-    AFMM_TRY(dalloc_t(p, &ctr, ccap));
-    AFMM_TRY(dalloc_t(p, &ne, ccap));
-    AFMM_TRY(dalloc_t(p, &cpos, ccap + 1));
     AFMM_TRY(dalloc_t(p, &flag, bcap));
     AFMM_TRY(dalloc_t(p, &fpos, bcap + 1));
-    AFMM_TRY(dalloc_t(p, &ctmp, 2 * (ncap / 1024 + 64) + 256));
+    AFMM_TRY(dalloc_t(p, &ctmp, 2 * (4 * bcap / 1024 + 64) + 256));
     const uint32_t *pkey = nullptr;  // level 1: the four boxes, all split
     int64_t npar = 4;
     int l = 1;
@@ -766,7 +782,8 @@ static afmm_status build_levels_adaptive(afmm_plan p)
         int64_t nsplit = 4;
         if (pkey) {
             if (l >= lmax) break;
-            k_split_flags<<<nblk(npar), 256, 0, st>>>(p->lv[l].srng, p->lv[l].trng, npar, leaf, flag);
+            k_split_flags<<<nblk(npar), 256, 0, st>>>(p->lv[l].key, p->lv[l].srng, p->lv[l].trng, npar, l, leaf,
+                                                      lim, flag);
             AFMM_LAUNCH_CHECK();
             AFMM_TRY(scan_excl(flag, fpos, npar, ctmp, st));
             AFMM_TRY(readback(p, &nsplit, fpos + npar, sizeof(int64_t)));
@@ -774,7 +791,15 @@ static afmm_status build_levels_adaptive(afmm_plan p)
         }
         const int lc = l + 1;
         const int64_t ncand = 4 * nsplit;
-        if (ncand > ccap) return AFMM_ECUDA;  // cannot happen: split boxes hold > leaf_size points
+        if (ncand > ccap) {
+            ccap = ccap * 2 > ncand ? ccap * 2 : ncand + 64;
+            AFMM_TRY(dalloc_t(p, &ckey, ccap));
+            AFMM_TRY(dalloc_t(p, &cpar, ccap));
+            AFMM_TRY(dalloc_t(p, &csr, ccap));
+            AFMM_TRY(dalloc_t(p, &ctr, ccap));
+            AFMM_TRY(dalloc_t(p, &ne, ccap));
+            AFMM_TRY(dalloc_t(p, &cpos, ccap + 1));
+        }
         k_child_cand<<<nblk(4 * npar), 256, 0, st>>>(pkey, flag, fpos, npar, lc, p->s_key, ns, p->t_key, nf, ckey,
                                                       cpar, csr, ctr, ne);
         AFMM_LAUNCH_CHECK();
@@ -881,9 +906,10 @@ static afmm_status build_near_adaptive(afmm_plan p)
             AFMM_LAUNCH_CHECK();
         }
     }
-    unsigned long long h[2];
+    unsigned long long h[4];
     AFMM_TRY(readback(p, h, acc, sizeof(h)));
     p->near_pairs = (int64_t)h[0];
+    p->near_max_src = (int64_t)h[3];
     return AFMM_OK;
 }
 
@@ -1076,8 +1102,8 @@ afmm_status build_tree(afmm_plan p, const double *src_r, const double *src_z, co
             AFMM_LAUNCH_CHECK();
         }
         unsigned long long *acc = nullptr;
-        AFMM_TRY(dalloc_t(p, &acc, 3));
-        AFMM_CUDA(cudaMemsetAsync(acc, 0, 3 * sizeof(unsigned long long), st));
+        AFMM_TRY(dalloc_t(p, &acc, 4));
+        AFMM_CUDA(cudaMemsetAsync(acc, 0, 4 * sizeof(unsigned long long), st));
         k_near_pairs<<<nblk(nb), 256, 0, st>>>(v.trng, v.srng, v.nbr, nb, acc);
         AFMM_LAUNCH_CHECK();
         for (int l = 2; l <= d; ++l) {
@@ -1085,11 +1111,12 @@ afmm_status build_tree(afmm_plan p, const double *src_r, const double *src_z, co
             k_s2l_count<<<nblk(u.nbox), 256, 0, st>>>(u.s2l, u.trng, u.srng, u.nbox, acc + 1);
             AFMM_LAUNCH_CHECK();
         }
-        unsigned long long h[3];
+        unsigned long long h[4];
         AFMM_TRY(readback(p, h, acc, sizeof(h)));
         p->near_pairs = (int64_t)h[0];
         p->s2l_pairs = (int64_t)h[1];
         p->s2l_point_pairs = (int64_t)h[2];
+        p->near_max_src = (int64_t)h[3];
     }
     p->n_max = nmax;
     return AFMM_OK;

@@ -3,8 +3,9 @@ adaptive oracle (oracle.adaptive, the variant that sums the W and X pairs direct
 the C ABI.
 
 Both sides build the same tree from the same square (every box of levels 0..1 split, a box
-of level >= 2 split while it holds more than leaf_size sources or field points, up to the
-maximum level) and apply the same expansions (Sec. 2: moments, shifts, the S2L of
+of level >= 2 split while it holds more than leaf_size sources or field points, or, with the
+balance factor K, while a same-level neighbour holds more than K leaf_size of either, up to
+the maximum level) and apply the same expansions (Sec. 2: moments, shifts, the S2L of
 Eq. analysis:s2l over the V lists, local expansions), so they agree to rounding: bar 1e-10
 per mode (Eq. results:error) on the FP64 path, 2e-5 for MIXED (its stated FMM bound).  The
 tree itself is compared box for box: boxes and leaves per level, the directly summed pairs
@@ -22,23 +23,26 @@ TOL = 1e-10
 TOL_MIXED = 2e-5
 
 
-def _plan(w, M, leaf, maxlev, precision="fp64"):
+def _plan(w, M, leaf, maxlev, precision="fp64", K=4):
+    """GPU plan on the adaptive tree; K: balance factor (0: the rule off)."""
     from paper_2301_01179_gb300 import binding
     sr, sz, tr, tz = to_dev(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"])
     return binding.Plan(sr, sz, tr, tz, w["n_modes"], order=M, leaf_size=leaf, depth=maxlev, precision=precision,
-                        tree="adaptive")
+                        tree="adaptive", balance=K if K > 0 else -1)
 
 
-def _tree(w, leaf, maxlev):
-    return A.AdaptiveTree(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], leaf, max_level=maxlev, refine_to=2)
+def _tree(w, leaf, maxlev, K=4):
+    return A.AdaptiveTree(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], leaf, max_level=maxlev, refine_to=2,
+                          balance=K)
 
 
-@pytest.mark.parametrize("kind,ns,nf,leaf,maxlev", [("cfg5", 6000, 5000, 32, 12), ("cfg5", 5000, 6000, 20, 5),
-                                                    ("cfg3", 4000, 4000, 16, 12), ("cfg1", 3000, 2000, 40, 12)])
-def test_adaptive_tree_matches_oracle_tree(kind, ns, nf, leaf, maxlev):
+@pytest.mark.parametrize("kind,ns,nf,leaf,maxlev,K", [("cfg5", 6000, 5000, 32, 12, 4), ("cfg5", 6000, 5000, 32, 12, 0),
+                                                      ("cfg5", 5000, 6000, 20, 5, 2), ("cfg3", 4000, 4000, 16, 12, 4),
+                                                      ("cfg1", 3000, 2000, 40, 12, 4)])
+def test_adaptive_tree_matches_oracle_tree(kind, ns, nf, leaf, maxlev, K):
     w = W.make(kind, ns=ns, nf=nf, n_modes=1)
-    T = _tree(w, leaf, maxlev)
-    info = _plan(w, 4, leaf, maxlev).info()
+    T = _tree(w, leaf, maxlev, K)
+    info = _plan(w, 4, leaf, maxlev, K=K).info()
     assert info["tree"] == "adaptive"
     levels = sorted({b[0] for b in T.boxes})
     assert info["depth"] == max(levels)
@@ -54,17 +58,18 @@ def test_adaptive_tree_matches_oracle_tree(kind, ns, nf, leaf, maxlev):
         assert any(max(len(T.src[b]), len(T.tgt[b])) > leaf for b in T.leaves if b[0] == 5)
 
 
-@pytest.mark.parametrize("kind,ns,nf,nm,M,leaf,maxlev", [
-    ("cfg5", 6000, 5000, 9, 8, 32, 12),
-    ("cfg5", 12000, 10000, 33, 12, 64, 12),  # the headline shape: modes 0..32, order 12, leaf 64
-    ("cfg5", 5000, 6000, 5, 6, 20, 5),       # leaves held at the maximum level
-    ("cfg3", 5000, 4000, 9, 10, 24, 12),     # points on a curve
+@pytest.mark.parametrize("kind,ns,nf,nm,M,leaf,maxlev,K", [
+    ("cfg5", 6000, 5000, 9, 8, 32, 12, 4),
+    ("cfg5", 6000, 5000, 9, 8, 32, 12, 0),      # without the balance rule
+    ("cfg5", 12000, 10000, 33, 12, 64, 12, 4),  # the headline shape: modes 0..32, order 12, leaf 64
+    ("cfg5", 5000, 6000, 5, 6, 20, 5, 2),       # leaves held at the maximum level
+    ("cfg3", 5000, 4000, 9, 10, 24, 12, 4),     # points on a curve
 ])
-def test_adaptive_fmm_grad_matches_oracle(kind, ns, nf, nm, M, leaf, maxlev):
+def test_adaptive_fmm_grad_matches_oracle(kind, ns, nf, nm, M, leaf, maxlev, K):
     w = W.make(kind, ns=ns, nf=nf, n_modes=nm)
-    T = _tree(w, leaf, maxlev)
+    T = _tree(w, leaf, maxlev, K)
     assert len({b[0] for b in T.leaves}) >= 3
-    pl = _plan(w, M, leaf, maxlev)
+    pl = _plan(w, M, leaf, maxlev, K=K)
     q_re, q_im = to_dev(w["q_re"], w["q_im"])
     g = to_np(*pl.grad(q_re, q_im))
     F = A.adaptive_fmm(T, w["q_re"], w["q_im"], M, grad=True, wx="direct")
@@ -111,3 +116,19 @@ def test_adaptive_fewer_near_pairs_than_uniform_on_clustered_points():
     for i in (u, a):
         assert i["near_pairs"] + i["s2l_point_pairs"] == 200000 * 200000
     assert a["near_pairs"] < 0.6 * u["near_pairs"], (a["near_pairs"], u["near_pairs"])
+
+
+def test_adaptive_balance_bounds_near_lists_at_full_size():
+    """The 4e6-ring workload's laws at full size: with the balance rule the largest direct
+    sum of a leaf stays within (9 K + 8 (d - 2)) leaf_size sources (afmm_plan_info reports
+    the largest near list), without it a sparse coarse leaf sums a dense subtree."""
+    from paper_2301_01179_gb300 import binding
+    w = W.make("cfg5", n_modes=1)
+    sr, sz, tr, tz = to_dev(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"])
+    n = w["src_r"].size
+    for K in (4, 2):
+        i = binding.Plan(sr, sz, tr, tz, 1, order=4, leaf_size=64, tree="adaptive", balance=K).info()
+        assert i["near_pairs"] + i["s2l_point_pairs"] == n * n
+        assert 0 < i["near_max_sources"] <= (9 * K + 8 * (i["depth"] - 2)) * 64, i["near_max_sources"]
+    f = binding.Plan(sr, sz, tr, tz, 1, order=4, leaf_size=64, tree="adaptive", balance=-1).info()
+    assert f["near_max_sources"] > 10 * (9 * 4 + 8 * (f["depth"] - 2)) * 64

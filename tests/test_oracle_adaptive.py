@@ -161,3 +161,42 @@ def test_adaptive_adjoint_matches_the_direct_adjoint():
     assert _eps(a, u, 0) < 1e-5
     for k in (2, 3):
         assert np.max(np.abs(a[k] - u[k])) < 1e-5 * np.max(np.abs(u[k]))
+
+
+@pytest.mark.parametrize("K", [2, 4])
+def test_balanced_tree_lists_partition_and_bound_the_direct_sums(K):
+    """With the balance rule every leaf's directly summed sources are bounded by
+    (9 K + 8 (l - 2)) leaf_size, and the lists still cover every pair exactly once."""
+    w = W.make("cfg5", ns=2500, nf=2000, n_modes=1)
+    leaf = 12
+    tree = A.AdaptiveTree(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], leaf, refine_to=2, balance=K)
+    free = A.AdaptiveTree(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], leaf, refine_to=2)
+    assert len(tree.boxes) > len(free.boxes)
+    ns = w["src_r"].size
+    worst_free = max(len(A.direct_sources(free, B)) for B in free.leaves)
+    for B in tree.leaves:
+        s = A.direct_sources(tree, B)
+        assert len(s) <= (9 * K + 8 * (B[0] - 2)) * leaf, (B, len(s))
+        cnt = np.bincount(s, minlength=ns)
+        for D in _ancestors(tree, B):
+            for c in tree.V[D]:
+                cnt += np.bincount(tree.src[c], minlength=ns)
+        assert cnt.min() == 1 and cnt.max() == 1
+    worst = max(len(A.direct_sources(tree, B)) for B in tree.leaves)
+    assert worst_free > 5 * worst  # the rule is what bounds them
+    T = A.transposed(tree)
+    assert T.boxes == tree.boxes and all(T.V[b] == tree.V[b] for b in tree.boxes)
+
+
+def test_balanced_tree_converges_to_direct():
+    w = W.make("cfg5", ns=1200, nf=900, n_modes=3)
+    sr, sz, tr, tz = w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"]
+    tree = A.AdaptiveTree(sr, sz, tr, tz, 16, refine_to=2, balance=4)
+    D = oracle.direct(sr, sz, tr, tz, w["q_re"], w["q_im"], grad=True)
+    errs = []
+    for M in (4, 7, 10):
+        F = A.adaptive_fmm(tree, w["q_re"], w["q_im"], M, grad=True, wx="direct")
+        errs.append([_eps(F, D, c) for c in (0, 2, 4)])
+    errs = np.array(errs)
+    assert np.all(errs[1:] < 0.2 * errs[:-1]), errs
+    assert errs[-1].max() < 1e-5, errs
