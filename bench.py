@@ -268,10 +268,10 @@ def run_reference(args):
     return 0
 
 
-def fwd_bwd(kind, precision, steps, warmup, dev):
+def fwd_bwd(kind, precision, steps, warmup, dev, tree="uniform"):
     """One forward (potential) and backward (adjoint of L = sum |Phi - T|^2) step of a
     configuration, timed end to end on the device (plan creation included), plus the plan
-    creation alone.  Returns a dict for the JSON line."""
+    creation alone, on the uniform or the adaptive tree.  Returns a dict for the JSON line."""
     import numpy as np
     import torch
     from paper_2301_01179_gb300 import binding, workloads as W
@@ -285,7 +285,7 @@ def fwd_bwd(kind, precision, steps, warmup, dev):
                                              w["T_re"], w["T_im"]))
 
     def step():
-        pl = binding.Plan(sr, sz, tr, tz, nm, order=w["order"], leaf_size=w["leaf"], precision=precision)
+        pl = binding.Plan(sr, sz, tr, tz, nm, order=w["order"], leaf_size=w["leaf"], precision=precision, tree=tree)
         pr, pi = pl.eval(qr, qi)
         out = pl.adjoint(qr, qi, 2.0 * (pr - Tr), 2.0 * (pi - Ti))
         return pl, out
@@ -304,14 +304,52 @@ def fwd_bwd(kind, precision, steps, warmup, dev):
     t_step = e0.elapsed_time(e1) / steps
     e0.record()
     for _ in range(steps):
-        pl = binding.Plan(sr, sz, tr, tz, nm, order=w["order"], leaf_size=w["leaf"], precision=precision)
+        pl = binding.Plan(sr, sz, tr, tz, nm, order=w["order"], leaf_size=w["leaf"], precision=precision, tree=tree)
+        inf = pl.info()
         pl.close()
     e1.record()
     torch.cuda.synchronize()
     t_plan = e0.elapsed_time(e1) / steps
     return {"workload": "%s: %d x %d, modes 0..%d, order %d, leaf %d" % (kind, ns, nf, nm - 1, w["order"], w["leaf"]),
-            "precision": precision, "fwd_bwd_ms": t_step, "plan_ms": t_plan, "steps": steps,
+            "precision": precision, "tree": tree, "depth": inf["depth"], "near_pairs": inf["near_pairs"],
+            "s2l_pairs": inf["s2l_pairs"], "fwd_bwd_ms": t_step, "plan_ms": t_plan, "steps": steps,
             "modal_ring_interactions_per_s": 2.0 * ns * nf * nm / (t_step / 1e3)}
+
+
+def trees_vs_direct_sampled(kind, k, precision, dev):
+    """The FMM on the uniform and on the adaptive tree against the direct sum at k sampled
+    field points of a configuration (all its sources): each tree's plan spans all field
+    points, the direct sum (the FP64 path's FP32-pair kernel, within 1e-10 of the oracle)
+    only the sample; eps^(n) = max |fmm - direct| / max |direct| per mode and component."""
+    import numpy as np
+    import torch
+    from paper_2301_01179_gb300 import binding, workloads as W
+    w = W.make(kind)
+    nm = w["n_modes"]
+    idx = W.subset(w["tgt_r"].size, k, seed=17)
+
+    def d(a):
+        return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+
+    sr, sz, tr, tz, qr, qi = map(d, (w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], w["q_re"], w["q_im"]))
+    ps = binding.Plan(sr, sz, d(w["tgt_r"][idx]), d(w["tgt_z"][idx]), nm, order=4, leaf_size=w["leaf"])
+    ref = [o.cpu().numpy() for o in ps.direct_grad(qr, qi)]
+    ps.close()
+    ii = torch.as_tensor(idx, device=dev)
+    out = {"workload": "%s: %d x %d, modes 0..%d, order %d, leaf %d, %s; %d sampled field points"
+                       % (kind, w["src_r"].size, w["tgt_r"].size, nm - 1, w["order"], w["leaf"], precision, k)}
+    for tree in ("uniform", "adaptive"):
+        pl = binding.Plan(sr, sz, tr, tz, nm, order=w["order"], leaf_size=w["leaf"], precision=precision, tree=tree)
+        res = [o[:, ii].cpu().numpy() for o in pl.grad(qr, qi)]
+        pl.close()
+        eps = {}
+        for name, c in (("potential", 0), ("d_dr", 2), ("d_dz", 4)):
+            a = res[c] + 1j * res[c + 1]
+            b = ref[c] + 1j * ref[c + 1]
+            den = np.max(np.abs(b), axis=1)
+            eps[name] = float((np.max(np.abs(a - b), axis=1) / np.where(den > 0, den, 1.0)).max())
+        out[tree] = eps
+    return out
 
 
 def mixed_vs_fp64(kind, steps, dev):
@@ -652,13 +690,20 @@ def run_ours(args):
         extra["plan_ms"] = e0.elapsed_time(e1) / 3
         # forward + backward (adjoint) steps of the gradient configurations (not the headline)
         fb = {}
-        kinds = [("cfg4", "fp64")] + ([] if args.no_cfg5 else [("cfg5", "mixed")])
-        for kind, prec in kinds:
+        kinds = [("cfg4", "fp64", "uniform")] + ([] if args.no_cfg5 else [("cfg5", "mixed", "adaptive"),
+                                                                          ("cfg5", "mixed", "uniform")])
+        for kind, prec, tree in kinds:
+            key = kind + ("_adaptive" if tree == "adaptive" else "")
             try:
-                fb[kind] = fwd_bwd(kind, prec, 2 if kind == "cfg5" else 3, 1, dev)
+                fb[key] = fwd_bwd(kind, prec, 2 if kind == "cfg5" else 3, 1, dev, tree=tree)
             except Exception as exc:  # an extra must not cost the headline line
-                fb[kind] = {"error": str(exc)[:200]}
+                fb[key] = {"error": str(exc)[:200]}
         extra["fwd_bwd"] = fb
+        if not args.no_cfg5:
+            try:  # the 4e6-ring workload's FMM error on both trees (MIXED) at sampled points
+                extra["cfg5_trees_vs_direct"] = trees_vs_direct_sampled("cfg5", 512, "mixed", dev)
+            except Exception as exc:
+                extra["cfg5_trees_vs_direct"] = {"error": str(exc)[:200]}
         # the mixed-precision path on the near-singular curve workload, and on the 4e6-ring
         # workload at sampled field points (not the headline)
         try:
