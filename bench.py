@@ -756,6 +756,9 @@ def main():
                     help="skip the 4e6-ring MIXED forward+adjoint step and its sampled error (about 40 s)")
     ap.add_argument("--peaks", action="store_true",
                     help="print only the measured FMA peaks (FP32, f32x2, FP64) with the clocks seen, and exit")
+    ap.add_argument("--fwd-bwd-only", default=None, metavar="KIND:PREC:TREE",
+                    help="profiling captures: time only one forward + backward step of a configuration "
+                         "(e.g. cfg5:mixed:adaptive) over --steps steps after --warmup, print it, and exit")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -763,6 +766,13 @@ def main():
     B.build()
     if args.peaks:
         return run_peaks()
+    if args.fwd_bwd_only:
+        import torch
+        kind, prec, tree = (args.fwd_bwd_only.split(":") + ["fp64", "uniform"])[:3]
+        torch.cuda.set_device(0)
+        out = fwd_bwd(kind, prec, args.steps, args.warmup, torch.device("cuda", 0), tree=tree)
+        print(json.dumps({"fwd_bwd": out}), flush=True)
+        return 0
     return run_ours(args)
 
 
