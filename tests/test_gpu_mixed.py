@@ -1,7 +1,8 @@
 """GPU parity of the mixed-precision path (AFMM_MIXED) against the FP64 oracle.
 
-MIXED forms the pair geometry (r - r1, r + r1, z - z1) in FP64 and splits it exactly into
-FP32 pairs; the elliptic (AGM) start values and the Legendre recursion run in FP32-pair
+MIXED forms the pair geometry (r - r1, r + r1, z - z1) as FP32 pairs, by error-free FP32 sums
+of exact FP32 triples of the coordinates (about 2^-47 of each difference, no FP64 arithmetic
+per pair); the elliptic (AGM) start values and the Legendre recursion run in FP32-pair
 arithmetic (48-bit significands, FP32 exponent range with exact power-of-two rescaling),
 not in IEEE FP64; the products with the strengths are FP32 with Kahan-compensated FP32
 sums, and the far field (moments, shifts, S2L) is FP32 on box-scaled coordinates.  Its
