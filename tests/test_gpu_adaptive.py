@@ -132,3 +132,45 @@ def test_adaptive_balance_bounds_near_lists_at_full_size():
         assert 0 < i["near_max_sources"] <= (9 * K + 8 * (i["depth"] - 2)) * 64, i["near_max_sources"]
     f = binding.Plan(sr, sz, tr, tz, 1, order=4, leaf_size=64, tree="adaptive", balance=-1).info()
     assert f["near_max_sources"] > 10 * (9 * 4 + 8 * (f["depth"] - 2)) * 64
+
+
+@pytest.mark.parametrize("ns,nf", [(1, 1), (5, 3), (70, 2)])
+def test_adaptive_tiny_sets_match_oracle(ns, nf):
+    """Few points: the tree stops at level 2 (or a little below)."""
+    w = W.make("cfg5", ns=ns, nf=nf, n_modes=5)
+    T = _tree(w, 8, 12)
+    pl = _plan(w, 6, 8, 12)
+    info = pl.info()
+    assert info["depth"] == max(b[0] for b in T.boxes)
+    assert info["near_pairs"] + info["s2l_point_pairs"] == ns * nf
+    q_re, q_im = to_dev(w["q_re"], w["q_im"])
+    g = to_np(*pl.grad(q_re, q_im))
+    F = A.adaptive_fmm(T, w["q_re"], w["q_im"], 6, grad=True, wx="direct")
+    D = oracle.direct(w["src_r"], w["src_z"], w["tgt_r"], w["tgt_z"], w["q_re"], w["q_im"], grad=True)
+    for c in (0, 2, 4):
+        assert eps_modes(g[c], g[c + 1], F[c], F[c + 1]).max() < TOL
+        if info["s2l_point_pairs"] == 0:  # every pair is direct: the FMM is the direct sum
+            assert eps_modes(g[c], g[c + 1], D[c], D[c + 1]).max() < TOL
+
+
+def test_adaptive_long_near_lists_and_coincident_points():
+    """Leaves of up to 200 points with the balance rule give near lists of several thousand
+    sources over many ranges (past the kernel's staged source list, so each producer finds
+    its source by a binary search over the ranges); a cluster of coincident points holds
+    leaves at the maximum level with more than leaf_size points."""
+    w = W.make("cfg5", ns=9000, nf=7000, n_modes=9)
+    for k in ("src", "tgt"):  # 400 points of each role on one spot
+        w[k + "_r"][:400] = 0.3
+        w[k + "_z"][:400] = 0.1
+    leaf, maxlev = 200, 9
+    T = _tree(w, leaf, maxlev)
+    assert any(len(T.src[b]) > leaf for b in T.leaves if b[0] == maxlev)
+    pl = _plan(w, 8, leaf, maxlev)
+    info = pl.info()
+    assert info["near_max_sources"] > 1024
+    assert info["near_pairs"] + info["s2l_point_pairs"] == 9000 * 7000
+    q_re, q_im = to_dev(w["q_re"], w["q_im"])
+    g = to_np(*pl.grad(q_re, q_im))
+    F = A.adaptive_fmm(T, w["q_re"], w["q_im"], 8, grad=True, wx="direct")
+    for c in (0, 2, 4):
+        assert eps_modes(g[c], g[c + 1], F[c], F[c + 1]).max() < TOL
