@@ -155,6 +155,9 @@ struct TcTables {
     float2 rjl[16 * 16];      // 1 / (j! l!) as FP32 pairs, j, l <= 15
     float2 jfact[16];         // j! as FP32 pairs (a single float up to 13!)
     int8_t ci[128], cj[128];  // coefficient index -> (first, second) exponent
+    // per parity pr + 2 pz: interaction-list slots in processing order, each beside its
+    // axial mirror (dr, -dz); mir = 1 where a slot follows its mirror
+    int8_t ord[4][27], mir[4][27];
 };
 
 // amplitude of mode n, source s: FP64 copies are planar [n][ns]; FP32 copies (MIXED) are

@@ -271,6 +271,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
     __shared__ int offK[2][KP], offI[2][KP];  // cube offsets (outward, inward) of kl and ij
     __shared__ float2 rj[16];               // 1 / j! as FP32 pairs
     __shared__ int wait_ok;
+    __shared__ int sdr[27], sdz[27];        // slot offsets of the unit's parity
+    __shared__ uint4 fmask[2][KG];          // sign bits of the K chunks: odd j (0), valid ij (1)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t u = blockIdx.x;
@@ -298,6 +300,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
     const int ucol = a.unit_col[u];
     const int col = ucol & 0xffff, pz = (ucol >> 30) & 1, pr = col & 1;
     const int nl = 1 << a.level;
+    // Slots (dr, dz) and (dr, -dz) share the cube, the station and the orientation; their B
+    // operands differ by the sign (-1)^(j + l) of each entry (G is even in x), and the digits
+    // of -v are the digits of v negated.  So mirrored slots run back to back (tp.ord) and the
+    // second takes the first one's B with those signs flipped instead of a new slicing.
+    if (tid < 27) s2l_offset(pr, pz, tid, &sdr[tid], &sdz[tid]);
+    for (int kc = tid; kc < KG; kc += TC_THREADS) {
+        uint32_t mj[4], mv[4];
+        for (int w = 0; w < 4; ++w) {
+            mj[w] = mv[w] = 0u;
+            for (int h = 0; h < 2; ++h) {
+                const int ij = kc * 8 + 2 * w + h;
+                if (ij < nc) {
+                    mv[w] |= 0x8000u << (16 * h);
+                    if (tp.cj[ij] & 1) mj[w] |= 0x8000u << (16 * h);
+                }
+            }
+        }
+        fmask[0][kc] = make_uint4(mj[0], mj[1], mj[2], mj[3]);
+        fmask[1][kc] = make_uint4(mv[0], mv[1], mv[2], mv[3]);
+    }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tbase)),
                      "r"(NCOL));
@@ -343,9 +365,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
 
     constexpr int ntaskB = KP * KG;   // 16-byte chunks of one B slice
     constexpr int ntaskA = 128 * KG;  // 16-byte chunks of one A slice
-    for (int slot = 0; slot < 27 && !abort_; ++slot) {
-        int dr, dz;
-        s2l_offset(pr, pz, slot, &dr, &dz);
+    const int par = pr + 2 * pz;
+    int bko = -2;  // the position in the order of the slot whose B is in shared memory
+    for (int ko = 0; ko < 27 && !abort_; ++ko) {
+        const int slot = tp.ord[par][ko];
+        const int dr = sdr[slot], dz = sdz[slot];
         const int scol = col + dr;
         if (scol < 0 || scol >= nl) continue;
         __syncthreads();  // rbase[] of the previous slot is no longer read
@@ -381,9 +405,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
             }
             cp_async_commit();
         };
+        // the B in shared memory belongs to this slot's axial mirror
+        const bool mirror = tp.mir[par][ko] && bko == ko - 1;
+        bko = ko;
         wait_buf(0);
         if (abort_) break;
-        // the cube (8-byte copies: its offset is a multiple of 8 bytes only), then A slice 0
+        // the cube (8-byte copies: its offset is a multiple of 8 bytes only), then A slice 0;
+        // a mirror slot needs no cube (its group is committed empty)
+        if (!mirror)
         for (int t = tid; t < slab; t += TC_THREADS)
             if constexpr (C32)
                 asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(sE32 + t)), "l"(&Eg[t].x) : "memory");
@@ -394,57 +423,82 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
         cp_async_wait<1>();
         __syncthreads();
 
-        // B: pass 1, the grid exponent of every column kl (max over ij of |E / j!|)
-        for (int kl = warp; kl < KP; kl += NW) {
-            float m = 0.f;
-            if (kl < nc) {
-                const int ok = offK[inward][kl] >> 4;
-                for (int ij = lane; ij < nc; ij += 32) {
-                    const int oi = offI[inward][ij];
-                    m = fmaxf(m, fabsf(cube(ok + (oi >> 4)).x) * rj[oi & 15].x);
-                }
+        if (mirror) {
+            // B of the mirror slot with the signs of the entries of odd j + l flipped
+            // (zero digits keep their sign, as the slicing would give them)
+            constexpr int ntaskF = NS * KP * KG;  // 16-byte chunks of all slices
+            for (int T = tid; T < ntaskF; T += TC_THREADS) {
+                const int t = T % ntaskB;
+                const int kl = (t / (KG * 8)) * 8 + (t & 7), kc = (t >> 3) % KG;
+                if (kl >= nc) continue;
+                const uint4 mj = fmask[0][kc], mv = fmask[1][kc];
+                const bool lodd = (offK[0][kl] & 15) & 1;
+                uint4 *q4 = reinterpret_cast<uint4 *>(sB + (T / ntaskB) * BT + t * 16);
+                uint4 v = *q4;
+                auto fl = [&](uint32_t w, uint32_t j, uint32_t va) {
+                    const uint32_t m = lodd ? (j ^ va) : j;                        // odd j + l, valid ij
+                    const uint32_t nz = ((w & 0x7fff7fffu) + 0x7fff7fffu) & 0x80008000u;  // nonzero halves
+                    return w ^ (m & nz);
+                };
+                v.x = fl(v.x, mj.x, mv.x);
+                v.y = fl(v.y, mj.y, mv.y);
+                v.z = fl(v.z, mj.z, mv.z);
+                v.w = fl(v.w, mj.w, mv.w);
+                *q4 = v;
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-            if (lane == 0) colE[kl] = (m >= 1e-30f && m < 1e30f) ? grid_exp(m) + 1 : -1000;
-        }
-        __syncthreads();
-        // B: pass 2, digits of E_{k,i,j+l} / j! into the NS slices (chunk T at byte 16 T)
-        for (int T = tid; T < ntaskB; T += TC_THREADS) {
-            const int kl = (T / (KG * 8)) * 8 + (T & 7), kc = (T >> 3) % KG;
-            uint32_t w[NS][4];
-#pragma unroll
-            for (int s = 0; s < NS; ++s) w[s][0] = w[s][1] = w[s][2] = w[s][3] = 0u;
-            const int Ec = kl < nc ? colE[kl] : -1000;
-            if (Ec > -1000) {
-                const int okl = offK[inward][kl];
-                const int ok = okl >> 4, l = okl & 15;
-#pragma unroll
-                for (int e2 = 0; e2 < 4; ++e2) {
-                    float dd[2][NS];
-#pragma unroll
-                    for (int e1 = 0; e1 < 2; ++e1) {
-                        const int ij = kc * 8 + e2 * 2 + e1;
-                        if (ij < nc) {
-                            const int oi = offI[inward][ij];
-                            const int j = oi & 15;
-                            float2 ev = cube(ok + (oi >> 4));
-                            if (backward && ((j + l) & 1)) ev = make_float2(-ev.x, -ev.y);
-                            const float2 rf = rj[j];
-                            const dfv v = df_mul(df_make(ev.x, ev.y), df_make(rf.x, rf.y));
-                            digits<NS>(v.hi, v.lo, Ec, dd[e1]);
-                        } else {
-#pragma unroll
-                            for (int s = 0; s < NS; ++s) dd[e1][s] = 0.f;
-                        }
+        } else {
+            // B: pass 1, the grid exponent of every column kl (max over ij of |E / j!|)
+            for (int kl = warp; kl < KP; kl += NW) {
+                float m = 0.f;
+                if (kl < nc) {
+                    const int ok = offK[inward][kl] >> 4;
+                    for (int ij = lane; ij < nc; ij += 32) {
+                        const int oi = offI[inward][ij];
+                        m = fmaxf(m, fabsf(cube(ok + (oi >> 4)).x) * rj[oi & 15].x);
                     }
-#pragma unroll
-                    for (int s = 0; s < NS; ++s) w[s][e2] = pack_bf16(dd[0][s], dd[1][s]);
                 }
-            }
 #pragma unroll
-            for (int s = 0; s < NS; ++s)
-                *reinterpret_cast<uint4 *>(sB + s * BT + T * 16) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+                for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                if (lane == 0) colE[kl] = (m >= 1e-30f && m < 1e30f) ? grid_exp(m) + 1 : -1000;
+            }
+            __syncthreads();
+            // B: pass 2, digits of E_{k,i,j+l} / j! into the NS slices (chunk T at byte 16 T)
+            for (int T = tid; T < ntaskB; T += TC_THREADS) {
+                const int kl = (T / (KG * 8)) * 8 + (T & 7), kc = (T >> 3) % KG;
+                uint32_t w[NS][4];
+#pragma unroll
+                for (int s = 0; s < NS; ++s) w[s][0] = w[s][1] = w[s][2] = w[s][3] = 0u;
+                const int Ec = kl < nc ? colE[kl] : -1000;
+                if (Ec > -1000) {
+                    const int okl = offK[inward][kl];
+                    const int ok = okl >> 4, l = okl & 15;
+#pragma unroll
+                    for (int e2 = 0; e2 < 4; ++e2) {
+                        float dd[2][NS];
+#pragma unroll
+                        for (int e1 = 0; e1 < 2; ++e1) {
+                            const int ij = kc * 8 + e2 * 2 + e1;
+                            if (ij < nc) {
+                                const int oi = offI[inward][ij];
+                                const int j = oi & 15;
+                                float2 ev = cube(ok + (oi >> 4));
+                                if (backward && ((j + l) & 1)) ev = make_float2(-ev.x, -ev.y);
+                                const float2 rf = rj[j];
+                                const dfv v = df_mul(df_make(ev.x, ev.y), df_make(rf.x, rf.y));
+                                digits<NS>(v.hi, v.lo, Ec, dd[e1]);
+                            } else {
+#pragma unroll
+                                for (int s = 0; s < NS; ++s) dd[e1][s] = 0.f;
+                            }
+                        }
+#pragma unroll
+                        for (int s = 0; s < NS; ++s) w[s][e2] = pack_bf16(dd[0][s], dd[1][s]);
+                    }
+                }
+#pragma unroll
+                for (int s = 0; s < NS; ++s)
+                    *reinterpret_cast<uint4 *>(sB + s * BT + T * 16) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+            }
         }
 
         // slices of A in turn, double-buffered; slice i meets B slices 0 .. NS - 1 - i
@@ -575,6 +629,28 @@ afmm_status make_tc_tables(afmm_plan p)
             double x = 1.0 / (f[j] * f[l]);
             float hi = (float)x;
             t->rjl[j * 16 + l] = make_float2(hi, (float)(x - (double)hi));
+        }
+    }
+    for (int par = 0; par < 4; ++par) {
+        bool done[27] = {};
+        int c = 0;
+        for (int s0 = 0; s0 < 27; ++s0) {
+            if (done[s0]) continue;
+            int dr0, dz0;
+            s2l_offset(par & 1, par >> 1, s0, &dr0, &dz0);
+            t->ord[par][c] = (int8_t)s0;
+            t->mir[par][c++] = 0;
+            done[s0] = true;
+            for (int s1 = s0 + 1; s1 < 27 && dz0 != 0; ++s1) {
+                int dr1, dz1;
+                s2l_offset(par & 1, par >> 1, s1, &dr1, &dz1);
+                if (!done[s1] && dr1 == dr0 && dz1 == -dz0) {
+                    t->ord[par][c] = (int8_t)s1;
+                    t->mir[par][c++] = 1;
+                    done[s1] = true;
+                    break;
+                }
+            }
         }
     }
     for (int i = 0; i < 128; ++i) t->ci[i] = t->cj[i] = -1;
