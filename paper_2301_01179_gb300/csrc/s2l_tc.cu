@@ -244,6 +244,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
     constexpr int AT = 128 * KP * 2;        // bytes of one A slice buffer
     constexpr int QC = KP / 4;              // accumulator columns drained per thread
     constexpr uint32_t IDESC = umma_idesc(128, KP);
+    constexpr uint32_t IDESC2 = umma_idesc(128, 2 * KP <= 256 ? 2 * KP : KP);  // two B slices at once
     constexpr int NACC = NE + 1;            // accumulators: the exact levels and the rest
     static_assert(NACC * KP <= 512, "TMEM holds 512 FP32 columns");
     constexpr uint32_t NCOL = NACC * KP <= 32 ? 32 : NACC * KP <= 64 ? 64 : NACC * KP <= 128 ? 128 : NACC * KP <= 256 ? 256 : 512;
@@ -517,16 +518,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
             if (tid == 0 && !(a.inject_timeout && first_slot)) {
                 tc_fence_after();
                 const uint32_t abase = smem_u32(sA + b * AT), bbase = smem_u32(sB);
-                for (int j = 0; j + i < NS; ++j) {
+                // B slices j and j + 1 are adjacent in shared memory and levels lv and lv + 1
+                // adjacent in tensor memory: one MMA of N = 2 KP covers both products when the
+                // two accumulators take the same accumulate flag (both exact, or the exact level
+                // before NE in phases i > 0, where NE already holds a sum)
+                for (int j = 0; j + i < NS;) {
                     const int lv = i + j < NE ? i + j : NE;
+                    const bool two = 2 * KP <= 256 && j + 1 + i < NS && lv < NE && (lv + 1 < NE || i > 0);
                     for (int ks = 0; ks < KP / 16; ++ks) {
                         const uint64_t ad = umma_desc(abase + ks * 256, 128, KG * 128);
                         const uint64_t bd = umma_desc(bbase + j * BT + ks * 256, 128, KG * 128);
                         // exact levels restart every slot with the pair (0, lv); level NE spans all slots
                         const uint32_t acc = lv < NE ? (ks > 0 || i > 0) : (ks > 0 || lx_init);
-                        umma_bf16(tmem + (uint32_t)(KP * lv), ad, bd, IDESC, acc);
+                        umma_bf16(tmem + (uint32_t)(KP * lv), ad, bd, two ? IDESC2 : IDESC, acc);
                         if (lv == NE) lx_init = true;
                     }
+                    j += two ? 2 : 1;
                 }
                 umma_commit(&mbar[b]);
             }
