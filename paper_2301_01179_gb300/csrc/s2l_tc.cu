@@ -273,6 +273,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
     __shared__ float2 rj[16];               // 1 / j! as FP32 pairs
     __shared__ int wait_ok;
     __shared__ int sdr[27], sdz[27];        // slot offsets of the unit's parity
+    __shared__ int sflag[27], act_ko[27], nact_s;  // active slots, as positions in the order
     __shared__ uint4 fmask[2][KG];          // sign bits of the K chunks: odd j (0), valid ij (1)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -300,12 +301,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
     if (tid < 16) rj[tid] = tp.rjl[tid * 16];
     const int ucol = a.unit_col[u];
     const int col = ucol & 0xffff, pz = (ucol >> 30) & 1, pr = col & 1;
-    const int nl = 1 << a.level;
     // Slots (dr, dz) and (dr, -dz) share the cube, the station and the orientation; their B
     // operands differ by the sign (-1)^(j + l) of each entry (G is even in x), and the digits
     // of -v are the digits of v negated.  So mirrored slots run back to back (tp.ord) and the
     // second takes the first one's B with those signs flipped instead of a new slicing.
-    if (tid < 27) s2l_offset(pr, pz, tid, &sdr[tid], &sdz[tid]);
+    if (tid < 27) {
+        s2l_offset(pr, pz, tid, &sdr[tid], &sdz[tid]);
+        sflag[tid] = 0;
+    }
     for (int kc = tid; kc < KG; kc += TC_THREADS) {
         uint32_t mj[4], mv[4];
         for (int w = 0; w < 4; ++w) {
@@ -367,61 +370,75 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
     constexpr int ntaskB = KP * KG;   // 16-byte chunks of one B slice
     constexpr int ntaskA = 128 * KG;  // 16-byte chunks of one A slice
     const int par = pr + 2 * pz;
-    int bko = -2;  // the position in the order of the slot whose B is in shared memory
-    for (int ko = 0; ko < 27 && !abort_; ++ko) {
-        const int slot = tp.ord[par][ko];
-        const int dr = sdr[slot], dz = sdz[slot];
-        const int scol = col + dr;
-        if (scol < 0 || scol >= nl) continue;
-        __syncthreads();  // rbase[] of the previous slot is no longer read
-        int has = 0;
+    // the active slots (some box of the unit has a source box there; the table holds -1 for
+    // positions outside the level's square), in processing order
+    for (int e = tid; e < 64 * 27; e += TC_THREADS) {
+        const int b = bx[e / 27], slot = e % 27;
+        if (b >= 0 && a.s2l[(size_t)b * 27 + slot] >= 0) sflag[slot] = 1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int c = 0;
+        for (int ko = 0; ko < 27; ++ko)
+            if (sflag[tp.ord[par][ko]]) act_ko[c++] = ko;
+        nact_s = c;
+    }
+    __syncthreads();
+    const int nact = nact_s;
+    // a slot whose axial mirror ran just before it takes that slot's B with signs flipped
+    auto is_mirror = [&](int k) { return k > 0 && tp.mir[par][act_ko[k]] && act_ko[k - 1] == act_ko[k] - 1; };
+    // A slice s of the current slot -> buffer b (rows without a source box read zeros)
+    auto load_A = [&](int s, int b) {
+        uint8_t *dstb = sA + b * AT;
+#pragma unroll
+        for (int T0 = 0; T0 < ntaskA; T0 += TC_THREADS) {
+            const int T = T0 + tid;
+            if (T < ntaskA) {
+                const int r = (T / (KG * 8)) * 8 + (T & 7), kc = (T >> 3) % KG;
+                const long long rb = rbase[r];
+                const __nv_bfloat16 *g = rb >= 0 ? a.asl + rb + s * KP + kc * 8 : a.asl;
+                cp_async16(dstb + T * 16, g, rb >= 0 ? 16 : 0);
+            }
+        }
+        cp_async_commit();
+    };
+    // active slot k's A rows, its cube (8-byte copies: the cube's offset is a multiple of 8
+    // bytes only; a mirror slot needs none, its group is committed empty) and A slice 0.
+    // Issued before the previous slot's drain, which touches no shared memory.
+    auto issue_slot = [&](int k) {
+        const int slot = tp.ord[par][act_ko[k]];
         if (tid < 128) {
             const int b = bx[tid & 63];
             const int s2 = b >= 0 ? a.s2l[(size_t)b * 27 + slot] : -1;
             rbase[tid] = s2 >= 0 ? (((long long)s2 * nm + n) * 2 + (tid >> 6)) * NS * KP : -1ll;
-            has = s2 >= 0;
         }
-        if (!__syncthreads_or(has)) continue;
-        const bool first_slot = !any_work;
-        any_work = true;
-        const int station = dr < 0 ? scol : col;
-        const int sidx = a.station_of_col[station];
-        const int ea = dr < 0 ? -dr : dr, eb = dz < 0 ? -dz : dz;
-        const int inward = dr > 0 ? 1 : 0;
-        const bool backward = dz > 0;
-        const float2 *Eg = a.gexp_df + (((size_t)sidx * 16 + ea * 4 + eb) * nm + n) * (size_t)slab;
-
-        // A slice s -> buffer b (rows without a source box read zeros)
-        auto load_A = [&](int s, int b) {
-            uint8_t *dstb = sA + b * AT;
-#pragma unroll
-            for (int T0 = 0; T0 < ntaskA; T0 += TC_THREADS) {
-                const int T = T0 + tid;
-                if (T < ntaskA) {
-                    const int r = (T / (KG * 8)) * 8 + (T & 7), kc = (T >> 3) % KG;
-                    const long long rb = rbase[r];
-                    const __nv_bfloat16 *g = rb >= 0 ? a.asl + rb + s * KP + kc * 8 : a.asl;
-                    cp_async16(dstb + T * 16, g, rb >= 0 ? 16 : 0);
-                }
-            }
-            cp_async_commit();
-        };
-        // the B in shared memory belongs to this slot's axial mirror
-        const bool mirror = tp.mir[par][ko] && bko == ko - 1;
-        bko = ko;
-        wait_buf(0);
-        if (abort_) break;
-        // the cube (8-byte copies: its offset is a multiple of 8 bytes only), then A slice 0;
-        // a mirror slot needs no cube (its group is committed empty)
-        if (!mirror)
-        for (int t = tid; t < slab; t += TC_THREADS)
-            if constexpr (C32)
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(sE32 + t)), "l"(&Eg[t].x) : "memory");
-            else
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(sE + t)), "l"(Eg + t) : "memory");
+        __syncthreads();
+        if (!is_mirror(k)) {
+            const int dr = sdr[slot], dz = sdz[slot];
+            const int scol = col + dr;
+            const int station = dr < 0 ? scol : col;
+            const int sidx = a.station_of_col[station];
+            const int ea = dr < 0 ? -dr : dr, eb = dz < 0 ? -dz : dz;
+            const float2 *Eg = a.gexp_df + (((size_t)sidx * 16 + ea * 4 + eb) * nm + n) * (size_t)slab;
+            for (int t = tid; t < slab; t += TC_THREADS)
+                if constexpr (C32)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(sE32 + t)), "l"(&Eg[t].x) : "memory");
+                else
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(sE + t)), "l"(Eg + t) : "memory");
+        }
         cp_async_commit();
         load_A(0, 0);
-        cp_async_wait<1>();
+    };
+    if (nact > 0) issue_slot(0);
+    for (int k = 0; k < nact && !abort_; ++k) {
+        const int slot = tp.ord[par][act_ko[k]];
+        const int dr = sdr[slot], dz = sdz[slot];
+        const bool first_slot = k == 0;
+        any_work = true;
+        const int inward = dr > 0 ? 1 : 0;
+        const bool backward = dz > 0;
+        const bool mirror = is_mirror(k);
+        cp_async_wait<1>();  // the cube (A slice 0 may still be in flight)
         __syncthreads();
 
         if (mirror) {
@@ -546,6 +563,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_s2l_tc(const S2LTcArgs a, con
         wait_buf(1);
         wait_buf(0);
         if (abort_) break;
+        if (k + 1 < nact) issue_slot(k + 1);  // its copies land during the drain
         tc_fence_after();
 #pragma unroll
         for (int lv = 0; lv < NE; ++lv) {
