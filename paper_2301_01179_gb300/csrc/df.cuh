@@ -264,6 +264,21 @@ __device__ __forceinline__ df2 df2_mul_np(df2 a, df2 b, float2 np, float2 &nhi)
     return r;
 }
 
+// a * b left unnormalised for a product that only feeds other pair products: hi = fl(a.hi
+// b.hi) (= -np exactly, np given), lo = its exact error plus the cross terms (|lo| about
+// 2^-23 |hi|; the dropped a.lo b.lo and the later lo * lo terms stay near 2^-46 of the
+// product).  The negated high part is np itself.
+__device__ __forceinline__ df2 df2_mul_nr(df2 a, df2 b, float2 np)
+{
+    float2 e = ffma2(a.hi, b.hi, np);  // a.hi b.hi - p, exact
+    e = ffma2(a.hi, b.lo, e);
+    e = ffma2(a.lo, b.hi, e);
+    df2 r;
+    r.hi = fmul2(a.hi, b.hi);
+    r.lo = e;
+    return r;
+}
+
 // df2_acc(S, E, a, b) given nbh = -b.hi: the same roundings, no negation
 __device__ __forceinline__ void df2_acc_n(float2 &S, float2 &E, df2 a, df2 b, float2 nbh)
 {

@@ -840,12 +840,15 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
                     const float2 nYP = make_float2(nyprev.x, nY.x);
                     yprev = df2_y(Y);
                     nyprev.x = nY.y;
-                    float2 nT, nWT, nXW, nQW;
+                    float2 nWT;
                     const df2 R = df2_from4(rho4[m]);
-                    const df2 T = df2_mul_np(R, YP, fmul2(R.hi, nYP), nT);
+                    // T, XW and QW only feed pair products: left unnormalised (df2_mul_nr)
+                    const float2 nT = fmul2(R.hi, nYP);
+                    const df2 T = df2_mul_nr(R, YP, nT);
                     const df2 WT = df2_dot2_np(Y, nY, AS, T, nT, BS, nWT);
-                    const df2 XW = df2_mul_np(WT, GX, fmul2(nWT, GX.hi), nXW);
-                    const df2 QW = df2_mul_np(WT, QF, fmul2(nWT, QF.hi), nQW);
+                    const float2 nXW = fmul2(nWT, GX.hi), nQW = fmul2(nWT, QF.hi);
+                    const df2 XW = df2_mul_nr(WT, GX, nXW);
+                    const df2 QW = df2_mul_nr(WT, QF, nQW);
                     df2_acc_n(aS[2 % NC][j], aE[2 % NC][j], QR, QW, nQW);
                     df2_acc_n(aS[3 % NC][j], aE[3 % NC][j], QI, QW, nQW);
                     df2_acc_n(aS[4 % NC][j], aE[4 % NC][j], QR, XW, nXW);
