@@ -234,6 +234,23 @@ __device__ __forceinline__ df2 df2_mul(df2 a, df2 b)
     return r;
 }
 
+// a * b + c componentwise, given nb = -b.hi: the product's exact error by FMA, one two-sum
+// with c's high part, one renormalisation (one rounding fewer than df2_add(df2_mul(a, b), c))
+__device__ __forceinline__ df2 df2_fma(df2 a, df2 b, float2 nb, df2 c)
+{
+    const float2 np = fmul2(a.hi, nb);  // -p, p = fl(a.hi b.hi)
+    float2 e = ffma2(a.hi, b.hi, np);  // a.hi b.hi - p, exact
+    e = ffma2(a.hi, b.lo, e);
+    e = ffma2(a.lo, b.hi, e);
+    const float2 s = fsub2(c.hi, np);  // c.hi + p
+    const float2 v = fsub2(s, c.hi);
+    const float2 err = fsub2(fsub2(c.hi, fsub2(s, v)), fadd2(np, v));  // (c.hi - (s - v)) + (p - v)
+    const float2 t = fadd2(fadd2(e, c.lo), err);
+    df2 r;
+    quick_two_sum2(s, t, r.hi, r.lo);
+    return r;
+}
+
 // (S, E) += a * b componentwise, as df_acc
 __device__ __forceinline__ void df2_acc(float2 &S, float2 &E, df2 a, df2 b)
 {

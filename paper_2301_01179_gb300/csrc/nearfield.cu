@@ -998,20 +998,21 @@ __global__ void __launch_bounds__(L2P_WARPS * 32) k_l2p(const NearArgs a)
             }
         } else {
             const df2 U = df2_bcast(df_from_double(ud)), V = df2_bcast(df_from_double(vd));
+            const float2 nU = fneg2(U.hi), nV = fneg2(V.hi);
             const df2 Z = df2_make(make_float2(0.f, 0.f), make_float2(0.f, 0.f));
             df2 pu = Z, pdu = Z, pdv = Z;
             for (int k = M; k >= 0; --k) {
                 const int base = k * (M + 1) - k * (k - 1) / 2;
                 df2 pk = Z, pkd = Z;
                 for (int l = M - k; l >= 0; --l) {
-                    if (GRAD) pkd = df2_add(df2_mul(pkd, V), pk);
-                    pk = df2_add(df2_mul(pk, V), df2_from4(F[base + l]));
+                    if (GRAD) pkd = df2_fma(pkd, V, nV, pk);
+                    pk = df2_fma(pk, V, nV, df2_from4(F[base + l]));
                 }
                 if (GRAD) {
-                    pdu = df2_add(df2_mul(pdu, U), pu);
-                    pdv = df2_add(df2_mul(pdv, U), pkd);
+                    pdu = df2_fma(pdu, U, nU, pu);
+                    pdv = df2_fma(pdv, U, nU, pkd);
                 }
-                pu = df2_add(df2_mul(pu, U), pk);
+                pu = df2_fma(pu, U, nU, pk);
             }
             pr = df_to_double(df2_x(pu));
             pi = df_to_double(df2_y(pu));
