@@ -58,6 +58,21 @@ __device__ __forceinline__ dfv df_mul(dfv a, dfv b)
     return quick_two_sum(p, e);
 }
 
+// a * b - c: the product's exact error by FMA, one two-sum with -c.hi, one renormalisation
+// (one rounding fewer than df_sub(df_mul(a, b), c))
+__device__ __forceinline__ dfv df_fms(dfv a, dfv b, dfv c)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const float s = __fsub_rn(p, c.hi);
+    const float v = __fsub_rn(s, p);
+    const float err = __fsub_rn(__fsub_rn(p, __fsub_rn(s, v)), __fadd_rn(c.hi, v));  // (p - (s - v)) + (-c.hi - v)
+    const float t = __fadd_rn(__fsub_rn(e, c.lo), err);
+    return quick_two_sum(s, t);
+}
+
 __device__ __forceinline__ dfv df_mulf(dfv a, float b)
 {
     float p = __fmul_rn(a.hi, b);

@@ -138,14 +138,14 @@ __device__ __forceinline__ dfv pair_sweep_df(dfv chi, float t, float zero, dfv i
         int n = 2;
         for (; n + 1 <= N; n += 2) {
             const df2 GC = df2_mul(df2_from4(gam4[n >> 1]), CHI);
-            const dfv ya = df_sub(df_mul(df2_x(GC), ym1), ym2);
-            const dfv yb = df_sub(df_mul(df2_y(GC), ya), ym1);
+            const dfv ya = df_fms(df2_x(GC), ym1, ym2);
+            const dfv yb = df_fms(df2_y(GC), ya, ym1);
             yp[(n >> 1) * 32] = make_float4(ya.hi, yb.hi, ya.lo, yb.lo);
             ym2 = ya;
             ym1 = yb;
         }
         if (n == N) {  // N even: the last mode alone, with the pad
-            const dfv ya = df_sub(df_mul(df_mul(df_make(gam2[n].x, gam2[n].y), chi), ym1), ym2);
+            const dfv ya = df_fms(df_mul(df_make(gam2[n].x, gam2[n].y), chi), ym1, ym2);
             yp[(n >> 1) * 32] = make_float4(ya.hi, 0.f, ya.lo, 0.f);
         }
         if (allf) return df_make(zero, 0.f);
@@ -167,7 +167,7 @@ __device__ __forceinline__ dfv pair_sweep_df(dfv chi, float t, float zero, dfv i
     dfv y1 = df_make(__int_as_float((127 - e2) << 23), 0.f);
     for (int n = L; n >= 2; --n) {
         const float2 gm = gam2[n];
-        const dfv yn = df_sub(df_mul(df_mul(df_make(gm.x, gm.y), chi), y1), y0);  // y_{n-2}
+        const dfv yn = df_fms(df_mul(df_make(gm.x, gm.y), chi), y1, y0);  // y_{n-2}
         y0 = y1;
         y1 = yn;
         const int idx = n - 2;
