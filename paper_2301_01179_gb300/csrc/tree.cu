@@ -1,12 +1,13 @@
-// tree.cu -- uniform quadtree over (r, z) (Sec. 2.1; Algorithm 1, first two steps).
+// tree.cu -- quadtree over (r, z): the paper's uniform tree (Sec. 2.1; Algorithm 1, first two
+// steps) and the adaptive tree (boxes split only where points are dense, with its near lists).
 //
 // Domain: the square anchored at (min r, min z) over sources and field points with side
 // L = max(r extent, z extent) (the paper's square 0 <= r, z <= r_max, moved to the data).
 // A point's box at level l is floor((v - v0) * 2^l / L), clamped to 2^l - 1.  Keys are
 // computed once at level 16; 2^l / L is a power-of-two multiple of 2^16 / L, so a level-l
 // index is exactly the level-16 index shifted right by 16 - l.
-// Depth: the smallest d >= 2 whose non-empty source leaves hold at most leaf_size sources
-// on average, unless overridden.
+// Depth (uniform tree): the smallest d >= 2 whose non-empty source leaves hold at most
+// leaf_size sources on average, unless overridden.  Adaptive tree: see build_levels_adaptive.
 // All steps are device kernels; the host reads back a handful of counts.
 #include "common.cuh"
 #include "df.cuh"
@@ -544,9 +545,10 @@ __global__ void k_s2l_count(const int32_t *__restrict__ tab, const int2 *__restr
 
 // ------------------------------------------------------------------------------------
 // adaptive tree: levels built top-down.  Level 2 holds every non-empty box; a box of level
-// l is split while it holds more than leaf_size sources or field points and l < lmax, and
-// its non-empty children form level l + 1 (sorted by key, since the parents are and the
-// child quadrant c = (radial bit << 1) | axial bit is the key's lowest digit).
+// l < lmax is split while it holds more than leaf_size sources or field points, or (balance
+// rule) while a same-level neighbour holds more than lim = K leaf_size of either, and its
+// non-empty children form level l + 1 (sorted by key, since the parents are and the child
+// quadrant c = (radial bit << 1) | axial bit is the key's lowest digit).
 // ------------------------------------------------------------------------------------
 // split flags of level l: more than leaf points of either role, or (balance lim > 0) a
 // same-level neighbour with more than lim points of either role
