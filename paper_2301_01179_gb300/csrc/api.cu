@@ -43,7 +43,19 @@ static cudaMemPool_t plan_pool(int dev)
             g_pool_state[dev] = -1;
             return nullptr;
         }
-        uint64_t keep = 32ull << 30;
+        // released plan memory kept reserved for the next plan (a plan built per step, as in
+        // a training loop, then reuses it instead of mapping fresh memory): half the device's
+        // memory, at most 128 GiB, or AFMM_POOL_KEEP_GB
+        size_t fr = 0, total = 0;
+        if (cudaMemGetInfo(&fr, &total) != cudaSuccess) {
+            cudaGetLastError();
+            total = 64ull << 30;
+        }
+        uint64_t keep = total / 2 < (128ull << 30) ? total / 2 : (128ull << 30);
+        if (const char *e = getenv("AFMM_POOL_KEEP_GB")) {
+            const double gb = atof(e);
+            if (gb >= 0.0) keep = (uint64_t)(gb * (double)(1ull << 30));
+        }
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
         g_pool[dev] = pool;
         g_pool_state[dev] = 1;
