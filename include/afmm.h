@@ -137,14 +137,18 @@ typedef struct {
 void afmm_options_default(afmm_options *opt);
 
 /* Build a plan over sources (src_r, src_z)[ns] and field points (tgt_r, tgt_z)[nf]:
- * validates the coordinates on the device, chooses the depth, sorts both point sets by
- * Morton key into a uniform quadtree over the square domain (Sec. 2.1 and Algorithm 1,
- * first two steps), and allocates all scratch the evaluations need, so that afmm_eval,
- * afmm_grad, afmm_direct and afmm_adjoint allocate nothing.  The plan copies the
- * coordinates (the caller may free them) and is bound to `stream` (cudaStream_t, NULL =
- * legacy default stream).  n_modes = N + 1 >= 1.
+ * validates the coordinates on the device, sorts both point sets by Morton key into a
+ * quadtree over the square domain (uniform: chooses the depth, Sec. 2.1 and Algorithm 1,
+ * first two steps; or adaptive, see afmm_options.tree), and allocates all scratch the
+ * evaluations need, so that afmm_eval, afmm_grad, afmm_direct and afmm_adjoint allocate
+ * nothing.  Plan memory comes from a library-owned stream-ordered pool per device, which
+ * keeps released memory reserved for the next plan: up to half the device's memory, at most
+ * 128 GiB, or AFMM_POOL_KEEP_GB (environment, read when the device's pool is made).  The plan
+ * copies the coordinates (the caller may free them) and is bound to `stream` (cudaStream_t,
+ * NULL = legacy default stream).  n_modes = N + 1 >= 1.
  * Errors: EINVAL (ns < 1, nf < 1, n_modes < 1, bad options, NULL pointers, non-finite or
- * r <= 0 coordinates), ENOMEM, ECUDA, EUNSUPPORTED (depth > 16 required). */
+ * r <= 0 coordinates), ENOMEM, ECUDA, EUNSUPPORTED (depth > 16 required, or the adaptive
+ * tree with AFMM_FP64_NATIVE). */
 afmm_status afmm_plan_create(afmm_plan *out, int64_t ns, const double *src_r, const double *src_z,
                              int64_t nf, const double *tgt_r, const double *tgt_z, int n_modes,
                              const afmm_options *opt, void *stream);
