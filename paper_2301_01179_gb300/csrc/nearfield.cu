@@ -791,7 +791,7 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
         const bool fullp = 2 * (m0 + NP - 1) < nhi;
         if (MIX) {
             // FP32 products of the pairs' high words, Kahan-compensated sums (aE: compensation)
-            const float2 GXf = GX.hi, QFf = QF.hi;
+            const float2 GXf = GX.hi, QFf = QF.hi, nBS = fneg2(BS.hi);
             auto step = [&](const int j) {
                 const int m = m0 + j;
                 const df2 Y = df2_from4(y4[m * 32 + lane]);
@@ -804,7 +804,10 @@ __global__ void __launch_bounds__(NWS_THREADS, 1) k_near_ws(const NearArgs a, co
                     // y_n A + rho_n y_{n-1} B cancels for near pairs (A ~ -B): FP32 pairs
                     const df2 YP = df2_pack(yprev, df2_x(Y));
                     yprev = df2_y(Y);
-                    const float2 wt = df2_add(df2_mul(Y, AS), df2_mul(df2_mul(df2_from4(rho4[m]), YP), BS)).hi;
+                    const df2 R = df2_from4(rho4[m]);
+                    const float2 nT = fmul2(R.hi, fneg2(YP.hi));
+                    const df2 T = df2_mul_nr(R, YP, nT);  // rho_n y_{n-1}, only feeds a product
+                    const float2 wt = df2_fma(T, BS, nBS, df2_mul(Y, AS)).hi;
                     const float2 xw = fmul2(GXf, wt), qw = fmul2(QFf, wt);
                     kahan2(aS[2 % NC][j], aE[2 % NC][j], fmul2(QR, qw));
                     kahan2(aS[3 % NC][j], aE[3 % NC][j], fmul2(QI, qw));
