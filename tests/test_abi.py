@@ -77,3 +77,34 @@ def test_oracle_builds_and_is_independent():
     for f in ("binding.py", "build.py", "workloads.py", "__init__.py"):
         text = open(os.path.join(ROOT, "paper_2301_01179_gb300", f)).read()
         assert "import oracle" not in text and "from oracle" not in text
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of afmm_options and afmm_plan_info_t have the C layout: every
+    field at the offset the C compiler gives it, and the same total size."""
+    import shutil
+    import subprocess
+    from paper_2301_01179_gb300 import binding
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"afmm_options": binding.Options, "afmm_plan_info_t": binding.PlanInfo}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "afmm.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _t in py._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = {}
+    for ln in subprocess.check_output([str(exe)]).decode().split("\n"):
+        if ln:
+            s, f, v = ln.split()
+            out[(s, f)] = int(v)
+    for cname, py in structs.items():
+        assert out[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for f, _t in py._fields_:
+            assert out[(cname, f)] == getattr(py, f).offset, (cname, f)
