@@ -549,8 +549,9 @@ def run_ours(args):
 
     # ---- rooflines, from the live phase split of the timed steps (CUDA events recorded by the
     # library on the plan's stream around each phase) and the FMA peaks measured on this GPU.
-    # Achieved = the method's work (SURVEY-style per-unit counts, not the FP32-pair emulation's
-    # own instructions) / the kernel's time; the emulation's issue rate is reported beside it.
+    # Achieved = the method's work (per-pair and per-box-pair operation counts of the method
+    # itself, not the FP32-pair emulation's own instructions) / the kernel's time; the
+    # emulation's issue rate is reported beside it.
     nc = (M + 1) * (M + 2) // 2
     s2l_ms = statistics.mean(p["s2l"] for p in phases)
     near_ms = statistics.mean(p["near"] for p in phases)
