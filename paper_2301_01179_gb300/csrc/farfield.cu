@@ -339,18 +339,29 @@ __global__ void k_p2m_df(const uint32_t *__restrict__ key, const int2 *__restric
             }
         }
         __syncthreads();
-        for (int o = threadIdx.x; o < nm * nc; o += blockDim.x) {
-            const int n = o / nc, c = o % nc;
-            float2 ar = acc[o], ai = acc[nm * nc + o];
+        // two outputs per thread at a time: four independent accumulation chains (each
+        // output's sum keeps its order)
+        for (int o0 = threadIdx.x; o0 < nm * nc; o0 += 2 * blockDim.x) {
+            const int o1 = o0 + blockDim.x;
+            const bool h1 = o1 < nm * nc;
+            const int n0 = o0 / nc, c0 = o0 % nc, n1 = h1 ? o1 / nc : n0, c1 = h1 ? o1 % nc : c0;
+            float2 ar0 = acc[o0], ai0 = acc[nm * nc + o0];
+            float2 ar1 = h1 ? acc[o1] : make_float2(0.f, 0.f), ai1 = h1 ? acc[nm * nc + o1] : make_float2(0.f, 0.f);
             for (int t = 0; t < cnt; ++t) {
-                const float2 m2 = mono[t * nc + c];
-                const dfv m = df_make(m2.x, m2.y);
-                const float4 q = qst[t * nm + n];
-                df_acc(ar.x, ar.y, df_make(q.x, q.y), m);
-                df_acc(ai.x, ai.y, df_make(q.z, q.w), m);
+                const float2 m2a = mono[t * nc + c0], m2b = mono[t * nc + c1];
+                const dfv ma = df_make(m2a.x, m2a.y), mb = df_make(m2b.x, m2b.y);
+                const float4 qa = qst[t * nm + n0], qb = qst[t * nm + n1];
+                df_acc(ar0.x, ar0.y, df_make(qa.x, qa.y), ma);
+                df_acc(ai0.x, ai0.y, df_make(qa.z, qa.w), ma);
+                df_acc(ar1.x, ar1.y, df_make(qb.x, qb.y), mb);
+                df_acc(ai1.x, ai1.y, df_make(qb.z, qb.w), mb);
             }
-            acc[o] = ar;
-            acc[nm * nc + o] = ai;
+            acc[o0] = ar0;
+            acc[nm * nc + o0] = ai0;
+            if (h1) {
+                acc[o1] = ar1;
+                acc[nm * nc + o1] = ai1;
+            }
         }
         __syncthreads();
     }
